@@ -1,0 +1,203 @@
+/*
+ * atsne.h -- C ABI of the GB300 (sm_103a) library for A-tSNE's high-dimensional
+ * similarity matrix P (Pezzotti et al., "Approximated and User Steerable tSNE
+ * for Progressive Visual Analytics").
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named X, idx, d2, P_cond, beta, rho, row_ptr, col, val, nnz_dev,
+ *    queries, subset, workspace and forest are DEVICE pointers owned by the
+ *    caller. Arrays are dense and row-major. The library allocates no device
+ *    memory: temporary storage comes from the caller's workspace, whose size
+ *    atsne_workspace_bytes() returns (256-byte aligned base required).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). All work is
+ *    enqueued on it; calls return without synchronising, except where noted.
+ *  - Point indices are int32 (N <= 2^31 - 1); CSR row offsets are int64.
+ *  - Return value: ATSNE_OK, or an error code with a message available from
+ *    atsne_last_error() (thread-local). Argument errors are detected on the
+ *    host before anything is enqueued. Problems found on the device
+ *    (non-finite input, an expired bounded wait) set a device status word
+ *    that atsne_check() reads.
+ *  - kNN lists: row i of idx/d2 holds the k neighbours j != i of query i in
+ *    ascending (squared distance, index) order; d2 is the FP32 squared
+ *    Euclidean distance.
+ */
+#ifndef ATSNE_H
+#define ATSNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ATSNE_OK = 0,
+    ATSNE_EINVAL = 1,       /* bad argument, or non-finite input found on the device */
+    ATSNE_ENOMEM = 2,       /* workspace or output buffer too small */
+    ATSNE_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+    ATSNE_ETIMEOUT = 4,     /* a bounded device-side wait expired */
+    ATSNE_EUNSUPPORTED = 5  /* valid request this build does not handle */
+} atsne_status;
+
+typedef enum { ATSNE_KNN_EXACT = 0, ATSNE_KNN_FOREST = 1 } atsne_knn_method;
+
+/* Arithmetic of the exact path's distance contraction (Eq. 8 needs only the
+ * order of distances; every variant ends with an FP32 direct-difference rerank). */
+typedef enum {
+    ATSNE_FP32 = 0,        /* FP32-accurate: exact top-k by FP32 distances */
+    ATSNE_BF16_RERANK = 1  /* BF16 candidates, FP32 rerank of the best rerank_k */
+} atsne_precision;
+
+/* Operation codes for atsne_workspace_bytes(). */
+typedef enum {
+    ATSNE_OP_KNN = 0,
+    ATSNE_OP_CALIBRATE = 1,
+    ATSNE_OP_SYMMETRIZE = 2,
+    ATSNE_OP_REFINE = 3,
+    ATSNE_OP_FOREST_BUILD = 4,
+    ATSNE_OP_FOREST_QUERY = 5
+} atsne_op;
+
+/* Options of the kNN step. atsne_knn_opts_default() fills the defaults. */
+typedef struct {
+    int32_t method;        /* atsne_knn_method */
+    int32_t precision;     /* atsne_precision (exact method) */
+    int32_t trees;         /* forest: number of randomized KD-trees T (Sec. 4.2), default 4 */
+    int32_t top_var_dims;  /* forest: V, split among the V highest-spread dims, default 5 */
+    int32_t checks;        /* forest: budget of evaluated points ("leaves" L, Sec. 4.2) */
+    int32_t leaf_size;     /* forest: maximum points per leaf, default 1 */
+    int32_t queue_cap;     /* forest: capacity of the per-query priority queue, default 1024 */
+    int32_t rerank_k;      /* exact BF16 path: candidates per row kept for rerank (0 = 4k) */
+    uint64_t seed;         /* forest: seed of the counter-based split choice */
+} atsne_knn_opts;
+
+void atsne_knn_opts_default(atsne_knn_opts *opts);
+
+/*
+ * Bytes of workspace `op` needs. N = corpus rows, D = dimensions, k = neighbours,
+ * S = number of listed queries/subset rows (0 = all N rows), opts may be NULL
+ * (defaults) and is read for ATSNE_OP_KNN / FOREST_* / REFINE.
+ */
+size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_t S,
+                             const atsne_knn_opts *opts);
+
+/*
+ * k-nearest neighbours, Eq. 8 (Sec. 3.1); with method FOREST the approximate
+ * neighbourhoods N^A_i of Sec. 4.1, found by the forest search of Sec. 4.2
+ * (the forest is built in the workspace on every call; see atsne_forest_*).
+ *  X        [N][D] fp32, finite.
+ *  queries  NULL: every row i of X is a query, S ignored, outputs have N rows.
+ *           else [S] int32 row indices into X; output row s belongs to
+ *           queries[s]. A query never lists itself.
+ *  k        1 <= k <= N - 1 (the paper uses k = floor(3 * perplexity)).
+ *  idx_out  [rows][k] int32, d2_out [rows][k] fp32, sorted as described above.
+ * Errors: EINVAL (sizes, NULLs, index out of range), ENOMEM (workspace), ECUDA.
+ */
+atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *queries, int64_t S,
+                       int32_t k, const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                       void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Gaussian bandwidths and conditional probabilities, Eq. 3 and Eq. 4 (Sec. 3)
+ * over the kNN support of Eq. 8: for each row, beta = 1/(2 sigma^2) is found by
+ * bisection so that exp(H) = perplexity (H in nats, equal to Eq. 4's base-2
+ * form), and P_cond[r][j] = exp(-beta d2[r][j]) / sum_l exp(-beta d2[r][l]).
+ *  d2         [rows][k] fp32 squared distances (any order; finite, >= 0).
+ *  perplexity 0 < perplexity < k.   tol: stop when |H - ln perplexity| < tol
+ *  (<= 0 selects 1e-5).  max_iter: bisection steps (<= 0 selects 200).
+ *  P_cond_out [rows][k] fp32 (rows sum to 1), beta_out [rows] fp32 (may be NULL).
+ * Rows whose target is unreachable (k equal distances, or at least
+ * `perplexity` neighbours tied at the smallest distance) end at max_iter.
+ */
+atsne_status atsne_calibrate_P(const float *d2, int64_t rows, int32_t k, float perplexity,
+                               float tol, int32_t max_iter, float *P_cond_out, float *beta_out,
+                               void *stream);
+
+/*
+ * Symmetrised joint probabilities, Eq. 2 in the split form of Eq. 10
+ * (Sec. 4.3): p_ij = (p_{j|i} + p_{i|j}) / (2N) over the union of the kNN
+ * patterns, as CSR with ascending columns and no diagonal.
+ *  idx [N][k] int32 (row i: distinct j != i), P_cond [N][k] fp32.
+ *  row_ptr [N+1] int64; col, val: capacity 2*N*k entries (the maximum nnz).
+ *  nnz_dev: device int64 receiving nnz (= row_ptr[N]); may be NULL.
+ * Errors: EINVAL, ENOMEM (workspace), ECUDA. Malformed idx (out of range or
+ * self) sets the device status word (EINVAL from atsne_check()).
+ */
+atsne_status atsne_symmetrize(const int32_t *idx, const float *P_cond, int64_t N, int32_t k,
+                              int64_t *row_ptr, int32_t *col, float *val, int64_t *nnz_dev,
+                              void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Refinement of a user selection, Sec. 4.3 and Sec. 5.1.1: for each listed
+ * point the exact neighbourhood (Eq. 8, FP32 path) against all N points, its
+ * Gaussian (Eq. 3-4) and rho_i = 1 (Sec. 4.3's per-point precision). Rows of
+ * the state not listed are untouched; call atsne_symmetrize() afterwards to
+ * rebuild P (Eq. 10 makes that a per-row update of the stored conditionals).
+ *  subset [S] int32 in [0, N); duplicates allowed (same values written).
+ *  idx/d2/P_cond [N][k], beta [N], rho [N] (beta and rho may be NULL): in/out.
+ */
+atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int32_t *subset,
+                                 int64_t S, int32_t k, float perplexity, int32_t *idx, float *d2,
+                                 float *P_cond, float *beta, float *rho, void *workspace,
+                                 size_t ws_bytes, void *stream);
+
+/*
+ * Precision of approximate neighbourhoods, Eq. 9 (Sec. 4.1):
+ * rho_i = |N^A_i intersect N_i| / k. rho_i_out [rows] fp32; rho_sum_dev: device
+ * double receiving sum_i rho_i (divide by rows for rho); either may be NULL.
+ */
+atsne_status atsne_knn_precision(const int32_t *idx_approx, const int32_t *idx_exact,
+                                 int64_t rows, int32_t k, float *rho_i_out, double *rho_sum_dev,
+                                 void *stream);
+
+/*
+ * Randomized KD-forest kept by the caller (Sec. 4.2), for building once and
+ * searching many times. Layout of the `forest` buffer (all offsets in bytes
+ * from its start, filled by atsne_forest_layout()):
+ *   split_dim [trees][2^depth - 1] int32, split_val [trees][2^depth - 1] fp32,
+ *   perm [trees][N] int32 (points in leaf order),
+ *   leaf_ofs [2^depth + 1] int32 (leaf m holds perm[t][leaf_ofs[m] .. leaf_ofs[m+1])).
+ * Trees are level-ordered: node v has children 2v+1 and 2v+2.
+ */
+typedef struct {
+    int32_t depth;
+    int32_t trees;
+    int64_t n_internal;
+    size_t off_split_dim, off_split_val, off_perm, off_leaf_ofs;
+    size_t bytes;
+} atsne_forest_layout_t;
+
+atsne_status atsne_forest_layout(int64_t N, int32_t D, const atsne_knn_opts *opts,
+                                 atsne_forest_layout_t *out);
+atsne_status atsne_forest_build(const float *X, int64_t N, int32_t D, const atsne_knn_opts *opts,
+                                void *forest, size_t forest_bytes, void *workspace,
+                                size_t ws_bytes, void *stream);
+atsne_status atsne_forest_query(const float *X, int64_t N, int32_t D, const void *forest,
+                                const int32_t *queries, int64_t S, int32_t k,
+                                const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                                int64_t *evaluated_out, void *workspace, size_t ws_bytes,
+                                void *stream);
+
+/* Synchronise `stream`, then read and clear the device status word
+ * (ATSNE_OK, ATSNE_EINVAL for non-finite or malformed input, ATSNE_ETIMEOUT). */
+atsne_status atsne_check(void *stream);
+
+/* Message of the last error on this thread ("" if none). */
+const char *atsne_last_error(void);
+
+/*
+ * Per-kernel timing: while enabled, every kernel launch is bracketed by CUDA
+ * events recorded on the launching stream. atsne_profile_read() synchronises
+ * those events and returns the launch count and summed milliseconds of every
+ * kernel whose name equals `kernel` (or all, if kernel is NULL).
+ */
+atsne_status atsne_profile_enable(int32_t on);
+atsne_status atsne_profile_reset(void);
+atsne_status atsne_profile_read(const char *kernel, int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATSNE_H */

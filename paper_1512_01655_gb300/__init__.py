@@ -1,0 +1,287 @@
+"""Python binding of the sm_103a A-tSNE similarity library (include/atsne.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory (outputs and workspaces) and the current CUDA
+stream. There is no CPU fallback: if the compiled library is missing, or no
+CUDA device is present, the calls raise.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libatsne.so")
+
+ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPPORTED = range(6)
+KNN_EXACT, KNN_FOREST = 0, 1
+FP32, BF16_RERANK = 0, 1
+OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY = range(6)
+
+EXPORTED = (
+    "atsne_knn_opts_default", "atsne_workspace_bytes", "atsne_knn", "atsne_calibrate_P",
+    "atsne_symmetrize", "atsne_refine_subset", "atsne_knn_precision", "atsne_forest_layout",
+    "atsne_forest_build", "atsne_forest_query", "atsne_check", "atsne_last_error",
+    "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read",
+)
+
+
+class AtsneError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("atsne status %d: %s" % (status, message))
+        self.status = status
+
+
+class KnnOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("trees", ctypes.c_int32), ("top_var_dims", ctypes.c_int32),
+                ("checks", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("queue_cap", ctypes.c_int32), ("rerank_k", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class ForestLayout(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("trees", ctypes.c_int32),
+                ("n_internal", ctypes.c_int64), ("off_split_dim", ctypes.c_size_t),
+                ("off_split_val", ctypes.c_size_t), ("off_perm", ctypes.c_size_t),
+                ("off_leaf_ofs", ctypes.c_size_t), ("bytes", ctypes.c_size_t)]
+
+
+_lib = None
+_vp, _i32, _i64, _f32, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                              ctypes.c_size_t)
+
+
+def lib():
+    """The loaded C library (ctypes.CDLL). Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libatsne.so is not built (run __graft_entry__.build()); "
+                               "there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        L.atsne_knn_opts_default.argtypes = [ctypes.POINTER(KnnOpts)]
+        L.atsne_knn_opts_default.restype = None
+        L.atsne_workspace_bytes.argtypes = [_i32, _i64, _i32, _i32, _i64, ctypes.POINTER(KnnOpts)]
+        L.atsne_workspace_bytes.restype = _sz
+        L.atsne_knn.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, ctypes.POINTER(KnnOpts), _vp, _vp,
+                                _vp, _sz, _vp]
+        L.atsne_calibrate_P.argtypes = [_vp, _i64, _i32, _f32, _f32, _i32, _vp, _vp, _vp]
+        L.atsne_symmetrize.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+        L.atsne_refine_subset.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _vp, _vp,
+                                          _vp, _vp, _vp, _sz, _vp]
+        L.atsne_knn_precision.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
+        L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
+                                          ctypes.POINTER(ForestLayout)]
+        L.atsne_forest_build.argtypes = [_vp, _i64, _i32, ctypes.POINTER(KnnOpts), _vp, _sz, _vp,
+                                         _sz, _vp]
+        L.atsne_forest_query.argtypes = [_vp, _i64, _i32, _vp, _vp, _i64, _i32,
+                                         ctypes.POINTER(KnnOpts), _vp, _vp, _vp, _vp, _sz, _vp]
+        L.atsne_check.argtypes = [_vp]
+        L.atsne_last_error.restype = ctypes.c_char_p
+        L.atsne_last_error.argtypes = []
+        L.atsne_profile_enable.argtypes = [_i32]
+        L.atsne_profile_reset.argtypes = []
+        L.atsne_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_i64),
+                                         ctypes.POINTER(ctypes.c_double)]
+        for name in EXPORTED:
+            f = getattr(L, name)
+            if name not in ("atsne_knn_opts_default", "atsne_workspace_bytes",
+                            "atsne_last_error"):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _raise(rc):
+    if rc != ATSNE_OK:
+        msg = lib().atsne_last_error()
+        raise AtsneError(rc, msg.decode() if msg else "")
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA %s tensor" % (name, dtype))
+    return t
+
+
+def knn_opts(method="exact", precision="fp32", trees=4, top_var_dims=5, checks=1024, leaf_size=1,
+             queue_cap=1024, rerank_k=0, seed=0):
+    o = KnnOpts()
+    lib().atsne_knn_opts_default(ctypes.byref(o))
+    o.method = {"exact": KNN_EXACT, "forest": KNN_FOREST}[method] if isinstance(method, str) else method
+    o.precision = {"fp32": FP32, "bf16": BF16_RERANK}[precision] if isinstance(precision, str) \
+        else precision
+    o.trees, o.top_var_dims, o.checks, o.leaf_size = trees, top_var_dims, checks, leaf_size
+    o.queue_cap, o.rerank_k, o.seed = queue_cap, rerank_k, seed
+    return o
+
+
+def workspace_bytes(op, N, D, k, S=0, opts=None):
+    return int(lib().atsne_workspace_bytes(op, N, D, k, S, ctypes.byref(opts) if opts else None))
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def atsne_knn(X, k, queries=None, opts=None, stream=None, **kw):
+    """kNN lists (idx int32 [rows,k], d2 float32 [rows,k]) -- Eq. 8; forest: Sec. 4.2."""
+    _dev(X, torch.float32, "X")
+    N, D = X.shape
+    o = opts or knn_opts(**kw)
+    S = 0
+    if queries is not None:
+        _dev(queries, torch.int32, "queries")
+        S = queries.shape[0]
+    rows = S if queries is not None else N
+    idx = torch.empty((rows, k), dtype=torch.int32, device=X.device)
+    d2 = torch.empty((rows, k), dtype=torch.float32, device=X.device)
+    ws = _workspace(workspace_bytes(OP_KNN, N, D, k, S, o), X.device)
+    _raise(lib().atsne_knn(_p(X), N, D, _p(queries), S, k, ctypes.byref(o), _p(idx), _p(d2),
+                           _p(ws), ws.numel(), _stream(stream)))
+    return idx, d2
+
+
+def atsne_calibrate_P(d2, perplexity, tol=0.0, max_iter=0, stream=None):
+    """Conditional rows P_{j|i} and beta by bisection -- Eq. 3-4 over N_i."""
+    _dev(d2, torch.float32, "d2")
+    rows, k = d2.shape
+    P = torch.empty_like(d2)
+    beta = torch.empty(rows, dtype=torch.float32, device=d2.device)
+    _raise(lib().atsne_calibrate_P(_p(d2), rows, k, perplexity, tol, max_iter, _p(P), _p(beta),
+                                   _stream(stream)))
+    return P, beta
+
+
+def atsne_symmetrize(idx, P_cond, stream=None, trim=True):
+    """Joint P as CSR (row_ptr int64, col int32, val float32) -- Eq. 2 / Eq. 10.
+    With trim=True col/val are cut to nnz (one device-to-host read of nnz)."""
+    _dev(idx, torch.int32, "idx")
+    _dev(P_cond, torch.float32, "P_cond")
+    N, k = idx.shape
+    dev = idx.device
+    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(2 * N * k, dtype=torch.int32, device=dev)
+    val = torch.empty(2 * N * k, dtype=torch.float32, device=dev)
+    nnz = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = _workspace(workspace_bytes(OP_SYMMETRIZE, N, 0, k), dev)
+    _raise(lib().atsne_symmetrize(_p(idx), _p(P_cond), N, k, _p(row_ptr), _p(col), _p(val),
+                                  _p(nnz), _p(ws), ws.numel(), _stream(stream)))
+    if trim:
+        n = int(nnz.item())
+        return row_ptr, col[:n], val[:n]
+    return row_ptr, col, val, nnz
+
+
+def atsne_refine_subset(X, subset, perplexity, idx, d2, P_cond, beta=None, rho=None, stream=None):
+    """Exact refinement of the listed rows, in place -- Sec. 4.3, 5.1.1."""
+    _dev(X, torch.float32, "X")
+    _dev(subset, torch.int32, "subset")
+    N, D = X.shape
+    k = idx.shape[1]
+    S = subset.shape[0]
+    ws = _workspace(workspace_bytes(OP_REFINE, N, D, k, S), X.device)
+    _raise(lib().atsne_refine_subset(_p(X), N, D, _p(subset), S, k, perplexity, _p(idx), _p(d2),
+                                     _p(P_cond), _p(beta), _p(rho), _p(ws), ws.numel(),
+                                     _stream(stream)))
+
+
+def atsne_knn_precision(idx_approx, idx_exact, stream=None):
+    """rho_i (float32 [rows]) and rho (Python float) -- Eq. 9."""
+    _dev(idx_approx, torch.int32, "idx_approx")
+    _dev(idx_exact, torch.int32, "idx_exact")
+    rows, k = idx_approx.shape
+    rho_i = torch.empty(rows, dtype=torch.float32, device=idx_approx.device)
+    s = torch.empty(1, dtype=torch.float64, device=idx_approx.device)
+    _raise(lib().atsne_knn_precision(_p(idx_approx), _p(idx_exact), rows, k, _p(rho_i), _p(s),
+                                     _stream(stream)))
+    return rho_i, float(s.item()) / max(rows, 1)
+
+
+class Forest:
+    """A randomized KD-forest held in one device buffer (layout of atsne.h)."""
+
+    def __init__(self, buf, layout, N, D, opts):
+        self.buf, self.layout, self.N, self.D, self.opts = buf, layout, N, D, opts
+
+    def _view(self, off, count, dtype):
+        esz = torch.tensor([], dtype=dtype).element_size()
+        return self.buf[off:off + count * esz].view(dtype)
+
+    def arrays(self):
+        L = self.layout
+        T, n_int = L.trees, L.n_internal
+        return dict(
+            depth=L.depth,
+            split_dim=self._view(L.off_split_dim, T * n_int, torch.int32).view(T, n_int),
+            split_val=self._view(L.off_split_val, T * n_int, torch.float32).view(T, n_int),
+            perm=self._view(L.off_perm, T * self.N, torch.int32).view(T, self.N),
+            leaf_ofs=self._view(L.off_leaf_ofs, (1 << L.depth) + 1, torch.int32))
+
+
+def atsne_forest_build(X, stream=None, opts=None, **kw):
+    _dev(X, torch.float32, "X")
+    N, D = X.shape
+    o = opts or knn_opts(method="forest", **kw)
+    L = ForestLayout()
+    _raise(lib().atsne_forest_layout(N, D, ctypes.byref(o), ctypes.byref(L)))
+    buf = torch.empty(L.bytes, dtype=torch.uint8, device=X.device)
+    ws = _workspace(workspace_bytes(OP_FOREST_BUILD, N, D, 1, 0, o), X.device)
+    _raise(lib().atsne_forest_build(_p(X), N, D, ctypes.byref(o), _p(buf), L.bytes, _p(ws),
+                                    ws.numel(), _stream(stream)))
+    return Forest(buf, L, N, D, o)
+
+
+def atsne_forest_query(X, forest, k, checks=None, queries=None, queue_cap=None, stream=None):
+    _dev(X, torch.float32, "X")
+    N, D = X.shape
+    o = KnnOpts.from_buffer_copy(forest.opts)
+    if checks is not None:
+        o.checks = checks
+    if queue_cap is not None:
+        o.queue_cap = queue_cap
+    S = 0
+    if queries is not None:
+        _dev(queries, torch.int32, "queries")
+        S = queries.shape[0]
+    rows = S if queries is not None else N
+    idx = torch.empty((rows, k), dtype=torch.int32, device=X.device)
+    d2 = torch.empty((rows, k), dtype=torch.float32, device=X.device)
+    ev = torch.empty(rows, dtype=torch.int64, device=X.device)
+    ws = _workspace(workspace_bytes(OP_FOREST_QUERY, N, D, k, S, o), X.device)
+    _raise(lib().atsne_forest_query(_p(X), N, D, _p(forest.buf), _p(queries), S, k,
+                                    ctypes.byref(o), _p(idx), _p(d2), _p(ev), _p(ws), ws.numel(),
+                                    _stream(stream)))
+    return idx, d2, ev
+
+
+def atsne_check(stream=None):
+    """Synchronise and raise if a kernel flagged bad input or an expired wait."""
+    _raise(lib().atsne_check(_stream(stream)))
+
+
+def profile_enable(on=True):
+    _raise(lib().atsne_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _raise(lib().atsne_profile_reset())
+
+
+def profile_read(kernel=None):
+    n = _i64(0)
+    ms = ctypes.c_double(0.0)
+    _raise(lib().atsne_profile_read(kernel.encode() if kernel else None, ctypes.byref(n),
+                                    ctypes.byref(ms)))
+    return int(n.value), float(ms.value)

@@ -1,0 +1,460 @@
+// C ABI entry points (declared in include/atsne.h): argument validation on the
+// host, workspace layouts, the device status word, launch profiling, and the
+// composition of kernels into the four operations.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace atsne {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+atsne_status set_error(atsne_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+atsne_status cuda_error(cudaError_t e, const char *what) {
+    return set_error(ATSNE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// device status word (one int per device, no allocation)
+// ---------------------------------------------------------------------------
+static __device__ int g_status_word;
+static int *g_status_ptr[64];
+
+int *device_status_word() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_status_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+        g_status_ptr[dev] = static_cast<int *>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+// ---------------------------------------------------------------------------
+// launch profiling
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pool;
+size_t g_prof_used = 0;
+constexpr size_t PROF_POOL = 8192;
+}  // namespace
+
+ProfScope::ProfScope(const char *kernel, cudaStream_t s) : slot(-1), stream(s) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_used >= g_prof_pool.size()) return;
+    slot = (int)g_prof_used++;
+    g_prof_pool[slot].name = kernel;
+    cudaEventRecord(g_prof_pool[slot].a, stream);
+}
+
+ProfScope::~ProfScope() {
+    if (slot >= 0) cudaEventRecord(g_prof_pool[slot].b, stream);
+}
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void check_finite_kernel(const float4 *__restrict__ x4, int64_t n4,
+                                    const float *__restrict__ tail, int64_t ntail, int *status) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x4[i];
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+    }
+    if (blockIdx.x == 0)
+        for (int64_t i = threadIdx.x; i < ntail; i += blockDim.x) bad |= !isfinite(tail[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, DEV_NONFINITE);
+}
+
+__global__ void check_indices_kernel(const int32_t *__restrict__ list, int64_t n, int64_t N,
+                                     int *status) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= list[i] < 0 || list[i] >= N;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, DEV_MALFORMED);
+}
+
+atsne_status check_finite(const float *X, int64_t n, cudaStream_t stream) {
+    ProfScope prof("check_finite", stream);
+    const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    const int64_t n4 = aligned ? n / 4 : 0;
+    const int64_t done = n4 * 4;
+    const int grid = (int)hmin(4 * num_sms(), ceil_div(n4 > 0 ? n4 : 1, 256));
+    check_finite_kernel<<<grid, 256, 0, stream>>>(reinterpret_cast<const float4 *>(X), n4, X + done,
+                                                  n - done, device_status_word());
+    ATSNE_LAUNCH_CHECK("check_finite launch");
+    return ATSNE_OK;
+}
+
+atsne_status check_indices(const int32_t *list, int64_t n, int64_t N, cudaStream_t stream) {
+    if (n <= 0) return ATSNE_OK;
+    ProfScope prof("check_indices", stream);
+    const int grid = (int)hmin(2 * num_sms(), ceil_div(n, 256));
+    check_indices_kernel<<<grid, 256, 0, stream>>>(list, n, N, device_status_word());
+    ATSNE_LAUNCH_CHECK("check_indices launch");
+    return ATSNE_OK;
+}
+
+atsne_knn_opts opts_or_default(const atsne_knn_opts *o) {
+    atsne_knn_opts d;
+    atsne_knn_opts_default(&d);
+    return o ? *o : d;
+}
+
+atsne_status validate_knn_opts(const atsne_knn_opts &o) {
+    if (o.method != ATSNE_KNN_EXACT && o.method != ATSNE_KNN_FOREST)
+        return set_error(ATSNE_EINVAL, "knn: unknown method %d", o.method);
+    if (o.precision != ATSNE_FP32 && o.precision != ATSNE_BF16_RERANK)
+        return set_error(ATSNE_EINVAL, "knn: unknown precision %d", o.precision);
+    if (o.method == ATSNE_KNN_FOREST) {
+        if (o.trees < 1 || o.trees > 64) return set_error(ATSNE_EINVAL, "forest: trees=%d not in [1,64]", o.trees);
+        if (o.top_var_dims < 1 || o.top_var_dims > 8)
+            return set_error(ATSNE_EINVAL, "forest: top_var_dims=%d not in [1,8]", o.top_var_dims);
+        if (o.checks < 1) return set_error(ATSNE_EINVAL, "forest: checks=%d < 1", o.checks);
+        if (o.leaf_size < 1) return set_error(ATSNE_EINVAL, "forest: leaf_size=%d < 1", o.leaf_size);
+        if (o.queue_cap < 2) return set_error(ATSNE_EINVAL, "forest: queue_cap=%d < 2", o.queue_cap);
+    }
+    return ATSNE_OK;
+}
+
+atsne_status validate_xk(const float *X, int64_t N, int32_t D, int32_t k) {
+    if (!X) return set_error(ATSNE_EINVAL, "X is NULL");
+    if (N < 2 || N > INT32_MAX) return set_error(ATSNE_EINVAL, "N=%lld not in [2, 2^31-1]", (long long)N);
+    if (D < 1) return set_error(ATSNE_EINVAL, "D=%d < 1", D);
+    if (k < 1 || (int64_t)k > N - 1) return set_error(ATSNE_EINVAL, "k=%d not in [1, N-1]", k);
+    return ATSNE_OK;
+}
+
+ForestView forest_view(void *forest, int64_t N, int32_t D, const atsne_knn_opts &o) {
+    atsne_forest_layout_t L;
+    forest_layout(N, o.trees, o.leaf_size, &L);
+    char *b = static_cast<char *>(forest);
+    ForestView f;
+    f.N = N;
+    f.D = D;
+    f.trees = o.trees;
+    f.depth = L.depth;
+    f.leaf_size = o.leaf_size;
+    f.top_var_dims = o.top_var_dims;
+    f.n_internal = L.n_internal;
+    f.seed = o.seed;
+    f.split_dim = reinterpret_cast<int32_t *>(b + L.off_split_dim);
+    f.split_val = reinterpret_cast<float *>(b + L.off_split_val);
+    f.perm = reinterpret_cast<int32_t *>(b + L.off_perm);
+    f.leaf_ofs = reinterpret_cast<int32_t *>(b + L.off_leaf_ofs);
+    return f;
+}
+
+// Workspace layouts (sizing and carving share these).
+size_t knn_ws(Carver &c, int64_t N, int32_t D, int32_t k, int64_t S, const atsne_knn_opts &o,
+              void **forest, void **sub_ws, size_t *sub_bytes) {
+    if (o.method == ATSNE_KNN_FOREST) {
+        const size_t fb = forest_layout(N, o.trees, o.leaf_size, nullptr);
+        char *f = c.take<char>(fb);
+        if (forest) *forest = f;
+        Carver b(nullptr), q(nullptr);
+        const size_t bb = forest_build_workspace(b, N, D, o.trees, o.leaf_size, nullptr);
+        const size_t qb = forest_query_workspace(q, N, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
+        const size_t need = bb > qb ? bb : qb;
+        char *w = c.take<char>(need);
+        if (sub_ws) *sub_ws = w;
+        if (sub_bytes) *sub_bytes = need;
+    }
+    return c.bytes();
+}
+
+size_t refine_ws(Carver &c, int64_t S, int32_t k, int32_t **ti, float **td, float **tp, float **tb) {
+    int32_t *a = c.take<int32_t>((size_t)S * k);
+    float *b = c.take<float>((size_t)S * k);
+    float *p = c.take<float>((size_t)S * k);
+    float *q = c.take<float>((size_t)(S > 0 ? S : 1));
+    if (ti) *ti = a;
+    if (td) *td = b;
+    if (tp) *tp = p;
+    if (tb) *tb = q;
+    return c.bytes();
+}
+
+}  // namespace
+}  // namespace atsne
+
+using namespace atsne;
+
+extern "C" {
+
+void atsne_knn_opts_default(atsne_knn_opts *o) {
+    if (!o) return;
+    o->method = ATSNE_KNN_EXACT;
+    o->precision = ATSNE_FP32;
+    o->trees = 4;
+    o->top_var_dims = 5;
+    o->checks = 1024;
+    o->leaf_size = 1;
+    o->queue_cap = 1024;
+    o->rerank_k = 0;
+    o->seed = 0;
+}
+
+const char *atsne_last_error(void) { return g_err; }
+
+size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_t S,
+                             const atsne_knn_opts *opts) {
+    const atsne_knn_opts o = opts_or_default(opts);
+    Carver c(nullptr);
+    switch (op) {
+    case ATSNE_OP_KNN:
+        return knn_ws(c, N, D, k, S, o, nullptr, nullptr, nullptr);
+    case ATSNE_OP_CALIBRATE:
+        return 0;
+    case ATSNE_OP_SYMMETRIZE:
+        return symmetrize_workspace(c, N, k, nullptr);
+    case ATSNE_OP_REFINE:
+        return refine_ws(c, S, k, nullptr, nullptr, nullptr, nullptr);
+    case ATSNE_OP_FOREST_BUILD:
+        return forest_build_workspace(c, N, D, o.trees, o.leaf_size, nullptr);
+    case ATSNE_OP_FOREST_QUERY:
+        return forest_query_workspace(c, N, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
+    default:
+        return 0;
+    }
+}
+
+atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *queries, int64_t S,
+                       int32_t k, const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                       void *workspace, size_t ws_bytes, void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_status st = validate_xk(X, N, D, k);
+    if (st) return st;
+    const atsne_knn_opts o = opts_or_default(opts);
+    if ((st = validate_knn_opts(o))) return st;
+    if (!idx_out || !d2_out) return set_error(ATSNE_EINVAL, "knn: NULL output");
+    if (queries && S < 0) return set_error(ATSNE_EINVAL, "knn: S=%lld < 0", (long long)S);
+    const int64_t nq = queries ? S : N;
+    if (nq == 0) return ATSNE_OK;
+    Carver c(workspace);
+    void *forest = nullptr, *sub = nullptr;
+    size_t sub_bytes = 0;
+    knn_ws(c, N, D, k, queries ? S : 0, o, &forest, &sub, &sub_bytes);
+    if (c.bytes() > 0 && (!workspace || ws_bytes < c.bytes()))
+        return set_error(ATSNE_ENOMEM, "knn: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
+    if (queries && (st = check_indices(queries, S, N, stream))) return st;
+    if (o.method == ATSNE_KNN_EXACT)
+        return knn_bruteforce(X, N, D, queries, nq, k, idx_out, d2_out, stream);
+    ForestView f = forest_view(forest, N, D, o);
+    if ((st = forest_build_launch(X, f, sub, sub_bytes, stream))) return st;
+    return forest_query_launch(X, f, queries, nq, k, o.checks, o.queue_cap, idx_out, d2_out,
+                               nullptr, sub, sub_bytes, stream);
+}
+
+atsne_status atsne_calibrate_P(const float *d2, int64_t rows, int32_t k, float perplexity,
+                               float tol, int32_t max_iter, float *P_cond_out, float *beta_out,
+                               void *stream) {
+    if (!d2 || !P_cond_out) return set_error(ATSNE_EINVAL, "calibrate: NULL pointer");
+    if (rows < 0 || k < 1) return set_error(ATSNE_EINVAL, "calibrate: rows=%lld k=%d", (long long)rows, k);
+    if (!(perplexity > 0.f) || !(perplexity < (float)k))
+        return set_error(ATSNE_EINVAL, "calibrate: perplexity=%g not in (0, k=%d)", (double)perplexity, k);
+    if (calibrate_smem_bytes(k) > 227 * 1024)
+        return set_error(ATSNE_EUNSUPPORTED, "calibrate: k=%d too large", k);
+    if (!(tol > 0.f)) tol = 1e-5f;
+    if (max_iter <= 0) max_iter = 200;
+    return calibrate_launch(d2, rows, k, perplexity, tol, max_iter, P_cond_out, beta_out,
+                            static_cast<cudaStream_t>(stream));
+}
+
+atsne_status atsne_symmetrize(const int32_t *idx, const float *P_cond, int64_t N, int32_t k,
+                              int64_t *row_ptr, int32_t *col, float *val, int64_t *nnz_dev,
+                              void *workspace, size_t ws_bytes, void *stream) {
+    if (!idx || !P_cond || !row_ptr || !col || !val) return set_error(ATSNE_EINVAL, "symmetrize: NULL pointer");
+    if (N < 2 || N > INT32_MAX || k < 1 || (int64_t)k > N - 1)
+        return set_error(ATSNE_EINVAL, "symmetrize: N=%lld k=%d", (long long)N, k);
+    if (k > 512) return set_error(ATSNE_EUNSUPPORTED, "symmetrize: k=%d above 512", k);
+    Carver c(workspace);
+    SymWs w;
+    symmetrize_workspace(c, N, k, &w);
+    if (!workspace || ws_bytes < c.bytes())
+        return set_error(ATSNE_ENOMEM, "symmetrize: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    return symmetrize_launch(idx, P_cond, N, k, row_ptr, col, val, nnz_dev, w,
+                             static_cast<cudaStream_t>(stream));
+}
+
+atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int32_t *subset,
+                                 int64_t S, int32_t k, float perplexity, int32_t *idx, float *d2,
+                                 float *P_cond, float *beta, float *rho, void *workspace,
+                                 size_t ws_bytes, void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_status st = validate_xk(X, N, D, k);
+    if (st) return st;
+    if (!subset || !idx || !d2 || !P_cond) return set_error(ATSNE_EINVAL, "refine: NULL pointer");
+    if (S < 0) return set_error(ATSNE_EINVAL, "refine: S=%lld < 0", (long long)S);
+    if (!(perplexity > 0.f) || !(perplexity < (float)k))
+        return set_error(ATSNE_EINVAL, "refine: perplexity=%g not in (0, k=%d)", (double)perplexity, k);
+    if (S == 0) return ATSNE_OK;
+    Carver c(workspace);
+    int32_t *ti;
+    float *td, *tp, *tb;
+    refine_ws(c, S, k, &ti, &td, &tp, &tb);
+    if (!workspace || ws_bytes < c.bytes())
+        return set_error(ATSNE_ENOMEM, "refine: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
+    if ((st = check_indices(subset, S, N, stream))) return st;
+    if ((st = knn_bruteforce(X, N, D, subset, S, k, ti, td, stream))) return st;
+    if ((st = calibrate_launch(td, S, k, perplexity, 1e-5f, 200, tp, tb, stream))) return st;
+    return refine_scatter_launch(subset, S, N, k, ti, td, tp, tb, idx, d2, P_cond, beta, rho, stream);
+}
+
+atsne_status atsne_knn_precision(const int32_t *idx_approx, const int32_t *idx_exact,
+                                 int64_t rows, int32_t k, float *rho_i_out, double *rho_sum_dev,
+                                 void *stream) {
+    if (!idx_approx || !idx_exact) return set_error(ATSNE_EINVAL, "precision: NULL pointer");
+    if (rows < 0 || k < 1 || k > 4096) return set_error(ATSNE_EINVAL, "precision: rows=%lld k=%d", (long long)rows, k);
+    return precision_launch(idx_approx, idx_exact, rows, k, rho_i_out, rho_sum_dev,
+                            static_cast<cudaStream_t>(stream));
+}
+
+atsne_status atsne_forest_layout(int64_t N, int32_t D, const atsne_knn_opts *opts,
+                                 atsne_forest_layout_t *out) {
+    atsne_knn_opts o = opts_or_default(opts);
+    o.method = ATSNE_KNN_FOREST;
+    atsne_status st = validate_knn_opts(o);
+    if (st) return st;
+    if (N < 2 || N > INT32_MAX || D < 1 || !out) return set_error(ATSNE_EINVAL, "forest layout: bad arguments");
+    forest_layout(N, o.trees, o.leaf_size, out);
+    return ATSNE_OK;
+}
+
+atsne_status atsne_forest_build(const float *X, int64_t N, int32_t D, const atsne_knn_opts *opts,
+                                void *forest, size_t forest_bytes, void *workspace,
+                                size_t ws_bytes, void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_knn_opts o = opts_or_default(opts);
+    o.method = ATSNE_KNN_FOREST;
+    atsne_status st = validate_knn_opts(o);
+    if (st) return st;
+    if (!X || !forest || N < 2 || N > INT32_MAX || D < 1) return set_error(ATSNE_EINVAL, "forest build: bad arguments");
+    if (forest_bytes < forest_layout(N, o.trees, o.leaf_size, nullptr))
+        return set_error(ATSNE_ENOMEM, "forest build: forest buffer too small");
+    if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
+    return forest_build_launch(X, forest_view(forest, N, D, o), workspace, ws_bytes, stream);
+}
+
+atsne_status atsne_forest_query(const float *X, int64_t N, int32_t D, const void *forest,
+                                const int32_t *queries, int64_t S, int32_t k,
+                                const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                                int64_t *evaluated_out, void *workspace, size_t ws_bytes,
+                                void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_status st = validate_xk(X, N, D, k);
+    if (st) return st;
+    atsne_knn_opts o = opts_or_default(opts);
+    o.method = ATSNE_KNN_FOREST;
+    if ((st = validate_knn_opts(o))) return st;
+    if (!forest || !idx_out || !d2_out) return set_error(ATSNE_EINVAL, "forest query: NULL pointer");
+    if (queries && S < 0) return set_error(ATSNE_EINVAL, "forest query: S < 0");
+    const int64_t nq = queries ? S : N;
+    if (nq == 0) return ATSNE_OK;
+    if (queries && (st = check_indices(queries, S, N, stream))) return st;
+    return forest_query_launch(X, forest_view(const_cast<void *>(forest), N, D, o), queries, nq, k,
+                               o.checks, o.queue_cap, idx_out, d2_out, evaluated_out, workspace,
+                               ws_bytes, stream);
+}
+
+atsne_status atsne_check(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_error(e, "check: stream synchronize");
+    int *p = device_status_word();
+    if (!p) return set_error(ATSNE_ECUDA, "check: no status word");
+    int v = 0;
+    e = cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "check: read status");
+    const int zero = 0;
+    e = cudaMemcpy(p, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "check: clear status");
+    switch (v) {
+    case DEV_OK:
+        return ATSNE_OK;
+    case DEV_NONFINITE:
+        return set_error(ATSNE_EINVAL, "device: non-finite input");
+    case DEV_MALFORMED:
+        return set_error(ATSNE_EINVAL, "device: index out of range or malformed neighbour list");
+    case DEV_TIMEOUT:
+        return set_error(ATSNE_ETIMEOUT, "device: a bounded wait expired");
+    default:
+        return set_error(ATSNE_ECUDA, "device: unknown status %d", v);
+    }
+}
+
+atsne_status atsne_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (on && g_prof_pool.empty()) {
+        g_prof_pool.resize(PROF_POOL);
+        for (auto &r : g_prof_pool) {
+            r.name = "";
+            if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+                g_prof_pool.clear();
+                return set_error(ATSNE_ECUDA, "profile: event creation failed");
+            }
+        }
+    }
+    g_prof_on = on != 0;
+    return ATSNE_OK;
+}
+
+atsne_status atsne_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_used = 0;
+    return ATSNE_OK;
+}
+
+atsne_status atsne_profile_read(const char *kernel, int64_t *launches, double *total_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int64_t n = 0;
+    double ms = 0.0;
+    for (size_t i = 0; i < g_prof_used; ++i) {
+        const ProfRec &r = g_prof_pool[i];
+        if (kernel && strcmp(kernel, r.name) != 0) continue;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_error(e, "profile: event synchronize");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return cuda_error(e, "profile: elapsed time");
+        ms += t;
+        ++n;
+    }
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = ms;
+    return ATSNE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Per-point Gaussian bandwidth by bisection and the conditional rows P_{j|i}
+// (Eq. 3 and Eq. 4, Sec. 3, over the kNN support of Eq. 8).
+//
+// One thread owns one row. A CTA of 128 threads stages its 128 contiguous rows
+// (128*k floats, one coalesced sweep) into shared memory with an odd row
+// stride, so the per-thread row walks are bank-conflict free; the P rows leave
+// the same way. Each bisection step evaluates, for the shifted distances
+// s_j = d_j - min d, w_j = exp(-beta s_j), Z = sum w_j and
+// H = ln Z + beta sum_j w_j s_j / Z (nats), compares H with ln(perplexity) and
+// halves the bracket exactly as the definition prescribes: start beta = 1,
+// double while no upper bound is known, then bisect.
+//
+// Arithmetic: FP32 throughout. GB300 runs FP64 at 1/64 of the FP32 rate, and
+// the parity bound for P (1e-5 absolute) needs H only to about 1e-6, which the
+// 90-term FP32 sums give with a wide margin; the stopping tolerance defaults to
+// 1e-5 nats for that reason.
+#include <float.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace atsne {
+namespace {
+
+constexpr int CAL_THREADS = 128;
+
+__global__ void __launch_bounds__(CAL_THREADS)
+calibrate_kernel(const float *__restrict__ d2, int64_t rows, int k, float target, float tol,
+                 int max_iter, float *__restrict__ P, float *__restrict__ beta_out, int *status) {
+    extern __shared__ float sm[];
+    const int stride = k | 1;
+    const int64_t r0 = (int64_t)blockIdx.x * CAL_THREADS;
+    const int nr = (int)(rows - r0 < CAL_THREADS ? rows - r0 : CAL_THREADS);
+    const float *src = d2 + r0 * k;
+    for (int t = threadIdx.x; t < nr * k; t += CAL_THREADS) {
+        int r = t / k, c = t - r * k;
+        sm[r * stride + c] = src[t];
+    }
+    __syncthreads();
+
+    if ((int)threadIdx.x < nr) {
+        float *row = sm + threadIdx.x * stride;
+        float dmin = row[0];
+        bool finite = true;
+        for (int j = 0; j < k; ++j) {
+            float v = row[j];
+            finite &= isfinite(v) && v >= 0.f;
+            dmin = fminf(dmin, v);
+        }
+        if (!finite) raise_status(status, DEV_NONFINITE);
+        for (int j = 0; j < k; ++j) row[j] -= dmin;  // s_j
+
+        float beta = 1.f, lo = 0.f, hi = INFINITY, bf = 1.f, Z = 1.f;
+        for (int it = 1;; ++it) {
+            bf = fminf(beta, FLT_MAX);
+            float z = 0.f, ws = 0.f;
+            for (int j = 0; j < k; ++j) {
+                const float s = row[j];
+                const float w = expf(-bf * s);
+                z += w;
+                ws = fmaf(w, s, ws);
+            }
+            const float H = logf(z) + bf * ws / z;
+            Z = z;
+            if (fabsf(H - target) < tol || it >= max_iter) break;
+            if (H > target) {
+                lo = beta;
+                beta = isinf(hi) ? 2.f * beta : 0.5f * (beta + hi);
+            } else {
+                hi = beta;
+                beta = 0.5f * (lo + beta);
+            }
+        }
+        const float inv = 1.f / Z;
+        for (int j = 0; j < k; ++j) row[j] = expf(-bf * row[j]) * inv;
+        if (beta_out) beta_out[r0 + threadIdx.x] = bf;
+    }
+    __syncthreads();
+    float *dst = P + r0 * k;
+    for (int t = threadIdx.x; t < nr * k; t += CAL_THREADS) {
+        int r = t / k, c = t - r * k;
+        dst[t] = sm[r * stride + c];
+    }
+}
+
+}  // namespace
+
+size_t calibrate_smem_bytes(int k) { return sizeof(float) * CAL_THREADS * (size_t)(k | 1); }
+
+atsne_status calibrate_launch(const float *d2, int64_t rows, int k, float perplexity, float tol,
+                              int max_iter, float *P, float *beta, cudaStream_t stream) {
+    if (rows <= 0) return ATSNE_OK;
+    const size_t smem = calibrate_smem_bytes(k);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(calibrate_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "calibrate attribute");
+        attr = smem;
+    }
+    ProfScope prof("calibrate_beta", stream);
+    calibrate_kernel<<<ceil_div(rows, CAL_THREADS), CAL_THREADS, smem, stream>>>(
+        d2, rows, k, logf(perplexity), tol, max_iter, P, beta, device_status_word());
+    ATSNE_LAUNCH_CHECK("calibrate launch");
+    return ATSNE_OK;
+}
+
+}  // namespace atsne

@@ -1,0 +1,136 @@
+// Shared host/device helpers of the sm_103a library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "atsne.h"
+
+namespace atsne {
+
+// ---------------------------------------------------------------------------
+// Host side: errors, workspace carving, launch profiling
+// ---------------------------------------------------------------------------
+atsne_status set_error(atsne_status st, const char *fmt, ...);
+atsne_status cuda_error(cudaError_t e, const char *what);
+int *device_status_word();  // device address of the status word (current device)
+
+// Device status codes written by kernels (first writer wins).
+enum : int { DEV_OK = 0, DEV_NONFINITE = 1, DEV_MALFORMED = 2, DEV_TIMEOUT = 3 };
+
+// Carves 256-byte aligned slices out of a caller workspace. With base == nullptr
+// it only measures, so one layout function serves sizing and carving.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+    size_t bytes() const { return (off + 255) & ~size_t(255); }
+};
+
+// Brackets one kernel launch with CUDA events on its stream while profiling is on.
+struct ProfScope {
+    int slot;
+    cudaStream_t stream;
+    ProfScope(const char *kernel, cudaStream_t s);
+    ~ProfScope();
+};
+
+#define ATSNE_LAUNCH_CHECK(what)                                              \
+    do {                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess) return ::atsne::cuda_error(e_, what);          \
+    } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int64_t hmin(int64_t a, int64_t b) { return a < b ? a : b; }
+inline int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// Device side
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ void raise_status(int *status, int code) {
+    if (status) atomicCAS(status, DEV_OK, code);
+}
+
+// Total order on (distance, index) used for every neighbour list.
+__device__ __forceinline__ bool pair_less(float da, int ja, float db, int jb) {
+    return da < db || (da == db && ja < jb);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Lexicographic max of (d, j) over the warp; returns it in every lane.
+__device__ __forceinline__ void warp_argmax_pair(float &d, int &j, int &pos) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float od = __shfl_xor_sync(0xffffffffu, d, o);
+        int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        int op = __shfl_xor_sync(0xffffffffu, pos, o);
+        if (pair_less(d, j, od, oj)) {
+            d = od;
+            j = oj;
+            pos = op;
+        }
+    }
+}
+
+// Order-preserving map of a float to uint32 (-0 folded onto +0, so that the
+// ordering of values equals IEEE comparison order; inputs are finite).
+__device__ __forceinline__ uint32_t float_key(float f) {
+    f = f + 0.0f;  // -0 -> +0
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// In-warp bitonic sort of n (key, value) pairs held in shared memory,
+// ascending by (key, value). n is a power of two; the caller pads the unused
+// tail with entries that sort last.
+template <typename K, typename V>
+__device__ __forceinline__ void warp_bitonic_sort_smem(K *key, V *val, int n, int lane) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < (n >> 1); t += 32) {
+                int i = 2 * t - (t & (stride - 1));
+                int j = i + stride;
+                bool up = ((i & size) == 0);
+                K ki = key[i], kj = key[j];
+                V vi = val[i], vj = val[j];
+                bool gt = (kj < ki) || (kj == ki && vj < vi);
+                if (gt == up) {
+                    key[i] = kj;
+                    key[j] = ki;
+                    val[i] = vj;
+                    val[j] = vi;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace atsne

@@ -1,0 +1,67 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "atsne.h"
+#include "common.cuh"
+
+namespace atsne {
+
+// ---- exact kNN ------------------------------------------------------------
+atsne_status knn_bruteforce(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq,
+                            int k, int32_t *idx_out, float *d2_out, cudaStream_t stream);
+
+// ---- calibrate ------------------------------------------------------------
+size_t calibrate_smem_bytes(int k);
+atsne_status calibrate_launch(const float *d2, int64_t rows, int k, float perplexity, float tol,
+                              int max_iter, float *P, float *beta, cudaStream_t stream);
+
+// ---- symmetrize -------------------------------------------------------------
+struct SymWs {
+    int32_t *scol = nullptr;
+    float *sval = nullptr;
+    int32_t *rev = nullptr, *cursor = nullptr, *long_rows = nullptr, *n_long = nullptr;
+    int64_t *scan = nullptr;
+};
+size_t scan_partials_count(int64_t n);
+atsne_status scan_rowlen(const int32_t *rev, int64_t n, int add, int64_t *out, int64_t *total,
+                         int64_t *part, cudaStream_t stream);
+size_t symmetrize_workspace(Carver &c, int64_t N, int k, SymWs *ws);
+atsne_status symmetrize_launch(const int32_t *idx, const float *P, int64_t N, int k,
+                               int64_t *row_ptr, int32_t *col, float *val, int64_t *nnz_dev,
+                               const SymWs &w, cudaStream_t stream);
+
+// ---- precision / refine -----------------------------------------------------
+atsne_status precision_launch(const int32_t *a, const int32_t *e, int64_t rows, int k,
+                              float *rho_i, double *rho_sum, cudaStream_t stream);
+atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, int k, const int32_t *ti,
+                                   const float *td, const float *tp, const float *tb, int32_t *idx,
+                                   float *d2, float *P, float *beta, float *rho,
+                                   cudaStream_t stream);
+
+// ---- forest -------------------------------------------------------------------
+struct ForestView {
+    int64_t N;
+    int D, trees, depth, leaf_size, top_var_dims;
+    int64_t n_internal;
+    uint64_t seed;
+    int32_t *split_dim;
+    float *split_val;
+    int32_t *perm;
+    int32_t *leaf_ofs;
+};
+int forest_depth(int64_t N, int leaf_size);
+size_t forest_layout(int64_t N, int trees, int leaf_size, atsne_forest_layout_t *out);
+size_t forest_build_workspace(Carver &c, int64_t N, int D, int trees, int leaf_size, void *ws_out);
+atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_base, size_t ws_bytes,
+                                 cudaStream_t stream);
+size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int checks, int leaf_size,
+                              void *ws_out);
+atsne_status forest_query_launch(const float *X, const ForestView &f, const int32_t *qlist,
+                                 int64_t nq, int k, int checks, int qcap, int32_t *idx_out,
+                                 float *d2_out, int64_t *evaluated_out, void *ws_base,
+                                 size_t ws_bytes, cudaStream_t stream);
+
+}  // namespace atsne

@@ -1,0 +1,184 @@
+// Exact kNN by direct differences on the CUDA cores (Eq. 8, Sec. 3.1).
+//
+// Each CTA takes 32 queries and streams the whole corpus in tiles of 64
+// points; 256 threads accumulate (q - c)^2 over 32-dimension slices (8 pairs
+// per thread), then each warp folds a tile's 64 candidates per query into a
+// per-query list of the best k in shared memory. A candidate enters only if it
+// beats the list's current worst entry under the (distance, index) order, so
+// after the first tiles almost every candidate costs one compare. The FP32
+// distances are the exact-path's definition of d2; this kernel is the
+// reference GPU path for small problems and the fallback for rows whose
+// tensor-core candidates cannot be certified.
+#include <float.h>
+#include <limits.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace atsne {
+namespace {
+
+constexpr int BF_QB = 32;       // queries per CTA
+constexpr int BF_CB = 64;       // corpus points per tile
+constexpr int BF_DC = 32;       // dimensions per slice
+constexpr int BF_THREADS = 256;
+
+template <int KCAP>
+__global__ void __launch_bounds__(BF_THREADS)
+knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
+                      const int32_t *__restrict__ qlist, int64_t nq, int k,
+                      int32_t *__restrict__ idx_out, float *__restrict__ d2_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Qs = reinterpret_cast<float *>(smem_raw);      // [QB][DC+1]
+    float *Cs = Qs + BF_QB * (BF_DC + 1);                 // [CB][DC+1]
+    float *Dt = Cs + BF_CB * (BF_DC + 1);                 // [QB][CB+1]
+    float *td = Dt + BF_QB * (BF_CB + 1);                 // [QB][KCAP]
+    int *tj = reinterpret_cast<int *>(td + BF_QB * KCAP); // [QB][KCAP]
+    __shared__ int qid[BF_QB];
+    __shared__ float thr_d[BF_QB];
+    __shared__ int thr_j[BF_QB];
+    __shared__ int thr_p[BF_QB];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t q0 = (int64_t)blockIdx.x * BF_QB;
+    if (tid < BF_QB) {
+        int64_t s = q0 + tid;
+        int q = s < nq ? (qlist ? qlist[s] : (int)s) : -1;
+        qid[tid] = (q >= 0 && q < N) ? q : -1;  // out-of-range queries are flagged by the caller
+        thr_d[tid] = INFINITY;
+        thr_j[tid] = INT_MAX;
+        thr_p[tid] = 0;
+    }
+    for (int t = tid; t < BF_QB * KCAP; t += BF_THREADS) {
+        td[t] = INFINITY;
+        tj[t] = INT_MAX;
+    }
+    __syncthreads();
+
+    const int qi = tid >> 3, cg = tid & 7;
+    for (int64_t c0 = 0; c0 < N; c0 += BF_CB) {
+        float acc[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+        for (int d0 = 0; d0 < D; d0 += BF_DC) {
+            for (int t = tid; t < BF_QB * BF_DC; t += BF_THREADS) {
+                int r = t / BF_DC, c = t - r * BF_DC;
+                int q = qid[r];
+                Qs[r * (BF_DC + 1) + c] = (q >= 0 && d0 + c < D) ? X[(int64_t)q * D + d0 + c] : 0.f;
+            }
+            for (int t = tid; t < BF_CB * BF_DC; t += BF_THREADS) {
+                int r = t / BF_DC, c = t - r * BF_DC;
+                int64_t j = c0 + r;
+                Cs[r * (BF_DC + 1) + c] = (j < N && d0 + c < D) ? X[j * D + d0 + c] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int c = 0; c < BF_DC; ++c) {
+                float qv = Qs[qi * (BF_DC + 1) + c];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    float diff = qv - Cs[(cg + 8 * m) * (BF_DC + 1) + c];
+                    acc[m] = fmaf(diff, diff, acc[m]);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) Dt[qi * (BF_CB + 1) + cg + 8 * m] = acc[m];
+        __syncthreads();
+
+        // Fold the tile into the per-query lists; warp w owns queries 4w..4w+3.
+        for (int r = warp * 4; r < warp * 4 + 4; ++r) {
+            const int q = qid[r];
+            if (q < 0) continue;
+            float md = thr_d[r];
+            int mj = thr_j[r], mp = thr_p[r];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                const int64_t j = c0 + c;
+                const bool valid = j < N && j != q;
+                const float cd = valid ? Dt[r * (BF_CB + 1) + c] : INFINITY;
+                const int cj = valid ? (int)j : INT_MAX;
+                unsigned ball = __ballot_sync(0xffffffffu, pair_less(cd, cj, md, mj));
+                while (ball) {
+                    const int src = __ffs(ball) - 1;
+                    ball &= ball - 1;
+                    const float d = __shfl_sync(0xffffffffu, cd, src);
+                    const int jj = __shfl_sync(0xffffffffu, cj, src);
+                    if (!pair_less(d, jj, md, mj)) continue;
+                    if (lane == 0) {
+                        td[r * KCAP + mp] = d;
+                        tj[r * KCAP + mp] = jj;
+                    }
+                    __syncwarp();
+                    float bd = -INFINITY;
+                    int bj = INT_MIN, bp = 0;
+                    for (int s = lane; s < k; s += 32) {
+                        float sd = td[r * KCAP + s];
+                        int sj = tj[r * KCAP + s];
+                        if (pair_less(bd, bj, sd, sj)) {
+                            bd = sd;
+                            bj = sj;
+                            bp = s;
+                        }
+                    }
+                    warp_argmax_pair(bd, bj, bp);
+                    md = bd;
+                    mj = bj;
+                    mp = bp;
+                }
+            }
+            if (lane == 0) {
+                thr_d[r] = md;
+                thr_j[r] = mj;
+                thr_p[r] = mp;
+            }
+        }
+        __syncthreads();
+    }
+
+    for (int r = warp * 4; r < warp * 4 + 4; ++r) {
+        const int64_t s = q0 + r;
+        if (s >= nq) continue;
+        warp_bitonic_sort_smem(td + r * KCAP, tj + r * KCAP, KCAP, lane);
+        for (int t = lane; t < k; t += 32) {
+            idx_out[s * k + t] = tj[r * KCAP + t];
+            d2_out[s * k + t] = td[r * KCAP + t];
+        }
+    }
+}
+
+template <int KCAP>
+atsne_status launch_bf(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq, int k,
+                       int32_t *idx_out, float *d2_out, cudaStream_t stream) {
+    const size_t smem = sizeof(float) * (BF_QB * (BF_DC + 1) + BF_CB * (BF_DC + 1) +
+                                         BF_QB * (BF_CB + 1) + BF_QB * KCAP) +
+                        sizeof(int) * BF_QB * KCAP;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(knn_bruteforce_kernel<KCAP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "knn_bruteforce attribute");
+        attr_set = true;
+    }
+    const int grid = ceil_div(nq, BF_QB);
+    ProfScope prof("knn_bruteforce", stream);
+    knn_bruteforce_kernel<KCAP><<<grid, BF_THREADS, smem, stream>>>(X, N, D, qlist, nq, k, idx_out,
+                                                                     d2_out);
+    ATSNE_LAUNCH_CHECK("knn_bruteforce launch");
+    return ATSNE_OK;
+}
+
+}  // namespace
+
+atsne_status knn_bruteforce(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq,
+                            int k, int32_t *idx_out, float *d2_out, cudaStream_t stream) {
+    if (nq <= 0) return ATSNE_OK;
+    if (k <= 128) return launch_bf<128>(X, N, D, qlist, nq, k, idx_out, d2_out, stream);
+    if (k <= 256) return launch_bf<256>(X, N, D, qlist, nq, k, idx_out, d2_out, stream);
+    if (k <= 512) return launch_bf<512>(X, N, D, qlist, nq, k, idx_out, d2_out, stream);
+    return set_error(ATSNE_EUNSUPPORTED, "knn: k=%d above the supported maximum of 512", k);
+}
+
+}  // namespace atsne

@@ -1,0 +1,87 @@
+"""The C ABI library loads and exports every symbol include/atsne.h declares;
+host-side argument validation (no device work) behaves as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1512_01655_gb300 as at
+    return at
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "atsne.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(atsne_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = declared_symbols()
+    assert "atsne_knn" in syms and "atsne_refine_subset" in syms
+    lib = ctypes.CDLL(L.LIB_PATH)
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+    assert sorted(L.EXPORTED) == syms
+
+
+def test_defaults_and_workspace_sizes(L):
+    o = L.knn_opts()
+    assert (o.method, o.trees, o.top_var_dims, o.leaf_size) == (L.KNN_EXACT, 4, 5, 1)
+    assert L.workspace_bytes(L.OP_CALIBRATE, 1000, 64, 90) == 0
+    sym = L.workspace_bytes(L.OP_SYMMETRIZE, 70000, 784, 90)
+    assert sym >= 70000 * 90 * 8
+    fo = L.knn_opts(method="forest", checks=256)
+    fb = L.workspace_bytes(L.OP_KNN, 70000, 784, 90, 0, fo)
+    assert fb > 70000 * 4 * 4
+
+
+def test_forest_layout_matches_depth_rule(L, oracle_mod):
+    for N, leaf in [(2000, 1), (70000, 8), (3, 1)]:
+        lay = L.ForestLayout()
+        o = L.knn_opts(method="forest", leaf_size=leaf, trees=3)
+        assert L.lib().atsne_forest_layout(N, 16, ctypes.byref(o), ctypes.byref(lay)) == 0
+        assert lay.depth == oracle_mod.forest_depth(N, leaf)
+        assert lay.n_internal == (1 << lay.depth) - 1
+        assert lay.off_perm % 256 == 0 and lay.bytes >= lay.off_leaf_ofs + 4 * ((1 << lay.depth) + 1)
+
+
+@pytest.mark.parametrize("N,D,k", [(1, 4, 1), (10, 0, 3), (10, 4, 10), (10, 4, 0)])
+def test_bad_sizes_rejected_on_host(L, N, D, k):
+    lib = L.lib()
+    fake = ctypes.c_void_p(256)  # never dereferenced: validation fails first
+    rc = lib.atsne_knn(fake, N, D, None, 0, k, None, fake, fake, None, 0, None)
+    assert rc == L.ATSNE_EINVAL
+    assert lib.atsne_last_error()
+
+
+def test_calibrate_rejects_bad_perplexity(L):
+    lib = L.lib()
+    fake = ctypes.c_void_p(256)
+    assert lib.atsne_calibrate_P(fake, 10, 9, 9.5, 0.0, 0, fake, None, None) == L.ATSNE_EINVAL
+    assert lib.atsne_calibrate_P(fake, 10, 9, 0.0, 0.0, 0, fake, None, None) == L.ATSNE_EINVAL
+    assert b"perplexity" in lib.atsne_last_error()
+
+
+def test_forest_option_validation(L):
+    lib = L.lib()
+    fake = ctypes.c_void_p(256)
+    for bad in [dict(trees=0), dict(top_var_dims=9), dict(checks=0), dict(leaf_size=0),
+                dict(queue_cap=1)]:
+        o = L.knn_opts(method="forest", **bad)
+        rc = lib.atsne_knn(fake, 100, 4, None, 0, 5, ctypes.byref(o), fake, fake, None, 0, None)
+        assert rc == L.ATSNE_EINVAL, bad
+
+
+def test_workspace_too_small_is_enomem(L):
+    lib = L.lib()
+    fake = ctypes.c_void_p(256)
+    rc = lib.atsne_symmetrize(fake, fake, 100, 5, fake, fake, fake, None, fake, 16, None)
+    assert rc == L.ATSNE_ENOMEM
