@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark of the A-tSNE similarity path (tSNE's P matrix) on one GB300.
+
+One step = one pass of the whole hot path over the MNIST-shaped synthetic
+workload (N=70000, D=784, integer values in [0, 255], ~80% zeros; perplexity
+30, k = 90):
+  exact P:        exact kNN -> beta bisection -> symmetrised CSR P  (Eq. 8, 3-4, 2)
+  approximate P:  KD-forest build (T=4, V=5) -> forest kNN (checks) -> beta
+                  bisection -> CSR P^A                              (Sec. 4.2)
+  precision:      rho of P^A's neighbourhoods against the exact ones (Eq. 9)
+  refinement:     exact refinement of a brushed selection of P^A's rows, then
+                  the CSR rebuild of Eq. 10                          (Sec. 4.3)
+value = N points / step time (whole job: N points per rank, summed over ranks).
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+method the library is checked against) on the host cores, on a bounded sample
+of the same workload extrapolated to points/s.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_NN, PERPLEXITY = 90, 30.0
+
+WORKLOADS = {
+    "mnist70k": dict(N=70000, D=784, seed=2, kind="sparse_prototypes",
+                     desc="70000x784 fp32, integer values in [0,255], ~80% zeros, 10 sparse "
+                          "prototypes + noise (MNIST-shaped)"),
+    "mnist20k": dict(N=20000, D=784, seed=2, kind="sparse_prototypes",
+                     desc="20000x784 fp32, MNIST-shaped sparse prototypes (profiling case)"),
+    "gauss2k": dict(N=2000, D=64, seed=1, kind="gaussian_mixture",
+                    desc="2000x64 fp32, 10 isotropic Gaussians (sigma 1, centres N(0,5^2))"),
+}
+
+
+def make_data(w):
+    from paper_1512_01655_gb300 import synth
+    if w["kind"] == "sparse_prototypes":
+        X, labels = synth.sparse_prototypes(N=w["N"], D=w["D"], seed=w["seed"], return_labels=True)
+    else:
+        X, labels = synth.gaussian_mixture(w["N"], w["D"], seed=w["seed"], return_labels=True)
+    return X, labels
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="mnist70k")
+    p.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    p.add_argument("--trees", type=int, default=4)
+    p.add_argument("--checks", type=int, default=1024)
+    p.add_argument("--refine", type=int, default=2000, help="points in the refined selection")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=256)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (torchrun: one rank per GPU; replicas of the workload)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    elif args.impl == "ours":
+        torch.cuda.set_device(0)
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v, device=None):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu),
+                                          "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+class Pipeline:
+    """Buffers and the step of the whole path, all through the C ABI binding."""
+
+    def __init__(self, at, X, labels, args, dev):
+        import torch
+        self.at, self.X, self.args = at, X, args
+        N, D = X.shape
+        self.N, self.D = N, D
+        from paper_1512_01655_gb300 import synth
+        sel = synth.refine_subsets(labels, 1, lo=args.refine, hi=args.refine, seed=4)[0]
+        self.subset = torch.from_numpy(sel).to(dev)
+        self.exact_opts = at.knn_opts(method="exact", precision=args.precision)
+        self.forest_opts = at.knn_opts(method="forest", trees=args.trees, checks=args.checks,
+                                       leaf_size=1, seed=7)
+
+    def step(self):
+        at, X = self.at, self.X
+        # exact P
+        idx_e, d2_e = at.atsne_knn(X, K_NN, opts=self.exact_opts)
+        P_e, _ = at.atsne_calibrate_P(d2_e, PERPLEXITY)
+        csr_e = at.atsne_symmetrize(idx_e, P_e, trim=False)
+        # approximate P^A
+        forest = at.atsne_forest_build(X, opts=self.forest_opts)
+        idx_a, d2_a, _ = at.atsne_forest_query(X, forest, K_NN)
+        P_a, beta_a = at.atsne_calibrate_P(d2_a, PERPLEXITY)
+        # precision of the approximate neighbourhoods
+        rho_i, _ = self._precision(idx_a, idx_e)
+        # refinement of a selection, then the CSR rebuild
+        at.atsne_refine_subset(X, self.subset, PERPLEXITY, idx_a, d2_a, P_a, beta_a, rho_i)
+        csr_a = at.atsne_symmetrize(idx_a, P_a, trim=False)
+        return csr_e, csr_a, rho_i
+
+    def _precision(self, a, e):
+        import torch
+        import ctypes
+        at = self.at
+        rows = a.shape[0]
+        rho_i = torch.empty(rows, dtype=torch.float32, device=a.device)
+        s = torch.empty(1, dtype=torch.float64, device=a.device)
+        at._raise(at.lib().atsne_knn_precision(at._p(a), at._p(e), rows, K_NN, at._p(rho_i),
+                                               at._p(s), at._stream()))
+        return rho_i, s
+
+
+def algorithmic_flops_knn(N, D):
+    return 2.0 * N * N * D
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    import paper_1512_01655_gb300 as at
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    Xh, labels = make_data(w)
+    X = torch.from_numpy(Xh).to(dev)
+    N, D = Xh.shape
+    pipe = Pipeline(at, X, labels, args, dev)
+    stream = torch.cuda.current_stream()
+    l2_flush = None
+    if Xh.nbytes < 256 * 2**20:
+        l2_flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        pipe.step()
+    torch.cuda.synchronize()
+    at.atsne_check()
+
+    # timed region: K steps, events per step on the launching stream, L2 flushed
+    # between steps when the input alone does not exceed L2
+    at.profile_enable(True)
+    at.profile_reset()
+    launches0 = at.launch_count()
+    clocks = ClockSampler(local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        if l2_flush is not None:
+            l2_flush.fill_(1)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        out = pipe.step()
+        ev1.record(stream)
+        times.append((ev0, ev1))
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    launches = at.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in times]
+    total_ms = sum(step_ms)
+    per_kernel = {}
+    for name in ["knn_bruteforce", "knn_tc", "knn_tc_merge", "calibrate_beta", "forest_query",
+                 "forest_choose", "forest_partial", "forest_sort_smem", "forest_sort_global",
+                 "sym_scatter", "sym_count", "sym_sort_rows", "sym_sort_tails", "knn_prep"]:
+        n, ms = at.profile_read(name)
+        if n:
+            per_kernel[name] = {"launches": n, "ms": ms}
+    at.profile_enable(False)
+    csr_e, csr_a, rho_i = out
+    rho = float(rho_i.double().mean().item())
+    nnz = int(csr_e[3].item())
+    at.atsne_check()
+
+    total_ms = max_over_ranks(pg, total_ms, dev)
+    value = world * N * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel
+    dom = max(per_kernel.items(), key=lambda kv: kv[1]["ms"])[0] if per_kernel else None
+    roofline = None
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    if dom in ("knn_bruteforce",):
+        # FP32 CUDA-core kernel: 3 flops (sub, fma) per pair and dimension.
+        sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        per_launch_flops = 3.0 * N * N * D
+        avg_ms = per_kernel[dom]["ms"] / per_kernel[dom]["launches"]
+        ach = per_launch_flops / (avg_ms / 1e3) / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 2),
+                    "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                    "traffic": None,
+                    "peak_source": "FP32 FMA rate: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+    elif dom == "knn_tc":
+        mult = 3.0 if args.precision == "fp32" else 1.0
+        peak = peaks.get("bf16_tflops", 1900.0)
+        per_launch_flops = algorithmic_flops_knn(N, D)
+        avg_ms = per_kernel[dom]["ms"] / per_kernel[dom]["launches"]
+        ach = per_launch_flops / (avg_ms / 1e3) / 1e12
+        roofline = {"kernel": dom, "bound": "tensor", "achieved": round(ach, 1),
+                    "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                    "traffic": None, "tensor_passes": mult,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
+    elif dom is not None:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": None,
+                    "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s", "frac": None,
+                    "traffic": None}
+
+    # end to end through the public API with host buffers: H2D of X from pinned
+    # memory, the step, D2H of both CSR matrices (trimmed to nnz) and rho
+    e2e = None
+    if args.e2e_steps > 0:
+        Xpin = torch.from_numpy(Xh).pin_memory()
+        e2e_ms, h2d, d2h = [], 0, 0
+        for it in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pipe.X = Xpin.to(dev, non_blocking=True)
+            csr_e, csr_a, rho_i = pipe.step()
+            host = []
+            for rp, col, val, nz in (csr_e, csr_a):
+                n_ = int(nz.item())
+                host += [rp.cpu(), col[:n_].cpu(), val[:n_].cpu()]
+            host.append(rho_i.cpu())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if it > 0:
+                e2e_ms.append((t1 - t0) * 1e3)
+                h2d = Xpin.numel() * 4
+                d2h = sum(t.numel() * t.element_size() for t in host)
+        pipe.X = X
+        e2e_total = max_over_ranks(pg, sum(e2e_ms), dev)
+        e2e = {"value": round(world * N * len(e2e_ms) / (e2e_total / 1e3), 1),
+               "unit": "points/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, Xh, labels)
+
+    if rank == 0:
+        line = {
+            "metric": "P-matrix points/s at k=90 (exact FP32 kNN + beta bisection + CSR P, "
+                      "KD-forest P^A, rho, refinement)",
+            "value": round(value, 1), "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "data": "synthetic (seeded, MNIST-shaped; no dataset)",
+            "config": {"workload": w["desc"], "N": N, "D": D, "k": K_NN,
+                       "perplexity": PERPLEXITY, "exact_precision": args.precision,
+                       "forest": {"trees": args.trees, "top_var_dims": 5, "checks": args.checks,
+                                  "leaf_size": 1},
+                       "refine_points": int(pipe.subset.numel()),
+                       "l2": "input larger than L2" if l2_flush is None else "L2 flushed between steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "rho": round(rho, 5), "nnz_exact_P": nnz,
+            "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
+            "step_ms": [round(t, 3) for t in step_ms],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample_timing(Xh, sample_rows, args):
+    """Time the oracle's work for the whole path on a sample of query rows and
+    extrapolate to all N rows: per-row costs (exact kNN, bisection, forest
+    search, refinement) scale with the rows; the forest build and the CSR
+    symmetrisation are timed once at full size on oracle-made inputs."""
+    import oracle
+    from paper_1512_01655_gb300 import synth
+    N = Xh.shape[0]
+    q = synth.sample_rows(N, sample_rows, seed=17)
+    t = {}
+    t0 = time.perf_counter()
+    idx_e, d2_e = oracle.knn_exact(Xh, K_NN, queries=q)
+    t["knn_exact"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.calibrate(d2_e, PERPLEXITY)
+    t["calibrate"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    f = oracle.forest_build(Xh, trees=args.trees, top_var_dims=5, leaf_size=1, seed=7)
+    t["forest_build_full"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.forest_query(Xh, f, K_NN, args.checks, queries=q)
+    t["forest_query"] = time.perf_counter() - t0
+    # symmetrisation at full size on a random valid kNN graph of the same shape
+    rng = np.random.default_rng(3)
+    g_idx = (np.arange(N)[:, None] + rng.integers(1, N, size=(N, K_NN))) % N
+    g_idx = g_idx.astype(np.int32)
+    g_P = np.full((N, K_NN), 1.0 / K_NN)
+    t0 = time.perf_counter()
+    oracle.symmetrize(g_idx, g_P)
+    t["symmetrize_full"] = time.perf_counter() - t0
+    per_row = (2 * t["calibrate"] + t["knn_exact"] + t["forest_query"]) / len(q)
+    refine_rows = args.refine
+    est = (per_row * N + t["knn_exact"] / len(q) * refine_rows + t["forest_build_full"]
+           + 2 * t["symmetrize_full"])
+    return N / est, t, len(q)
+
+
+def cpu_baseline(args, Xh, labels):
+    import oracle
+    value, t, n = oracle_sample_timing(Xh, args.cpu_sample, args)
+    return {"value": round(value, 3), "unit": "points/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": ("exact kNN, 2x beta bisection and forest search (T=%d, checks=%d) for %d "
+                       "sampled query rows against the full corpus, extrapolated linearly to all "
+                       "rows; forest build and 2x CSR symmetrisation timed once at full size"
+                       % (args.trees, args.checks, n)),
+            "seconds": {k_: round(v, 3) for k_, v in t.items()}}
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    import oracle
+    w = WORKLOADS[args.workload]
+    Xh, labels = make_data(w)
+    sample = max(16, args.cpu_sample // 4)
+    vals = []
+    for it in range(args.warmup + args.steps):
+        v, t, n = oracle_sample_timing(Xh, sample, args)
+        if it >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "metric": "P-matrix points/s at k=90 (exact FP32 kNN + beta bisection + CSR P, "
+                  "KD-forest P^A, rho, refinement)",
+        "value": round(value, 3), "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded, MNIST-shaped; no dataset)",
+        "config": {"workload": w["desc"], "N": w["N"], "D": w["D"], "k": K_NN,
+                   "perplexity": PERPLEXITY},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 3), "unit": "points/s", "kind": "oracle",
+                         "cores": oracle.num_threads(),
+                         "sample": "%d sampled query rows per step, per-row work extrapolated; "
+                                   "forest build and symmetrisation at full size" % sample},
+        "e2e": {"value": round(value, 3), "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

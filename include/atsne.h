@@ -186,6 +186,10 @@ atsne_status atsne_check(void *stream);
 /* Message of the last error on this thread ("" if none). */
 const char *atsne_last_error(void);
 
+/* Number of kernel launches this library has enqueued since it was loaded
+ * (all threads, all devices). */
+int64_t atsne_launch_count(void);
+
 /*
  * Per-kernel timing: while enabled, every kernel launch is bracketed by CUDA
  * events recorded on the launching stream. atsne_profile_read() synchronises

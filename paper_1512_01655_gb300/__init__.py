@@ -22,7 +22,7 @@ EXPORTED = (
     "atsne_knn_opts_default", "atsne_workspace_bytes", "atsne_knn", "atsne_calibrate_P",
     "atsne_symmetrize", "atsne_refine_subset", "atsne_knn_precision", "atsne_forest_layout",
     "atsne_forest_build", "atsne_forest_query", "atsne_check", "atsne_last_error",
-    "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read",
+    "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
 )
 
 
@@ -80,6 +80,8 @@ def lib():
         L.atsne_check.argtypes = [_vp]
         L.atsne_last_error.restype = ctypes.c_char_p
         L.atsne_last_error.argtypes = []
+        L.atsne_launch_count.restype = ctypes.c_int64
+        L.atsne_launch_count.argtypes = []
         L.atsne_profile_enable.argtypes = [_i32]
         L.atsne_profile_reset.argtypes = []
         L.atsne_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_i64),
@@ -87,7 +89,7 @@ def lib():
         for name in EXPORTED:
             f = getattr(L, name)
             if name not in ("atsne_knn_opts_default", "atsne_workspace_bytes",
-                            "atsne_last_error"):
+                            "atsne_last_error", "atsne_launch_count"):
                 f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -269,6 +271,11 @@ def atsne_forest_query(X, forest, k, checks=None, queries=None, queue_cap=None, 
 def atsne_check(stream=None):
     """Synchronise and raise if a kernel flagged bad input or an expired wait."""
     _raise(lib().atsne_check(_stream(stream)))
+
+
+def launch_count():
+    """Kernel launches enqueued by the library since it was loaded."""
+    return int(lib().atsne_launch_count())
 
 
 def profile_enable(on=True):

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -65,6 +66,9 @@ size_t g_prof_used = 0;
 constexpr size_t PROF_POOL = 8192;
 }  // namespace
 
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 ProfScope::ProfScope(const char *kernel, cudaStream_t s) : slot(-1), stream(s) {
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -106,24 +110,20 @@ __global__ void check_indices_kernel(const int32_t *__restrict__ list, int64_t n
 }
 
 atsne_status check_finite(const float *X, int64_t n, cudaStream_t stream) {
-    ProfScope prof("check_finite", stream);
     const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     const int64_t n4 = aligned ? n / 4 : 0;
     const int64_t done = n4 * 4;
     const int grid = (int)hmin(4 * num_sms(), ceil_div(n4 > 0 ? n4 : 1, 256));
-    check_finite_kernel<<<grid, 256, 0, stream>>>(reinterpret_cast<const float4 *>(X), n4, X + done,
-                                                  n - done, device_status_word());
-    ATSNE_LAUNCH_CHECK("check_finite launch");
-    return ATSNE_OK;
+    return launch_kernel("check_finite", check_finite_kernel, grid, 256, 0, stream,
+                         reinterpret_cast<const float4 *>(X), n4, X + done, n - done,
+                         device_status_word());
 }
 
 atsne_status check_indices(const int32_t *list, int64_t n, int64_t N, cudaStream_t stream) {
     if (n <= 0) return ATSNE_OK;
-    ProfScope prof("check_indices", stream);
     const int grid = (int)hmin(2 * num_sms(), ceil_div(n, 256));
-    check_indices_kernel<<<grid, 256, 0, stream>>>(list, n, N, device_status_word());
-    ATSNE_LAUNCH_CHECK("check_indices launch");
-    return ATSNE_OK;
+    return launch_kernel("check_indices", check_indices_kernel, grid, 256, 0, stream, list, n, N,
+                         device_status_word());
 }
 
 atsne_knn_opts opts_or_default(const atsne_knn_opts *o) {
@@ -227,6 +227,8 @@ void atsne_knn_opts_default(atsne_knn_opts *o) {
 }
 
 const char *atsne_last_error(void) { return g_err; }
+
+int64_t atsne_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_t S,
                              const atsne_knn_opts *opts) {

@@ -98,11 +98,9 @@ atsne_status calibrate_launch(const float *d2, int64_t rows, int k, float perple
         if (e != cudaSuccess) return cuda_error(e, "calibrate attribute");
         attr = smem;
     }
-    ProfScope prof("calibrate_beta", stream);
-    calibrate_kernel<<<ceil_div(rows, CAL_THREADS), CAL_THREADS, smem, stream>>>(
-        d2, rows, k, logf(perplexity), tol, max_iter, P, beta, device_status_word());
-    ATSNE_LAUNCH_CHECK("calibrate launch");
-    return ATSNE_OK;
+    return launch_kernel("calibrate_beta", calibrate_kernel, ceil_div(rows, CAL_THREADS),
+                         CAL_THREADS, smem, stream, d2, rows, k, logf(perplexity), tol, max_iter, P,
+                         beta, device_status_word());
 }
 
 }  // namespace atsne

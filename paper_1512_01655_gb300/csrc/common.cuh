@@ -43,6 +43,27 @@ struct ProfScope {
     ~ProfScope();
 };
 
+void count_launch();  // one kernel launch enqueued by this library
+
+// Launch `kern` on `stream`, bracketed by profiling events and counted.
+template <typename... KArgs, typename... Args>
+atsne_status launch_kernel(const char *name, void (*kern)(KArgs...), dim3 grid, dim3 block,
+                           size_t smem, cudaStream_t stream, Args &&...args) {
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return ATSNE_OK;
+    ProfScope prof(name, stream);
+    kern<<<grid, block, smem, stream>>>(static_cast<KArgs>(args)...);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, name);
+    return ATSNE_OK;
+}
+
+#define ATSNE_TRY(expr)                                                       \
+    do {                                                                      \
+        atsne_status st_ = (expr);                                            \
+        if (st_ != ATSNE_OK) return st_;                                      \
+    } while (0)
+
 #define ATSNE_LAUNCH_CHECK(what)                                              \
     do {                                                                      \
         cudaError_t e_ = cudaGetLastError();                                  \

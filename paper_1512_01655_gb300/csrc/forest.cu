@@ -626,12 +626,10 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
     forest_build_workspace(c, f.N, f.D, f.trees, f.leaf_size, &w);
     if (c.bytes() > ws_bytes) return set_error(ATSNE_ENOMEM, "forest build: workspace too small");
     const int h = f.depth, T = f.trees;
-    {
-        ProfScope prof("forest_init", stream);
-        leaf_ofs_kernel<<<ceil_div(((int64_t)1 << h) + 1, 256), 256, 0, stream>>>(f.N, h, f.leaf_ofs);
-        iota_kernel<<<ceil_div(f.N * T, 256), 256, 0, stream>>>(f.perm, f.N, T);
-        ATSNE_LAUNCH_CHECK("forest init launch");
-    }
+    ATSNE_TRY(launch_kernel("forest_leaf_ofs", leaf_ofs_kernel, ceil_div(((int64_t)1 << h) + 1, 256),
+                            256, 0, stream, f.N, h, f.leaf_ofs));
+    ATSNE_TRY(launch_kernel("forest_iota", iota_kernel, ceil_div(f.N * T, 256), 256, 0, stream, f.perm,
+                            f.N, T));
     const size_t choose_smem = sizeof(float2) * (size_t)f.D;
     if (choose_smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(choose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -642,51 +640,37 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
         const int64_t nodes = (int64_t)1 << l;
         const int64_t nmax = (f.N + nodes - 1) >> l;
         const int chunks = ceil_div(nmax, CHUNK);
-        const int threads = f.D >= CHOOSE_THREADS ? CHOOSE_THREADS : ((f.D + 31) / 32) * 32;
-        if (chunks > 1) {
-            ProfScope prof("forest_partial", stream);
-            partial_kernel<<<dim3(chunks, (unsigned)nodes, T), threads, 0, stream>>>(
-                X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks, w.part);
-            ATSNE_LAUNCH_CHECK("forest partial launch");
-        }
-        {
-            ProfScope prof("forest_choose", stream);
-            choose_kernel<<<dim3((unsigned)nodes, T), threads < 32 ? 32 : threads, choose_smem, stream>>>(
-                X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks, w.part, f.top_var_dims, f.seed,
-                f.split_dim, f.split_val, f.n_internal);
-            ATSNE_LAUNCH_CHECK("forest choose launch");
-        }
+        int threads = f.D >= CHOOSE_THREADS ? CHOOSE_THREADS : ((f.D + 31) / 32) * 32;
+        if (threads < 32) threads = 32;
+        if (chunks > 1)
+            ATSNE_TRY(launch_kernel("forest_partial", partial_kernel, dim3(chunks, (unsigned)nodes, T),
+                                    threads, 0, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
+                                    w.part));
+        ATSNE_TRY(launch_kernel("forest_choose", choose_kernel, dim3((unsigned)nodes, T), threads,
+                                choose_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
+                                w.part, f.top_var_dims, f.seed, f.split_dim, f.split_val,
+                                f.n_internal));
         const int64_t P = pow2_at_least(nmax);
         const int64_t total = nodes * P * T;
-        {
-            ProfScope prof("forest_keys", stream);
-            keys_kernel<<<ceil_div(total, 256), 256, 0, stream>>>(X, f.D, f.perm, f.N, f.leaf_ofs, h,
-                                                                  l, P, f.split_dim, f.n_internal,
-                                                                  T, w.keys);
-            ATSNE_LAUNCH_CHECK("forest keys launch");
+        ATSNE_TRY(launch_kernel("forest_keys", keys_kernel, ceil_div(total, 256), 256, 0, stream, X,
+                                f.D, f.perm, f.N, f.leaf_ofs, h, l, P, f.split_dim, f.n_internal, T,
+                                w.keys));
+        const int blocks = ceil_div(total, SMEM_SORT);
+        ATSNE_TRY(launch_kernel("forest_sort_smem", sort_smem_kernel, blocks, 1024, 0, stream, w.keys,
+                                total, (int)(P < SMEM_SORT ? P : SMEM_SORT), 0));
+        for (int64_t size = 2 * SMEM_SORT; size <= P; size <<= 1) {
+            ATSNE_TRY(launch_kernel("forest_sort_global", sort_global_kernel, ceil_div(total / 2, 256),
+                                    256, 0, stream, w.keys, total, size, (int64_t)0, 1));
+            for (int64_t stride = size >> 2; stride >= SMEM_SORT; stride >>= 1)
+                ATSNE_TRY(launch_kernel("forest_sort_global", sort_global_kernel,
+                                        ceil_div(total / 2, 256), 256, 0, stream, w.keys, total, size,
+                                        stride, 0));
+            ATSNE_TRY(launch_kernel("forest_sort_smem", sort_smem_kernel, blocks, 1024, 0, stream,
+                                    w.keys, total, (int)SMEM_SORT, 1));
         }
-        {
-            ProfScope prof("forest_sort", stream);
-            const int blocks = ceil_div(total, SMEM_SORT);
-            sort_smem_kernel<<<blocks, 1024, 0, stream>>>(w.keys, total,
-                                                          (int)(P < SMEM_SORT ? P : SMEM_SORT), 0);
-            for (int64_t size = 2 * SMEM_SORT; size <= P; size <<= 1) {
-                sort_global_kernel<<<ceil_div(total / 2, 256), 256, 0, stream>>>(w.keys, total,
-                                                                               size, 0, 1);
-                for (int64_t stride = size >> 2; stride >= SMEM_SORT; stride >>= 1)
-                    sort_global_kernel<<<ceil_div(total / 2, 256), 256, 0, stream>>>(
-                        w.keys, total, size, stride, 0);
-                sort_smem_kernel<<<blocks, 1024, 0, stream>>>(w.keys, total, SMEM_SORT, 1);
-            }
-            ATSNE_LAUNCH_CHECK("forest sort launch");
-        }
-        {
-            ProfScope prof("forest_scatter", stream);
-            scatter_kernel<<<ceil_div(total, 256), 256, 0, stream>>>(
-                X, f.D, f.perm, f.N, f.leaf_ofs, h, l, P, f.split_dim, f.split_val, f.n_internal, T,
-                w.keys);
-            ATSNE_LAUNCH_CHECK("forest scatter launch");
-        }
+        ATSNE_TRY(launch_kernel("forest_scatter", scatter_kernel, ceil_div(total, 256), 256, 0, stream,
+                                X, f.D, f.perm, f.N, f.leaf_ofs, h, l, P, f.split_dim, f.split_val,
+                                f.n_internal, T, w.keys));
     }
     return ATSNE_OK;
 }
@@ -747,10 +731,7 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     a.d2_out = d2_out;
     a.evaluated_out = evaluated_out;
     const int grid = (int)hmin(FQ_SLOTS / FQ_WARPS, ceil_div(nq, FQ_WARPS));
-    ProfScope prof("forest_query", stream);
-    forest_query_kernel<<<grid, FQ_WARPS * 32, smem, stream>>>(a);
-    ATSNE_LAUNCH_CHECK("forest query launch");
-    return ATSNE_OK;
+    return launch_kernel("forest_query", forest_query_kernel, grid, FQ_WARPS * 32, smem, stream, a);
 }
 
 }  // namespace atsne

@@ -163,11 +163,8 @@ atsne_status launch_bf(const float *X, int64_t N, int D, const int32_t *qlist, i
         attr_set = true;
     }
     const int grid = ceil_div(nq, BF_QB);
-    ProfScope prof("knn_bruteforce", stream);
-    knn_bruteforce_kernel<KCAP><<<grid, BF_THREADS, smem, stream>>>(X, N, D, qlist, nq, k, idx_out,
-                                                                     d2_out);
-    ATSNE_LAUNCH_CHECK("knn_bruteforce launch");
-    return ATSNE_OK;
+    return launch_kernel("knn_bruteforce", knn_bruteforce_kernel<KCAP>, grid, BF_THREADS, smem,
+                         stream, X, N, D, qlist, nq, k, idx_out, d2_out);
 }
 
 }  // namespace

@@ -72,16 +72,12 @@ atsne_status precision_launch(const int32_t *a, const int32_t *e, int64_t rows, 
         cudaError_t err = cudaMemsetAsync(rho_sum, 0, sizeof(double), stream);
         if (err != cudaSuccess) return cuda_error(err, "precision memset");
     }
-    if (rows > 0) {
-        ProfScope prof("knn_precision", stream);
-        precision_kernel<<<ceil_div(rows, 4), 128, sizeof(int) * 4 * k, stream>>>(a, e, rows, k,
-                                                                                 rho_i, rho_sum);
-        ATSNE_LAUNCH_CHECK("precision launch");
-    }
-    if (rho_sum) {
-        scale_kernel<<<1, 1, 0, stream>>>(rho_sum, 1.0 / (double)k);
-        ATSNE_LAUNCH_CHECK("precision scale launch");
-    }
+    if (rows > 0)
+        ATSNE_TRY(launch_kernel("knn_precision", precision_kernel, ceil_div(rows, 4), 128,
+                                sizeof(int) * 4 * k, stream, a, e, rows, k, rho_i, rho_sum));
+    if (rho_sum)
+        ATSNE_TRY(launch_kernel("knn_precision_scale", scale_kernel, 1, 1, 0, stream, rho_sum,
+                                1.0 / (double)k));
     return ATSNE_OK;
 }
 
@@ -90,11 +86,8 @@ atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, 
                                    float *d2, float *P, float *beta, float *rho,
                                    cudaStream_t stream) {
     if (S <= 0) return ATSNE_OK;
-    ProfScope prof("refine_scatter", stream);
-    refine_scatter_kernel<<<ceil_div(S * k, 256), 256, 0, stream>>>(subset, S, N, k, ti, td, tp, tb,
-                                                                   idx, d2, P, beta, rho);
-    ATSNE_LAUNCH_CHECK("refine scatter launch");
-    return ATSNE_OK;
+    return launch_kernel("refine_scatter", refine_scatter_kernel, ceil_div(S * k, 256), 256, 0,
+                         stream, subset, S, N, k, ti, td, tp, tb, idx, d2, P, beta, rho);
 }
 
 }  // namespace atsne

@@ -96,12 +96,11 @@ size_t scan_partials_count(int64_t n) { return (size_t)ceil_div(n > 0 ? n : 1, S
 atsne_status scan_rowlen(const int32_t *rev, int64_t n, int add, int64_t *out, int64_t *total,
                          int64_t *part, cudaStream_t stream) {
     const int64_t np = (int64_t)scan_partials_count(n);
-    ProfScope prof("scan_rowlen", stream);
-    scan_reduce_kernel<<<(int)np, SCAN_THREADS, 0, stream>>>(rev, n, add, part);
-    scan_partials_kernel<<<1, 1024, 0, stream>>>(part, np);
-    scan_down_kernel<<<(int)np, SCAN_THREADS, 0, stream>>>(rev, n, add, part, out, total);
-    ATSNE_LAUNCH_CHECK("scan launch");
-    return ATSNE_OK;
+    ATSNE_TRY(launch_kernel("scan_reduce", scan_reduce_kernel, (int)np, SCAN_THREADS, 0, stream,
+                            rev, n, add, part));
+    ATSNE_TRY(launch_kernel("scan_partials", scan_partials_kernel, 1, 1024, 0, stream, part, np));
+    return launch_kernel("scan_down", scan_down_kernel, (int)np, SCAN_THREADS, 0, stream, rev, n,
+                         add, part, out, total);
 }
 
 }  // namespace atsne

@@ -206,42 +206,29 @@ atsne_status symmetrize_launch(const int32_t *idx, const float *P, int64_t N, in
     if (e == cudaSuccess) e = cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * N, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.n_long, 0, sizeof(int32_t), stream);
     if (e != cudaSuccess) return cuda_error(e, "symmetrize memset");
-    {
-        ProfScope prof("sym_sort_rows", stream);
-        const int grid = ceil_div(N, 4);
-        if (k <= 128) sym_sort_rows_kernel<128><<<grid, 128, 0, stream>>>(idx, P, N, k, w.scol, w.sval, status);
-        else if (k <= 256) sym_sort_rows_kernel<256><<<grid, 128, 0, stream>>>(idx, P, N, k, w.scol, w.sval, status);
-        else if (k <= 512) sym_sort_rows_kernel<512><<<grid, 128, 0, stream>>>(idx, P, N, k, w.scol, w.sval, status);
-        else return set_error(ATSNE_EUNSUPPORTED, "symmetrize: k=%d above 512", k);
-        ATSNE_LAUNCH_CHECK("sym_sort_rows launch");
-    }
+    const int grid4 = ceil_div(N, 4);
+    if (k <= 128)
+        ATSNE_TRY(launch_kernel("sym_sort_rows", sym_sort_rows_kernel<128>, grid4, 128, 0, stream,
+                                idx, P, N, k, w.scol, w.sval, status));
+    else if (k <= 256)
+        ATSNE_TRY(launch_kernel("sym_sort_rows", sym_sort_rows_kernel<256>, grid4, 128, 0, stream,
+                                idx, P, N, k, w.scol, w.sval, status));
+    else if (k <= 512)
+        ATSNE_TRY(launch_kernel("sym_sort_rows", sym_sort_rows_kernel<512>, grid4, 128, 0, stream,
+                                idx, P, N, k, w.scol, w.sval, status));
+    else
+        return set_error(ATSNE_EUNSUPPORTED, "symmetrize: k=%d above 512", k);
     const int64_t M = N * k;
-    {
-        ProfScope prof("sym_count", stream);
-        sym_count_kernel<<<ceil_div(M, 256), 256, 0, stream>>>(w.scol, N, k, w.rev);
-        ATSNE_LAUNCH_CHECK("sym_count launch");
-    }
-    atsne_status st = scan_rowlen(w.rev, N, k, row_ptr, nnz_dev, w.scan, stream);
-    if (st != ATSNE_OK) return st;
-    {
-        ProfScope prof("sym_scatter", stream);
-        sym_scatter_kernel<<<ceil_div(M, 256), 256, 0, stream>>>(w.scol, w.sval, N, k,
-                                                                 (float)(0.5 / (double)N), row_ptr,
-                                                                 w.cursor, col, val);
-        ATSNE_LAUNCH_CHECK("sym_scatter launch");
-    }
-    {
-        ProfScope prof("sym_sort_tails", stream);
-        sym_sort_tails_kernel<<<ceil_div(N, 4), 128, 0, stream>>>(row_ptr, w.rev, N, col, val,
-                                                                  w.long_rows, w.n_long);
-        ATSNE_LAUNCH_CHECK("sym_sort_tails launch");
-    }
-    {
-        ProfScope prof("sym_sort_long", stream);
-        sym_sort_long_kernel<<<2 * num_sms(), 1024, 0, stream>>>(row_ptr, w.long_rows, w.n_long,
-                                                                 col, val);
-        ATSNE_LAUNCH_CHECK("sym_sort_long launch");
-    }
+    ATSNE_TRY(launch_kernel("sym_count", sym_count_kernel, ceil_div(M, 256), 256, 0, stream, w.scol,
+                            N, k, w.rev));
+    ATSNE_TRY(scan_rowlen(w.rev, N, k, row_ptr, nnz_dev, w.scan, stream));
+    ATSNE_TRY(launch_kernel("sym_scatter", sym_scatter_kernel, ceil_div(M, 256), 256, 0, stream,
+                            w.scol, w.sval, N, k, (float)(0.5 / (double)N), row_ptr, w.cursor, col,
+                            val));
+    ATSNE_TRY(launch_kernel("sym_sort_tails", sym_sort_tails_kernel, grid4, 128, 0, stream, row_ptr,
+                            w.rev, N, col, val, w.long_rows, w.n_long));
+    ATSNE_TRY(launch_kernel("sym_sort_long", sym_sort_long_kernel, 2 * num_sms(), 1024, 0, stream,
+                            row_ptr, w.long_rows, w.n_long, col, val));
     return ATSNE_OK;
 }
 
