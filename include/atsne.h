@@ -143,6 +143,28 @@ atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int
                                  size_t ws_bytes, void *stream);
 
 /*
+ * Refinement without device allocation. The paper has no counterpart: this is
+ * atsne_refine_subset for callers that cannot allocate device memory when they
+ * refine (inside an open CUDA stream capture, where cudaMalloc is not allowed;
+ * in a render or UI callback that must not wait on an allocator; under a fixed
+ * device-memory budget). Instead of a workspace it uses one fixed device array
+ * inside the library (3 MiB + 8 KiB, held on every GPU that loads the library
+ * until the process exits), so it accepts at most
+ * ATSNE_REFINE_NOALLOC_MAX_ROWS selected rows and k <= ATSNE_REFINE_NOALLOC_MAX_K;
+ * larger requests return ATSNE_ENOMEM with a message. Arguments, outputs and
+ * results are those of atsne_refine_subset. The first call on a device looks up
+ * the array's address (cudaGetSymbolAddress); make it before any stream
+ * capture. All calls share the array: calls whose work may overlap on the GPU
+ * race and must be ordered (one stream, or events).
+ */
+#define ATSNE_REFINE_NOALLOC_MAX_ROWS 2048
+#define ATSNE_REFINE_NOALLOC_MAX_K 128
+atsne_status atsne_refine_subset_noalloc(const float *X, int64_t N, int32_t D,
+                                         const int32_t *subset, int64_t S, int32_t k,
+                                         float perplexity, int32_t *idx, float *d2, float *P_cond,
+                                         float *beta, float *rho, void *stream);
+
+/*
  * Precision of approximate neighbourhoods, Eq. 9 (Sec. 4.1):
  * rho_i = |N^A_i intersect N_i| / k. rho_i_out [rows] fp32; rho_sum_dev: device
  * double receiving sum_i rho_i (divide by rows for rho); either may be NULL.

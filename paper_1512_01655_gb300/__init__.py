@@ -23,7 +23,9 @@ EXPORTED = (
     "atsne_symmetrize", "atsne_refine_subset", "atsne_knn_precision", "atsne_forest_layout",
     "atsne_forest_build", "atsne_forest_query", "atsne_check", "atsne_last_error",
     "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
+    "atsne_refine_subset_noalloc",
 )
+REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
 
 class AtsneError(RuntimeError):
@@ -70,6 +72,8 @@ def lib():
         L.atsne_symmetrize.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.atsne_refine_subset.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _vp, _vp,
                                           _vp, _vp, _vp, _sz, _vp]
+        L.atsne_refine_subset_noalloc.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp,
+                                                  _vp, _vp, _vp, _vp, _vp]
         L.atsne_knn_precision.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
                                           ctypes.POINTER(ForestLayout)]
@@ -197,6 +201,20 @@ def atsne_refine_subset(X, subset, perplexity, idx, d2, P_cond, beta=None, rho=N
     _raise(lib().atsne_refine_subset(_p(X), N, D, _p(subset), S, k, perplexity, _p(idx), _p(d2),
                                      _p(P_cond), _p(beta), _p(rho), _p(ws), ws.numel(),
                                      _stream(stream)))
+
+
+def atsne_refine_subset_noalloc(X, subset, perplexity, idx, d2, P_cond, beta=None, rho=None,
+                                stream=None):
+    """Refinement as atsne_refine_subset, for callers that cannot allocate: the
+    library's fixed device scratch replaces the workspace (at most
+    REFINE_NOALLOC_MAX_ROWS rows, k <= REFINE_NOALLOC_MAX_K). This wrapper
+    allocates nothing either."""
+    _dev(X, torch.float32, "X")
+    _dev(subset, torch.int32, "subset")
+    N, D = X.shape
+    _raise(lib().atsne_refine_subset_noalloc(_p(X), N, D, _p(subset), subset.shape[0],
+                                             idx.shape[1], perplexity, _p(idx), _p(d2), _p(P_cond),
+                                             _p(beta), _p(rho), _stream(stream)))
 
 
 def atsne_knn_precision(idx_approx, idx_exact, stream=None):

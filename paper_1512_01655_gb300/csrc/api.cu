@@ -109,6 +109,8 @@ __global__ void check_indices_kernel(const int32_t *__restrict__ list, int64_t n
     if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, DEV_MALFORMED);
 }
 
+}  // namespace
+
 atsne_status check_finite(const float *X, int64_t n, cudaStream_t stream) {
     const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     const int64_t n4 = aligned ? n / 4 : 0;
@@ -125,6 +127,8 @@ atsne_status check_indices(const int32_t *list, int64_t n, int64_t N, cudaStream
     return launch_kernel("check_indices", check_indices_kernel, grid, 256, 0, stream, list, n, N,
                          device_status_word());
 }
+
+namespace {
 
 atsne_knn_opts opts_or_default(const atsne_knn_opts *o) {
     atsne_knn_opts d;

@@ -9,6 +9,10 @@
 
 namespace atsne {
 
+// ---- input checks (device side; they raise the status word) -----------------
+atsne_status check_finite(const float *X, int64_t n, cudaStream_t stream);
+atsne_status check_indices(const int32_t *list, int64_t n, int64_t N, cudaStream_t stream);
+
 // ---- exact kNN ------------------------------------------------------------
 atsne_status knn_bruteforce(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq,
                             int k, int32_t *idx_out, float *d2_out, cudaStream_t stream);
