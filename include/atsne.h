@@ -42,11 +42,14 @@ typedef enum {
 
 typedef enum { ATSNE_KNN_EXACT = 0, ATSNE_KNN_FOREST = 1 } atsne_knn_method;
 
-/* Arithmetic of the exact path's distance contraction (Eq. 8 needs only the
- * order of distances; every variant ends with an FP32 direct-difference rerank). */
+/* Arithmetic of the exact path's distance contraction. Every variant returns the
+ * exact kNN under FP32 direct-difference distances: the tensor-core variants
+ * re-rank their candidates in FP32 and certify each row (rows that cannot be
+ * certified are recomputed on the CUDA cores). */
 typedef enum {
-    ATSNE_FP32 = 0,        /* FP32-accurate: exact top-k by FP32 distances */
-    ATSNE_BF16_RERANK = 1  /* BF16 candidates, FP32 rerank of the best rerank_k */
+    ATSNE_FP32 = 0,            /* tensor cores, 3 BF16 passes (hi.hi + hi.lo + lo.hi) */
+    ATSNE_BF16_RERANK = 1,     /* tensor cores, 1 BF16 pass, rerank_k candidates per row */
+    ATSNE_FP32_CUDA_CORES = 2  /* FP32 direct differences on the CUDA cores */
 } atsne_precision;
 
 /* Operation codes for atsne_workspace_bytes(). */
@@ -68,7 +71,8 @@ typedef struct {
     int32_t checks;        /* forest: budget of evaluated points ("leaves" L, Sec. 4.2) */
     int32_t leaf_size;     /* forest: maximum points per leaf, default 1 */
     int32_t queue_cap;     /* forest: capacity of the per-query priority queue, default 1024 */
-    int32_t rerank_k;      /* exact BF16 path: candidates per row kept for rerank (0 = 4k) */
+    int32_t rerank_k;      /* exact tensor path: candidates kept per row and column split
+                              (0 = k + 38 for FP32, 2k for BF16) */
     uint64_t seed;         /* forest: seed of the counter-based split choice */
 } atsne_knn_opts;
 

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libatsne.so")
 
 ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPPORTED = range(6)
 KNN_EXACT, KNN_FOREST = 0, 1
-FP32, BF16_RERANK = 0, 1
+FP32, BF16_RERANK, FP32_CUDA_CORES = 0, 1, 2
 OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY = range(6)
 
 EXPORTED = (
@@ -126,8 +126,8 @@ def knn_opts(method="exact", precision="fp32", trees=4, top_var_dims=5, checks=1
     o = KnnOpts()
     lib().atsne_knn_opts_default(ctypes.byref(o))
     o.method = {"exact": KNN_EXACT, "forest": KNN_FOREST}[method] if isinstance(method, str) else method
-    o.precision = {"fp32": FP32, "bf16": BF16_RERANK}[precision] if isinstance(precision, str) \
-        else precision
+    o.precision = {"fp32": FP32, "bf16": BF16_RERANK, "fp32_cuda": FP32_CUDA_CORES}[precision] \
+        if isinstance(precision, str) else precision
     o.trees, o.top_var_dims, o.checks, o.leaf_size = trees, top_var_dims, checks, leaf_size
     o.queue_cap, o.rerank_k, o.seed = queue_cap, rerank_k, seed
     return o

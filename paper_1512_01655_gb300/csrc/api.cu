@@ -139,7 +139,8 @@ atsne_knn_opts opts_or_default(const atsne_knn_opts *o) {
 atsne_status validate_knn_opts(const atsne_knn_opts &o) {
     if (o.method != ATSNE_KNN_EXACT && o.method != ATSNE_KNN_FOREST)
         return set_error(ATSNE_EINVAL, "knn: unknown method %d", o.method);
-    if (o.precision != ATSNE_FP32 && o.precision != ATSNE_BF16_RERANK)
+    if (o.precision != ATSNE_FP32 && o.precision != ATSNE_BF16_RERANK &&
+        o.precision != ATSNE_FP32_CUDA_CORES)
         return set_error(ATSNE_EINVAL, "knn: unknown precision %d", o.precision);
     if (o.method == ATSNE_KNN_FOREST) {
         if (o.trees < 1 || o.trees > 64) return set_error(ATSNE_EINVAL, "forest: trees=%d not in [1,64]", o.trees);
@@ -180,9 +181,20 @@ ForestView forest_view(void *forest, int64_t N, int32_t D, const atsne_knn_opts 
     return f;
 }
 
+bool exact_on_tensor_cores(const atsne_knn_opts &o, int32_t k) {
+    return o.method == ATSNE_KNN_EXACT && o.precision != ATSNE_FP32_CUDA_CORES && k <= 200;
+}
+
 // Workspace layouts (sizing and carving share these).
 size_t knn_ws(Carver &c, int64_t N, int32_t D, int32_t k, int64_t S, const atsne_knn_opts &o,
-              void **forest, void **sub_ws, size_t *sub_bytes) {
+              void **forest, void **sub_ws, size_t *sub_bytes, TcPlan *plan = nullptr,
+              TcWs *tws = nullptr) {
+    if (exact_on_tensor_cores(o, k)) {
+        const int64_t Q = S > 0 ? S : N;
+        const TcPlan pl = tc_plan(N, D, Q, k, o.precision, o.rerank_k);
+        if (plan) *plan = pl;
+        tc_workspace(c, N, D, Q, S > 0, pl, tws);
+    }
     if (o.method == ATSNE_KNN_FOREST) {
         const size_t fb = forest_layout(N, o.trees, o.leaf_size, nullptr);
         char *f = c.take<char>(fb);
@@ -271,11 +283,15 @@ atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *quer
     Carver c(workspace);
     void *forest = nullptr, *sub = nullptr;
     size_t sub_bytes = 0;
-    knn_ws(c, N, D, k, queries ? S : 0, o, &forest, &sub, &sub_bytes);
+    TcPlan plan;
+    TcWs tws;
+    knn_ws(c, N, D, k, queries ? S : 0, o, &forest, &sub, &sub_bytes, &plan, &tws);
     if (c.bytes() > 0 && (!workspace || ws_bytes < c.bytes()))
         return set_error(ATSNE_ENOMEM, "knn: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
-    if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
     if (queries && (st = check_indices(queries, S, N, stream))) return st;
+    if (exact_on_tensor_cores(o, k))  // the prep kernel checks X for non-finite values
+        return knn_exact_tc(X, N, D, queries, nq, k, plan, tws, idx_out, d2_out, stream);
+    if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
     if (o.method == ATSNE_KNN_EXACT)
         return knn_bruteforce(X, N, D, queries, nq, k, idx_out, d2_out, stream);
     ForestView f = forest_view(forest, N, D, o);

@@ -16,6 +16,27 @@ atsne_status check_indices(const int32_t *list, int64_t n, int64_t N, cudaStream
 // ---- exact kNN ------------------------------------------------------------
 atsne_status knn_bruteforce(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq,
                             int k, int32_t *idx_out, float *d2_out, cudaStream_t stream);
+// The rows listed in rows_list[0 .. *rows_count) (device count, at most nq).
+atsne_status knn_bruteforce_rows(const float *X, int64_t N, int D, const int32_t *qlist,
+                                 const int32_t *rows_list, const int32_t *rows_count, int64_t nq,
+                                 int k, int32_t *idx_out, float *d2_out, cudaStream_t stream);
+
+// Tensor-core exact kNN: plan (tile split, candidate capacity) and workspace.
+struct TcPlan {
+    int passes = 1, Dp = 0, row_tiles = 0, splits = 1, cols_per_split = 0, ksel = 0, cap = 0;
+};
+struct TcWs {
+    uint16_t *hi = nullptr, *lo = nullptr, *qhi = nullptr, *qlo = nullptr;
+    float *nrm = nullptr, *stats = nullptr;
+    unsigned *gmax = nullptr;
+    char *cand = nullptr, *meta = nullptr;
+    int32_t *flag_rows = nullptr, *flag_count = nullptr;
+};
+TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k);
+size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcPlan &pl, TcWs *ws);
+atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist, int64_t Q, int k,
+                          const TcPlan &pl, const TcWs &w, int32_t *idx_out, float *d2_out,
+                          cudaStream_t stream);
 
 // ---- calibrate ------------------------------------------------------------
 size_t calibrate_smem_bytes(int k);

@@ -23,11 +23,15 @@ constexpr int BF_CB = 64;       // corpus points per tile
 constexpr int BF_DC = 32;       // dimensions per slice
 constexpr int BF_THREADS = 256;
 
+// Work item s (0 <= s < nq, or < *rows_count when rows_list is given) is output
+// row r = rows_list ? rows_list[s] : s, whose query point is qlist ? qlist[r] : r.
+// CTAs stride over blocks of 32 work items.
 template <int KCAP>
 __global__ void __launch_bounds__(BF_THREADS)
 knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
-                      const int32_t *__restrict__ qlist, int64_t nq, int k,
-                      int32_t *__restrict__ idx_out, float *__restrict__ d2_out) {
+                      const int32_t *__restrict__ qlist, int64_t nq,
+                      const int32_t *__restrict__ rows_list, const int32_t *__restrict__ rows_count,
+                      int k, int32_t *__restrict__ idx_out, float *__restrict__ d2_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *Qs = reinterpret_cast<float *>(smem_raw);      // [QB][DC+1]
     float *Cs = Qs + BF_QB * (BF_DC + 1);                 // [CB][DC+1]
@@ -35,16 +39,24 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
     float *td = Dt + BF_QB * (BF_CB + 1);                 // [QB][KCAP]
     int *tj = reinterpret_cast<int *>(td + BF_QB * KCAP); // [QB][KCAP]
     __shared__ int qid[BF_QB];
+    __shared__ int64_t orow[BF_QB];
     __shared__ float thr_d[BF_QB];
     __shared__ int thr_j[BF_QB];
     __shared__ int thr_p[BF_QB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t q0 = (int64_t)blockIdx.x * BF_QB;
+    const int64_t n_items = rows_count ? (int64_t)*rows_count : nq;
+    for (int64_t q0 = (int64_t)blockIdx.x * BF_QB; q0 < n_items; q0 += (int64_t)gridDim.x * BF_QB) {
     if (tid < BF_QB) {
-        int64_t s = q0 + tid;
-        int q = s < nq ? (qlist ? qlist[s] : (int)s) : -1;
+        const int64_t s = q0 + tid;
+        int64_t r = -1;
+        int q = -1;
+        if (s < n_items) {
+            r = rows_list ? rows_list[s] : s;
+            q = qlist ? qlist[r] : (int)r;
+        }
         qid[tid] = (q >= 0 && q < N) ? q : -1;  // out-of-range queries are flagged by the caller
+        orow[tid] = r;
         thr_d[tid] = INFINITY;
         thr_j[tid] = INT_MAX;
         thr_p[tid] = 0;
@@ -139,18 +151,21 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
     }
 
     for (int r = warp * 4; r < warp * 4 + 4; ++r) {
-        const int64_t s = q0 + r;
-        if (s >= nq) continue;
+        const int64_t o = orow[r];
+        if (o < 0) continue;
         warp_bitonic_sort_smem(td + r * KCAP, tj + r * KCAP, KCAP, lane);
         for (int t = lane; t < k; t += 32) {
-            idx_out[s * k + t] = tj[r * KCAP + t];
-            d2_out[s * k + t] = td[r * KCAP + t];
+            idx_out[o * k + t] = tj[r * KCAP + t];
+            d2_out[o * k + t] = td[r * KCAP + t];
         }
+    }
+    __syncthreads();
     }
 }
 
 template <int KCAP>
-atsne_status launch_bf(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq, int k,
+atsne_status launch_bf(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq,
+                       const int32_t *rows_list, const int32_t *rows_count, int k,
                        int32_t *idx_out, float *d2_out, cudaStream_t stream) {
     const size_t smem = sizeof(float) * (BF_QB * (BF_DC + 1) + BF_CB * (BF_DC + 1) +
                                          BF_QB * (BF_CB + 1) + BF_QB * KCAP) +
@@ -162,19 +177,26 @@ atsne_status launch_bf(const float *X, int64_t N, int D, const int32_t *qlist, i
         if (e != cudaSuccess) return cuda_error(e, "knn_bruteforce attribute");
         attr_set = true;
     }
-    const int grid = ceil_div(nq, BF_QB);
-    return launch_kernel("knn_bruteforce", knn_bruteforce_kernel<KCAP>, grid, BF_THREADS, smem,
-                         stream, X, N, D, qlist, nq, k, idx_out, d2_out);
+    const int grid = rows_count ? (int)hmin(2 * num_sms(), ceil_div(nq, BF_QB)) : ceil_div(nq, BF_QB);
+    return launch_kernel(rows_count ? "knn_fallback" : "knn_bruteforce", knn_bruteforce_kernel<KCAP>,
+                         grid, BF_THREADS, smem, stream, X, N, D, qlist, nq, rows_list, rows_count,
+                         k, idx_out, d2_out);
 }
 
 }  // namespace
 
 atsne_status knn_bruteforce(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq,
                             int k, int32_t *idx_out, float *d2_out, cudaStream_t stream) {
+    return knn_bruteforce_rows(X, N, D, qlist, nullptr, nullptr, nq, k, idx_out, d2_out, stream);
+}
+
+atsne_status knn_bruteforce_rows(const float *X, int64_t N, int D, const int32_t *qlist,
+                                 const int32_t *rows_list, const int32_t *rows_count, int64_t nq,
+                                 int k, int32_t *idx_out, float *d2_out, cudaStream_t stream) {
     if (nq <= 0) return ATSNE_OK;
-    if (k <= 128) return launch_bf<128>(X, N, D, qlist, nq, k, idx_out, d2_out, stream);
-    if (k <= 256) return launch_bf<256>(X, N, D, qlist, nq, k, idx_out, d2_out, stream);
-    if (k <= 512) return launch_bf<512>(X, N, D, qlist, nq, k, idx_out, d2_out, stream);
+    if (k <= 128) return launch_bf<128>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream);
+    if (k <= 256) return launch_bf<256>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream);
+    if (k <= 512) return launch_bf<512>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream);
     return set_error(ATSNE_EUNSUPPORTED, "knn: k=%d above the supported maximum of 512", k);
 }
 

@@ -1,0 +1,819 @@
+// Exact kNN (Eq. 8, Sec. 3.1) on the tcgen05 tensor cores.
+//
+// Distances are ranked by key_j = ||x_j||^2 - 2 x_i.x_j (||x_i||^2 is common to
+// a query row). The contraction x_i.x_j runs on the tensor cores in BF16 with
+// FP32 accumulation in TMEM: one pass (x ~ hi) for the BF16 mode, three passes
+// (x ~ hi + lo; hi.hi' + hi.lo' + lo.hi') for the FP32 mode. The N x N key
+// matrix never leaves the SM:
+//
+//   knn_prep   x -> hi (+ lo) BF16 copies padded to Dp = 64*ceil(D/64), the
+//              FP32 norm ||x||^2, and the norms of what the BF16 copies miss
+//              (used to bound the key error).
+//   knn_tc     persistent, warp-specialised: warp 0 issues TMA loads of
+//              128-query x 64 and 256-point x 64 BF16 tiles (128-byte swizzle)
+//              into a shared-memory ring; warp 1 issues tcgen05.mma
+//              (M=128, N=256, K=16) into one of two TMEM accumulators; warps
+//              2-5 read the other accumulator back (tcgen05.ld, one query row
+//              per thread), form the keys, and append every key below the
+//              row's running threshold tau to a per-(row, column split)
+//              candidate buffer. When a buffer reaches 2*ksel entries the warp
+//              selects its ksel-th smallest key (radix select), makes it the
+//              new tau and compacts the buffer to the ksel best, so a buffer
+//              never exceeds 2*ksel + 256 entries.
+//   knn_merge  one warp per query: the k-th smallest key over all splits,
+//              every candidate within 2E of it (E bounds the key error, see
+//              row_error_bound) re-ranked by FP32 direct differences, and a
+//              certificate: if the k-th exact distance is below
+//              ||x_i||^2 + min(tau) - E, no point outside the buffers can
+//              belong to the k nearest, and the row is exact. Rows that fail
+//              are listed for the brute-force kernel.
+//
+// Every wait on an mbarrier is bounded (1 s); on expiry the CTA raises the
+// device status word, stops issuing work, drains its own copies and MMAs and
+// releases TMEM before it exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <float.h>
+#include <limits.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace atsne {
+namespace {
+
+using namespace tc;
+
+constexpr int TC_BM = 128;       // query rows per tile (TMEM lanes)
+constexpr int TC_BN = 256;       // corpus points per tile (TMEM columns per accumulator)
+constexpr int TC_BK = 64;        // BF16 per k-block (one 128-byte swizzle row)
+constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int TC_EPI = 128;
+constexpr uint64_t WAIT_NS = 1000000000ull;
+constexpr int MERGE_WARPS = 4;
+constexpr int RCAP = 256;        // candidates re-ranked per row at most
+
+struct Cand {
+    float key;
+    int32_t idx;
+};
+
+template <int PASSES>
+struct TcCfg {
+    static constexpr int STAGES = PASSES == 1 ? 4 : 2;
+    static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+    static constexpr int B_BYTES = TC_BN * TC_BK * 2;
+    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (PASSES == 1 ? 1 : 2);
+};
+
+template <int PASSES>
+struct __align__(1024) TcSmem {
+    unsigned char stage[TcCfg<PASSES>::STAGES][TcCfg<PASSES>::STAGE_BYTES];
+    float ny[4][TC_BN];  // per epilogue warp: the tile's corpus norms
+    uint32_t hist[4][256];
+    uint64_t full[TcCfg<PASSES>::STAGES];
+    uint64_t empty[TcCfg<PASSES>::STAGES];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+    int zero;
+};
+
+struct TcParams {
+    CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;
+    const float *nrm;      // [N] corpus ||x||^2
+    const int32_t *qlist;  // query row -> corpus index (nullptr: identity)
+    int64_t Q, N;
+    int KB;                // Dp / 64
+    int splits, cols_per_split, row_tiles;
+    int ksel, cap;
+    Cand *cand;            // [Q][splits][cap]
+    int4 *meta;            // [Q][splits]: count, tau bits, overflow
+    int *status;
+};
+
+__device__ __forceinline__ float key_of_bits(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Radix select over (key) of `count` candidates fetched by get(i): returns the
+// order-preserving bits of the kth smallest key (1-based) and, in n_less, how
+// many keys are strictly smaller. Warp-cooperative; hist is 256 words of
+// shared memory private to the warp.
+template <typename Get>
+__device__ uint32_t warp_select(Get get, int count, int kth, uint32_t *hist, int lane, int &n_less) {
+    uint32_t prefix = 0, mask = 0;
+    int rem = kth;
+    n_less = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = lane; i < 256; i += 32) hist[i] = 0u;
+        __syncwarp();
+        for (int i = lane; i < count; i += 32) {
+            const uint32_t u = float_key(get(i));
+            if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            c[q] = hist[8 * lane + q];
+            sum += c[q];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t excl = incl - sum;
+        const bool mine = excl < (uint32_t)rem && (uint32_t)rem <= incl;
+        const unsigned who = __ballot_sync(0xffffffffu, mine);
+        const int src = who ? __ffs(who) - 1 : 31;
+        int bin = 255;
+        uint32_t before = 0;
+        if (lane == src) {
+            uint32_t acc = excl;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (acc + c[q] >= (uint32_t)rem) {
+                    bin = 8 * lane + q;
+                    before = acc;
+                    break;
+                }
+                acc += c[q];
+            }
+        }
+        bin = __shfl_sync(0xffffffffu, bin, src);
+        before = __shfl_sync(0xffffffffu, before, src);
+        rem -= (int)before;
+        n_less += (int)before;
+        prefix |= (uint32_t)bin << shift;
+        mask |= 255u << shift;
+        __syncwarp();
+    }
+    return prefix;
+}
+
+// ---------------------------------------------------------------------------
+// prep: BF16 hi/lo copies, norms, error norms
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+knn_prep_kernel(const float *__restrict__ X, const int32_t *__restrict__ rows, int64_t nrows, int64_t N,
+                int D, int Dp, int passes, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+                float *__restrict__ nrm, float4 *__restrict__ stats, unsigned *__restrict__ gmax,
+                int *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= nrows) return;
+    int64_t src = rows ? rows[r] : r;
+    if (src < 0 || src >= N) src = 0;  // flagged by the caller's index check
+    const float *x = X + src * D;
+    float n = 0.f, res = 0.f, l2 = 0.f;
+    bool finite = true;
+    for (int d = lane; d < Dp; d += 32) {
+        const float v = d < D ? x[d] : 0.f;
+        finite &= isfinite(v);
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(h);
+        hi[r * Dp + d] = h;
+        n = fmaf(v, v, n);
+        if (passes == 3) {
+            const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+            const float lf = __bfloat162float(l);
+            const float r2 = r1 - lf;
+            lo[r * Dp + d] = l;
+            res = fmaf(r2, r2, res);
+            l2 = fmaf(lf, lf, l2);
+        } else {
+            res = fmaf(r1, r1, res);
+        }
+    }
+    n = warp_sum(n);
+    res = warp_sum(res);
+    l2 = warp_sum(l2);
+    if (!__all_sync(0xffffffffu, finite) && lane == 0) raise_status(status, DEV_NONFINITE);
+    if (lane == 0 && nrm) {
+        nrm[r] = n;
+        const float a = sqrtf(n), e = sqrtf(res), l = sqrtf(l2);
+        stats[r] = make_float4(a, e, l, 0.f);
+        atomicMax(&gmax[0], __float_as_uint(a));
+        atomicMax(&gmax[1], __float_as_uint(e));
+        atomicMax(&gmax[2], __float_as_uint(l));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the fused contraction + filter kernel
+// ---------------------------------------------------------------------------
+template <int PASSES>
+__global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_constant__ TcParams p) {
+    using C = TcCfg<PASSES>;
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    const uint32_t pad = (1024u - (smem_u32(tc_raw) & 1023u)) & 1023u;
+    TcSmem<PASSES> &s = *reinterpret_cast<TcSmem<PASSES> *>(tc_raw + pad);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < C::STAGES; ++i) {
+            mbar_init(&s.full[i], 1);
+            mbar_init(&s.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&s.acc_full[i], 1);
+            mbar_init(&s.acc_empty[i], TC_EPI);
+        }
+        mbar_init(&s.drain, 1);
+        s.abort_flag = 0;
+        s.zero = 0;
+        fence_mbar_init();
+    }
+    if (threadIdx.x == 32) {
+        tma_prefetch_desc(&p.tm_a_hi);
+        tma_prefetch_desc(&p.tm_b_hi);
+        if (PASSES == 3) {
+            tma_prefetch_desc(&p.tm_a_lo);
+            tma_prefetch_desc(&p.tm_b_lo);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tmem_alloc(&s.tmem_base, 512);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = s.tmem_base;
+    const int n_units = p.row_tiles * p.splits;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            uint32_t armed_phase[C::STAGES];
+            bool armed[C::STAGES];
+            for (int i = 0; i < C::STAGES; ++i) armed[i] = false;
+            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                const int rt = u / p.splits, sp = u % p.splits;
+                const int64_t c0 = (int64_t)sp * p.cols_per_split;
+                const int64_t c1 = min(p.N, c0 + p.cols_per_split);
+                for (int64_t ct = c0; ct < c1 && ok; ct += TC_BN) {
+                    for (int kb = 0; kb < p.KB; ++kb) {
+                        if (!mbar_wait(&s.empty[stage], phase ^ 1u, &s.abort_flag, WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        unsigned char *st = s.stage[stage];
+                        mbar_arrive_expect_tx(&s.full[stage], C::STAGE_BYTES);
+                        armed[stage] = true;
+                        armed_phase[stage] = phase;
+                        tma_load_2d(st, &p.tm_a_hi, kb * TC_BK, rt * TC_BM, &s.full[stage]);
+                        tma_load_2d(st + C::A_BYTES, &p.tm_b_hi, kb * TC_BK, (int)ct, &s.full[stage]);
+                        if (PASSES == 3) {
+                            tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.tm_a_lo, kb * TC_BK,
+                                        rt * TC_BM, &s.full[stage]);
+                            tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &p.tm_b_lo, kb * TC_BK,
+                                        (int)ct, &s.full[stage]);
+                        }
+                        if (++stage == C::STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                s.abort_flag = 1;
+                raise_status(p.status, DEV_TIMEOUT);
+                // let the copies already issued land before the CTA exits
+                for (int i = 0; i < C::STAGES; ++i)
+                    if (armed[i]) mbar_wait(&s.full[i], armed_phase[i], &s.zero, WAIT_NS);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = idesc_bf16_f32(TC_BM, TC_BN);
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                const int sp = u % p.splits;
+                const int64_t c0 = (int64_t)sp * p.cols_per_split;
+                const int64_t c1 = min(p.N, c0 + p.cols_per_split);
+                for (int64_t ct = c0; ct < c1 && ok; ct += TC_BN) {
+                    if (!mbar_wait(&s.acc_empty[acc], acc_phase ^ 1u, &s.abort_flag, WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t d = tbase + (uint32_t)(acc * TC_BN);
+                    for (int kb = 0; kb < p.KB; ++kb) {
+                        if (!mbar_wait(&s.full[stage], phase, &s.abort_flag, WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after_sync();
+                        const uint32_t a_hi = smem_u32(s.stage[stage]);
+                        const uint32_t b_hi = a_hi + C::A_BYTES;
+                        const uint32_t a_lo = b_hi + C::B_BYTES;
+                        const uint32_t b_lo = a_lo + C::A_BYTES;
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k) {
+                            mma_bf16(d, sw128_kmajor_desc(a_hi + 32 * k), sw128_kmajor_desc(b_hi + 32 * k),
+                                     idesc, (kb | k) != 0);
+                            if (PASSES == 3) {
+                                mma_bf16(d, sw128_kmajor_desc(a_hi + 32 * k),
+                                         sw128_kmajor_desc(b_lo + 32 * k), idesc, 1u);
+                                mma_bf16(d, sw128_kmajor_desc(a_lo + 32 * k),
+                                         sw128_kmajor_desc(b_hi + 32 * k), idesc, 1u);
+                            }
+                        }
+                        mma_commit(&s.empty[stage]);
+                        if (++stage == C::STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(&s.acc_full[acc]);
+                    if (++acc == 2) {
+                        acc = 0;
+                        acc_phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                s.abort_flag = 1;
+                raise_status(p.status, DEV_TIMEOUT);
+            }
+            // all MMAs of this CTA complete before TMEM is released
+            mma_commit(&s.drain);
+            mbar_wait(&s.drain, 0, &s.zero, WAIT_NS);
+        }
+    } else {
+        // ---------------- epilogue: keys, filter, per-row candidate buffers ----------------
+        const int quarter = warp & 3;
+        float *ny = s.ny[warp - 2];
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        uint32_t *hist = s.hist[warp - 2];
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const int rt = u / p.splits, sp = u % p.splits;
+            const int64_t c0 = (int64_t)sp * p.cols_per_split;
+            const int64_t c1 = min(p.N, c0 + p.cols_per_split);
+            const int64_t row = (int64_t)rt * TC_BM + quarter * 32 + lane;
+            const bool qv = row < p.Q;
+            const int qid = qv ? (p.qlist ? p.qlist[row] : (int)row) : -1;
+            Cand *buf = qv ? p.cand + ((size_t)row * p.splits + sp) * p.cap : nullptr;
+            float tau = qv ? INFINITY : -INFINITY;
+            int cnt = 0;
+            for (int64_t ct = c0; ct < c1; ct += TC_BN) {
+                // this warp's copy of the tile's corpus norms (+inf past the split)
+                for (int t = lane; t < TC_BN; t += 32) {
+                    const int64_t c = ct + t;
+                    ny[t] = c < c1 ? p.nrm[c] : INFINITY;
+                }
+                __syncwarp();
+                ok = mbar_wait(&s.acc_full[acc], acc_phase, &s.abort_flag, WAIT_NS);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    if (lane == 0) {
+                        s.abort_flag = 1;
+                        raise_status(p.status, DEV_TIMEOUT);
+                    }
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t taddr = tbase + lane_base + (uint32_t)(acc * TC_BN);
+#pragma unroll 1
+                for (int c = 0; c < TC_BN / 32; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)(c * 32), r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = (int)ct + c * 32 + j;
+                        const float key = fmaf(-2.f, __uint_as_float(r[j]), ny[c * 32 + j]);
+                        if (key < tau && col != qid) {
+                            if (cnt < p.cap) buf[cnt] = Cand{key, col};
+                            ++cnt;
+                        }
+                    }
+                }
+                fence_before_sync();
+                __syncwarp();  // the norms of this tile are no longer read
+                mbar_arrive(&s.acc_empty[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1u;
+                }
+                // compact full buffers to their ksel best and tighten tau
+                unsigned m = __ballot_sync(0xffffffffu, cnt >= 2 * p.ksel && cnt <= p.cap);
+                if (m) __syncwarp();
+                while (m) {
+                    const int l = __ffs(m) - 1;
+                    m &= m - 1;
+                    Cand *b = reinterpret_cast<Cand *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(buf), l));
+                    const int n = __shfl_sync(0xffffffffu, cnt, l);
+                    int n_less = 0;
+                    const uint32_t tk = warp_select([&](int i) { return b[i].key; }, n, p.ksel, hist,
+                                                    lane, n_less);
+                    const int eq_quota = p.ksel - n_less;
+                    int wpos = 0, eq_seen = 0;
+                    for (int base = 0; base < n; base += 32) {
+                        const int i = base + lane;
+                        Cand e{INFINITY, -1};
+                        if (i < n) e = b[i];
+                        const uint32_t uk = float_key(e.key);
+                        const bool lt = i < n && uk < tk;
+                        const bool eq = i < n && uk == tk;
+                        const unsigned eqm = __ballot_sync(0xffffffffu, eq);
+                        const int eq_rank = eq_seen + __popc(eqm & lanemask_lt());
+                        const bool keep = lt || (eq && eq_rank < eq_quota);
+                        const unsigned km = __ballot_sync(0xffffffffu, keep);
+                        if (keep) b[wpos + __popc(km & lanemask_lt())] = e;
+                        wpos += __popc(km);
+                        eq_seen += __popc(eqm);
+                    }
+                    __syncwarp();
+                    if (lane == l) {
+                        cnt = wpos;
+                        tau = key_of_bits(tk);
+                    }
+                }
+            }
+            if (!ok) break;
+            if (qv)
+                p.meta[(size_t)row * p.splits + sp] =
+                    make_int4(cnt < p.cap ? cnt : p.cap, __float_as_int(tau), cnt > p.cap ? 1 : 0, 0);
+        }
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 1) tmem_dealloc(tbase, 512);
+}
+
+// ---------------------------------------------------------------------------
+// merge, FP32 rerank and certificate
+// ---------------------------------------------------------------------------
+struct MergeParams {
+    const Cand *cand;
+    const int4 *meta;
+    int splits, cap;
+    int64_t Q, N;
+    const int32_t *qlist;
+    const float *X;
+    int D, k;
+    const float *nrm;
+    const float4 *stats;
+    const unsigned *gmax;
+    float acc_coef;        // (passes * Dp / 16 + 8) * 2^-21
+    int32_t *idx_out;
+    float *d2_out;
+    int32_t *flag_rows;
+    int32_t *flag_count;
+};
+
+// Bound on |estimated - true| squared distance for query i and any point j:
+// the terms the BF16 copies drop (Cauchy-Schwarz on the residual norms), the
+// FP32 accumulation of the products, and the FP32 norms.
+__device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st) {
+    const float amax = __uint_as_float(p.gmax[0]);
+    const float rmax = __uint_as_float(p.gmax[1]);
+    const float lmax = __uint_as_float(p.gmax[2]);
+    const float a = st.x, r = st.y, l = st.z;
+    const float drop = l * lmax + r * amax + a * rmax;
+    return 2.f * drop + p.acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
+}
+
+__global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams p) {
+    __shared__ uint32_t hist_s[MERGE_WARPS][256];
+    __shared__ float rd[MERGE_WARPS][RCAP];
+    __shared__ int rj[MERGE_WARPS][RCAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * MERGE_WARPS + w;
+    if (row >= p.Q) return;
+    const int qid = p.qlist ? p.qlist[row] : (int)row;
+    const int S = p.splits;
+    const Cand *cb = p.cand + (size_t)row * S * p.cap;
+    const int4 *mt = p.meta + (size_t)row * S;
+
+    // totals over the splits
+    int total = 0, ovf = 0;
+    float tau_min = INFINITY;
+    for (int u = lane; u < S; u += 32) {
+        const int4 m = mt[u];
+        total += m.x;
+        ovf |= m.z;
+        tau_min = fminf(tau_min, __int_as_float(m.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        ovf |= __shfl_xor_sync(0xffffffffu, ovf, o);
+        tau_min = fminf(tau_min, __shfl_xor_sync(0xffffffffu, tau_min, o));
+    }
+    bool good = !ovf && total >= p.k && qid >= 0 && qid < p.N;
+    int nr = 0;
+    if (good) {
+        // k-th smallest key over all splits (splits hold their entries contiguously)
+        // k-th smallest key over all splits: radix select, splits walked in order
+        int n_less = 0;
+        uint32_t *hist = hist_s[w];
+        uint32_t prefix = 0, mask = 0;
+        int rem = p.k;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int i = lane; i < 256; i += 32) hist[i] = 0u;
+            __syncwarp();
+            for (int u = 0; u < S; ++u) {
+                const int c = mt[u].x;
+                const Cand *b = cb + (size_t)u * p.cap;
+                for (int i = lane; i < c; i += 32) {
+                    const uint32_t uk = float_key(b[i].key);
+                    if ((uk & mask) == prefix) atomicAdd(&hist[(uk >> shift) & 255u], 1u);
+                }
+            }
+            __syncwarp();
+            uint32_t cc[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                cc[q] = hist[8 * lane + q];
+                sum += cc[q];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t excl = incl - sum;
+            const unsigned who = __ballot_sync(0xffffffffu, excl < (uint32_t)rem && (uint32_t)rem <= incl);
+            const int src = who ? __ffs(who) - 1 : 31;
+            int bin = 255;
+            uint32_t before = 0;
+            if (lane == src) {
+                uint32_t a = excl;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (a + cc[q] >= (uint32_t)rem) {
+                        bin = 8 * lane + q;
+                        before = a;
+                        break;
+                    }
+                    a += cc[q];
+                }
+            }
+            bin = __shfl_sync(0xffffffffu, bin, src);
+            before = __shfl_sync(0xffffffffu, before, src);
+            rem -= (int)before;
+            n_less += (int)before;
+            prefix |= (uint32_t)bin << shift;
+            mask |= 255u << shift;
+            __syncwarp();
+        }
+        const float theta = key_of_bits(prefix);
+        const float E = row_error_bound(p, p.stats[qid]);
+        const float lim = theta + 2.f * E;
+        // collect the re-rank set
+        for (int u = 0; u < S && good; ++u) {
+            const int c = mt[u].x;
+            const Cand *b = cb + (size_t)u * p.cap;
+            for (int base = 0; base < c; base += 32) {
+                const int i = base + lane;
+                Cand e{INFINITY, -1};
+                if (i < c) e = b[i];
+                const bool take = i < c && e.key <= lim;
+                const unsigned tm = __ballot_sync(0xffffffffu, take);
+                const int pos = nr + __popc(tm & lanemask_lt());
+                if (take && pos < RCAP) rj[w][pos] = e.idx;
+                nr += __popc(tm);
+            }
+            if (nr > RCAP) good = false;
+        }
+        __syncwarp();
+        if (good && nr >= p.k) {
+            // exact FP32 direct-difference distances
+            const float *xq = p.X + (int64_t)qid * p.D;
+            for (int t = 0; t < nr; ++t) {
+                const float *xc = p.X + (int64_t)rj[w][t] * p.D;
+                float a = 0.f;
+                if ((p.D & 3) == 0) {
+                    const float4 *q4 = reinterpret_cast<const float4 *>(xq);
+                    const float4 *c4 = reinterpret_cast<const float4 *>(xc);
+                    for (int d = lane; d < (p.D >> 2); d += 32) {
+                        const float4 qv = q4[d], cv = c4[d];
+                        float df = qv.x - cv.x;
+                        a = fmaf(df, df, a);
+                        df = qv.y - cv.y;
+                        a = fmaf(df, df, a);
+                        df = qv.z - cv.z;
+                        a = fmaf(df, df, a);
+                        df = qv.w - cv.w;
+                        a = fmaf(df, df, a);
+                    }
+                } else {
+                    for (int d = lane; d < p.D; d += 32) {
+                        const float df = xq[d] - xc[d];
+                        a = fmaf(df, df, a);
+                    }
+                }
+                a = warp_sum(a);
+                if (lane == 0) rd[w][t] = a;
+            }
+            for (int t = nr + lane; t < RCAP; t += 32) {
+                rd[w][t] = INFINITY;
+                rj[w][t] = INT_MAX;
+            }
+            __syncwarp();
+            warp_bitonic_sort_smem(rd[w], rj[w], RCAP, lane);
+            const float dk = rd[w][p.k - 1];
+            const float nx = p.nrm[qid];
+            const float lb = nx + tau_min - E;
+            // certified: no point outside the buffers can be closer than dk
+            good = isinf(tau_min) || dk < lb * (1.f - 1e-6f);
+        } else {
+            good = false;
+        }
+    }
+    if (good) {
+        for (int t = lane; t < p.k; t += 32) {
+            p.idx_out[row * p.k + t] = rj[w][t];
+            p.d2_out[row * p.k + t] = rd[w][t];
+        }
+    } else if (lane == 0) {
+        p.flag_rows[atomicAdd(p.flag_count, 1)] = (int)row;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+atsne_status make_bf16_map(CUtensorMap *m, const void *base, int64_t rows, int Dp, int box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return set_error(ATSNE_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Dp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(ATSNE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ATSNE_OK;
+}
+
+template <int PASSES>
+size_t tc_smem_bytes() {
+    return sizeof(TcSmem<PASSES>) + 1024;
+}
+
+}  // namespace
+
+TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) {
+    TcPlan pl;
+    pl.passes = precision == ATSNE_FP32 ? 3 : 1;
+    pl.Dp = ((D + TC_BK - 1) / TC_BK) * TC_BK;
+    pl.row_tiles = (int)((Q + TC_BM - 1) / TC_BM);
+    const int64_t col_tiles = (N + TC_BN - 1) / TC_BN;
+    int64_t S = (2048 + pl.row_tiles - 1) / pl.row_tiles;
+    if (S > col_tiles) S = col_tiles;
+    if (S < 1) S = 1;
+    const int64_t tiles_per = (col_tiles + S - 1) / S;
+    pl.cols_per_split = (int)(tiles_per * TC_BN);
+    pl.splits = (int)((N + pl.cols_per_split - 1) / pl.cols_per_split);
+    int ks = rerank_k > 0 ? rerank_k : (pl.passes == 3 ? k + 38 : 2 * k);
+    if (ks < k) ks = k;
+    pl.ksel = ks;
+    pl.cap = 2 * ks + TC_BN;
+    return pl;
+}
+
+size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcPlan &pl, TcWs *ws) {
+    TcWs w;
+    w.hi = c.take<uint16_t>((size_t)N * pl.Dp);
+    w.lo = pl.passes == 3 ? c.take<uint16_t>((size_t)N * pl.Dp) : nullptr;
+    w.qhi = list ? c.take<uint16_t>((size_t)Q * pl.Dp) : nullptr;
+    w.qlo = (list && pl.passes == 3) ? c.take<uint16_t>((size_t)Q * pl.Dp) : nullptr;
+    w.nrm = c.take<float>((size_t)N);
+    w.stats = c.take<float>((size_t)N * 4);
+    w.gmax = c.take<unsigned>(4);
+    w.cand = c.take<char>((size_t)Q * pl.splits * pl.cap * sizeof(Cand));
+    w.meta = c.take<char>((size_t)Q * pl.splits * sizeof(int4));
+    w.flag_rows = c.take<int32_t>((size_t)Q);
+    w.flag_count = c.take<int32_t>(1);
+    if (ws) *ws = w;
+    return c.bytes();
+}
+
+atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist, int64_t Q, int k,
+                          const TcPlan &pl, const TcWs &w, int32_t *idx_out, float *d2_out,
+                          cudaStream_t stream) {
+    int *status = device_status_word();
+    cudaError_t e = cudaMemsetAsync(w.gmax, 0, 4 * sizeof(unsigned), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.flag_count, 0, sizeof(int32_t), stream);
+    if (e != cudaSuccess) return cuda_error(e, "knn_tc memset");
+    auto *hi = reinterpret_cast<__nv_bfloat16 *>(w.hi);
+    auto *lo = reinterpret_cast<__nv_bfloat16 *>(w.lo);
+    ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
+                            (const int32_t *)nullptr, N, N, D, pl.Dp, pl.passes, hi, lo, w.nrm,
+                            reinterpret_cast<float4 *>(w.stats), w.gmax, status));
+    const void *a_hi = w.hi, *a_lo = w.lo;
+    if (qlist) {
+        ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(Q * 32, 256), 256, 0, stream, X,
+                                qlist, Q, N, D, pl.Dp, pl.passes,
+                                reinterpret_cast<__nv_bfloat16 *>(w.qhi),
+                                reinterpret_cast<__nv_bfloat16 *>(w.qlo), (float *)nullptr,
+                                (float4 *)nullptr, (unsigned *)nullptr, status));
+        a_hi = w.qhi;
+        a_lo = w.qlo;
+    }
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    ATSNE_TRY(make_bf16_map(&p.tm_a_hi, a_hi, qlist ? Q : N, pl.Dp, TC_BM));
+    ATSNE_TRY(make_bf16_map(&p.tm_b_hi, w.hi, N, pl.Dp, TC_BN));
+    if (pl.passes == 3) {
+        ATSNE_TRY(make_bf16_map(&p.tm_a_lo, a_lo, qlist ? Q : N, pl.Dp, TC_BM));
+        ATSNE_TRY(make_bf16_map(&p.tm_b_lo, w.lo, N, pl.Dp, TC_BN));
+    } else {
+        p.tm_a_lo = p.tm_a_hi;
+        p.tm_b_lo = p.tm_b_hi;
+    }
+    p.nrm = w.nrm;
+    p.qlist = qlist;
+    p.Q = Q;
+    p.N = N;
+    p.KB = pl.Dp / TC_BK;
+    p.splits = pl.splits;
+    p.cols_per_split = pl.cols_per_split;
+    p.row_tiles = pl.row_tiles;
+    p.ksel = pl.ksel;
+    p.cap = pl.cap;
+    p.cand = reinterpret_cast<Cand *>(w.cand);
+    p.meta = reinterpret_cast<int4 *>(w.meta);
+    p.status = status;
+    const int units = pl.row_tiles * pl.splits;
+    const int grid = (int)hmin(units, num_sms());
+    if (pl.passes == 3) {
+        const size_t smem = tc_smem_bytes<3>();
+        e = cudaFuncSetAttribute(knn_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "knn_tc attribute");
+        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<3>, grid, TC_THREADS, smem, stream, p));
+    } else {
+        const size_t smem = tc_smem_bytes<1>();
+        e = cudaFuncSetAttribute(knn_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "knn_tc attribute");
+        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<1>, grid, TC_THREADS, smem, stream, p));
+    }
+    MergeParams m;
+    m.cand = p.cand;
+    m.meta = p.meta;
+    m.splits = pl.splits;
+    m.cap = pl.cap;
+    m.Q = Q;
+    m.N = N;
+    m.qlist = qlist;
+    m.X = X;
+    m.D = D;
+    m.k = k;
+    m.nrm = w.nrm;
+    m.stats = reinterpret_cast<const float4 *>(w.stats);
+    m.gmax = w.gmax;
+    m.acc_coef = (float)((pl.passes * pl.Dp / 16 + 8) * (1.0 / (1 << 21)));
+    m.idx_out = idx_out;
+    m.d2_out = d2_out;
+    m.flag_rows = w.flag_rows;
+    m.flag_count = w.flag_count;
+    ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel, ceil_div(Q, MERGE_WARPS), MERGE_WARPS * 32,
+                            0, stream, m));
+    return knn_bruteforce_rows(X, N, D, qlist, w.flag_rows, w.flag_count, Q, k, idx_out, d2_out, stream);
+}
+
+}  // namespace atsne

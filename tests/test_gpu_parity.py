@@ -21,6 +21,7 @@ def at():
 
 
 DEV = "cuda:0"
+PRECISIONS = ["fp32", "bf16", "fp32_cuda"]
 
 
 def to_dev(a):
@@ -53,41 +54,63 @@ def knn_parity(g_idx, g_d2, X, k, queries=None, rtol=1e-5):
     return clear.mean()
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("N,D,k,seed", [(2000, 64, 90, 1), (91, 1, 90, 2), (100, 3, 10, 3),
-                                        (257, 17, 40, 4), (777, 784, 90, 5), (130, 128, 33, 6)])
-def test_knn_exact_continuous(at, N, D, k, seed):
+                                        (257, 17, 40, 4), (777, 784, 90, 5), (130, 128, 33, 6),
+                                        (1000, 200, 90, 7)])
+def test_knn_exact_continuous(at, N, D, k, seed, precision):
     X = synth.gaussian_mixture(N, D, seed=seed)
-    idx, d2 = at.atsne_knn(to_dev(X), k)
+    idx, d2 = at.atsne_knn(to_dev(X), k, precision=precision)
     frac = knn_parity(idx.cpu().numpy(), d2.cpu().numpy(), X, k)
     assert frac > 0.5  # most rows have a clear k-th/(k+1)-th gap, so the exact check bites
 
 
-def test_knn_exact_integer_data_bit_exact(at):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_knn_exact_integer_data_bit_exact(at, precision):
     # integer-valued data: FP32 sums of squared integer differences below 2^24
     # are exact, so distances and the (d2, index) order match the oracle exactly.
     X = synth.sparse_prototypes(N=3000, D=784, seed=7)
-    idx, d2 = at.atsne_knn(to_dev(X), 90)
+    idx, d2 = at.atsne_knn(to_dev(X), 90, precision=precision)
     o_idx, o_d2 = oracle.knn_exact(X, 90)
     assert np.array_equal(idx.cpu().numpy(), o_idx)
     assert np.array_equal(d2.cpu().numpy().astype(np.float64), o_d2)
 
 
-def test_knn_query_list_and_duplicates(at):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_knn_query_list_and_duplicates(at, precision):
     X = synth.gaussian_mixture(500, 24, seed=8)
     X[10] = X[20]  # an exact duplicate pair
     q = np.array([20, 10, 0, 499, 20], np.int32)
-    idx, d2 = at.atsne_knn(to_dev(X), 30, queries=to_dev(q))
+    idx, d2 = at.atsne_knn(to_dev(X), 30, queries=to_dev(q), precision=precision)
     knn_parity(idx.cpu().numpy(), d2.cpu().numpy(), X, 30, queries=q)
     assert idx[0, 0].item() == 10 and d2[0, 0].item() == 0.0
     assert np.array_equal(idx[0].cpu().numpy(), idx[4].cpu().numpy())
 
 
-def test_knn_all_identical_points(at):
-    X = np.ones((200, 5), np.float32)
-    idx, d2 = at.atsne_knn(to_dev(X), 20)
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_knn_all_identical_points(at, precision):
+    # every key ties: no row can be certified, all fall back to the CUDA cores
+    X = np.ones((1200, 5), np.float32)
+    idx, d2 = at.atsne_knn(to_dev(X), 20, precision=precision)
     o_idx, _ = oracle.knn_exact(X, 20)
     assert np.array_equal(idx.cpu().numpy(), o_idx)  # ties broken by index
     assert torch.all(d2 == 0)
+
+
+def test_knn_tensor_rows_that_fail_the_certificate_fall_back(at):
+    # one BF16 pass with the smallest candidate budget on continuous data: many
+    # rows cannot be certified and are recomputed; the result is still exact
+    X = synth.gaussian_mixture(3000, 96, seed=9)
+    idx, d2 = at.atsne_knn(to_dev(X), 60, precision="bf16", rerank_k=60)
+    knn_parity(idx.cpu().numpy(), d2.cpu().numpy(), X, 60)
+
+
+def test_knn_many_tiles_query_list(at):
+    # more than one 128-row query tile and a ragged last corpus tile
+    X = synth.gaussian_mixture(5000, 70, seed=10)
+    q = synth.sample_rows(5000, 700, seed=3)
+    idx, d2 = at.atsne_knn(to_dev(X), 90, queries=to_dev(q))
+    knn_parity(idx.cpu().numpy(), d2.cpu().numpy(), X, 90, queries=q)
 
 
 @pytest.mark.parametrize("N,D,k,mu,seed", [(2000, 64, 90, 30.0, 1), (300, 10, 30, 10.0, 2),
@@ -284,13 +307,14 @@ def test_out_of_range_subset_is_reported(at):
         at.atsne_check()
 
 
-def test_mnist_shaped_full_size_sampled(at):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_mnist_shaped_full_size_sampled(at, precision):
     # full-size workload (N=70000, D=784): the launch the benchmark times,
     # checked on 48 sampled rows the oracle computes one by one, and P/CSR by
     # properties that hold at any size.
     X = synth.sparse_prototypes(seed=2)
     Xd = to_dev(X)
-    idx, d2 = at.atsne_knn(Xd, 90)
+    idx, d2 = at.atsne_knn(Xd, 90, precision=precision)
     rows = synth.sample_rows(X.shape[0], 48, seed=21)
     o_idx, o_d2 = oracle.knn_exact(X, 90, queries=rows)
     assert np.array_equal(idx.cpu().numpy()[rows], o_idx)
