@@ -295,10 +295,36 @@ def run_ours(args, world, rank, local, pg):
                     "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
                     "traffic": None, "tensor_passes": mult,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
+    elif dom == "forest_query":
+        # gather-bound: every evaluated point's row (D floats) is read once per
+        # query, plus the query row and the k (index, distance) outputs; with one
+        # point per leaf exactly max(checks, k) points are evaluated per query
+        need = max(args.checks, K_NN)
+        per_launch = N * ((need + 1) * D * 4 + K_NN * 8)
+        avg_ms = per_kernel[dom]["ms"] / per_kernel[dom]["launches"]
+        ach = per_launch / (avg_ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                    "algorithmic_bytes_per_launch": per_launch,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     elif dom is not None:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": None,
                     "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s", "frac": None,
                     "traffic": None}
+    # the exact-kNN contraction's own line (the tensor-bound kernel), whichever dominates
+    knn_line = None
+    if "knn_tc" in per_kernel:
+        launches_tc = per_kernel["knn_tc"]["launches"]
+        # one full launch (all N rows) per step plus the refinement's launch
+        full_ms = per_kernel["knn_tc"]["ms"] / args.steps
+        flops = algorithmic_flops_knn(N, D) + 2.0 * pipe.subset.numel() * N * D
+        peak = peaks.get("bf16_tflops", 1900.0)
+        ach = flops / (full_ms / 1e3) / 1e12
+        knn_line = {"kernel": "knn_tc", "bound": "tensor", "launches_per_step": launches_tc // args.steps,
+                    "ms_per_step": round(full_ms, 3), "achieved": round(ach, 1), "peak": peak,
+                    "unit": "TFLOP/s (algorithmic 2*Q*N*D)", "frac": round(ach / peak, 4),
+                    "tensor_passes": 3 if args.precision == "fp32" else 1}
 
     # end to end through the public API with host buffers: H2D of X from pinned
     # memory, the step, D2H of both CSR matrices (trimmed to nnz) and rho
@@ -350,7 +376,7 @@ def run_ours(args, world, rank, local, pg):
             "rho": round(rho, 5), "nnz_exact_P": nnz,
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "knn_tc_roofline": knn_line, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line))

@@ -210,7 +210,11 @@ size_t knn_ws(Carver &c, int64_t N, int32_t D, int32_t k, int64_t S, const atsne
     return c.bytes();
 }
 
-size_t refine_ws(Carver &c, int64_t S, int32_t k, int32_t **ti, float **td, float **tp, float **tb) {
+// Selections of at least this many rows are refined on the tensor-core path.
+constexpr int64_t REFINE_TC_MIN_ROWS = 128;
+
+size_t refine_ws(Carver &c, int64_t N, int32_t D, int64_t S, int32_t k, int32_t **ti, float **td,
+                 float **tp, float **tb, TcPlan *plan = nullptr, TcWs *tws = nullptr) {
     int32_t *a = c.take<int32_t>((size_t)S * k);
     float *b = c.take<float>((size_t)S * k);
     float *p = c.take<float>((size_t)S * k);
@@ -219,6 +223,11 @@ size_t refine_ws(Carver &c, int64_t S, int32_t k, int32_t **ti, float **td, floa
     if (td) *td = b;
     if (tp) *tp = p;
     if (tb) *tb = q;
+    if (S >= REFINE_TC_MIN_ROWS && k <= 200) {
+        const TcPlan pl = tc_plan(N, D, S, k, ATSNE_FP32, 0);
+        if (plan) *plan = pl;
+        tc_workspace(c, N, D, S, true, pl, tws);
+    }
     return c.bytes();
 }
 
@@ -258,7 +267,7 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
     case ATSNE_OP_SYMMETRIZE:
         return symmetrize_workspace(c, N, k, nullptr);
     case ATSNE_OP_REFINE:
-        return refine_ws(c, S, k, nullptr, nullptr, nullptr, nullptr);
+        return refine_ws(c, N, D, S, k, nullptr, nullptr, nullptr, nullptr);
     case ATSNE_OP_FOREST_BUILD:
         return forest_build_workspace(c, N, D, o.trees, o.leaf_size, nullptr);
     case ATSNE_OP_FOREST_QUERY:
@@ -346,12 +355,18 @@ atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int
     Carver c(workspace);
     int32_t *ti;
     float *td, *tp, *tb;
-    refine_ws(c, S, k, &ti, &td, &tp, &tb);
+    TcPlan plan;
+    TcWs tws;
+    refine_ws(c, N, D, S, k, &ti, &td, &tp, &tb, &plan, &tws);
     if (!workspace || ws_bytes < c.bytes())
         return set_error(ATSNE_ENOMEM, "refine: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
-    if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
     if ((st = check_indices(subset, S, N, stream))) return st;
-    if ((st = knn_bruteforce(X, N, D, subset, S, k, ti, td, stream))) return st;
+    if (S >= REFINE_TC_MIN_ROWS && k <= 200) {  // the prep kernel checks X for non-finite values
+        if ((st = knn_exact_tc(X, N, D, subset, S, k, plan, tws, ti, td, stream))) return st;
+    } else {
+        if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
+        if ((st = knn_bruteforce(X, N, D, subset, S, k, ti, td, stream))) return st;
+    }
     if ((st = calibrate_launch(td, S, k, perplexity, 1e-5f, 200, tp, tb, stream))) return st;
     return refine_scatter_launch(subset, S, N, k, ti, td, tp, tb, idx, d2, P_cond, beta, rho, stream);
 }

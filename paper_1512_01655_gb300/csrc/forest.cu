@@ -21,9 +21,7 @@
 //   scatter: sorted points back into the permutation; split value = float
 //            midpoint of the last left and first right value (+inf when the
 //            node has fewer than two points).
-// Search: one warp per query (persistent grid), queue and result list in
-// shared memory, a per-warp "seen" bitmap in the workspace (cleared from the
-// list of points it marked), distances as FP32 direct differences.
+// The search is in forest_query.cu.
 #include <float.h>
 #include <limits.h>
 
@@ -346,241 +344,6 @@ __global__ void scatter_kernel(const float *__restrict__ X, int D, int32_t *__re
     }
 }
 
-// ------------------------------------------------------------------------
-// Search
-// ------------------------------------------------------------------------
-constexpr int FQ_WARPS = 4;        // warps per CTA
-constexpr int FQ_SLOTS = 2048;     // warps in the persistent grid (seen bitmaps)
-constexpr int FQ_KCAP = 128;
-
-struct QEnt {
-    float key;
-    int32_t tree;
-    uint32_t node;
-};
-__device__ __forceinline__ bool qless(const QEnt &a, const QEnt &b) {
-    if (a.key != b.key) return a.key < b.key;
-    if (a.tree != b.tree) return a.tree < b.tree;
-    return a.node < b.node;
-}
-
-struct FqArgs {
-    const float *X;
-    int64_t N;
-    int D, T, h, k, checks, qcap;
-    int64_t n_int;
-    const int32_t *split_dim;
-    const float *split_val;
-    const int32_t *perm;
-    const int32_t *leaf_ofs;
-    const int32_t *qlist;
-    int64_t nq;
-    int32_t *idx_out;
-    float *d2_out;
-    int64_t *evaluated_out;
-    uint32_t *seen;      // [FQ_SLOTS][words]
-    int64_t words;
-    int32_t *marked;     // [FQ_SLOTS][mark_cap]
-    int64_t mark_cap;
-};
-
-// Min-heap push with eviction of the largest entry when full (lane 0 only;
-// the eviction's search for the maximum uses the whole warp).
-__device__ void heap_push(QEnt *hp, int &hn, int cap, QEnt x, int lane) {
-    int pos;
-    if (hn == cap) {
-        // the maximum sits among the leaves [cap/2, cap)
-        float bk = -INFINITY;
-        int bt = -1;
-        uint32_t bn = 0;
-        int bpos = -1;
-        for (int i = cap / 2 + lane; i < cap; i += 32) {
-            const QEnt e = hp[i];
-            if (bpos < 0 || qless(QEnt{bk, bt, bn}, e)) {
-                bk = e.key;
-                bt = e.tree;
-                bn = e.node;
-                bpos = i;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ok = __shfl_xor_sync(0xffffffffu, bk, o);
-            const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-            const uint32_t on = __shfl_xor_sync(0xffffffffu, bn, o);
-            const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
-            if (op >= 0 && (bpos < 0 || qless(QEnt{bk, bt, bn}, QEnt{ok, ot, on}))) {
-                bk = ok;
-                bt = ot;
-                bn = on;
-                bpos = op;
-            }
-        }
-        if (!qless(x, QEnt{bk, bt, bn})) return;
-        pos = bpos;
-    } else {
-        pos = hn++;
-    }
-    if (lane == 0) {
-        while (pos > 0) {
-            const int par = (pos - 1) >> 1;
-            const QEnt pe = hp[par];
-            if (!qless(x, pe)) break;
-            hp[pos] = pe;
-            pos = par;
-        }
-        hp[pos] = x;
-    }
-    __syncwarp();
-}
-
-__device__ QEnt heap_pop(QEnt *hp, int &hn, int lane) {
-    const QEnt top = hp[0];
-    __syncwarp();
-    const int n = --hn;
-    if (lane == 0 && n > 0) {
-        const QEnt x = hp[n];
-        int pos = 0;
-        for (;;) {
-            int c = 2 * pos + 1;
-            if (c >= n) break;
-            if (c + 1 < n && qless(hp[c + 1], hp[c])) ++c;
-            if (!qless(hp[c], x)) break;
-            hp[pos] = hp[c];
-            pos = c;
-        }
-        hp[pos] = x;
-    }
-    __syncwarp();
-    return top;
-}
-
-__global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
-    extern __shared__ __align__(16) unsigned char fq_smem[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)A.qcap * sizeof(QEnt) + (size_t)A.D * sizeof(float) +
-                            FQ_KCAP * (sizeof(float) + sizeof(int));
-    unsigned char *base = fq_smem + w * ((per_warp + 15) & ~size_t(15));
-    QEnt *hp = reinterpret_cast<QEnt *>(base);
-    float *qv = reinterpret_cast<float *>(base + (size_t)A.qcap * sizeof(QEnt));
-    float *td = qv + A.D;
-    int *tj = reinterpret_cast<int *>(td + FQ_KCAP);
-
-    const int slot = blockIdx.x * FQ_WARPS + w;
-    uint32_t *seen = A.seen + (int64_t)slot * A.words;
-    int32_t *marked = A.marked + (int64_t)slot * A.mark_cap;
-    const int64_t need = A.checks > A.k ? A.checks : A.k;
-
-    for (int64_t s = slot; s < A.nq; s += (int64_t)gridDim.x * FQ_WARPS) {
-        const int64_t qi = A.qlist ? A.qlist[s] : s;
-        if (qi < 0 || qi >= A.N) continue;  // flagged by the caller's index check
-        const float *xq = A.X + qi * A.D;
-        for (int d = lane; d < A.D; d += 32) qv[d] = xq[d];
-        for (int t = lane; t < FQ_KCAP; t += 32) {
-            td[t] = INFINITY;
-            tj[t] = INT_MAX;
-        }
-        int hn = 0;
-        int64_t evaluated = 0, n_marked = 0;
-        float md = INFINITY;
-        int mj = INT_MAX, mp = 0;
-        if (lane == 0) {
-            seen[qi >> 5] |= 1u << (qi & 31);
-            marked[n_marked] = (int32_t)qi;
-        }
-        n_marked++;
-        __syncwarp();
-
-        auto evaluate = [&](int32_t p) {
-            // caller guarantees p unseen; mark, count, distance, insert
-            if (lane == 0) {
-                seen[p >> 5] |= 1u << (p & 31);
-                if (n_marked < A.mark_cap) marked[n_marked] = p;
-            }
-            n_marked++;
-            evaluated++;
-            const float *xp = A.X + (int64_t)p * A.D;
-            float acc = 0.f;
-            for (int d = lane; d < A.D; d += 32) {
-                const float diff = qv[d] - xp[d];
-                acc = fmaf(diff, diff, acc);
-            }
-            const float dist = warp_sum(acc);
-            if (pair_less(dist, p, md, mj)) {
-                if (lane == 0) {
-                    td[mp] = dist;
-                    tj[mp] = p;
-                }
-                __syncwarp();
-                float bd = -INFINITY;
-                int bj = INT_MIN, bp = 0;
-                for (int u = lane; u < A.k; u += 32) {
-                    if (pair_less(bd, bj, td[u], tj[u])) {
-                        bd = td[u];
-                        bj = tj[u];
-                        bp = u;
-                    }
-                }
-                warp_argmax_pair(bd, bj, bp);
-                md = bd;
-                mj = bj;
-                mp = bp;
-            }
-            __syncwarp();
-        };
-
-        auto descend_scan = [&](int tr, int64_t v, float key) {
-            while (v < A.n_int) {
-                const int dim = A.split_dim[(int64_t)tr * A.n_int + v];
-                const float sv = A.split_val[(int64_t)tr * A.n_int + v];
-                const float qd = qv[dim];
-                const bool left = qd < sv;
-                const int64_t nearc = left ? 2 * v + 1 : 2 * v + 2;
-                const int64_t farc = left ? 2 * v + 2 : 2 * v + 1;
-                const float diff = __fsub_rn(qd, sv);
-                const float fk = __fadd_rn(key, __fmul_rn(diff, diff));
-                if (!isinf(fk)) heap_push(hp, hn, A.qcap, QEnt{fk, tr, (uint32_t)farc}, lane);
-                v = nearc;
-            }
-            const int64_t m = v - A.n_int;
-            const int32_t *pt = A.perm + (int64_t)tr * A.N;
-            const int b = A.leaf_ofs[m], e = A.leaf_ofs[m + 1];
-            for (int q = b; q < e; ++q) {
-                const int32_t p = pt[q];
-                const bool was = (seen[p >> 5] >> (p & 31)) & 1u;
-                if (!was) evaluate(p);
-            }
-        };
-
-        for (int t = 0; t < A.T && evaluated < need; ++t) descend_scan(t, 0, 0.f);
-        while (evaluated < need && hn > 0) {
-            const QEnt e = heap_pop(hp, hn, lane);
-            descend_scan(e.tree, e.node, e.key);
-        }
-        for (int64_t p = 0; evaluated < A.k && p < A.N; ++p) {
-            const bool was = (seen[p >> 5] >> (p & 31)) & 1u;
-            if (!was) evaluate((int32_t)p);
-        }
-
-        warp_bitonic_sort_smem(td, tj, FQ_KCAP, lane);
-        for (int t = lane; t < A.k; t += 32) {
-            A.idx_out[s * A.k + t] = tj[t];
-            A.d2_out[s * A.k + t] = td[t];
-        }
-        if (lane == 0 && A.evaluated_out) A.evaluated_out[s] = evaluated;
-        // clear the bits this query set
-        if (n_marked <= A.mark_cap) {
-            for (int64_t u = lane; u < n_marked; u += 32) {
-                const int32_t p = marked[u];
-                atomicAnd(&seen[p >> 5], ~(1u << (p & 31)));
-            }
-        } else {
-            for (int64_t u = lane; u < A.words; u += 32) seen[u] = 0u;
-        }
-        __syncwarp();
-    }
-}
-
 struct BuildWs {
     uint64_t *keys;
     float4 *part;
@@ -673,65 +436,6 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
                                 f.n_internal, T, w.keys));
     }
     return ATSNE_OK;
-}
-
-size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int checks, int leaf_size,
-                              void *ws_out) {
-    FqArgs a{};
-    a.words = (N + 31) / 32;
-    const int64_t need = checks > k ? checks : k;
-    a.mark_cap = need + leaf_size + k + 1;
-    a.seen = c.take<uint32_t>((size_t)FQ_SLOTS * a.words);
-    a.marked = c.take<int32_t>((size_t)FQ_SLOTS * a.mark_cap);
-    (void)nq;
-    if (ws_out) *static_cast<FqArgs *>(ws_out) = a;
-    return c.bytes();
-}
-
-size_t forest_query_smem(int D, int qcap) {
-    const size_t per_warp = (size_t)qcap * sizeof(QEnt) + (size_t)D * sizeof(float) +
-                            FQ_KCAP * (sizeof(float) + sizeof(int));
-    return FQ_WARPS * ((per_warp + 15) & ~size_t(15));
-}
-
-atsne_status forest_query_launch(const float *X, const ForestView &f, const int32_t *qlist,
-                                 int64_t nq, int k, int checks, int qcap, int32_t *idx_out,
-                                 float *d2_out, int64_t *evaluated_out, void *ws_base,
-                                 size_t ws_bytes, cudaStream_t stream) {
-    if (k > FQ_KCAP) return set_error(ATSNE_EUNSUPPORTED, "forest query: k=%d above %d", k, FQ_KCAP);
-    Carver c(ws_base);
-    FqArgs a;
-    forest_query_workspace(c, f.N, nq, k, checks, f.leaf_size, &a);
-    if (c.bytes() > ws_bytes) return set_error(ATSNE_ENOMEM, "forest query: workspace too small");
-    const size_t smem = forest_query_smem(f.D, qcap);
-    if (smem > 227 * 1024)
-        return set_error(ATSNE_EUNSUPPORTED, "forest query: queue_cap %d with D=%d needs %zu B of shared memory",
-                         qcap, f.D, smem);
-    cudaError_t e = cudaFuncSetAttribute(forest_query_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "forest query attribute");
-    e = cudaMemsetAsync(a.seen, 0, sizeof(uint32_t) * (size_t)FQ_SLOTS * a.words, stream);
-    if (e != cudaSuccess) return cuda_error(e, "forest query memset");
-    a.X = X;
-    a.N = f.N;
-    a.D = f.D;
-    a.T = f.trees;
-    a.h = f.depth;
-    a.k = k;
-    a.checks = checks;
-    a.qcap = qcap;
-    a.n_int = f.n_internal;
-    a.split_dim = f.split_dim;
-    a.split_val = f.split_val;
-    a.perm = f.perm;
-    a.leaf_ofs = f.leaf_ofs;
-    a.qlist = qlist;
-    a.nq = nq;
-    a.idx_out = idx_out;
-    a.d2_out = d2_out;
-    a.evaluated_out = evaluated_out;
-    const int grid = (int)hmin(FQ_SLOTS / FQ_WARPS, ceil_div(nq, FQ_WARPS));
-    return launch_kernel("forest_query", forest_query_kernel, grid, FQ_WARPS * 32, smem, stream, a);
 }
 
 }  // namespace atsne

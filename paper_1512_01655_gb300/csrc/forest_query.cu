@@ -1,0 +1,424 @@
+// Forest search (Sec. 4.2): best-bin-first over all T trees with one priority
+// queue ordered by the distance to the decision boundary, stopped once a budget
+// of `checks` distinct points has been evaluated.
+//
+// The visiting order never depends on distances (no pruning by the current
+// k-th distance), so each query runs in two phases inside one warp:
+//   1. traversal: queue pops, descents and de-duplication only. A descent
+//      fetches the next five levels below the current node in one round (one
+//      node per lane, 31 independent loads), then walks them with shuffles, so
+//      a 17-level descent costs four memory round trips instead of 17. Queue
+//      entries are 64-bit words (key bits << 32 | tree << 26 | node), so one
+//      integer compare orders them by (key, tree, node). Leaf boundaries are
+//      recomputed arithmetically from N (the halving rule) instead of loaded.
+//      The points collected are appended to a per-warp list in the workspace.
+//   2. evaluation: the warp streams the collected points' rows four at a time
+//      (FP32 direct differences, float4 loads when D % 4 == 0) and keeps the k
+//      best in shared memory under the (distance, index) order.
+// Warps fetch queries from a global counter; the grid is sized by occupancy.
+#include <float.h>
+#include <limits.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace atsne {
+namespace {
+
+constexpr int FQ_WARPS = 4;
+constexpr int FQ_MAX_SLOTS = 4096;  // warps of the persistent grid (one seen bitmap each)
+constexpr int FQ_KCAP = 128;
+constexpr int SUB_DEPTH = 5;        // levels fetched per descent round (31 nodes, one per lane)
+
+struct FqArgs {
+    const float *X;
+    int64_t N;
+    int D, T, h, k, checks, qcap;
+    int64_t n_int;
+    const int32_t *split_dim;
+    const float *split_val;
+    const int32_t *perm;
+    const int32_t *qlist;
+    int64_t nq;
+    int32_t *idx_out;
+    float *d2_out;
+    int64_t *evaluated_out;
+    uint32_t *seen;    // [slots][words]
+    int64_t words;
+    int32_t *marked;   // [slots][mark_cap]
+    int64_t mark_cap;
+    int *next_query;
+};
+
+// First point and size of leaf m: the halving rule of the build applied along
+// the bits of m.
+__device__ __forceinline__ int64_t leaf_start(int64_t N, int h, int64_t m, int64_t &n_out) {
+    int64_t lo = 0, n = N;
+    for (int l = 0; l < h; ++l) {
+        const int64_t nl = (n + 1) >> 1;
+        if ((m >> (h - 1 - l)) & 1) {
+            lo += nl;
+            n -= nl;
+        } else {
+            n = nl;
+        }
+    }
+    n_out = n;
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t qpack(float key, int tree, int64_t node) {
+    return ((uint64_t)__float_as_uint(key) << 32) | ((uint64_t)tree << 26) | (uint64_t)node;
+}
+
+// Bounded min-queue: when full, a new entry replaces the largest (a leaf of the
+// heap) if it is smaller. All lanes call it with the same arguments; lane 0
+// writes.
+__device__ void q_push(uint64_t *hp, int &hn, int cap, uint64_t x, int lane) {
+    int pos;
+    if (hn == cap) {
+        uint64_t mx = 0;
+        int mp = -1;
+        for (int i = cap / 2 + lane; i < cap; i += 32) {
+            const uint64_t e = hp[i];
+            if (mp < 0 || e > mx) {
+                mx = e;
+                mp = i;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t om = __shfl_xor_sync(0xffffffffu, mx, o);
+            const int op = __shfl_xor_sync(0xffffffffu, mp, o);
+            if (op >= 0 && (mp < 0 || om > mx)) {
+                mx = om;
+                mp = op;
+            }
+        }
+        if (!(x < mx)) return;
+        pos = mp;
+    } else {
+        pos = hn++;
+    }
+    if (lane == 0) {
+        while (pos > 0) {
+            const int par = (pos - 1) >> 1;
+            const uint64_t pe = hp[par];
+            if (!(x < pe)) break;
+            hp[pos] = pe;
+            pos = par;
+        }
+        hp[pos] = x;
+    }
+    __syncwarp();
+}
+
+__device__ uint64_t q_pop(uint64_t *hp, int &hn, int lane) {
+    const uint64_t top = hp[0];
+    __syncwarp();
+    const int n = --hn;
+    if (lane == 0 && n > 0) {
+        const uint64_t x = hp[n];
+        int pos = 0;
+        for (;;) {
+            int c = 2 * pos + 1;
+            if (c >= n) break;
+            uint64_t cv = hp[c];
+            if (c + 1 < n) {
+                const uint64_t cr = hp[c + 1];
+                if (cr < cv) {
+                    cv = cr;
+                    ++c;
+                }
+            }
+            if (!(cv < x)) break;
+            hp[pos] = cv;
+            pos = c;
+        }
+        hp[pos] = x;
+    }
+    __syncwarp();
+    return top;
+}
+
+// Descend tree `tr` from node v (queue key `key`) to a leaf, pushing the far
+// child of every node passed; returns the leaf index.
+__device__ int64_t descend(const FqArgs &A, const float *qv, uint64_t *hp, int &hn, int tr,
+                           int64_t v, float key, int lane) {
+    const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
+    const float *sv = A.split_val + (int64_t)tr * A.n_int;
+    while (v < A.n_int) {
+        const int lv = 63 - __clzll((unsigned long long)(v + 1));
+        const int d = min(SUB_DEPTH, A.h - lv);
+        int dim = 0;
+        float val = 0.f;
+        if (lane < (1 << d) - 1) {
+            const int j = 31 - __clz(lane + 1);
+            const int64_t node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
+            dim = sd[node];
+            val = sv[node];
+        }
+        int c = 0;
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+            const int cd = __shfl_sync(0xffffffffu, dim, c);
+            const float cs = __shfl_sync(0xffffffffu, val, c);
+            const float qd = qv[cd];
+            const bool left = qd < cs;
+            const int64_t vg = ((v + 1) << j) - 1 + (c + 1 - (1 << j));
+            const float diff = __fsub_rn(qd, cs);
+            const float fk = __fadd_rn(key, __fmul_rn(diff, diff));
+            if (!isinf(fk)) q_push(hp, hn, A.qcap, qpack(fk, tr, left ? 2 * vg + 2 : 2 * vg + 1), lane);
+            c = left ? 2 * c + 1 : 2 * c + 2;
+        }
+        v = ((v + 1) << d) - 1 + (c + 1 - (1 << d));
+    }
+    return v - A.n_int;
+}
+
+__global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
+    extern __shared__ __align__(16) unsigned char fq_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t heap_b = ((size_t)A.qcap * 8 + 15) & ~size_t(15);
+    const size_t q_b = ((size_t)A.D * 4 + 15) & ~size_t(15);
+    unsigned char *base = fq_smem + w * (heap_b + q_b + FQ_KCAP * 8);
+    uint64_t *hp = reinterpret_cast<uint64_t *>(base);
+    float *qv = reinterpret_cast<float *>(base + heap_b);
+    float *td = reinterpret_cast<float *>(base + heap_b + q_b);
+    int *tj = reinterpret_cast<int *>(td + FQ_KCAP);
+
+    const int slot = blockIdx.x * FQ_WARPS + w;
+    uint32_t *seen = A.seen + (int64_t)slot * A.words;
+    int32_t *marked = A.marked + (int64_t)slot * A.mark_cap;
+    const int64_t need = A.checks > A.k ? A.checks : A.k;
+    const bool vec4 = (A.D & 3) == 0 && (reinterpret_cast<uintptr_t>(A.X) & 15) == 0;
+
+    for (;;) {
+        int64_t s = 0;
+        if (lane == 0) s = atomicAdd(A.next_query, 1);
+        s = __shfl_sync(0xffffffffu, s, 0);
+        if (s >= A.nq) break;
+        const int64_t qi = A.qlist ? A.qlist[s] : s;
+        if (qi < 0 || qi >= A.N) continue;  // flagged by the caller's index check
+        const float *xq = A.X + qi * A.D;
+        for (int d = lane; d < A.D; d += 32) qv[d] = xq[d];
+        for (int t = lane; t < FQ_KCAP; t += 32) {
+            td[t] = INFINITY;
+            tj[t] = INT_MAX;
+        }
+        if (lane == 0) {
+            atomicOr(&seen[qi >> 5], 1u << (qi & 31));
+            marked[0] = (int32_t)qi;
+        }
+        int64_t n_marked = 1, evaluated = 0;
+        int hn = 0;
+        __syncwarp();
+
+        // ---- phase 1: traversal ----
+        auto scan_leaf = [&](int tr, int64_t m) {
+            int64_t cnt;
+            const int64_t s0 = leaf_start(A.N, A.h, m, cnt);
+            const int32_t *pt = A.perm + (int64_t)tr * A.N + s0;
+            for (int64_t b = 0; b < cnt; b += 32) {
+                const int64_t q = b + lane;
+                int32_t p = -1;
+                bool fresh = false;
+                if (q < cnt) {
+                    p = pt[q];
+                    fresh = !((__ldcg(&seen[p >> 5]) >> (p & 31)) & 1u);
+                }
+                const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+                if (fresh) {
+                    atomicOr(&seen[p >> 5], 1u << (p & 31));
+                    marked[n_marked + __popc(fm & ((1u << lane) - 1u))] = p;
+                }
+                n_marked += __popc(fm);
+                evaluated += __popc(fm);
+                __syncwarp();
+            }
+        };
+        for (int t = 0; t < A.T && evaluated < need; ++t) scan_leaf(t, descend(A, qv, hp, hn, t, 0, 0.f, lane));
+        while (evaluated < need && hn > 0) {
+            const uint64_t e = q_pop(hp, hn, lane);
+            const float key = __uint_as_float((uint32_t)(e >> 32));
+            const int tr = (int)((e >> 26) & 63u);
+            const int64_t v = (int64_t)(e & ((1u << 26) - 1u));
+            scan_leaf(tr, descend(A, qv, hp, hn, tr, v, key, lane));
+        }
+        // the queue ran dry with fewer than k points: lowest-index unseen points
+        for (int64_t b = 0; evaluated < A.k && b < A.N; b += 32) {
+            const int64_t p = b + lane;
+            const bool fresh = p < A.N && !((__ldcg(&seen[p >> 5]) >> (p & 31)) & 1u);
+            unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            const int64_t room = A.k - evaluated;
+            if (__popc(fm) > room) {  // keep the `room` lowest-index lanes
+                unsigned keep = 0, rest = fm;
+                for (int64_t r = 0; r < room; ++r) {
+                    keep |= rest & (0u - rest);
+                    rest &= rest - 1u;
+                }
+                fm = keep;
+            }
+            const bool take = (fm >> lane) & 1u;
+            if (take) {
+                atomicOr(&seen[p >> 5], 1u << (p & 31));
+                marked[n_marked + __popc(fm & ((1u << lane) - 1u))] = (int32_t)p;
+            }
+            n_marked += __popc(fm);
+            evaluated += __popc(fm);
+            __syncwarp();
+        }
+
+        // ---- phase 2: distances of the collected points, k best kept ----
+        float md = INFINITY;
+        int mj = INT_MAX, mp = 0;
+        auto insert = [&](float dist, int p) {
+            if (!pair_less(dist, p, md, mj)) return;
+            if (lane == 0) {
+                td[mp] = dist;
+                tj[mp] = p;
+            }
+            __syncwarp();
+            float bd = -INFINITY;
+            int bj = INT_MIN, bp = 0;
+            for (int u = lane; u < A.k; u += 32) {
+                if (pair_less(bd, bj, td[u], tj[u])) {
+                    bd = td[u];
+                    bj = tj[u];
+                    bp = u;
+                }
+            }
+            warp_argmax_pair(bd, bj, bp);
+            md = bd;
+            mj = bj;
+            mp = bp;
+            __syncwarp();
+        };
+        for (int64_t b = 1; b < n_marked; b += 4) {
+            int pj[4];
+            float acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                pj[u] = b + u < n_marked ? marked[b + u] : -1;
+                acc[u] = 0.f;
+            }
+            if (vec4) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+                for (int d = lane; d < (A.D >> 2); d += 32) {
+                    const float4 qq = q4[d];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (pj[u] < 0) continue;
+                        const float4 xv = reinterpret_cast<const float4 *>(A.X + (int64_t)pj[u] * A.D)[d];
+                        float df = qq.x - xv.x;
+                        acc[u] = fmaf(df, df, acc[u]);
+                        df = qq.y - xv.y;
+                        acc[u] = fmaf(df, df, acc[u]);
+                        df = qq.z - xv.z;
+                        acc[u] = fmaf(df, df, acc[u]);
+                        df = qq.w - xv.w;
+                        acc[u] = fmaf(df, df, acc[u]);
+                    }
+                }
+            } else {
+                for (int d = lane; d < A.D; d += 32) {
+                    const float qq = qv[d];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (pj[u] < 0) continue;
+                        const float df = qq - A.X[(int64_t)pj[u] * A.D + d];
+                        acc[u] = fmaf(df, df, acc[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float dist = warp_sum(acc[u]);
+                if (pj[u] >= 0) insert(dist, pj[u]);
+            }
+        }
+
+        warp_bitonic_sort_smem(td, tj, FQ_KCAP, lane);
+        for (int t = lane; t < A.k; t += 32) {
+            A.idx_out[s * A.k + t] = tj[t];
+            A.d2_out[s * A.k + t] = td[t];
+        }
+        if (lane == 0 && A.evaluated_out) A.evaluated_out[s] = evaluated;
+        for (int64_t u = lane; u < n_marked; u += 32) {
+            const int32_t p = marked[u];
+            atomicAnd(&seen[p >> 5], ~(1u << (p & 31)));
+        }
+        __syncwarp();
+    }
+}
+
+size_t fq_smem_bytes(int D, int qcap) {
+    return FQ_WARPS * ((((size_t)qcap * 8 + 15) & ~size_t(15)) + (((size_t)D * 4 + 15) & ~size_t(15)) +
+                       FQ_KCAP * 8);
+}
+
+}  // namespace
+
+size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int checks, int leaf_size,
+                              void *ws_out) {
+    FqArgs a{};
+    a.words = (N + 31) / 32;
+    const int64_t need = checks > k ? checks : k;
+    a.mark_cap = need + leaf_size + k + 1;
+    a.seen = c.take<uint32_t>((size_t)FQ_MAX_SLOTS * a.words);
+    a.marked = c.take<int32_t>((size_t)FQ_MAX_SLOTS * a.mark_cap);
+    a.next_query = c.take<int>(1);
+    (void)nq;
+    if (ws_out) *static_cast<FqArgs *>(ws_out) = a;
+    return c.bytes();
+}
+
+atsne_status forest_query_launch(const float *X, const ForestView &f, const int32_t *qlist,
+                                 int64_t nq, int k, int checks, int qcap, int32_t *idx_out,
+                                 float *d2_out, int64_t *evaluated_out, void *ws_base,
+                                 size_t ws_bytes, cudaStream_t stream) {
+    if (k > FQ_KCAP) return set_error(ATSNE_EUNSUPPORTED, "forest query: k=%d above %d", k, FQ_KCAP);
+    if (f.depth > 25 || f.trees > 64)
+        return set_error(ATSNE_EUNSUPPORTED, "forest query: depth %d / %d trees beyond the packed queue",
+                         f.depth, f.trees);
+    Carver c(ws_base);
+    FqArgs a;
+    forest_query_workspace(c, f.N, nq, k, checks, f.leaf_size, &a);
+    if (c.bytes() > ws_bytes) return set_error(ATSNE_ENOMEM, "forest query: workspace too small");
+    const size_t smem = fq_smem_bytes(f.D, qcap);
+    if (smem > 227 * 1024)
+        return set_error(ATSNE_EUNSUPPORTED,
+                         "forest query: queue_cap %d with D=%d needs %zu B of shared memory", qcap, f.D,
+                         smem);
+    cudaError_t e = cudaFuncSetAttribute(forest_query_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "forest query attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forest_query_kernel, FQ_WARPS * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int grid = (int)hmin(hmin((int64_t)per_sm * num_sms(), FQ_MAX_SLOTS / FQ_WARPS),
+                               ceil_div(nq, FQ_WARPS));
+    e = cudaMemsetAsync(a.seen, 0, sizeof(uint32_t) * (size_t)grid * FQ_WARPS * a.words, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.next_query, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_error(e, "forest query memset");
+    a.X = X;
+    a.N = f.N;
+    a.D = f.D;
+    a.T = f.trees;
+    a.h = f.depth;
+    a.k = k;
+    a.checks = checks;
+    a.qcap = qcap;
+    a.n_int = f.n_internal;
+    a.split_dim = f.split_dim;
+    a.split_val = f.split_val;
+    a.perm = f.perm;
+    a.qlist = qlist;
+    a.nq = nq;
+    a.idx_out = idx_out;
+    a.d2_out = d2_out;
+    a.evaluated_out = evaluated_out;
+    return launch_kernel("forest_query", forest_query_kernel, grid, FQ_WARPS * 32, smem, stream, a);
+}
+
+}  // namespace atsne

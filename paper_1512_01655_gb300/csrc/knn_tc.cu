@@ -703,8 +703,11 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
     pl.Dp = ((D + TC_BK - 1) / TC_BK) * TC_BK;
     pl.row_tiles = (int)((Q + TC_BM - 1) / TC_BM);
     const int64_t col_tiles = (N + TC_BN - 1) / TC_BN;
+    // about 2048 (row tile, column split) units to spread over the SMs, each
+    // unit at least 4 column tiles long
     int64_t S = (2048 + pl.row_tiles - 1) / pl.row_tiles;
-    if (S > col_tiles) S = col_tiles;
+    const int64_t max_s = (col_tiles + 3) / 4;
+    if (S > max_s) S = max_s;
     if (S < 1) S = 1;
     const int64_t tiles_per = (col_tiles + S - 1) / S;
     pl.cols_per_split = (int)(tiles_per * TC_BN);

@@ -50,7 +50,16 @@ def test_noalloc_matches_workspace_refine_twice(at):
         got = [to_dev(a) for a in (idx0, d20, P0, b0)] + [torch.zeros(N, device="cuda:0")]
         at.atsne_refine_subset_noalloc(Xd, sd, mu, *got)
         at.atsne_check()
-        assert torch.equal(got[0], ref[0])
+        # the two paths rank by FP32 distances summed in different orders, so rows
+        # compare as index sets wherever the k-th/(k+1)-th gap is clear (1e-4)
+        gi, ri = got[0].cpu().numpy(), ref[0].cpu().numpy()
+        _, od = oracle.knn_exact(X, k + 1, queries=np.unique(sub))
+        gap = (od[:, k] - od[:, k - 1]) / od[:, k]
+        rows = np.unique(sub)
+        for r, g in zip(rows, gap):
+            if g > 1e-4:
+                assert set(gi[r]) == set(ri[r]), r
+        assert np.array_equal(np.delete(gi, rows, 0), np.delete(ri, rows, 0))
         assert (got[1] - ref[1]).abs().max().item() <= 1e-5 * max(1.0, ref[1].abs().max().item())
         assert (got[2] - ref[2]).abs().max().item() <= 1e-5
         assert (got[3] - ref[3]).abs().max().item() <= 1e-5 * ref[3].abs().max().item()
