@@ -9,8 +9,8 @@
 //      node per lane, 31 independent loads), then walks them with shuffles, so
 //      a 17-level descent costs four memory round trips instead of 17. Queue
 //      entries are 64-bit words (key bits << 32 | tree << 26 | node), so one
-//      integer compare orders them by (key, tree, node). Leaf boundaries are
-//      recomputed arithmetically from N (the halving rule) instead of loaded.
+//      integer compare orders them by (key, tree, node). A full queue keeps an
+//      upper bound of its maximum, so most rejected pushes cost one compare.
 //      The points collected are appended to a per-warp list in the workspace.
 //   2. evaluation: the warp streams the collected points' rows four at a time
 //      (FP32 direct differences, float4 loads when D % 4 == 0) and keeps the k
@@ -38,6 +38,7 @@ struct FqArgs {
     const int32_t *split_dim;
     const float *split_val;
     const int32_t *perm;
+    const int32_t *leaf_ofs;
     const int32_t *qlist;
     int64_t nq;
     int32_t *idx_out;
@@ -50,33 +51,19 @@ struct FqArgs {
     int *next_query;
 };
 
-// First point and size of leaf m: the halving rule of the build applied along
-// the bits of m.
-__device__ __forceinline__ int64_t leaf_start(int64_t N, int h, int64_t m, int64_t &n_out) {
-    int64_t lo = 0, n = N;
-    for (int l = 0; l < h; ++l) {
-        const int64_t nl = (n + 1) >> 1;
-        if ((m >> (h - 1 - l)) & 1) {
-            lo += nl;
-            n -= nl;
-        } else {
-            n = nl;
-        }
-    }
-    n_out = n;
-    return lo;
-}
-
-__device__ __forceinline__ uint64_t qpack(float key, int tree, int64_t node) {
+__device__ __forceinline__ uint64_t qpack(float key, int tree, int node) {
     return ((uint64_t)__float_as_uint(key) << 32) | ((uint64_t)tree << 26) | (uint64_t)node;
 }
 
 // Bounded min-queue: when full, a new entry replaces the largest (a leaf of the
-// heap) if it is smaller. All lanes call it with the same arguments; lane 0
-// writes.
-__device__ void q_push(uint64_t *hp, int &hn, int cap, uint64_t x, int lane) {
+// heap) if it is smaller. `hmax` is an upper bound of the entries held (raised
+// on every insertion, lowered to the exact maximum whenever one is searched),
+// so a full queue rejects x >= hmax without searching. All lanes call it with
+// the same arguments; lane 0 writes.
+__device__ void q_push(uint64_t *hp, int &hn, uint64_t &hmax, int cap, uint64_t x, int lane) {
     int pos;
     if (hn == cap) {
+        if (x >= hmax) return;
         uint64_t mx = 0;
         int mp = -1;
         for (int i = cap / 2 + lane; i < cap; i += 32) {
@@ -95,10 +82,12 @@ __device__ void q_push(uint64_t *hp, int &hn, int cap, uint64_t x, int lane) {
                 mp = op;
             }
         }
+        hmax = mx;
         if (!(x < mx)) return;
         pos = mp;
     } else {
         pos = hn++;
+        if (x > hmax) hmax = x;
     }
     if (lane == 0) {
         while (pos > 0) {
@@ -142,38 +131,39 @@ __device__ uint64_t q_pop(uint64_t *hp, int &hn, int lane) {
 }
 
 // Descend tree `tr` from node v (queue key `key`) to a leaf, pushing the far
-// child of every node passed; returns the leaf index.
-__device__ int64_t descend(const FqArgs &A, const float *qv, uint64_t *hp, int &hn, int tr,
-                           int64_t v, float key, int lane) {
+// child of every node passed; returns the leaf index. Node ids fit in 26 bits.
+__device__ int descend(const FqArgs &A, const float *qv, uint64_t *hp, int &hn, uint64_t &hmax,
+                       int tr, int v, float key, int lane) {
     const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
     const float *sv = A.split_val + (int64_t)tr * A.n_int;
-    while (v < A.n_int) {
-        const int lv = 63 - __clzll((unsigned long long)(v + 1));
+    const int n_int = (int)A.n_int;
+    while (v < n_int) {
+        const int lv = 31 - __clz(v + 1);
         const int d = min(SUB_DEPTH, A.h - lv);
         int dim = 0;
         float val = 0.f;
         if (lane < (1 << d) - 1) {
             const int j = 31 - __clz(lane + 1);
-            const int64_t node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
+            const int node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
             dim = sd[node];
             val = sv[node];
         }
-        int c = 0;
+        int c = 0, vg = v;
 #pragma unroll 1
         for (int j = 0; j < d; ++j) {
             const int cd = __shfl_sync(0xffffffffu, dim, c);
             const float cs = __shfl_sync(0xffffffffu, val, c);
             const float qd = qv[cd];
             const bool left = qd < cs;
-            const int64_t vg = ((v + 1) << j) - 1 + (c + 1 - (1 << j));
             const float diff = __fsub_rn(qd, cs);
             const float fk = __fadd_rn(key, __fmul_rn(diff, diff));
-            if (!isinf(fk)) q_push(hp, hn, A.qcap, qpack(fk, tr, left ? 2 * vg + 2 : 2 * vg + 1), lane);
+            if (!isinf(fk)) q_push(hp, hn, hmax, A.qcap, qpack(fk, tr, left ? 2 * vg + 2 : 2 * vg + 1), lane);
             c = left ? 2 * c + 1 : 2 * c + 2;
+            vg = left ? 2 * vg + 1 : 2 * vg + 2;
         }
-        v = ((v + 1) << d) - 1 + (c + 1 - (1 << d));
+        v = vg;
     }
-    return v - A.n_int;
+    return v - n_int;
 }
 
 __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
@@ -198,6 +188,9 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
         if (lane == 0) s = atomicAdd(A.next_query, 1);
         s = __shfl_sync(0xffffffffu, s, 0);
         if (s >= A.nq) break;
+        // all-rows mode walks the points in the leaf order of tree 0, so warps
+        // running at the same time search neighbouring points (shared rows in L2)
+        if (!A.qlist) s = A.perm[s];
         const int64_t qi = A.qlist ? A.qlist[s] : s;
         if (qi < 0 || qi >= A.N) continue;  // flagged by the caller's index check
         const float *xq = A.X + qi * A.D;
@@ -212,15 +205,16 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
         }
         int64_t n_marked = 1, evaluated = 0;
         int hn = 0;
+        uint64_t hmax = 0;
         __syncwarp();
 
         // ---- phase 1: traversal ----
-        auto scan_leaf = [&](int tr, int64_t m) {
-            int64_t cnt;
-            const int64_t s0 = leaf_start(A.N, A.h, m, cnt);
+        auto scan_leaf = [&](int tr, int m) {
+            const int s0 = A.leaf_ofs[m];
+            const int cnt = A.leaf_ofs[m + 1] - s0;
             const int32_t *pt = A.perm + (int64_t)tr * A.N + s0;
-            for (int64_t b = 0; b < cnt; b += 32) {
-                const int64_t q = b + lane;
+            for (int b = 0; b < cnt; b += 32) {
+                const int q = b + lane;
                 int32_t p = -1;
                 bool fresh = false;
                 if (q < cnt) {
@@ -237,13 +231,14 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
                 __syncwarp();
             }
         };
-        for (int t = 0; t < A.T && evaluated < need; ++t) scan_leaf(t, descend(A, qv, hp, hn, t, 0, 0.f, lane));
+        for (int t = 0; t < A.T && evaluated < need; ++t)
+            scan_leaf(t, descend(A, qv, hp, hn, hmax, t, 0, 0.f, lane));
         while (evaluated < need && hn > 0) {
             const uint64_t e = q_pop(hp, hn, lane);
             const float key = __uint_as_float((uint32_t)(e >> 32));
             const int tr = (int)((e >> 26) & 63u);
-            const int64_t v = (int64_t)(e & ((1u << 26) - 1u));
-            scan_leaf(tr, descend(A, qv, hp, hn, tr, v, key, lane));
+            const int v = (int)(e & ((1u << 26) - 1u));
+            scan_leaf(tr, descend(A, qv, hp, hn, hmax, tr, v, key, lane));
         }
         // the queue ran dry with fewer than k points: lowest-index unseen points
         for (int64_t b = 0; evaluated < A.k && b < A.N; b += 32) {
@@ -294,47 +289,52 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
             mp = bp;
             __syncwarp();
         };
-        for (int64_t b = 1; b < n_marked; b += 4) {
-            int pj[4];
-            float acc[4];
+        for (int64_t b0 = 1; b0 < n_marked; b0 += 32) {
+            const int64_t nb = n_marked - b0 < 32 ? n_marked - b0 : 32;
+            const int my = lane < nb ? marked[b0 + lane] : -1;
+            for (int g = 0; g < nb; g += 8) {
+                int pj[8];
+                float acc[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                pj[u] = b + u < n_marked ? marked[b + u] : -1;
-                acc[u] = 0.f;
-            }
-            if (vec4) {
-                const float4 *q4 = reinterpret_cast<const float4 *>(qv);
-                for (int d = lane; d < (A.D >> 2); d += 32) {
-                    const float4 qq = q4[d];
+                for (int u = 0; u < 8; ++u) {
+                    pj[u] = __shfl_sync(0xffffffffu, my, (g + u) & 31);
+                    if (g + u >= nb) pj[u] = -1;
+                    acc[u] = 0.f;
+                }
+                if (vec4) {
+                    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+                    for (int d = lane; d < (A.D >> 2); d += 32) {
+                        const float4 qq = q4[d];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (pj[u] < 0) continue;
-                        const float4 xv = reinterpret_cast<const float4 *>(A.X + (int64_t)pj[u] * A.D)[d];
-                        float df = qq.x - xv.x;
-                        acc[u] = fmaf(df, df, acc[u]);
-                        df = qq.y - xv.y;
-                        acc[u] = fmaf(df, df, acc[u]);
-                        df = qq.z - xv.z;
-                        acc[u] = fmaf(df, df, acc[u]);
-                        df = qq.w - xv.w;
-                        acc[u] = fmaf(df, df, acc[u]);
+                        for (int u = 0; u < 8; ++u) {
+                            if (pj[u] < 0) continue;
+                            const float4 xv = reinterpret_cast<const float4 *>(A.X + (int64_t)pj[u] * A.D)[d];
+                            float df = qq.x - xv.x;
+                            acc[u] = fmaf(df, df, acc[u]);
+                            df = qq.y - xv.y;
+                            acc[u] = fmaf(df, df, acc[u]);
+                            df = qq.z - xv.z;
+                            acc[u] = fmaf(df, df, acc[u]);
+                            df = qq.w - xv.w;
+                            acc[u] = fmaf(df, df, acc[u]);
+                        }
+                    }
+                } else {
+                    for (int d = lane; d < A.D; d += 32) {
+                        const float qq = qv[d];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            if (pj[u] < 0) continue;
+                            const float df = qq - A.X[(int64_t)pj[u] * A.D + d];
+                            acc[u] = fmaf(df, df, acc[u]);
+                        }
                     }
                 }
-            } else {
-                for (int d = lane; d < A.D; d += 32) {
-                    const float qq = qv[d];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (pj[u] < 0) continue;
-                        const float df = qq - A.X[(int64_t)pj[u] * A.D + d];
-                        acc[u] = fmaf(df, df, acc[u]);
-                    }
+                for (int u = 0; u < 8; ++u) {
+                    const float dist = warp_sum(acc[u]);
+                    if (pj[u] >= 0) insert(dist, pj[u]);
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float dist = warp_sum(acc[u]);
-                if (pj[u] >= 0) insert(dist, pj[u]);
             }
         }
 
@@ -413,6 +413,7 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     a.split_dim = f.split_dim;
     a.split_val = f.split_val;
     a.perm = f.perm;
+    a.leaf_ofs = f.leaf_ofs;
     a.qlist = qlist;
     a.nq = nq;
     a.idx_out = idx_out;

@@ -16,10 +16,12 @@
 //              2-5 read the other accumulator back (tcgen05.ld, one query row
 //              per thread), form the keys, and append every key below the
 //              row's running threshold tau to a per-(row, column split)
-//              candidate buffer. When a buffer reaches 2*ksel entries the warp
-//              selects its ksel-th smallest key (radix select), makes it the
-//              new tau and compacts the buffer to the ksel best, so a buffer
-//              never exceeds 2*ksel + 256 entries.
+//              candidate buffer. Each thread also counts its buffered
+//              distances in 64 buckets (8 per octave below an upper bound of
+//              any distance of the row); tau is lowered to the upper edge of
+//              the bucket in which the count reaches ksel, a valid bound on
+//              the ksel-th distance within 9%. Only a buffer about to
+//              overflow is compacted exactly (warp radix select).
 //   knn_merge  one warp per query: the k-th smallest key over all splits,
 //              every candidate within 2E of it (E bounds the key error, see
 //              row_error_bound) re-ranked by FP32 direct differences, and a
@@ -54,6 +56,7 @@ constexpr int TC_EPI = 128;
 constexpr uint64_t WAIT_NS = 1000000000ull;
 constexpr int MERGE_WARPS = 4;
 constexpr int RCAP = 256;        // candidates re-ranked per row at most
+constexpr int NBUCKET = 48;      // distance buckets per row: 6 octaves, 8 per octave
 
 struct Cand {
     float key;
@@ -71,8 +74,12 @@ struct TcCfg {
 template <int PASSES>
 struct __align__(1024) TcSmem {
     unsigned char stage[TcCfg<PASSES>::STAGES][TcCfg<PASSES>::STAGE_BYTES];
-    float ny[4][TC_BN];  // per epilogue warp: the tile's corpus norms
-    uint32_t hist[4][256];
+    float ny[4][32];            // per epilogue warp: the chunk's corpus norms
+    // per epilogue thread: one row of 32 keys (padded to 33) from which its
+    // survivors are read back; between tiles the warp's first 256 words serve
+    // the radix select of an exact compaction
+    float tr[4][32 * 33];
+    uint16_t dhist[4][NBUCKET][32];  // per epilogue thread: buffered distances by bucket
     uint64_t full[TcCfg<PASSES>::STAGES];
     uint64_t empty[TcCfg<PASSES>::STAGES];
     uint64_t acc_full[2];
@@ -86,6 +93,7 @@ struct __align__(1024) TcSmem {
 struct TcParams {
     CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;
     const float *nrm;      // [N] corpus ||x||^2
+    const unsigned *gmax;  // max ||x|| over the corpus (float bits)
     const int32_t *qlist;  // query row -> corpus index (nullptr: identity)
     int64_t Q, N;
     int KB;                // Dp / 64
@@ -366,9 +374,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
     } else {
         // ---------------- epilogue: keys, filter, per-row candidate buffers ----------------
         const int quarter = warp & 3;
-        float *ny = s.ny[warp - 2];
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        uint32_t *hist = s.hist[warp - 2];
+        uint32_t *hist = reinterpret_cast<uint32_t *>(s.tr[warp - 2]);
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
@@ -381,14 +388,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             const int qid = qv ? (p.qlist ? p.qlist[row] : (int)row) : -1;
             Cand *buf = qv ? p.cand + ((size_t)row * p.splits + sp) * p.cap : nullptr;
             float tau = qv ? INFINITY : -INFINITY;
-            int cnt = 0;
+            int cnt = 0, since = 0;
+            // distance buckets (8 per octave) below t0 = (||x|| + max||y||)^2 >= d
+            const float nx = qv ? p.nrm[qid] : 0.f;
+            const float ai = sqrtf(nx), amax = __uint_as_float(p.gmax[0]);
+            int top = (int)(__float_as_uint((ai + amax) * (ai + amax) * 1.0001f + 1e-30f) >> 20);
+            uint16_t *dh = &s.dhist[warp - 2][0][lane];
+            for (int bk = 0; bk < NBUCKET; ++bk) dh[bk * 32] = 0;
+            // corpus norms of the first tile of the unit, then one tile ahead
+            float nyn[TC_BN / 32];
+#pragma unroll
+            for (int q = 0; q < TC_BN / 32; ++q) {
+                const int64_t cc = c0 + q * 32 + lane;
+                nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
+            }
+            float *nyw = s.ny[warp - 2];
+            float *mine = s.tr[warp - 2] + lane * 33;
             for (int64_t ct = c0; ct < c1; ct += TC_BN) {
-                // this warp's copy of the tile's corpus norms (+inf past the split)
-                for (int t = lane; t < TC_BN; t += 32) {
-                    const int64_t c = ct + t;
-                    ny[t] = c < c1 ? p.nrm[c] : INFINITY;
+                float nyc[TC_BN / 32];  // lane l: columns l, l + 32, ... of this tile
+#pragma unroll
+                for (int q = 0; q < TC_BN / 32; ++q) nyc[q] = nyn[q];
+                if (ct + TC_BN < c1) {
+#pragma unroll
+                    for (int q = 0; q < TC_BN / 32; ++q) {
+                        const int64_t cc = ct + TC_BN + q * 32 + lane;
+                        nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
+                    }
                 }
-                __syncwarp();
                 ok = mbar_wait(&s.acc_full[acc], acc_phase, &s.abort_flag, WAIT_NS);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) {
@@ -400,31 +426,75 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 }
                 fence_after_sync();
                 const uint32_t taddr = tbase + lane_base + (uint32_t)(acc * TC_BN);
-#pragma unroll 1
+                const int self_off = qid - (int)ct;  // the query's own column, if in this tile
+#pragma unroll
                 for (int c = 0; c < TC_BN / 32; ++c) {
                     uint32_t r[32];
                     tmem_ld32(taddr + (uint32_t)(c * 32), r);
+                    nyw[lane] = nyc[c];
                     tmem_ld_wait();
+                    __syncwarp();
+                    // branch-free filter: 32 keys, one survivor bit each
+                    float kk[32];
+                    uint32_t mask = 0;
+                    const float4 *ny4 = reinterpret_cast<const float4 *>(nyw);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = (int)ct + c * 32 + j;
-                        const float key = fmaf(-2.f, __uint_as_float(r[j]), ny[c * 32 + j]);
-                        if (key < tau && col != qid) {
-                            if (cnt < p.cap) buf[cnt] = Cand{key, col};
-                            ++cnt;
-                        }
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 n4 = ny4[q];
+                        kk[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), n4.x);
+                        kk[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), n4.y);
+                        kk[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), n4.z);
+                        kk[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), n4.w);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) mask |= (kk[j] < tau ? 1u : 0u) << j;
+                    const int so = self_off - c * 32;
+                    if (so >= 0 && so < 32) mask &= ~(1u << so);
+                    __syncwarp();  // the chunk's norms are read before the next chunk's
+                    if (mask) {
+                        // spill this row's keys to its own padded shared row and
+                        // walk its survivors: the warp pays the largest count of
+                        // any lane, not the union of survivor positions
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) mine[j] = kk[j];
+                        const int colb = (int)ct + c * 32;
+                        since += __popc(mask);
+                        do {
+                            const int j = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const float key = mine[j];
+                            buf[cnt++] = Cand{key, colb + j};
+                            int bk = (int)(__float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20) - (top - (NBUCKET - 1));
+                            bk = min(max(bk, 0), NBUCKET - 1);
+                            dh[bk * 32] += 1;
+                        } while (mask);
                     }
                 }
                 fence_before_sync();
-                __syncwarp();  // the norms of this tile are no longer read
+                __syncwarp();
                 mbar_arrive(&s.acc_empty[acc]);
                 if (++acc == 2) {
                     acc = 0;
                     acc_phase ^= 1u;
                 }
-                // compact full buffers to their ksel best and tighten tau
-                unsigned m = __ballot_sync(0xffffffffu, cnt >= 2 * p.ksel && cnt <= p.cap);
+                // lower tau to the upper edge of the bucket holding the ksel-th distance
+                if (since >= 16 && cnt >= p.ksel) {
+                    int cum = 0, bk = 0;
+                    for (; bk < NBUCKET; ++bk) {
+                        cum += dh[bk * 32];
+                        if (cum >= p.ksel) break;
+                    }
+                    if (bk < NBUCKET) {
+                        const float edge =
+                            __uint_as_float((uint32_t)(top - (NBUCKET - 1) + bk + 1) << 20);
+                        tau = fminf(tau, edge - nx);
+                    }
+                    since = 0;
+                }
+                // a buffer that the next tile could overflow is compacted exactly
+                unsigned m = __ballot_sync(0xffffffffu, cnt > p.cap - TC_BN);
                 if (m) __syncwarp();
+                const unsigned compacted = m;
                 while (m) {
                     const int l = __ffs(m) - 1;
                     m &= m - 1;
@@ -457,11 +527,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                         tau = key_of_bits(tk);
                     }
                 }
+                if ((compacted >> lane) & 1u) {
+                    // re-base the buckets below the new tau and recount the kept entries
+                    top = (int)(__float_as_uint(fmaxf(nx + tau, 1e-30f) * 1.0001f) >> 20) + 1;
+                    for (int bk = 0; bk < NBUCKET; ++bk) dh[bk * 32] = 0;
+                    for (int i = 0; i < cnt; ++i) {
+                        int bk = (int)(__float_as_uint(fmaxf(nx + buf[i].key, 1e-30f)) >> 20) -
+                                 (top - (NBUCKET - 1));
+                        bk = min(max(bk, 0), NBUCKET - 1);
+                        dh[bk * 32] += 1;
+                    }
+                    since = 0;
+                }
             }
             if (!ok) break;
             if (qv)
-                p.meta[(size_t)row * p.splits + sp] =
-                    make_int4(cnt < p.cap ? cnt : p.cap, __float_as_int(tau), cnt > p.cap ? 1 : 0, 0);
+                p.meta[(size_t)row * p.splits + sp] = make_int4(cnt, __float_as_int(tau), 0, 0);
         }
     }
 
@@ -694,6 +775,8 @@ template <int PASSES>
 size_t tc_smem_bytes() {
     return sizeof(TcSmem<PASSES>) + 1024;
 }
+static_assert(sizeof(TcSmem<1>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
+static_assert(sizeof(TcSmem<3>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
 
 }  // namespace
 
@@ -703,9 +786,11 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
     pl.Dp = ((D + TC_BK - 1) / TC_BK) * TC_BK;
     pl.row_tiles = (int)((Q + TC_BM - 1) / TC_BM);
     const int64_t col_tiles = (N + TC_BN - 1) / TC_BN;
-    // about 2048 (row tile, column split) units to spread over the SMs, each
-    // unit at least 4 column tiles long
-    int64_t S = (2048 + pl.row_tiles - 1) / pl.row_tiles;
+    // (row tile, column split) units: one split per row tile when the row tiles
+    // alone give every SM at least two units (a split restarts the streaming
+    // top-k, whose k' ln(n / k') survivors dominate the epilogue), else about
+    // 2048 units, each at least 4 column tiles long
+    int64_t S = pl.row_tiles >= 304 ? 1 : (2048 + pl.row_tiles - 1) / pl.row_tiles;
     const int64_t max_s = (col_tiles + 3) / 4;
     if (S > max_s) S = max_s;
     if (S < 1) S = 1;
@@ -715,7 +800,7 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
     int ks = rerank_k > 0 ? rerank_k : (pl.passes == 3 ? k + 38 : 2 * k);
     if (ks < k) ks = k;
     pl.ksel = ks;
-    pl.cap = 2 * ks + TC_BN;
+    pl.cap = 8 * ks + TC_BN;
     return pl;
 }
 
@@ -770,6 +855,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         p.tm_b_lo = p.tm_b_hi;
     }
     p.nrm = w.nrm;
+    p.gmax = w.gmax;
     p.qlist = qlist;
     p.Q = Q;
     p.N = N;
