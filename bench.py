@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
     p.add_argument("--trees", type=int, default=4)
     p.add_argument("--checks", type=int, default=1024)
+    p.add_argument("--queue-cap", type=int, default=0, help="forest queue capacity (0 = auto)")
     p.add_argument("--refine", type=int, default=2000, help="points in the refined selection")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -170,7 +171,7 @@ class Pipeline:
         self.subset = torch.from_numpy(sel).to(dev)
         self.exact_opts = at.knn_opts(method="exact", precision=args.precision)
         self.forest_opts = at.knn_opts(method="forest", trees=args.trees, checks=args.checks,
-                                       leaf_size=1, seed=7)
+                                       leaf_size=1, seed=7, queue_cap=args.queue_cap)
 
     def step(self):
         at, X = self.at, self.X
@@ -182,8 +183,9 @@ class Pipeline:
         forest = at.atsne_forest_build(X, opts=self.forest_opts)
         idx_a, d2_a, _ = at.atsne_forest_query(X, forest, K_NN)
         P_a, beta_a = at.atsne_calibrate_P(d2_a, PERPLEXITY)
-        # precision of the approximate neighbourhoods
-        rho_i, _ = self._precision(idx_a, idx_e)
+        # precision of the approximate neighbourhoods (Eq. 9), before refinement
+        rho_i, rho_sum = self._precision(idx_a, idx_e)
+        self.rho_sum = rho_sum
         # refinement of a selection, then the CSR rebuild
         at.atsne_refine_subset(X, self.subset, PERPLEXITY, idx_a, d2_a, P_a, beta_a, rho_i)
         csr_a = at.atsne_symmetrize(idx_a, P_a, trim=False)
@@ -199,6 +201,14 @@ class Pipeline:
         at._raise(at.lib().atsne_knn_precision(at._p(a), at._p(e), rows, K_NN, at._p(rho_i),
                                                at._p(s), at._stream()))
         return rho_i, s
+
+
+def default_queue_cap(checks):
+    # the library's default (queue_cap = 0): checks/2 as a power of two in [256, 4096]
+    q = 256
+    while q < checks // 2 and q < 4096:
+        q <<= 1
+    return q
 
 
 def algorithmic_flops_knn(N, D):
@@ -258,7 +268,8 @@ def run_ours(args, world, rank, local, pg):
             per_kernel[name] = {"launches": n, "ms": ms}
     at.profile_enable(False)
     csr_e, csr_a, rho_i = out
-    rho = float(rho_i.double().mean().item())
+    rho_refined = float(rho_i.double().mean().item())
+    rho = float(pipe.rho_sum.item()) / N
     nnz = int(csr_e[3].item())
     at.atsne_check()
 
@@ -369,11 +380,12 @@ def run_ours(args, world, rank, local, pg):
             "config": {"workload": w["desc"], "N": N, "D": D, "k": K_NN,
                        "perplexity": PERPLEXITY, "exact_precision": args.precision,
                        "forest": {"trees": args.trees, "top_var_dims": 5, "checks": args.checks,
-                                  "leaf_size": 1},
+                                  "leaf_size": 1,
+                                  "queue_cap": args.queue_cap or default_queue_cap(args.checks)},
                        "refine_points": int(pipe.subset.numel()),
                        "l2": "input larger than L2" if l2_flush is None else "L2 flushed between steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "rho": round(rho, 5), "nnz_exact_P": nnz,
+            "rho": round(rho, 5), "rho_after_refine": round(rho_refined, 5), "nnz_exact_P": nnz,
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
             "roofline": roofline, "knn_tc_roofline": knn_line, "cpu_baseline": cpu, "e2e": e2e,

@@ -70,7 +70,8 @@ typedef struct {
     int32_t top_var_dims;  /* forest: V, split among the V highest-spread dims, default 5 */
     int32_t checks;        /* forest: budget of evaluated points ("leaves" L, Sec. 4.2) */
     int32_t leaf_size;     /* forest: maximum points per leaf, default 1 */
-    int32_t queue_cap;     /* forest: capacity of the per-query priority queue, default 1024 */
+    int32_t queue_cap;     /* forest: capacity of the per-query priority queue; 0 (default)
+                              = checks/2 rounded up to a power of two, within [256, 4096] */
     int32_t rerank_k;      /* exact tensor path: candidates kept per row and column split
                               (0 = k + 38 for FP32, 2k for BF16) */
     uint64_t seed;         /* forest: seed of the counter-based split choice */

@@ -151,8 +151,19 @@ def forest_build(X, trees, top_var_dims=5, leaf_size=1, seed=0):
                 split_val=split_val[:, :n_int], perm=perm, leaf_ofs=leaf_ofs)
 
 
-def forest_query(X, forest, k, checks, qcap=1024, queries=None):
-    """Forest search, Sec. 4.2: (idx [Q,k], d2 float64 [Q,k], evaluated [Q])."""
+def auto_queue_cap(checks):
+    """Default queue capacity: checks/2 rounded up to a power of two, in [256, 4096]."""
+    q = 256
+    while q < checks // 2 and q < 4096:
+        q <<= 1
+    return q
+
+
+def forest_query(X, forest, k, checks, qcap=None, queries=None):
+    """Forest search, Sec. 4.2: (idx [Q,k], d2 float64 [Q,k], evaluated [Q]).
+    qcap None selects the default capacity auto_queue_cap(checks)."""
+    if qcap is None:
+        qcap = auto_queue_cap(checks)
     X = np.ascontiguousarray(X, dtype=np.float32)
     N, D = X.shape
     T, h = forest["trees"], forest["depth"]

@@ -122,7 +122,7 @@ def _dev(t, dtype, name):
 
 
 def knn_opts(method="exact", precision="fp32", trees=4, top_var_dims=5, checks=1024, leaf_size=1,
-             queue_cap=1024, rerank_k=0, seed=0):
+             queue_cap=0, rerank_k=0, seed=0):
     o = KnnOpts()
     lib().atsne_knn_opts_default(ctypes.byref(o))
     o.method = {"exact": KNN_EXACT, "forest": KNN_FOREST}[method] if isinstance(method, str) else method

@@ -148,7 +148,8 @@ atsne_status validate_knn_opts(const atsne_knn_opts &o) {
             return set_error(ATSNE_EINVAL, "forest: top_var_dims=%d not in [1,8]", o.top_var_dims);
         if (o.checks < 1) return set_error(ATSNE_EINVAL, "forest: checks=%d < 1", o.checks);
         if (o.leaf_size < 1) return set_error(ATSNE_EINVAL, "forest: leaf_size=%d < 1", o.leaf_size);
-        if (o.queue_cap < 2) return set_error(ATSNE_EINVAL, "forest: queue_cap=%d < 2", o.queue_cap);
+        if (o.queue_cap != 0 && o.queue_cap < 2)
+            return set_error(ATSNE_EINVAL, "forest: queue_cap=%d < 2", o.queue_cap);
     }
     return ATSNE_OK;
 }
@@ -159,6 +160,16 @@ atsne_status validate_xk(const float *X, int64_t N, int32_t D, int32_t k) {
     if (D < 1) return set_error(ATSNE_EINVAL, "D=%d < 1", D);
     if (k < 1 || (int64_t)k > N - 1) return set_error(ATSNE_EINVAL, "k=%d not in [1, N-1]", k);
     return ATSNE_OK;
+}
+
+// Queue capacity: the caller's, or checks/2 rounded up to a power of two in
+// [256, 4096] (a bound the search reaches only when it would not have popped
+// the evicted entries within its budget on the workloads measured).
+int queue_capacity(const atsne_knn_opts &o) {
+    if (o.queue_cap > 0) return o.queue_cap;
+    int q = 256;
+    while (q < o.checks / 2 && q < 4096) q <<= 1;
+    return q;
 }
 
 ForestView forest_view(void *forest, int64_t N, int32_t D, const atsne_knn_opts &o) {
@@ -246,7 +257,7 @@ void atsne_knn_opts_default(atsne_knn_opts *o) {
     o->top_var_dims = 5;
     o->checks = 1024;
     o->leaf_size = 1;
-    o->queue_cap = 1024;
+    o->queue_cap = 0;
     o->rerank_k = 0;
     o->seed = 0;
 }
@@ -305,7 +316,7 @@ atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *quer
         return knn_bruteforce(X, N, D, queries, nq, k, idx_out, d2_out, stream);
     ForestView f = forest_view(forest, N, D, o);
     if ((st = forest_build_launch(X, f, sub, sub_bytes, stream))) return st;
-    return forest_query_launch(X, f, queries, nq, k, o.checks, o.queue_cap, idx_out, d2_out,
+    return forest_query_launch(X, f, queries, nq, k, o.checks, queue_capacity(o), idx_out, d2_out,
                                nullptr, sub, sub_bytes, stream);
 }
 
@@ -423,7 +434,7 @@ atsne_status atsne_forest_query(const float *X, int64_t N, int32_t D, const void
     if (nq == 0) return ATSNE_OK;
     if (queries && (st = check_indices(queries, S, N, stream))) return st;
     return forest_query_launch(X, forest_view(const_cast<void *>(forest), N, D, o), queries, nq, k,
-                               o.checks, o.queue_cap, idx_out, d2_out, evaluated_out, workspace,
+                               o.checks, queue_capacity(o), idx_out, d2_out, evaluated_out, workspace,
                                ws_bytes, stream);
 }
 

@@ -92,15 +92,16 @@ def test_full_budget_gives_exact_knn(oracle_mod):
 
 
 def test_budget_only_extends_the_visit(oracle_mod):
-    # No pruning: the visiting order does not depend on checks, so per row the
-    # evaluated set grows with the budget and rho_i can only rise (Eq. 9).
+    # No pruning: the visiting order does not depend on checks (at a fixed queue
+    # capacity), so per row the evaluated set grows with the budget and rho_i can
+    # only rise (Eq. 9).
     X = synth.gaussian_mixture(800, 24, seed=4)
     k = 30
     f = oracle_mod.forest_build(X, trees=3, top_var_dims=5, leaf_size=1, seed=9)
     ex_idx, _ = oracle_mod.knn_exact(X, k)
     prev = None
     for checks in [1, 32, 64, 128, 256, 799]:
-        idx, d2, ev = oracle_mod.forest_query(X, f, k, checks)
+        idx, d2, ev = oracle_mod.forest_query(X, f, k, checks, qcap=4096)
         assert np.all(ev == max(checks, k))
         rho_i, rho = oracle_mod.precision(idx, ex_idx)
         if prev is not None:
