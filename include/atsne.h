@@ -184,14 +184,15 @@ atsne_status atsne_knn_precision(const int32_t *idx_approx, const int32_t *idx_e
  * from its start, filled by atsne_forest_layout()):
  *   split_dim [trees][2^depth - 1] int32, split_val [trees][2^depth - 1] fp32,
  *   perm [trees][N] int32 (points in leaf order),
- *   leaf_ofs [2^depth + 1] int32 (leaf m holds perm[t][leaf_ofs[m] .. leaf_ofs[m+1])).
+ *   leaf_ofs [2^depth + 1] int32 (leaf m holds perm[t][leaf_ofs[m] .. leaf_ofs[m+1])),
+ *   leaf_pt [trees][2^depth] int32 (first point of each leaf, -1 if the leaf is empty).
  * Trees are level-ordered: node v has children 2v+1 and 2v+2.
  */
 typedef struct {
     int32_t depth;
     int32_t trees;
     int64_t n_internal;
-    size_t off_split_dim, off_split_val, off_perm, off_leaf_ofs;
+    size_t off_split_dim, off_split_val, off_perm, off_leaf_ofs, off_leaf_pt;
     size_t bytes;
 } atsne_forest_layout_t;
 

@@ -46,7 +46,8 @@ class ForestLayout(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("trees", ctypes.c_int32),
                 ("n_internal", ctypes.c_int64), ("off_split_dim", ctypes.c_size_t),
                 ("off_split_val", ctypes.c_size_t), ("off_perm", ctypes.c_size_t),
-                ("off_leaf_ofs", ctypes.c_size_t), ("bytes", ctypes.c_size_t)]
+                ("off_leaf_ofs", ctypes.c_size_t), ("off_leaf_pt", ctypes.c_size_t),
+                ("bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -247,7 +248,8 @@ class Forest:
             split_dim=self._view(L.off_split_dim, T * n_int, torch.int32).view(T, n_int),
             split_val=self._view(L.off_split_val, T * n_int, torch.float32).view(T, n_int),
             perm=self._view(L.off_perm, T * self.N, torch.int32).view(T, self.N),
-            leaf_ofs=self._view(L.off_leaf_ofs, (1 << L.depth) + 1, torch.int32))
+            leaf_ofs=self._view(L.off_leaf_ofs, (1 << L.depth) + 1, torch.int32),
+            leaf_pt=self._view(L.off_leaf_pt, T * (1 << L.depth), torch.int32).view(T, 1 << L.depth))
 
 
 def atsne_forest_build(X, stream=None, opts=None, **kw):

@@ -189,6 +189,7 @@ ForestView forest_view(void *forest, int64_t N, int32_t D, const atsne_knn_opts 
     f.split_val = reinterpret_cast<float *>(b + L.off_split_val);
     f.perm = reinterpret_cast<int32_t *>(b + L.off_perm);
     f.leaf_ofs = reinterpret_cast<int32_t *>(b + L.off_leaf_ofs);
+    f.leaf_pt = reinterpret_cast<int32_t *>(b + L.off_leaf_pt);
     return f;
 }
 

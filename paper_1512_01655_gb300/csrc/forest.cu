@@ -56,6 +56,9 @@ size_t forest_layout(int64_t N, int trees, int leaf_size, atsne_forest_layout_t 
     c.off = (c.off + 255) & ~size_t(255);
     L.off_leaf_ofs = c.off;
     c.take<int32_t>(((size_t)1 << h) + 1);
+    c.off = (c.off + 255) & ~size_t(255);
+    L.off_leaf_pt = c.off;
+    c.take<int32_t>((size_t)trees << h);
     L.bytes = c.bytes();
     if (out) *out = L;
     return L.bytes;
@@ -140,6 +143,18 @@ __global__ void leaf_ofs_kernel(int64_t N, int h, int32_t *leaf_ofs) {
         }
     }
     leaf_ofs[m] = (int32_t)lo;
+}
+
+// leaf_pt[t][m]: the first point of leaf m of tree t, -1 for an empty leaf.
+__global__ void leaf_pt_kernel(const int32_t *__restrict__ perm, const int32_t *__restrict__ leaf_ofs,
+                               int64_t N, int h, int T, int32_t *__restrict__ leaf_pt) {
+    const int64_t L = (int64_t)1 << h;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= L * T) return;
+    const int t = (int)(g / L);
+    const int64_t m = g - (int64_t)t * L;
+    const int32_t a = leaf_ofs[m], b = leaf_ofs[m + 1];
+    leaf_pt[g] = b > a ? perm[(int64_t)t * N + a] : -1;
 }
 
 __global__ void iota_kernel(int32_t *perm, int64_t N, int T) {
@@ -435,7 +450,8 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
                                 X, f.D, f.perm, f.N, f.leaf_ofs, h, l, P, f.split_dim, f.split_val,
                                 f.n_internal, T, w.keys));
     }
-    return ATSNE_OK;
+    return launch_kernel("forest_leaf_pt", leaf_pt_kernel, ceil_div(((int64_t)T) << h, 256), 256, 0,
+                         stream, f.perm, f.leaf_ofs, f.N, h, T, f.leaf_pt);
 }
 
 }  // namespace atsne

@@ -39,6 +39,8 @@ struct FqArgs {
     const float *split_val;
     const int32_t *perm;
     const int32_t *leaf_ofs;
+    const int32_t *leaf_pt;
+    int leaf_size;
     const int32_t *qlist;
     int64_t nq;
     int32_t *idx_out;
@@ -166,6 +168,59 @@ __device__ int descend(const FqArgs &A, const float *qv, uint64_t *hp, int &hn, 
     return v - n_int;
 }
 
+// One point per leaf: descend as above and return the reached leaf's point (-1
+// if empty) and the seen-bitmap word holding it. The last round fetches the
+// points of all leaves of its subtree together with the split data; the word is
+// loaded after the walk and only read at the next step.
+struct LeafHit {
+    int p;
+    uint32_t word;
+};
+
+__device__ LeafHit descend_pt(const FqArgs &A, const float *qv, uint64_t *hp, int &hn,
+                              uint64_t &hmax, const uint32_t *seen, int tr, int v, float key,
+                              int lane) {
+    const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
+    const float *sv = A.split_val + (int64_t)tr * A.n_int;
+    const int32_t *lpt = A.leaf_pt + ((int64_t)tr << A.h);
+    const int n_int = (int)A.n_int;
+    int p = -1;
+    if (v >= n_int) {
+        p = lpt[v - n_int];
+    } else {
+        while (v < n_int) {
+            const int lv = 31 - __clz(v + 1);
+            const int d = min(SUB_DEPTH, A.h - lv);
+            const bool last = lv + d == A.h;
+            int dim = 0, lp = -1;
+            float val = 0.f;
+            if (lane < (1 << d) - 1) {
+                const int j = 31 - __clz(lane + 1);
+                const int node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
+                dim = sd[node];
+                val = sv[node];
+            }
+            if (last && lane < (1 << d)) lp = lpt[((v + 1) << d) - 1 + lane - n_int];
+            int c = 0, vg = v;
+#pragma unroll 1
+            for (int j = 0; j < d; ++j) {
+                const int cd = __shfl_sync(0xffffffffu, dim, c);
+                const float cs = __shfl_sync(0xffffffffu, val, c);
+                const float qd = qv[cd];
+                const bool left = qd < cs;
+                const float diff = __fsub_rn(qd, cs);
+                const float fk = __fadd_rn(key, __fmul_rn(diff, diff));
+                if (!isinf(fk)) q_push(hp, hn, hmax, A.qcap, qpack(fk, tr, left ? 2 * vg + 2 : 2 * vg + 1), lane);
+                c = left ? 2 * c + 1 : 2 * c + 2;
+                vg = left ? 2 * vg + 1 : 2 * vg + 2;
+            }
+            if (last) p = __shfl_sync(0xffffffffu, lp, c + 1 - (1 << d));
+            v = vg;
+        }
+    }
+    return LeafHit{p, p >= 0 ? __ldcg(&seen[p >> 5]) : 0u};
+}
+
 __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
     extern __shared__ __align__(16) unsigned char fq_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -231,14 +286,56 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
                 __syncwarp();
             }
         };
-        for (int t = 0; t < A.T && evaluated < need; ++t)
-            scan_leaf(t, descend(A, qv, hp, hn, hmax, t, 0, 0.f, lane));
-        while (evaluated < need && hn > 0) {
-            const uint64_t e = q_pop(hp, hn, lane);
-            const float key = __uint_as_float((uint32_t)(e >> 32));
-            const int tr = (int)((e >> 26) & 63u);
-            const int v = (int)(e & ((1u << 26) - 1u));
-            scan_leaf(tr, descend(A, qv, hp, hn, hmax, tr, v, key, lane));
+        if (A.leaf_size == 1) {
+            // one point per leaf: the seen test of step i is resolved after the
+            // descent of step i + 1 (descents never read the bitmap; a step made
+            // past the stopping point only adds queue entries that are not used)
+            int pend_p = -1;
+            uint32_t pend_w = 0;
+            auto resolve = [&]() {
+                if (pend_p >= 0 && !((pend_w >> (pend_p & 31)) & 1u)) {
+                    if (lane == 0) {
+                        atomicOr(&seen[pend_p >> 5], 1u << (pend_p & 31));
+                        marked[n_marked] = pend_p;
+                    }
+                    ++n_marked;
+                    ++evaluated;
+                }
+                pend_p = -1;
+            };
+            for (int t = 0;;) {
+                LeafHit hit;
+                if (t < A.T) {
+                    hit = descend_pt(A, qv, hp, hn, hmax, seen, t, 0, 0.f, lane);
+                    ++t;
+                } else {
+                    if (hn == 0) break;
+                    const uint64_t e = q_pop(hp, hn, lane);
+                    const float key = __uint_as_float((uint32_t)(e >> 32));
+                    const int tr = (int)((e >> 26) & 63u);
+                    const int v = (int)(e & ((1u << 26) - 1u));
+                    hit = descend_pt(A, qv, hp, hn, hmax, seen, tr, v, key, lane);
+                }
+                const int prev = pend_p;
+                resolve();
+                __syncwarp();
+                if (evaluated >= need) break;
+                if (hit.p >= 0 && hit.p == prev) hit.word |= 1u << (prev & 31);
+                pend_p = hit.p;
+                pend_w = hit.word;
+            }
+            resolve();
+            __syncwarp();
+        } else {
+            for (int t = 0; t < A.T && evaluated < need; ++t)
+                scan_leaf(t, descend(A, qv, hp, hn, hmax, t, 0, 0.f, lane));
+            while (evaluated < need && hn > 0) {
+                const uint64_t e = q_pop(hp, hn, lane);
+                const float key = __uint_as_float((uint32_t)(e >> 32));
+                const int tr = (int)((e >> 26) & 63u);
+                const int v = (int)(e & ((1u << 26) - 1u));
+                scan_leaf(tr, descend(A, qv, hp, hn, hmax, tr, v, key, lane));
+            }
         }
         // the queue ran dry with fewer than k points: lowest-index unseen points
         for (int64_t b = 0; evaluated < A.k && b < A.N; b += 32) {
@@ -414,6 +511,8 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     a.split_val = f.split_val;
     a.perm = f.perm;
     a.leaf_ofs = f.leaf_ofs;
+    a.leaf_pt = f.leaf_pt;
+    a.leaf_size = f.leaf_size;
     a.qlist = qlist;
     a.nq = nq;
     a.idx_out = idx_out;

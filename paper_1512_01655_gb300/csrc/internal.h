@@ -76,6 +76,7 @@ struct ForestView {
     float *split_val;
     int32_t *perm;
     int32_t *leaf_ofs;
+    int32_t *leaf_pt;
 };
 int forest_depth(int64_t N, int leaf_size);
 size_t forest_layout(int64_t N, int trees, int leaf_size, atsne_forest_layout_t *out);
