@@ -5,14 +5,17 @@
 // The visiting order never depends on distances (no pruning by the current
 // k-th distance), so each query runs in two phases inside one warp:
 //   1. traversal: queue pops, descents and de-duplication only. A descent
-//      fetches the next five levels below the current node in one round (one
-//      node per lane, 31 independent loads), then walks them with shuffles, so
-//      a 17-level descent costs four memory round trips instead of 17. Queue
-//      entries are 64-bit words (key bits << 32 | tree << 26 | node), so one
-//      integer compare orders them by (key, tree, node). A full queue keeps an
-//      upper bound of its maximum, so most rejected pushes cost one compare.
-//      The points collected are appended to a per-warp list in the workspace.
-//   2. evaluation: the warp streams the collected points' rows four at a time
+//      round covers five levels below the current node: each lane loads one
+//      of the 31 subtree nodes and compares the query with its split, one
+//      ballot gives the path, and the far children along it are pushed, so a
+//      17-level descent costs four memory round trips and no serial
+//      level-by-level walk. Queue entries are 64-bit words (key bits << 32 |
+//      tree << 26 | node), so one integer compare orders them by (key, tree,
+//      node). The queue is spread over the 32 lanes (ColQueue): pops and
+//      evictions take a warp-wide min or max reduction and one
+//      warp-cooperative column rescan, insertions one store. The points
+//      collected are appended to a per-warp list in the workspace.
+//   2. evaluation: the warp streams the collected points' rows eight at a time
 //      (FP32 direct differences, float4 loads when D % 4 == 0) and keeps the k
 //      best in shared memory under the (distance, index) order.
 // Warps fetch queries from a global counter; the grid is sized by occupancy.
@@ -57,177 +60,213 @@ __device__ __forceinline__ uint64_t qpack(float key, int tree, int node) {
     return ((uint64_t)__float_as_uint(key) << 32) | ((uint64_t)tree << 26) | (uint64_t)node;
 }
 
-// Bounded min-queue: when full, a new entry replaces the largest (a leaf of the
-// heap) if it is smaller. `hmax` is an upper bound of the entries held (raised
-// on every insertion, lowered to the exact maximum whenever one is searched),
-// so a full queue rejects x >= hmax without searching. All lanes call it with
-// the same arguments; lane 0 writes.
-__device__ void q_push(uint64_t *hp, int &hn, uint64_t &hmax, int cap, uint64_t x, int lane) {
-    int pos;
-    if (hn == cap) {
-        if (x >= hmax) return;
-        uint64_t mx = 0;
-        int mp = -1;
-        for (int i = cap / 2 + lane; i < cap; i += 32) {
-            const uint64_t e = hp[i];
-            if (mp < 0 || e > mx) {
-                mx = e;
-                mp = i;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t om = __shfl_xor_sync(0xffffffffu, mx, o);
-            const int op = __shfl_xor_sync(0xffffffffu, mp, o);
-            if (op >= 0 && (mp < 0 || om > mx)) {
-                mx = om;
-                mp = op;
-            }
-        }
-        hmax = mx;
-        if (!(x < mx)) return;
-        pos = mp;
-    } else {
-        pos = hn++;
-        if (x > hmax) hmax = x;
-    }
-    if (lane == 0) {
-        while (pos > 0) {
-            const int par = (pos - 1) >> 1;
-            const uint64_t pe = hp[par];
-            if (!(x < pe)) break;
-            hp[pos] = pe;
-            pos = par;
-        }
-        hp[pos] = x;
-    }
-    __syncwarp();
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+    const uint32_t hi = __reduce_min_sync(FULL, (uint32_t)(v >> 32));
+    const uint32_t lo = __reduce_min_sync(FULL, (uint32_t)(v >> 32) == hi ? (uint32_t)v : 0xffffffffu);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(v >> 32));
+    const uint32_t lo = __reduce_max_sync(FULL, (uint32_t)(v >> 32) == hi ? (uint32_t)v : 0u);
+    return ((uint64_t)hi << 32) | lo;
 }
 
-__device__ uint64_t q_pop(uint64_t *hp, int &hn, int lane) {
-    const uint64_t top = hp[0];
-    __syncwarp();
-    const int n = --hn;
-    if (lane == 0 && n > 0) {
-        const uint64_t x = hp[n];
-        int pos = 0;
-        for (;;) {
-            int c = 2 * pos + 1;
-            if (c >= n) break;
-            uint64_t cv = hp[c];
-            if (c + 1 < n) {
-                const uint64_t cr = hp[c + 1];
-                if (cr < cv) {
-                    cv = cr;
-                    ++c;
-                }
-            }
-            if (!(cv < x)) break;
-            hp[pos] = cv;
-            pos = c;
+// Bounded min-queue of distinct packed entries, spread over 32 columns in
+// shared memory (lane l owns col[l * stride ...], filled in slots 0..cnt-1).
+// Each lane keeps its column's count, minimum and maximum (and their slots) in
+// registers; the warp keeps the total and an upper bound of the maximum.
+//   pop:    the minimum over the lanes' minima; its column is closed up and
+//           rescanned by the whole warp.
+//   push:   into a column with room (round robin), or, when the queue is full,
+//           in place of the maximum if smaller, that column then rescanned.
+// All lanes call each operation with the same arguments. As entries are
+// distinct, the queue holds the same set as any bounded min-queue that evicts
+// its maximum, given the same pushes and pops.
+struct ColQueue {
+    uint64_t *col;
+    int stride, cap;
+    int lcap, cnt;    // this lane's column: capacity, entries
+    uint64_t mn, mx;  // this lane's minimum (~0 if empty) and maximum (0 if empty)
+    int mns, mxs;     // their slots
+    int n;            // entries held (warp-uniform)
+    uint64_t hmax;    // upper bound of the maximum held (warp-uniform)
+    int rr;           // next column tried by an insertion (warp-uniform)
+};
+
+__device__ __forceinline__ void cq_init(ColQueue &q, uint64_t *col, int cap, int lane) {
+    q.col = col;
+    q.cap = cap;
+    q.stride = (cap + 31) >> 5;
+    q.lcap = (cap - lane + 31) >> 5;
+    q.cnt = 0;
+    q.mn = ~0ull;
+    q.mx = 0;
+    q.mns = q.mxs = -1;
+    q.n = 0;
+    q.hmax = 0;
+    q.rr = 0;
+}
+
+// Lane w's column minimum (MIN) or maximum and its slot, found by the whole warp.
+template <bool MIN>
+__device__ __forceinline__ void cq_rescan(ColQueue &q, int w, int lane) {
+    const int c = __shfl_sync(FULL, q.cnt, w);
+    const uint64_t *cw = q.col + w * q.stride;
+    uint64_t best = MIN ? ~0ull : 0ull;
+    int bs = -1;
+    for (int s = lane; s < c; s += 32) {
+        const uint64_t e = cw[s];
+        if (MIN ? e < best : e > best) {
+            best = e;
+            bs = s;
         }
-        hp[pos] = x;
+    }
+    const uint64_t g = MIN ? warp_min_u64(best) : warp_max_u64(best);
+    const unsigned hit = __ballot_sync(FULL, bs >= 0 && best == g);
+    const int slot = hit ? __shfl_sync(FULL, bs, __ffs(hit) - 1) : -1;
+    if (lane == w) {
+        if (MIN) {
+            q.mn = hit ? g : ~0ull;
+            q.mns = slot;
+        } else {
+            q.mx = hit ? g : 0ull;
+            q.mxs = slot;
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t cq_pop(ColQueue &q, int lane) {
+    const uint64_t top = warp_min_u64(q.mn);
+    const int w = __ffs(__ballot_sync(FULL, q.cnt > 0 && q.mn == top)) - 1;
+    if (lane == w) {
+        uint64_t *cw = q.col + w * q.stride;
+        const int last = q.cnt - 1, hole = q.mns;
+        if (hole != last) cw[hole] = cw[last];
+        if (q.mxs == last) q.mxs = hole;
+        q.cnt = last;
+        if (last == 0) {
+            q.mx = 0;
+            q.mxs = -1;
+        }
     }
     __syncwarp();
+    cq_rescan<true>(q, w, lane);
+    --q.n;
     return top;
 }
 
-// Descend tree `tr` from node v (queue key `key`) to a leaf, pushing the far
-// child of every node passed; returns the leaf index. Node ids fit in 26 bits.
-__device__ int descend(const FqArgs &A, const float *qv, uint64_t *hp, int &hn, uint64_t &hmax,
-                       int tr, int v, float key, int lane) {
-    const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
-    const float *sv = A.split_val + (int64_t)tr * A.n_int;
-    const int n_int = (int)A.n_int;
-    while (v < n_int) {
-        const int lv = 31 - __clz(v + 1);
-        const int d = min(SUB_DEPTH, A.h - lv);
-        int dim = 0;
-        float val = 0.f;
-        if (lane < (1 << d) - 1) {
-            const int j = 31 - __clz(lane + 1);
-            const int node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
-            dim = sd[node];
-            val = sv[node];
+__device__ __forceinline__ void cq_push(ColQueue &q, uint64_t x, int lane) {
+    if (q.n == q.cap) {
+        if (x >= q.hmax) return;
+        const uint64_t m = warp_max_u64(q.mx);
+        q.hmax = m;
+        if (x >= m) return;
+        const int w = __ffs(__ballot_sync(FULL, q.cnt > 0 && q.mx == m)) - 1;
+        if (lane == w) {
+            q.col[w * q.stride + q.mxs] = x;
+            if (x < q.mn) {
+                q.mn = x;
+                q.mns = q.mxs;
+            }
         }
-        int c = 0, vg = v;
-#pragma unroll 1
-        for (int j = 0; j < d; ++j) {
-            const int cd = __shfl_sync(0xffffffffu, dim, c);
-            const float cs = __shfl_sync(0xffffffffu, val, c);
-            const float qd = qv[cd];
-            const bool left = qd < cs;
-            const float diff = __fsub_rn(qd, cs);
-            const float fk = __fadd_rn(key, __fmul_rn(diff, diff));
-            if (!isinf(fk)) q_push(hp, hn, hmax, A.qcap, qpack(fk, tr, left ? 2 * vg + 2 : 2 * vg + 1), lane);
-            c = left ? 2 * c + 1 : 2 * c + 2;
-            vg = left ? 2 * vg + 1 : 2 * vg + 2;
-        }
-        v = vg;
+        __syncwarp();
+        cq_rescan<false>(q, w, lane);
+        q.hmax = warp_max_u64(q.mx);
+        return;
     }
-    return v - n_int;
+    const unsigned nf = __ballot_sync(FULL, q.cnt < q.lcap);
+    const unsigned rot = __funnelshift_r(nf, nf, q.rr);
+    const int t = (q.rr + __ffs(rot) - 1) & 31;
+    if (lane == t) {
+        q.col[t * q.stride + q.cnt] = x;
+        if (x < q.mn) {
+            q.mn = x;
+            q.mns = q.cnt;
+        }
+        if (x > q.mx) {
+            q.mx = x;
+            q.mxs = q.cnt;
+        }
+        ++q.cnt;
+    }
+    q.rr = (t + 1) & 31;
+    ++q.n;
+    if (x > q.hmax) q.hmax = x;
 }
 
-// One point per leaf: descend as above and return the reached leaf's point (-1
-// if empty) and the seen-bitmap word holding it. The last round fetches the
-// points of all leaves of its subtree together with the split data; the word is
-// loaded after the walk and only read at the next step.
-struct LeafHit {
-    int p;
-    uint32_t word;
-};
+// Pushes the entries of the lanes with `valid` set, in lane order. With no
+// pop in between, the queue ends up holding the same set in any order; when
+// it is full at the start, entries at or above the bound are rejected at once.
+__device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool valid, int lane) {
+    unsigned m = __ballot_sync(FULL, valid && (q.n < q.cap || e < q.hmax));
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        cq_push(q, __shfl_sync(FULL, e, j), lane);
+    }
+}
 
-__device__ LeafHit descend_pt(const FqArgs &A, const float *qv, uint64_t *hp, int &hn,
-                              uint64_t &hmax, const uint32_t *seen, int tr, int v, float key,
-                              int lane) {
+// Descend tree `tr` from node v (queue key `key`) to a leaf, pushing the far
+// child of every node passed; returns the leaf index. Each round covers up to
+// five levels: lane j < 31 loads node j of the five-level subtree below the
+// current node and compares the query with its split, a ballot of the
+// outcomes gives the path, and lane j < (levels) pushes the far child of the
+// path's node on level j. With PT (one point per leaf) the last round also
+// fetches the points of the subtree's leaves and `pt` returns the reached
+// leaf's point (-1 if empty). Node ids fit in 26 bits.
+template <bool PT>
+__device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueue &q, int tr, int v,
+                                       float key, int lane, int &pt) {
     const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
     const float *sv = A.split_val + (int64_t)tr * A.n_int;
     const int32_t *lpt = A.leaf_pt + ((int64_t)tr << A.h);
     const int n_int = (int)A.n_int;
-    int p = -1;
-    if (v >= n_int) {
-        p = lpt[v - n_int];
-    } else {
-        while (v < n_int) {
-            const int lv = 31 - __clz(v + 1);
-            const int d = min(SUB_DEPTH, A.h - lv);
-            const bool last = lv + d == A.h;
-            int dim = 0, lp = -1;
-            float val = 0.f;
-            if (lane < (1 << d) - 1) {
-                const int j = 31 - __clz(lane + 1);
-                const int node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
-                dim = sd[node];
-                val = sv[node];
-            }
-            if (last && lane < (1 << d)) lp = lpt[((v + 1) << d) - 1 + lane - n_int];
-            int c = 0, vg = v;
-#pragma unroll 1
-            for (int j = 0; j < d; ++j) {
-                const int cd = __shfl_sync(0xffffffffu, dim, c);
-                const float cs = __shfl_sync(0xffffffffu, val, c);
-                const float qd = qv[cd];
-                const bool left = qd < cs;
-                const float diff = __fsub_rn(qd, cs);
-                const float fk = __fadd_rn(key, __fmul_rn(diff, diff));
-                if (!isinf(fk)) q_push(hp, hn, hmax, A.qcap, qpack(fk, tr, left ? 2 * vg + 2 : 2 * vg + 1), lane);
-                c = left ? 2 * c + 1 : 2 * c + 2;
-                vg = left ? 2 * vg + 1 : 2 * vg + 2;
-            }
-            if (last) p = __shfl_sync(0xffffffffu, lp, c + 1 - (1 << d));
-            v = vg;
+    pt = -1;
+    if (PT && v >= n_int) pt = lpt[v - n_int];
+    while (v < n_int) {
+        const int lv = 31 - __clz(v + 1);
+        const int d = min(SUB_DEPTH, A.h - lv);
+        const bool last = lv + d == A.h;
+        int node = 0, lp = -1;
+        bool left = false;
+        float fk = INFINITY;
+        if (lane < (1 << d) - 1) {
+            const int j = 31 - __clz(lane + 1);
+            node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
+            const float qd = qv[sd[node]];
+            const float val = sv[node];
+            left = qd < val;
+            const float diff = __fsub_rn(qd, val);
+            fk = __fadd_rn(key, __fmul_rn(diff, diff));
         }
+        if (PT && last && lane < (1 << d)) lp = lpt[((v + 1) << d) - 1 + lane - n_int];
+        const unsigned lm = __ballot_sync(FULL, left);
+        int c = 0, my_c = 0;
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+            if (lane == j) my_c = c;
+            c = ((lm >> c) & 1u) ? 2 * c + 1 : 2 * c + 2;
+        }
+        const float pk = __shfl_sync(FULL, fk, my_c);
+        const int pn = __shfl_sync(FULL, node, my_c);
+        const uint64_t e = qpack(pk, tr, ((lm >> my_c) & 1u) ? 2 * pn + 2 : 2 * pn + 1);
+        cq_push_lanes(q, e, lane < d && !isinf(pk), lane);
+        const int o = c + 1 - (1 << d);  // offset of the reached node on its level
+        if (PT && last) pt = __shfl_sync(FULL, lp, o);
+        v = ((v + 1) << d) - 1 + o;
     }
-    return LeafHit{p, p >= 0 ? __ldcg(&seen[p >> 5]) : 0u};
+    return v - n_int;
 }
 
 __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
     extern __shared__ __align__(16) unsigned char fq_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const size_t heap_b = ((size_t)A.qcap * 8 + 15) & ~size_t(15);
+    const size_t heap_b = (size_t)((A.qcap + 31) >> 5) * 32 * 8;
     const size_t q_b = ((size_t)A.D * 4 + 15) & ~size_t(15);
     unsigned char *base = fq_smem + w * (heap_b + q_b + FQ_KCAP * 8);
-    uint64_t *hp = reinterpret_cast<uint64_t *>(base);
+    uint64_t *qcol = reinterpret_cast<uint64_t *>(base);
     float *qv = reinterpret_cast<float *>(base + heap_b);
     float *td = reinterpret_cast<float *>(base + heap_b + q_b);
     int *tj = reinterpret_cast<int *>(td + FQ_KCAP);
@@ -259,8 +298,8 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
             marked[0] = (int32_t)qi;
         }
         int64_t n_marked = 1, evaluated = 0;
-        int hn = 0;
-        uint64_t hmax = 0;
+        ColQueue q;
+        cq_init(q, qcol, A.qcap, lane);
         __syncwarp();
 
         // ---- phase 1: traversal ----
@@ -304,37 +343,40 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
                 pend_p = -1;
             };
             for (int t = 0;;) {
-                LeafHit hit;
+                int hp_ = -1;
                 if (t < A.T) {
-                    hit = descend_pt(A, qv, hp, hn, hmax, seen, t, 0, 0.f, lane);
+                    descend<true>(A, qv, q, t, 0, 0.f, lane, hp_);
                     ++t;
                 } else {
-                    if (hn == 0) break;
-                    const uint64_t e = q_pop(hp, hn, lane);
+                    if (q.n == 0) break;
+                    const uint64_t e = cq_pop(q, lane);
                     const float key = __uint_as_float((uint32_t)(e >> 32));
                     const int tr = (int)((e >> 26) & 63u);
                     const int v = (int)(e & ((1u << 26) - 1u));
-                    hit = descend_pt(A, qv, hp, hn, hmax, seen, tr, v, key, lane);
+                    descend<true>(A, qv, q, tr, v, key, lane, hp_);
                 }
+                // the word is loaded now and only read at the next step
+                uint32_t hw = hp_ >= 0 ? __ldcg(&seen[hp_ >> 5]) : 0u;
                 const int prev = pend_p;
                 resolve();
                 __syncwarp();
                 if (evaluated >= need) break;
-                if (hit.p >= 0 && hit.p == prev) hit.word |= 1u << (prev & 31);
-                pend_p = hit.p;
-                pend_w = hit.word;
+                if (hp_ >= 0 && hp_ == prev) hw |= 1u << (prev & 31);
+                pend_p = hp_;
+                pend_w = hw;
             }
             resolve();
             __syncwarp();
         } else {
+            int unused;
             for (int t = 0; t < A.T && evaluated < need; ++t)
-                scan_leaf(t, descend(A, qv, hp, hn, hmax, t, 0, 0.f, lane));
-            while (evaluated < need && hn > 0) {
-                const uint64_t e = q_pop(hp, hn, lane);
+                scan_leaf(t, descend<false>(A, qv, q, t, 0, 0.f, lane, unused));
+            while (evaluated < need && q.n > 0) {
+                const uint64_t e = cq_pop(q, lane);
                 const float key = __uint_as_float((uint32_t)(e >> 32));
                 const int tr = (int)((e >> 26) & 63u);
                 const int v = (int)(e & ((1u << 26) - 1u));
-                scan_leaf(tr, descend(A, qv, hp, hn, hmax, tr, v, key, lane));
+                scan_leaf(tr, descend<false>(A, qv, q, tr, v, key, lane, unused));
             }
         }
         // the queue ran dry with fewer than k points: lowest-index unseen points
@@ -450,7 +492,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
 }
 
 size_t fq_smem_bytes(int D, int qcap) {
-    return FQ_WARPS * ((((size_t)qcap * 8 + 15) & ~size_t(15)) + (((size_t)D * 4 + 15) & ~size_t(15)) +
+    return FQ_WARPS * ((size_t)((qcap + 31) >> 5) * 32 * 8 + (((size_t)D * 4 + 15) & ~size_t(15)) +
                        FQ_KCAP * 8);
 }
 

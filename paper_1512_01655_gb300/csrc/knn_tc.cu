@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 #include <float.h>
 #include <limits.h>
+#include <math.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -56,6 +57,7 @@ constexpr int TC_EPI = 128;
 constexpr uint64_t WAIT_NS = 1000000000ull;
 constexpr int MERGE_WARPS = 4;
 constexpr int RCAP = 256;        // candidates re-ranked per row at most
+constexpr int MSTAGE = 1024;     // keys below tau staged per row for the merge's select
 constexpr int NBUCKET = 48;      // distance buckets per row: 6 octaves, 8 per octave
 
 struct Cand {
@@ -114,22 +116,36 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Adds one to hist[bin] for every active lane; must be called by the whole
+// warp. Lanes that share a bin are combined into one shared-memory atomic: the
+// keys of one query row mostly share their leading digits, so plain per-lane
+// atomics would serialise 32 ways on a single bin.
+__device__ __forceinline__ void warp_hist_add(uint32_t *hist, uint32_t bin, bool active) {
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (active) {
+        const unsigned peers = __match_any_sync(act, bin);
+        if ((peers & lanemask_lt()) == 0) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    }
+}
+
 // Radix select over (key) of `count` candidates fetched by get(i): returns the
 // order-preserving bits of the kth smallest key (1-based) and, in n_less, how
-// many keys are strictly smaller. Warp-cooperative; hist is 256 words of
-// shared memory private to the warp.
-template <typename Get>
-__device__ uint32_t warp_select(Get get, int count, int kth, uint32_t *hist, int lane, int &n_less) {
+// many keys are strictly smaller. Warp-cooperative (count and kth uniform over
+// the warp); hist is 256 words of shared memory private to the warp.
+// visit(fn) calls fn(valid, key) for every candidate, in iterations uniform
+// over the warp.
+template <typename Visit>
+__device__ uint32_t warp_select_visit(Visit visit, int kth, uint32_t *hist, int lane, int &n_less) {
     uint32_t prefix = 0, mask = 0;
     int rem = kth;
     n_less = 0;
     for (int shift = 24; shift >= 0; shift -= 8) {
         for (int i = lane; i < 256; i += 32) hist[i] = 0u;
         __syncwarp();
-        for (int i = lane; i < count; i += 32) {
-            const uint32_t u = float_key(get(i));
-            if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
-        }
+        visit([&](bool valid, float key) {
+            const uint32_t u = float_key(key);
+            warp_hist_add(hist, (u >> shift) & 255u, valid && (u & mask) == prefix);
+        });
         __syncwarp();
         uint32_t c[8], sum = 0;
 #pragma unroll
@@ -170,6 +186,18 @@ __device__ uint32_t warp_select(Get get, int count, int kth, uint32_t *hist, int
         __syncwarp();
     }
     return prefix;
+}
+
+template <typename Get>
+__device__ uint32_t warp_select(Get get, int count, int kth, uint32_t *hist, int lane, int &n_less) {
+    return warp_select_visit(
+        [&](auto fn) {
+            for (int base = 0; base < count; base += 32) {
+                const int i = base + lane;
+                fn(i < count, i < count ? get(i) : 0.f);
+            }
+        },
+        kth, hist, lane, n_less);
 }
 
 // ---------------------------------------------------------------------------
@@ -587,6 +615,8 @@ __device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st
 
 __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams p) {
     __shared__ uint32_t hist_s[MERGE_WARPS][256];
+    __shared__ float stage_k[MERGE_WARPS][MSTAGE];
+    __shared__ int stage_j[MERGE_WARPS][MSTAGE];
     __shared__ float rd[MERGE_WARPS][RCAP];
     __shared__ int rj[MERGE_WARPS][RCAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -615,109 +645,142 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
     bool good = !ovf && total >= p.k && qid >= 0 && qid < p.N;
     int nr = 0;
     if (good) {
-        // k-th smallest key over all splits (splits hold their entries contiguously)
-        // k-th smallest key over all splits: radix select, splits walked in order
-        int n_less = 0;
+        // One pass over the buffers stages every (key, index) at or below
+        // tau_min + 2E. When at least k keys lie below tau_min, the k-th
+        // smallest key theta lies among them, and every candidate the re-rank
+        // takes (key <= theta + 2E) is staged; otherwise the buffers are
+        // walked again.
+        const float E = row_error_bound(p, p.stats[qid]);
+        const float slim = tau_min + 2.f * E;
         uint32_t *hist = hist_s[w];
-        uint32_t prefix = 0, mask = 0;
-        int rem = p.k;
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            for (int i = lane; i < 256; i += 32) hist[i] = 0u;
-            __syncwarp();
+        float *sk = stage_k[w];
+        int *sj = stage_j[w];
+        int ns = 0, nlt = 0;
+        for (int u = 0; u < S; ++u) {
+            const int c = mt[u].x;
+            const Cand *b = cb + (size_t)u * p.cap;
+            for (int base = 0; base < c; base += 64) {
+                const int i = base + 2 * lane;  // two candidates per lane, one 16-byte load
+                Cand e0{INFINITY, -1}, e1{INFINITY, -1};
+                if (i + 1 < c) {
+                    const float4 v = __ldcs(reinterpret_cast<const float4 *>(b + i));
+                    e0 = Cand{v.x, __float_as_int(v.y)};
+                    e1 = Cand{v.z, __float_as_int(v.w)};
+                } else if (i < c) {
+                    e0 = b[i];
+                }
+                nlt += (e0.key < tau_min) + (e1.key < tau_min);
+                const bool t0 = e0.key <= slim, t1 = e1.key <= slim;
+                const unsigned m0 = __ballot_sync(0xffffffffu, t0);
+                const unsigned m1 = __ballot_sync(0xffffffffu, t1);
+                const unsigned lt = lanemask_lt();
+                const int pos = ns + __popc(m0 & lt) + __popc(m1 & lt);
+                if (t0 && pos < MSTAGE) {
+                    sk[pos] = e0.key;
+                    sj[pos] = e0.idx;
+                }
+                if (t1 && pos + t0 < MSTAGE) {
+                    sk[pos + t0] = e1.key;
+                    sj[pos + t0] = e1.idx;
+                }
+                ns += __popc(m0) + __popc(m1);
+            }
+        }
+        nlt = (int)__reduce_add_sync(0xffffffffu, (unsigned)nlt);
+        __syncwarp();
+        int n_less = 0;
+        const bool staged = nlt >= p.k && ns <= MSTAGE;
+        uint32_t prefix;
+        if (staged) {
+            prefix = warp_select([&](int i) { return sk[i]; }, ns, p.k, hist, lane, n_less);
+        } else {
+            prefix = warp_select_visit(
+                [&](auto fn) {
+                    for (int u = 0; u < S; ++u) {
+                        const int c = mt[u].x;
+                        const Cand *b = cb + (size_t)u * p.cap;
+                        for (int base = 0; base < c; base += 32) {
+                            const int i = base + lane;
+                            fn(i < c, i < c ? b[i].key : 0.f);
+                        }
+                    }
+                },
+                p.k, hist, lane, n_less);
+        }
+        const float theta = key_of_bits(prefix);
+        const float lim = theta + 2.f * E;
+        // collect the re-rank set
+        auto take_batch = [&](bool take, int idx) {
+            const unsigned tm = __ballot_sync(0xffffffffu, take);
+            const int pos = nr + __popc(tm & lanemask_lt());
+            if (take && pos < RCAP) rj[w][pos] = idx;
+            nr += __popc(tm);
+        };
+        if (staged) {
+            for (int base = 0; base < ns; base += 32) {
+                const int i = base + lane;
+                take_batch(i < ns && sk[i] <= lim, i < ns ? sj[i] : -1);
+            }
+        } else {
             for (int u = 0; u < S; ++u) {
                 const int c = mt[u].x;
                 const Cand *b = cb + (size_t)u * p.cap;
-                for (int i = lane; i < c; i += 32) {
-                    const uint32_t uk = float_key(b[i].key);
-                    if ((uk & mask) == prefix) atomicAdd(&hist[(uk >> shift) & 255u], 1u);
+                for (int base = 0; base < c; base += 32) {
+                    const int i = base + lane;
+                    Cand e{INFINITY, -1};
+                    if (i < c) e = b[i];
+                    take_batch(i < c && e.key <= lim, e.idx);
                 }
             }
-            __syncwarp();
-            uint32_t cc[8], sum = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                cc[q] = hist[8 * lane + q];
-                sum += cc[q];
-            }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const uint32_t excl = incl - sum;
-            const unsigned who = __ballot_sync(0xffffffffu, excl < (uint32_t)rem && (uint32_t)rem <= incl);
-            const int src = who ? __ffs(who) - 1 : 31;
-            int bin = 255;
-            uint32_t before = 0;
-            if (lane == src) {
-                uint32_t a = excl;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (a + cc[q] >= (uint32_t)rem) {
-                        bin = 8 * lane + q;
-                        before = a;
-                        break;
-                    }
-                    a += cc[q];
-                }
-            }
-            bin = __shfl_sync(0xffffffffu, bin, src);
-            before = __shfl_sync(0xffffffffu, before, src);
-            rem -= (int)before;
-            n_less += (int)before;
-            prefix |= (uint32_t)bin << shift;
-            mask |= 255u << shift;
-            __syncwarp();
         }
-        const float theta = key_of_bits(prefix);
-        const float E = row_error_bound(p, p.stats[qid]);
-        const float lim = theta + 2.f * E;
-        // collect the re-rank set
-        for (int u = 0; u < S && good; ++u) {
-            const int c = mt[u].x;
-            const Cand *b = cb + (size_t)u * p.cap;
-            for (int base = 0; base < c; base += 32) {
-                const int i = base + lane;
-                Cand e{INFINITY, -1};
-                if (i < c) e = b[i];
-                const bool take = i < c && e.key <= lim;
-                const unsigned tm = __ballot_sync(0xffffffffu, take);
-                const int pos = nr + __popc(tm & lanemask_lt());
-                if (take && pos < RCAP) rj[w][pos] = e.idx;
-                nr += __popc(tm);
-            }
-            if (nr > RCAP) good = false;
-        }
+        if (nr > RCAP) good = false;
         __syncwarp();
         if (good && nr >= p.k) {
-            // exact FP32 direct-difference distances
+            // exact FP32 direct-difference distances, four candidates at a time
             const float *xq = p.X + (int64_t)qid * p.D;
-            for (int t = 0; t < nr; ++t) {
-                const float *xc = p.X + (int64_t)rj[w][t] * p.D;
-                float a = 0.f;
-                if ((p.D & 3) == 0) {
+            const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0;
+            for (int t0 = 0; t0 < nr; t0 += 4) {
+                const float *xc[4];
+                float a[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xc[u] = t0 + u < nr ? p.X + (int64_t)rj[w][t0 + u] * p.D : nullptr;
+                    a[u] = 0.f;
+                }
+                if (vec4) {
                     const float4 *q4 = reinterpret_cast<const float4 *>(xq);
-                    const float4 *c4 = reinterpret_cast<const float4 *>(xc);
                     for (int d = lane; d < (p.D >> 2); d += 32) {
-                        const float4 qv = q4[d], cv = c4[d];
-                        float df = qv.x - cv.x;
-                        a = fmaf(df, df, a);
-                        df = qv.y - cv.y;
-                        a = fmaf(df, df, a);
-                        df = qv.z - cv.z;
-                        a = fmaf(df, df, a);
-                        df = qv.w - cv.w;
-                        a = fmaf(df, df, a);
+                        const float4 qv = q4[d];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (!xc[u]) continue;
+                            const float4 cv = reinterpret_cast<const float4 *>(xc[u])[d];
+                            float df = qv.x - cv.x;
+                            a[u] = fmaf(df, df, a[u]);
+                            df = qv.y - cv.y;
+                            a[u] = fmaf(df, df, a[u]);
+                            df = qv.z - cv.z;
+                            a[u] = fmaf(df, df, a[u]);
+                            df = qv.w - cv.w;
+                            a[u] = fmaf(df, df, a[u]);
+                        }
                     }
                 } else {
                     for (int d = lane; d < p.D; d += 32) {
-                        const float df = xq[d] - xc[d];
-                        a = fmaf(df, df, a);
+                        const float qv = xq[d];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (!xc[u]) continue;
+                            const float df = qv - xc[u][d];
+                            a[u] = fmaf(df, df, a[u]);
+                        }
                     }
                 }
-                a = warp_sum(a);
-                if (lane == 0) rd[w][t] = a;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float r = warp_sum(a[u]);
+                    if (lane == 0 && xc[u]) rd[w][t0 + u] = r;
+                }
             }
             for (int t = nr + lane; t < RCAP; t += 32) {
                 rd[w][t] = INFINITY;
@@ -800,7 +863,15 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
     int ks = rerank_k > 0 ? rerank_k : (pl.passes == 3 ? k + 38 : 2 * k);
     if (ks < k) ks = k;
     pl.ksel = ks;
-    pl.cap = 8 * ks + TC_BN;
+    // A streaming top-ksel over n columns in random order admits about
+    // ksel (1 + ln(n / ksel)) keys; the bucketed threshold about twice that.
+    // The buffer holds 2.5x the model so that the exact compaction of a full
+    // buffer (a radix select per row) stays rare.
+    const double ncol = (double)hmin(N, (int64_t)pl.cols_per_split);
+    const double model = ks * (1.0 + log(fmax(1.0, ncol / ks)));
+    int64_t cap = (int64_t)ceil(2.5 * model) + TC_BN;
+    if (cap < 8 * ks + TC_BN) cap = 8 * ks + TC_BN;
+    pl.cap = (int)((cap + 31) / 32 * 32);
     return pl;
 }
 
