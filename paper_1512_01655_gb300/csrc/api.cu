@@ -222,6 +222,14 @@ size_t knn_ws(Carver &c, int64_t N, int32_t D, int32_t k, int64_t S, const atsne
     return c.bytes();
 }
 
+// Workspaces and forests are carved at 256-byte offsets from their base, and
+// kernels read parts of them with 16-byte vector loads.
+atsne_status check_base(const void *p, const char *what) {
+    if (reinterpret_cast<uintptr_t>(p) & 255)
+        return set_error(ATSNE_EINVAL, "%s: base address not 256-byte aligned", what);
+    return ATSNE_OK;
+}
+
 // Selections of at least this many rows are refined on the tensor-core path.
 constexpr int64_t REFINE_TC_MIN_ROWS = 128;
 
@@ -309,6 +317,7 @@ atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *quer
     knn_ws(c, N, D, k, queries ? S : 0, o, &forest, &sub, &sub_bytes, &plan, &tws);
     if (c.bytes() > 0 && (!workspace || ws_bytes < c.bytes()))
         return set_error(ATSNE_ENOMEM, "knn: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    if ((st = check_base(workspace, "knn workspace"))) return st;
     if (queries && (st = check_indices(queries, S, N, stream))) return st;
     if (exact_on_tensor_cores(o, k))  // the prep kernel checks X for non-finite values
         return knn_exact_tc(X, N, D, queries, nq, k, plan, tws, idx_out, d2_out, stream);
@@ -348,6 +357,7 @@ atsne_status atsne_symmetrize(const int32_t *idx, const float *P_cond, int64_t N
     symmetrize_workspace(c, N, k, &w);
     if (!workspace || ws_bytes < c.bytes())
         return set_error(ATSNE_ENOMEM, "symmetrize: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    if (atsne_status st = check_base(workspace, "symmetrize workspace")) return st;
     return symmetrize_launch(idx, P_cond, N, k, row_ptr, col, val, nnz_dev, w,
                              static_cast<cudaStream_t>(stream));
 }
@@ -372,6 +382,7 @@ atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int
     refine_ws(c, N, D, S, k, &ti, &td, &tp, &tb, &plan, &tws);
     if (!workspace || ws_bytes < c.bytes())
         return set_error(ATSNE_ENOMEM, "refine: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    if ((st = check_base(workspace, "refine workspace"))) return st;
     if ((st = check_indices(subset, S, N, stream))) return st;
     if (S >= REFINE_TC_MIN_ROWS && k <= 200) {  // the prep kernel checks X for non-finite values
         if ((st = knn_exact_tc(X, N, D, subset, S, k, plan, tws, ti, td, stream))) return st;
@@ -414,6 +425,8 @@ atsne_status atsne_forest_build(const float *X, int64_t N, int32_t D, const atsn
     if (!X || !forest || N < 2 || N > INT32_MAX || D < 1) return set_error(ATSNE_EINVAL, "forest build: bad arguments");
     if (forest_bytes < forest_layout(N, o.trees, o.leaf_size, nullptr))
         return set_error(ATSNE_ENOMEM, "forest build: forest buffer too small");
+    if ((st = check_base(forest, "forest build: forest"))) return st;
+    if ((st = check_base(workspace, "forest build: workspace"))) return st;
     if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
     return forest_build_launch(X, forest_view(forest, N, D, o), workspace, ws_bytes, stream);
 }
@@ -431,6 +444,8 @@ atsne_status atsne_forest_query(const float *X, int64_t N, int32_t D, const void
     if ((st = validate_knn_opts(o))) return st;
     if (!forest || !idx_out || !d2_out) return set_error(ATSNE_EINVAL, "forest query: NULL pointer");
     if (queries && S < 0) return set_error(ATSNE_EINVAL, "forest query: S < 0");
+    if ((st = check_base(forest, "forest query: forest"))) return st;
+    if ((st = check_base(workspace, "forest query: workspace"))) return st;
     const int64_t nq = queries ? S : N;
     if (nq == 0) return ATSNE_OK;
     if (queries && (st = check_indices(queries, S, N, stream))) return st;

@@ -30,6 +30,7 @@ struct TcWs {
     float *nrm = nullptr, *stats = nullptr;
     unsigned *gmax = nullptr;
     char *cand = nullptr, *meta = nullptr;
+    unsigned *row_hist = nullptr;
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
 };
 TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k);

@@ -20,15 +20,22 @@
 //              distances in 64 buckets (8 per octave below an upper bound of
 //              any distance of the row); tau is lowered to the upper edge of
 //              the bucket in which the count reaches ksel, a valid bound on
-//              the ksel-th distance within 9%. Only a buffer about to
-//              overflow is compacted exactly (warp radix select).
-//   knn_merge  one warp per query: the k-th smallest key over all splits,
-//              every candidate within 2E of it (E bounds the key error, see
-//              row_error_bound) re-ranked by FP32 direct differences, and a
-//              certificate: if the k-th exact distance is below
-//              ||x_i||^2 + min(tau) - E, no point outside the buffers can
-//              belong to the k nearest, and the row is exact. Rows that fail
-//              are listed for the brute-force kernel.
+//              the ksel-th distance within 9%. Buffers are sized for about
+//              2.5x the survivors of a streaming top-ksel, so the exact
+//              compaction of a full buffer (warp radix select) is rare.
+//              When few query rows leave the SMs idle, the columns are cut
+//              into splits (units ordered split-major); the splits of a row
+//              then also count into one histogram per row in global memory,
+//              so each split filters with the bound of the whole row.
+//   knn_merge  one warp per query: one pass stages the keys below the
+//              splits' lowest tau (+2E) in shared memory; there the k-th
+//              smallest key is selected, every candidate within 2E of it (E
+//              bounds the key error, see row_error_bound) is re-ranked by
+//              FP32 direct differences, and a certificate is checked: if the
+//              k-th exact distance is below ||x_i||^2 + min(tau) - E, no
+//              point outside the buffers can belong to the k nearest, and
+//              the row is exact. Rows that fail are listed for the
+//              brute-force kernel.
 //
 // Every wait on an mbarrier is bounded (1 s); on expiry the CTA raises the
 // device status word, stops issuing work, drains its own copies and MMAs and
@@ -103,6 +110,7 @@ struct TcParams {
     int ksel, cap;
     Cand *cand;            // [Q][splits][cap]
     int4 *meta;            // [Q][splits]: count, tau bits, overflow
+    unsigned *row_hist;    // [Q][NBUCKET]: buffered distances of all splits by bucket (splits > 1)
     int *status;
 };
 
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             bool armed[C::STAGES];
             for (int i = 0; i < C::STAGES; ++i) armed[i] = false;
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const int rt = u / p.splits, sp = u % p.splits;
+                const int rt = u % p.row_tiles, sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
                 for (int64_t ct = c0; ct < c1 && ok; ct += TC_BN) {
@@ -346,7 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const int sp = u % p.splits;
+                const int sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
                 for (int64_t ct = c0; ct < c1 && ok; ct += TC_BN) {
@@ -408,7 +416,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
         uint32_t acc_phase = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            const int rt = u / p.splits, sp = u % p.splits;
+            const int rt = u % p.row_tiles, sp = u / p.row_tiles;
             const int64_t c0 = (int64_t)sp * p.cols_per_split;
             const int64_t c1 = min(p.N, c0 + p.cols_per_split);
             const int64_t row = (int64_t)rt * TC_BM + quarter * 32 + lane;
@@ -421,6 +429,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             const float nx = qv ? p.nrm[qid] : 0.f;
             const float ai = sqrtf(nx), amax = __uint_as_float(p.gmax[0]);
             int top = (int)(__float_as_uint((ai + amax) * (ai + amax) * 1.0001f + 1e-30f) >> 20);
+            // With column splits, every split of a row also counts its buffered
+            // distances in one histogram per row in global memory, on the fixed
+            // grid below t0: the splits cover disjoint columns and the counts
+            // only grow, so the bucket where the summed count reaches ksel
+            // bounds the row's ksel-th distance for all of them.
+            unsigned *gh = (p.splits > 1 && qv) ? p.row_hist + (size_t)row * NBUCKET : nullptr;
+            const int gbase = top - (NBUCKET - 1);
+            auto global_tau = [&]() {
+                int cum = 0, b = 0;
+                for (; b < NBUCKET; b += 4) {
+                    const uint4 h4 = __ldcg(reinterpret_cast<const uint4 *>(gh + b));
+                    if (cum + (int)(h4.x + h4.y + h4.z + h4.w) >= p.ksel) {
+                        if ((cum += h4.x) >= p.ksel) break;
+                        ++b;
+                        if ((cum += h4.y) >= p.ksel) break;
+                        ++b;
+                        if ((cum += h4.z) >= p.ksel) break;
+                        ++b;
+                        break;
+                    }
+                    cum += h4.x + h4.y + h4.z + h4.w;
+                }
+                if (b < NBUCKET) tau = fminf(tau, __uint_as_float((uint32_t)(gbase + b + 1) << 20) - nx);
+            };
+            if (gh) global_tau();
             uint16_t *dh = &s.dhist[warp - 2][0][lane];
             for (int bk = 0; bk < NBUCKET; ++bk) dh[bk * 32] = 0;
             // corpus norms of the first tile of the unit, then one tile ahead
@@ -495,6 +528,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                             int bk = (int)(__float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20) - (top - (NBUCKET - 1));
                             bk = min(max(bk, 0), NBUCKET - 1);
                             dh[bk * 32] += 1;
+                            if (gh) {
+                                int gb = (int)(__float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20) - gbase;
+                                atomicAdd(gh + min(max(gb, 0), NBUCKET - 1), 1u);
+                            }
                         } while (mask);
                     }
                 }
@@ -519,6 +556,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     }
                     since = 0;
                 }
+                if (gh) global_tau();
                 // a buffer that the next tile could overflow is compacted exactly
                 unsigned m = __ballot_sync(0xffffffffu, cnt > p.cap - TC_BN);
                 if (m) __syncwarp();
@@ -552,7 +590,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     __syncwarp();
                     if (lane == l) {
                         cnt = wpos;
-                        tau = key_of_bits(tk);
+                        tau = fminf(tau, key_of_bits(tk));  // never raised: dropped keys stay above it
                     }
                 }
                 if ((compacted >> lane) & 1u) {
@@ -656,9 +694,11 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         float *sk = stage_k[w];
         int *sj = stage_j[w];
         int ns = 0, nlt = 0;
-        for (int u = 0; u < S; ++u) {
-            const int c = mt[u].x;
-            const Cand *b = cb + (size_t)u * p.cap;
+        for (int u0 = 0; u0 < S; u0 += 32) {
+          const int cu = u0 + lane < S ? mt[u0 + lane].x : 0;  // the counts of 32 splits at once
+          for (int j = 0; j < 32 && u0 + j < S; ++j) {
+            const int c = __shfl_sync(0xffffffffu, cu, j);
+            const Cand *b = cb + (size_t)(u0 + j) * p.cap;
             for (int base = 0; base < c; base += 64) {
                 const int i = base + 2 * lane;  // two candidates per lane, one 16-byte load
                 Cand e0{INFINITY, -1}, e1{INFINITY, -1};
@@ -685,6 +725,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
                 }
                 ns += __popc(m0) + __popc(m1);
             }
+          }
         }
         nlt = (int)__reduce_add_sync(0xffffffffu, (unsigned)nlt);
         __syncwarp();
@@ -839,6 +880,7 @@ size_t tc_smem_bytes() {
     return sizeof(TcSmem<PASSES>) + 1024;
 }
 static_assert(sizeof(TcSmem<1>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
+static_assert(NBUCKET % 4 == 0, "row histograms are read as uint4");
 static_assert(sizeof(TcSmem<3>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
 
 }  // namespace
@@ -886,6 +928,7 @@ size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcP
     w.gmax = c.take<unsigned>(4);
     w.cand = c.take<char>((size_t)Q * pl.splits * pl.cap * sizeof(Cand));
     w.meta = c.take<char>((size_t)Q * pl.splits * sizeof(int4));
+    w.row_hist = pl.splits > 1 ? c.take<unsigned>((size_t)Q * NBUCKET) : nullptr;
     w.flag_rows = c.take<int32_t>((size_t)Q);
     w.flag_count = c.take<int32_t>(1);
     if (ws) *ws = w;
@@ -898,6 +941,8 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     int *status = device_status_word();
     cudaError_t e = cudaMemsetAsync(w.gmax, 0, 4 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.flag_count, 0, sizeof(int32_t), stream);
+    if (e == cudaSuccess && w.row_hist)
+        e = cudaMemsetAsync(w.row_hist, 0, (size_t)Q * NBUCKET * sizeof(unsigned), stream);
     if (e != cudaSuccess) return cuda_error(e, "knn_tc memset");
     auto *hi = reinterpret_cast<__nv_bfloat16 *>(w.hi);
     auto *lo = reinterpret_cast<__nv_bfloat16 *>(w.lo);
@@ -938,6 +983,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     p.cap = pl.cap;
     p.cand = reinterpret_cast<Cand *>(w.cand);
     p.meta = reinterpret_cast<int4 *>(w.meta);
+    p.row_hist = w.row_hist;
     p.status = status;
     const int units = pl.row_tiles * pl.splits;
     const int grid = (int)hmin(units, num_sms());

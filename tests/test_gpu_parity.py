@@ -307,6 +307,19 @@ def test_out_of_range_subset_is_reported(at):
         at.atsne_check()
 
 
+def test_misaligned_workspace_is_refused(at):
+    import ctypes
+    X = to_dev(synth.gaussian_mixture(300, 8, seed=1))
+    o = at.knn_opts()
+    n = at.workspace_bytes(at.OP_KNN, 300, 8, 10, 0, o)
+    ws = torch.empty(n + 256, dtype=torch.uint8, device=X.device)
+    idx = torch.empty((300, 10), dtype=torch.int32, device=X.device)
+    d2 = torch.empty((300, 10), dtype=torch.float32, device=X.device)
+    rc = at.lib().atsne_knn(at._p(X), 300, 8, None, 0, 10, ctypes.byref(o), at._p(idx), at._p(d2),
+                            ctypes.c_void_p(ws.data_ptr() + 16), n, at._stream(None))
+    assert rc == at.ATSNE_EINVAL
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_mnist_shaped_full_size_sampled(at, precision):
     # full-size workload (N=70000, D=784): the launch the benchmark times,
