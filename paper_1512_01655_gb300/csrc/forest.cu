@@ -68,7 +68,6 @@ namespace {
 
 constexpr int CHUNK = 1024;        // points per partial-sum chunk
 constexpr int SMEM_SORT = 4096;    // keys per shared-memory bitonic block
-constexpr int CHOOSE_THREADS = 256;
 
 // ---- counter-based SplitMix64 (Steele, Lea, Flood 2014): output number c ----
 __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
@@ -162,80 +161,317 @@ __global__ void iota_kernel(int32_t *perm, int64_t N, int T) {
     if (g < N * T) perm[g] = (int32_t)(g % N);
 }
 
+// ---- the sums of x and x^2 per dimension over a range of points ----
+//
+// A block of ACC_THREADS threads streams the rows of points pt[b..e) through
+// shared memory in tiles of TP rows (two buffers, cp.async), W columns at a
+// time; thread t accumulates columns t, t + ACC_THREADS, ... of the slice, in
+// point order, into float pairs (acc_point).
+constexpr int ACC_THREADS = 256;
+constexpr int ACC_MAXDPT = 8;                        // columns per thread per slice
+constexpr int ACC_SLICE = ACC_THREADS * ACC_MAXDPT;  // columns per slice
+constexpr int ACC_TILE_FLOATS = 12288;               // floats per tile buffer (48 KB)
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+struct SliceGeom {
+    int W, Wp, TP;  // columns, padded row length (multiple of 4), rows per tile
+};
+__host__ __device__ inline SliceGeom slice_geom(int D) {
+    SliceGeom g;
+    g.W = D < ACC_SLICE ? D : ACC_SLICE;
+    g.Wp = (g.W + 3) & ~3;
+    g.TP = ACC_TILE_FLOATS / g.Wp;
+    if (g.TP > 32) g.TP = 32;
+    return g;
+}
+
+// Accumulates columns [d0, d0 + W) of the points pt[b..e) into a[] (column
+// d0 + threadIdx.x + j * ACC_THREADS in a[j]). `tile` holds 2 * TP * Wp floats.
+// Called by the whole block; returns with the tile buffers free.
+__device__ void acc_slice(const float *__restrict__ X, int D, const int32_t *__restrict__ pt, int64_t b,
+                          int64_t e, int d0, const SliceGeom &g, int W, float *tile,
+                          float4 (&a)[ACC_MAXDPT]) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < ACC_MAXDPT; ++j) a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool v16 = (D & 3) == 0 && (d0 & 3) == 0 && (W & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    const int64_t n = e - b;
+    const int64_t nt = (n + g.TP - 1) / g.TP;
+    auto issue = [&](int64_t k) {
+        float *buf = tile + (k & 1) * g.TP * g.Wp;
+        const int64_t q0 = b + k * g.TP;
+        const int rows = (int)(e - q0 < g.TP ? e - q0 : g.TP);
+        // rows are split into groups of `per` copies; thread tid takes copy
+        // tid % per of rows tid / per, tid / per + step, ...
+        const int per = v16 ? W >> 2 : W;
+        const int step = ACC_THREADS / per > 0 ? ACC_THREADS / per : 1;
+        for (int c0 = 0; c0 < per; c0 += ACC_THREADS) {
+            const int c = c0 + (per >= ACC_THREADS ? tid : tid % per);
+            const int r0 = per >= ACC_THREADS ? 0 : tid / per;
+            if (c >= per || r0 >= step) continue;
+            for (int r = r0; r < rows; r += step) {
+                const float *src = X + (int64_t)pt[q0 + r] * D + d0;
+                if (v16)
+                    cp_async16(buf + r * g.Wp + 4 * c, src + 4 * c);
+                else
+                    cp_async4(buf + r * g.Wp + c, src + c);
+            }
+        }
+        cp_async_commit();
+    };
+    if (nt > 0) issue(0);
+    for (int64_t k = 0; k < nt; ++k) {
+        if (k + 1 < nt) {
+            issue(k + 1);
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        __syncthreads();
+        const float *buf = tile + (k & 1) * g.TP * g.Wp;
+        const int rows = (int)(e - (b + k * g.TP) < g.TP ? e - (b + k * g.TP) : g.TP);
+        for (int r = 0; r < rows; ++r) {
+#pragma unroll
+            for (int j = 0; j < ACC_MAXDPT; ++j) {
+                const int c = tid + j * ACC_THREADS;
+                if (c < W) acc_point(a[j], buf[r * g.Wp + c]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Partial sums over CHUNK-point pieces of big nodes: grid (chunks, nodes, trees).
-__global__ void __launch_bounds__(CHOOSE_THREADS)
+__global__ void __launch_bounds__(ACC_THREADS)
 partial_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
                const int32_t *__restrict__ leaf_ofs, int h, int l, int chunks,
                float4 *__restrict__ part) {
+    extern __shared__ __align__(16) float acc_tile[];
     const int ch = blockIdx.x, m = blockIdx.y, t = blockIdx.z;
     int64_t lo, hi;
     node_segment(leaf_ofs, h, l, m, lo, hi);
     const int64_t b = lo + (int64_t)ch * CHUNK, e = (hi < b + CHUNK ? hi : b + CHUNK);
     const int32_t *pt = perm + (int64_t)t * N;
     float4 *out = part + (((int64_t)t * gridDim.y + m) * chunks + ch) * D;
-    for (int d = threadIdx.x; d < D; d += blockDim.x) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t q = b; q < e; ++q) acc_point(a, X[(int64_t)pt[q] * D + d]);
-        out[d] = a;
+    const SliceGeom g = slice_geom(D);
+    for (int d0 = 0; d0 < D; d0 += g.W) {
+        const int W = D - d0 < g.W ? D - d0 : g.W;
+        float4 a[ACC_MAXDPT];
+        acc_slice(X, D, pt, b, e, d0, g, W, acc_tile, a);
+#pragma unroll
+        for (int j = 0; j < ACC_MAXDPT; ++j) {
+            const int c = threadIdx.x + j * ACC_THREADS;
+            if (c < W) out[d0 + c] = a[j];
+        }
     }
 }
 
-// Per node: spreads, top-V candidates, counter-based choice of the split dim.
-__global__ void __launch_bounds__(CHOOSE_THREADS)
+// ---- top-V dimensions by spread ----
+// Each lane keeps its best eight (spread, dim) pairs in registers, sorted by
+// spread_greater; V rounds of a warp-wide argmax over the lanes' heads then
+// give the V best in order.
+struct Top8 {
+    float2 s[8];
+    int d[8];
+};
+__device__ __forceinline__ void top8_init(Top8 &t) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        t.s[r] = make_float2(-INFINITY, -INFINITY);
+        t.d[r] = INT_MAX;
+    }
+}
+__device__ __forceinline__ void top8_insert(Top8 &t, float2 s, int d) {
+    if (!spread_greater(s, d, t.s[7], t.d[7])) return;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (spread_greater(s, d, t.s[r], t.d[r])) {
+            const float2 ts = t.s[r];
+            const int td = t.d[r];
+            t.s[r] = s;
+            t.d[r] = d;
+            s = ts;
+            d = td;
+        }
+    }
+}
+// The split dimension of node v of tree t: one of the V best (counter-based
+// draw). Whole warp; returns it on every lane.
+__device__ __forceinline__ int choose_from_top8(Top8 &t, int nV, uint64_t seed, int tree, int64_t v) {
+    const uint64_t rr = splitmix64_at(seed, ((uint64_t)tree << 32) + (uint64_t)v + 1u);
+    const int want = (int)(rr % (uint64_t)nV);
+    int pick = 0;
+    for (int r = 0; r < nV; ++r) {
+        float2 best = t.s[0];
+        int bd = t.d[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ox = __shfl_xor_sync(0xffffffffu, best.x, o);
+            const float oy = __shfl_xor_sync(0xffffffffu, best.y, o);
+            const int od = __shfl_xor_sync(0xffffffffu, bd, o);
+            if (od != INT_MAX && (bd == INT_MAX || spread_greater(make_float2(ox, oy), od, best, bd))) {
+                best = make_float2(ox, oy);
+                bd = od;
+            }
+        }
+        if (r == want) pick = bd;
+        if (t.d[0] == bd) {  // the winning lane drops its head
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                t.s[q] = t.s[q + 1];
+                t.d[q] = t.d[q + 1];
+            }
+            t.s[7] = make_float2(-INFINITY, -INFINITY);
+            t.d[7] = INT_MAX;
+        }
+    }
+    return pick;
+}
+
+// Nodes of fewer than two points have every spread zero: the V best are the
+// dimensions 0..V-1 (ties go to the smaller dimension).
+__device__ __forceinline__ int choose_degenerate(int nV, uint64_t seed, int tree, int64_t v) {
+    const uint64_t rr = splitmix64_at(seed, ((uint64_t)tree << 32) + (uint64_t)v + 1u);
+    return (int)(rr % (uint64_t)nV);
+}
+
+// Per node (one block): spreads, top-V candidates, counter-based choice of
+// the split dim. Nodes above CHUNK points combine their partial sums in order.
+__global__ void __launch_bounds__(ACC_THREADS)
 choose_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
               const int32_t *__restrict__ leaf_ofs, int h, int l, int chunks,
               const float4 *__restrict__ part, int V, uint64_t seed, int32_t *__restrict__ split_dim,
               float *__restrict__ split_val, int64_t n_int) {
-    extern __shared__ float2 spread[];  // [D]
+    extern __shared__ __align__(16) float acc_tile[];
+    const SliceGeom g = slice_geom(D);
+    float2 *spread = reinterpret_cast<float2 *>(acc_tile + 2 * g.TP * g.Wp);  // [D]
     const int m = blockIdx.x, t = blockIdx.y;
     const int64_t v = ((int64_t)1 << l) - 1 + m;
     int64_t lo, hi;
     node_segment(leaf_ofs, h, l, m, lo, hi);
+    const int nV = V < D ? V : D;
+    if (hi - lo < 2) {
+        if (threadIdx.x == 0) {
+            split_dim[(int64_t)t * n_int + v] = choose_degenerate(nV, seed, t, v);
+            split_val[(int64_t)t * n_int + v] = INFINITY;
+        }
+        return;
+    }
     const float n = (float)(hi - lo);
     const int32_t *pt = perm + (int64_t)t * N;
-    for (int d = threadIdx.x; d < D; d += blockDim.x) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (chunks > 1) {
+    if (chunks > 1) {
+        for (int d = threadIdx.x; d < D; d += blockDim.x) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 *src = part + ((int64_t)t * gridDim.x + m) * chunks * D + d;
             for (int c = 0; c < chunks; ++c) acc_pair(a, src[(int64_t)c * D]);
-        } else {
-            for (int64_t q = lo; q < hi; ++q) acc_point(a, X[(int64_t)pt[q] * D + d]);
+            spread[d] = spread_of(a, n);
         }
-        spread[d] = spread_of(a, n);
+    } else {
+        for (int d0 = 0; d0 < D; d0 += g.W) {
+            const int W = D - d0 < g.W ? D - d0 : g.W;
+            float4 a[ACC_MAXDPT];
+            acc_slice(X, D, pt, lo, hi, d0, g, W, acc_tile, a);
+#pragma unroll
+            for (int j = 0; j < ACC_MAXDPT; ++j) {
+                const int c = threadIdx.x + j * ACC_THREADS;
+                if (c < W) spread[d0 + c] = spread_of(a[j], n);
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        const int nV = V < D ? V : D;
-        int chosen[8];
-        for (int r = 0; r < nV; ++r) {
-            float2 best = make_float2(-INFINITY, -INFINITY);
-            int bd = INT_MAX;
-            for (int d = lane; d < D; d += 32) {
-                bool taken = false;
-                for (int u = 0; u < r; ++u) taken |= (chosen[u] == d);
-                if (!taken && spread_greater(spread[d], d, best, bd)) {
-                    best = spread[d];
-                    bd = d;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ox = __shfl_xor_sync(0xffffffffu, best.x, o);
-                const float oy = __shfl_xor_sync(0xffffffffu, best.y, o);
-                const int od = __shfl_xor_sync(0xffffffffu, bd, o);
-                if (od != INT_MAX && (bd == INT_MAX || spread_greater(make_float2(ox, oy), od, best, bd))) {
-                    best = make_float2(ox, oy);
-                    bd = od;
-                }
-            }
-            chosen[r] = bd;
-        }
-        if (lane == 0) {
-            const uint64_t rr = splitmix64_at(seed, ((uint64_t)t << 32) + (uint64_t)v + 1u);
-            split_dim[(int64_t)t * n_int + v] = chosen[rr % (uint64_t)nV];
+        Top8 tp;
+        top8_init(tp);
+        for (int d = threadIdx.x; d < D; d += 32) top8_insert(tp, spread[d], d);
+        const int dim = choose_from_top8(tp, nV, seed, t, v);
+        if (threadIdx.x == 0) {
+            split_dim[(int64_t)t * n_int + v] = dim;
             split_val[(int64_t)t * n_int + v] = INFINITY;
         }
+    }
+}
+
+// Nodes of at most SMALL_NODE points: one warp per node; lane l accumulates
+// the dimensions l, l + 32, ... (eight at a time, loads of all of a point's
+// eight values in flight together) and keeps its top eight.
+constexpr int SMALL_NODE = 64;
+constexpr int SMALL_WARPS = 8;
+__global__ void __launch_bounds__(SMALL_WARPS * 32)
+choose_small_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
+                    const int32_t *__restrict__ leaf_ofs, int h, int l, int V, uint64_t seed,
+                    int32_t *__restrict__ split_dim, float *__restrict__ split_val, int64_t n_int) {
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (int64_t)blockIdx.x * SMALL_WARPS + (threadIdx.x >> 5);
+    const int t = blockIdx.y;
+    if (m >= ((int64_t)1 << l)) return;
+    const int64_t v = ((int64_t)1 << l) - 1 + m;
+    int64_t lo, hi;
+    node_segment(leaf_ofs, h, l, m, lo, hi);
+    const int nV = V < D ? V : D;
+    if (hi - lo < 2) {
+        if (lane == 0) {
+            split_dim[(int64_t)t * n_int + v] = choose_degenerate(nV, seed, t, v);
+            split_val[(int64_t)t * n_int + v] = INFINITY;
+        }
+        return;
+    }
+    const float n = (float)(hi - lo);
+    const int cnt = (int)(hi - lo);
+    const int32_t *pt = perm + (int64_t)t * N;
+    // the node's points, lane r holding points r and r + 32
+    const int p0 = lane < cnt ? pt[lo + lane] : 0;
+    const int p1 = lane + 32 < cnt ? pt[lo + lane + 32] : 0;
+    Top8 tp;
+    top8_init(tp);
+    for (int d0 = 0; d0 < D; d0 += 256) {
+        float4 a[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // two points' loads in flight, accumulated in point order
+        for (int q = 0; q < cnt; q += 2) {
+            const int pa = __shfl_sync(0xffffffffu, q < 32 ? p0 : p1, q & 31);
+            const int pb = __shfl_sync(0xffffffffu, q + 1 < 32 ? p0 : p1, (q + 1) & 31);
+            const float *ra = X + (int64_t)pa * D + d0 + lane;
+            const float *rb = X + (int64_t)pb * D + d0 + lane;
+            const bool two = q + 1 < cnt;
+            float xa[8], xb[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bool in = d0 + lane + 32 * j < D;
+                xa[j] = in ? __ldg(ra + 32 * j) : 0.f;
+                xb[j] = in && two ? __ldg(rb + 32 * j) : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (d0 + lane + 32 * j < D) {
+                    acc_point(a[j], xa[j]);
+                    if (two) acc_point(a[j], xb[j]);
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int d = d0 + lane + 32 * j;
+            if (d < D) top8_insert(tp, spread_of(a[j], n), d);
+        }
+    }
+    const int dim = choose_from_top8(tp, nV, seed, t, v);
+    if (lane == 0) {
+        split_dim[(int64_t)t * n_int + v] = dim;
+        split_val[(int64_t)t * n_int + v] = INFINITY;
     }
 }
 
@@ -408,26 +644,36 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
                             256, 0, stream, f.N, h, f.leaf_ofs));
     ATSNE_TRY(launch_kernel("forest_iota", iota_kernel, ceil_div(f.N * T, 256), 256, 0, stream, f.perm,
                             f.N, T));
-    const size_t choose_smem = sizeof(float2) * (size_t)f.D;
-    if (choose_smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(choose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)choose_smem);
-        if (e != cudaSuccess) return cuda_error(e, "forest choose attribute");
-    }
+    const SliceGeom sg = slice_geom(f.D);
+    const size_t tile_smem = sizeof(float) * 2 * (size_t)sg.TP * sg.Wp;
+    const size_t choose_smem = tile_smem + sizeof(float2) * (size_t)f.D;
+    if (choose_smem > 227 * 1024)
+        return set_error(ATSNE_EUNSUPPORTED, "forest build: D=%d needs %zu B of shared memory", f.D,
+                         choose_smem);
+    cudaError_t ea = cudaFuncSetAttribute(choose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)choose_smem);
+    if (ea == cudaSuccess)
+        ea = cudaFuncSetAttribute(partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tile_smem);
+    if (ea != cudaSuccess) return cuda_error(ea, "forest choose attribute");
     for (int l = 0; l < h; ++l) {
         const int64_t nodes = (int64_t)1 << l;
         const int64_t nmax = (f.N + nodes - 1) >> l;
         const int chunks = ceil_div(nmax, CHUNK);
-        int threads = f.D >= CHOOSE_THREADS ? CHOOSE_THREADS : ((f.D + 31) / 32) * 32;
-        if (threads < 32) threads = 32;
         if (chunks > 1)
             ATSNE_TRY(launch_kernel("forest_partial", partial_kernel, dim3(chunks, (unsigned)nodes, T),
-                                    threads, 0, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
-                                    w.part));
-        ATSNE_TRY(launch_kernel("forest_choose", choose_kernel, dim3((unsigned)nodes, T), threads,
-                                choose_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
-                                w.part, f.top_var_dims, f.seed, f.split_dim, f.split_val,
-                                f.n_internal));
+                                    ACC_THREADS, tile_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h,
+                                    l, chunks, w.part));
+        if (nmax <= SMALL_NODE)
+            ATSNE_TRY(launch_kernel("forest_choose", choose_small_kernel,
+                                    dim3((unsigned)ceil_div(nodes, SMALL_WARPS), T), SMALL_WARPS * 32, 0,
+                                    stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, f.top_var_dims,
+                                    f.seed, f.split_dim, f.split_val, f.n_internal));
+        else
+            ATSNE_TRY(launch_kernel("forest_choose", choose_kernel, dim3((unsigned)nodes, T), ACC_THREADS,
+                                    choose_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
+                                    w.part, f.top_var_dims, f.seed, f.split_dim, f.split_val,
+                                    f.n_internal));
         const int64_t P = pow2_at_least(nmax);
         const int64_t total = nodes * P * T;
         ATSNE_TRY(launch_kernel("forest_keys", keys_kernel, ceil_div(total, 256), 256, 0, stream, X,
