@@ -163,14 +163,12 @@ __global__ void iota_kernel(int32_t *perm, int64_t N, int T) {
 
 // ---- the sums of x and x^2 per dimension over a range of points ----
 //
-// A block of ACC_THREADS threads streams the rows of points pt[b..e) through
-// shared memory in tiles of TP rows (two buffers, cp.async), W columns at a
-// time; thread t accumulates columns t, t + ACC_THREADS, ... of the slice, in
-// point order, into float pairs (acc_point).
-constexpr int ACC_THREADS = 256;
-constexpr int ACC_MAXDPT = 8;                        // columns per thread per slice
-constexpr int ACC_SLICE = ACC_THREADS * ACC_MAXDPT;  // columns per slice
-constexpr int ACC_TILE_FLOATS = 12288;               // floats per tile buffer (48 KB)
+// A block streams the rows of points pt[b..e) through shared memory in tiles
+// of TP rows (two buffers, cp.async), W <= ACC_SLICE columns at a time;
+// thread t accumulates columns 4t .. 4t+3 of the slice (one 16-byte shared
+// load per row), in point order, into float pairs (acc_point).
+constexpr int ACC_SLICE = 1024;         // columns per slice (256 threads x 4)
+constexpr int ACC_TILE_FLOATS = 12288;  // floats per tile buffer (48 KB)
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -197,16 +195,20 @@ __host__ __device__ inline SliceGeom slice_geom(int D) {
     if (g.TP > 32) g.TP = 32;
     return g;
 }
+// Threads of the blocks that call acc_slice: four columns each.
+inline int acc_threads(int D) {
+    const SliceGeom g = slice_geom(D);
+    return ((g.Wp / 4 + 31) / 32) * 32;
+}
 
 // Accumulates columns [d0, d0 + W) of the points pt[b..e) into a[] (column
-// d0 + threadIdx.x + j * ACC_THREADS in a[j]). `tile` holds 2 * TP * Wp floats.
-// Called by the whole block; returns with the tile buffers free.
+// d0 + 4 * threadIdx.x + i in a[i]). `tile` holds 2 * TP * Wp floats. Called
+// by the whole block; returns with the tile buffers free.
 __device__ void acc_slice(const float *__restrict__ X, int D, const int32_t *__restrict__ pt, int64_t b,
-                          int64_t e, int d0, const SliceGeom &g, int W, float *tile,
-                          float4 (&a)[ACC_MAXDPT]) {
-    const int tid = threadIdx.x;
+                          int64_t e, int d0, const SliceGeom &g, int W, float *tile, float4 (&a)[4]) {
+    const int tid = threadIdx.x, nth = blockDim.x;
 #pragma unroll
-    for (int j = 0; j < ACC_MAXDPT; ++j) a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < 4; ++i) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool v16 = (D & 3) == 0 && (d0 & 3) == 0 && (W & 3) == 0 &&
                      (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     const int64_t n = e - b;
@@ -215,13 +217,13 @@ __device__ void acc_slice(const float *__restrict__ X, int D, const int32_t *__r
         float *buf = tile + (k & 1) * g.TP * g.Wp;
         const int64_t q0 = b + k * g.TP;
         const int rows = (int)(e - q0 < g.TP ? e - q0 : g.TP);
-        // rows are split into groups of `per` copies; thread tid takes copy
-        // tid % per of rows tid / per, tid / per + step, ...
+        // row r is `per` copies; thread tid takes copy tid % per of rows
+        // tid / per, tid / per + step, ...
         const int per = v16 ? W >> 2 : W;
-        const int step = ACC_THREADS / per > 0 ? ACC_THREADS / per : 1;
-        for (int c0 = 0; c0 < per; c0 += ACC_THREADS) {
-            const int c = c0 + (per >= ACC_THREADS ? tid : tid % per);
-            const int r0 = per >= ACC_THREADS ? 0 : tid / per;
+        const int step = nth / per > 0 ? nth / per : 1;
+        for (int c0 = 0; c0 < per; c0 += nth) {
+            const int c = c0 + (per >= nth ? tid : tid % per);
+            const int r0 = per >= nth ? 0 : tid / per;
             if (c >= per || r0 >= step) continue;
             for (int r = r0; r < rows; r += step) {
                 const float *src = X + (int64_t)pt[q0 + r] * D + d0;
@@ -233,6 +235,8 @@ __device__ void acc_slice(const float *__restrict__ X, int D, const int32_t *__r
         }
         cp_async_commit();
     };
+    const int c4 = 4 * tid;
+    const bool full = c4 + 4 <= W;
     if (nt > 0) issue(0);
     for (int64_t k = 0; k < nt; ++k) {
         if (k + 1 < nt) {
@@ -242,13 +246,21 @@ __device__ void acc_slice(const float *__restrict__ X, int D, const int32_t *__r
             cp_async_wait0();
         }
         __syncthreads();
-        const float *buf = tile + (k & 1) * g.TP * g.Wp;
+        const float *buf = tile + (k & 1) * g.TP * g.Wp + c4;
         const int rows = (int)(e - (b + k * g.TP) < g.TP ? e - (b + k * g.TP) : g.TP);
-        for (int r = 0; r < rows; ++r) {
+        if (full) {
+            for (int r = 0; r < rows; ++r) {
+                const float4 x = *reinterpret_cast<const float4 *>(buf + r * g.Wp);
+                acc_point(a[0], x.x);
+                acc_point(a[1], x.y);
+                acc_point(a[2], x.z);
+                acc_point(a[3], x.w);
+            }
+        } else if (c4 < W) {
+            for (int r = 0; r < rows; ++r) {
 #pragma unroll
-            for (int j = 0; j < ACC_MAXDPT; ++j) {
-                const int c = tid + j * ACC_THREADS;
-                if (c < W) acc_point(a[j], buf[r * g.Wp + c]);
+                for (int i = 0; i < 4; ++i)
+                    if (c4 + i < W) acc_point(a[i], buf[r * g.Wp + i]);
             }
         }
         __syncthreads();
@@ -256,7 +268,7 @@ __device__ void acc_slice(const float *__restrict__ X, int D, const int32_t *__r
 }
 
 // Partial sums over CHUNK-point pieces of big nodes: grid (chunks, nodes, trees).
-__global__ void __launch_bounds__(ACC_THREADS)
+__global__ void __launch_bounds__(256)
 partial_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
                const int32_t *__restrict__ leaf_ofs, int h, int l, int chunks,
                float4 *__restrict__ part) {
@@ -270,12 +282,12 @@ partial_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ p
     const SliceGeom g = slice_geom(D);
     for (int d0 = 0; d0 < D; d0 += g.W) {
         const int W = D - d0 < g.W ? D - d0 : g.W;
-        float4 a[ACC_MAXDPT];
+        float4 a[4];
         acc_slice(X, D, pt, b, e, d0, g, W, acc_tile, a);
 #pragma unroll
-        for (int j = 0; j < ACC_MAXDPT; ++j) {
-            const int c = threadIdx.x + j * ACC_THREADS;
-            if (c < W) out[d0 + c] = a[j];
+        for (int i = 0; i < 4; ++i) {
+            const int c = 4 * threadIdx.x + i;
+            if (c < W) out[d0 + c] = a[i];
         }
     }
 }
@@ -351,7 +363,7 @@ __device__ __forceinline__ int choose_degenerate(int nV, uint64_t seed, int tree
 
 // Per node (one block): spreads, top-V candidates, counter-based choice of
 // the split dim. Nodes above CHUNK points combine their partial sums in order.
-__global__ void __launch_bounds__(ACC_THREADS)
+__global__ void __launch_bounds__(256)
 choose_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
               const int32_t *__restrict__ leaf_ofs, int h, int l, int chunks,
               const float4 *__restrict__ part, int V, uint64_t seed, int32_t *__restrict__ split_dim,
@@ -383,12 +395,12 @@ choose_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ pe
     } else {
         for (int d0 = 0; d0 < D; d0 += g.W) {
             const int W = D - d0 < g.W ? D - d0 : g.W;
-            float4 a[ACC_MAXDPT];
+            float4 a[4];
             acc_slice(X, D, pt, lo, hi, d0, g, W, acc_tile, a);
 #pragma unroll
-            for (int j = 0; j < ACC_MAXDPT; ++j) {
-                const int c = threadIdx.x + j * ACC_THREADS;
-                if (c < W) spread[d0 + c] = spread_of(a[j], n);
+            for (int i = 0; i < 4; ++i) {
+                const int c = 4 * threadIdx.x + i;
+                if (c < W) spread[d0 + c] = spread_of(a[i], n);
             }
         }
     }
@@ -406,10 +418,50 @@ choose_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ pe
 }
 
 // Nodes of at most SMALL_NODE points: one warp per node; lane l accumulates
-// the dimensions l, l + 32, ... (eight at a time, loads of all of a point's
-// eight values in flight together) and keeps its top eight.
+// the dimensions l, l + 32, ... (eight at a time, two points' loads in flight
+// together, in point order) and keeps its top eight.
 constexpr int SMALL_NODE = 64;
 constexpr int SMALL_WARPS = 8;
+
+// Columns d0 + lane + 32 j (j < 8) over the node's points; FULL: all 256 in range.
+template <bool FULL>
+__device__ __forceinline__ void small_group(const float *__restrict__ X, int D, int d0, int lane, int cnt,
+                                            int p0, int p1, float n, Top8 &tp) {
+    float4 a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < cnt; q += 2) {
+        const int pa = __shfl_sync(0xffffffffu, q < 32 ? p0 : p1, q & 31);
+        const int pb = __shfl_sync(0xffffffffu, q + 1 < 32 ? p0 : p1, (q + 1) & 31);
+        const float *ra = X + (int64_t)pa * D + d0 + lane;
+        const float *rb = X + (int64_t)pb * D + d0 + lane;
+        float xa[8], xb[8];
+        if (q + 1 < cnt) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bool in = FULL || d0 + lane + 32 * j < D;
+                xa[j] = in ? __ldg(ra + 32 * j) : 0.f;
+                xb[j] = in ? __ldg(rb + 32 * j) : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                acc_point(a[j], xa[j]);
+                acc_point(a[j], xb[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xa[j] = (FULL || d0 + lane + 32 * j < D) ? __ldg(ra + 32 * j) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc_point(a[j], xa[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int d = d0 + lane + 32 * j;
+        if (FULL || d < D) top8_insert(tp, spread_of(a[j], n), d);
+    }
+}
+
 __global__ void __launch_bounds__(SMALL_WARPS * 32)
 choose_small_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
                     const int32_t *__restrict__ leaf_ofs, int h, int l, int V, uint64_t seed,
@@ -437,37 +489,9 @@ choose_small_kernel(const float *__restrict__ X, int D, const int32_t *__restric
     const int p1 = lane + 32 < cnt ? pt[lo + lane + 32] : 0;
     Top8 tp;
     top8_init(tp);
-    for (int d0 = 0; d0 < D; d0 += 256) {
-        float4 a[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        // two points' loads in flight, accumulated in point order
-        for (int q = 0; q < cnt; q += 2) {
-            const int pa = __shfl_sync(0xffffffffu, q < 32 ? p0 : p1, q & 31);
-            const int pb = __shfl_sync(0xffffffffu, q + 1 < 32 ? p0 : p1, (q + 1) & 31);
-            const float *ra = X + (int64_t)pa * D + d0 + lane;
-            const float *rb = X + (int64_t)pb * D + d0 + lane;
-            const bool two = q + 1 < cnt;
-            float xa[8], xb[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const bool in = d0 + lane + 32 * j < D;
-                xa[j] = in ? __ldg(ra + 32 * j) : 0.f;
-                xb[j] = in && two ? __ldg(rb + 32 * j) : 0.f;
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (d0 + lane + 32 * j < D) {
-                    acc_point(a[j], xa[j]);
-                    if (two) acc_point(a[j], xb[j]);
-                }
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int d = d0 + lane + 32 * j;
-            if (d < D) top8_insert(tp, spread_of(a[j], n), d);
-        }
-    }
+    int d0 = 0;
+    for (; d0 + 256 <= D; d0 += 256) small_group<true>(X, D, d0, lane, cnt, p0, p1, n, tp);
+    if (d0 < D) small_group<false>(X, D, d0, lane, cnt, p0, p1, n, tp);
     const int dim = choose_from_top8(tp, nV, seed, t, v);
     if (lane == 0) {
         split_dim[(int64_t)t * n_int + v] = dim;
@@ -662,7 +686,7 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
         const int chunks = ceil_div(nmax, CHUNK);
         if (chunks > 1)
             ATSNE_TRY(launch_kernel("forest_partial", partial_kernel, dim3(chunks, (unsigned)nodes, T),
-                                    ACC_THREADS, tile_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h,
+                                    acc_threads(f.D), tile_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h,
                                     l, chunks, w.part));
         if (nmax <= SMALL_NODE)
             ATSNE_TRY(launch_kernel("forest_choose", choose_small_kernel,
@@ -670,8 +694,8 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
                                     stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, f.top_var_dims,
                                     f.seed, f.split_dim, f.split_val, f.n_internal));
         else
-            ATSNE_TRY(launch_kernel("forest_choose", choose_kernel, dim3((unsigned)nodes, T), ACC_THREADS,
-                                    choose_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
+            ATSNE_TRY(launch_kernel("forest_choose", choose_kernel, dim3((unsigned)nodes, T),
+                                    acc_threads(f.D), choose_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
                                     w.part, f.top_var_dims, f.seed, f.split_dim, f.split_val,
                                     f.n_internal));
         const int64_t P = pow2_at_least(nmax);
