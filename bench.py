@@ -211,6 +211,37 @@ def default_queue_cap(checks):
     return q
 
 
+# sources whose hash a recorded ncu traffic figure is tied to (profiles/dram_traffic.txt)
+TRAFFIC_SOURCES = {
+    "forest_query": ["forest_query.cu", "common.cuh", "internal.h"],
+    "knn_tc": ["knn_tc.cu", "tc_ptx.cuh", "common.cuh", "internal.h"],
+}
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    record, or None when there is none or the kernel's sources have changed."""
+    import hashlib
+    srcs = TRAFFIC_SOURCES.get(kernel)
+    if not srcs:
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1512_01655_gb300", "csrc")
+    try:
+        for f in srcs:
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) == 4 and not line.startswith("#") and parts[0] == kernel \
+                        and parts[1] == workload and parts[2] == h.hexdigest():
+                    return int(parts[3])
+    except OSError:
+        return None
+    return None
+
+
 def algorithmic_flops_knn(N, D):
     return 2.0 * N * N * D
 
@@ -316,7 +347,8 @@ def run_ours(args, world, rank, local, pg):
         ach = per_launch / (avg_ms / 1e3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         roofline = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                    "unit": "GB/s", "frac": round(ach / peak, 4),
+                    "traffic": recorded_traffic(dom, args.workload),
                     "algorithmic_bytes_per_launch": per_launch,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     elif dom is not None:
