@@ -11,6 +11,8 @@ workload (N=70000, D=784, integer values in [0, 255], ~80% zeros; perplexity
   refinement:     exact refinement of a brushed selection of P^A's rows, then
                   the CSR rebuild of Eq. 10                          (Sec. 4.3)
 value = N points / step time (whole job: N points per rank, summed over ranks).
+exact_P reports the exact path alone (kNN + beta + CSR P, N / time) in FP32 and
+in BF16+rerank, with the recall of BF16+rerank against FP32.
 
 --impl reference times the FP64 CPU oracle (the plain restatement of the
 method the library is checked against) on the host cores, on a bounded sample
@@ -65,6 +67,8 @@ def parse():
     p.add_argument("--queue-cap", type=int, default=0, help="forest queue capacity (0 = auto)")
     p.add_argument("--refine", type=int, default=2000, help="points in the refined selection")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--exact-reps", type=int, default=5,
+                   help="timed runs of the exact path alone per precision (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=256)
     return p.parse_args()
@@ -396,6 +400,46 @@ def run_ours(args, world, rank, local, pg):
         e2e = {"value": round(world * N * len(e2e_ms) / (e2e_total / 1e3), 1),
                "unit": "points/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # the exact path alone (kNN + beta + CSR P) in both precisions: the metric's
+    # FP32 vs BF16+rerank comparison. CUDA events on the launching stream, L2
+    # flushed before each run when the input alone does not exceed it, median of
+    # --exact-reps runs after 3 warm-ups; recall (Eq. 9) of BF16+rerank against
+    # FP32.
+    exact_p = None
+    if args.exact_reps > 0:
+        exact_p = {}
+        ref_idx = None
+        for prec in ("fp32", "bf16"):
+            o = at.knn_opts(method="exact", precision=prec)
+
+            def run_exact():
+                idx_, d2_ = at.atsne_knn(X, K_NN, opts=o)
+                P_, _ = at.atsne_calibrate_P(d2_, PERPLEXITY)
+                at.atsne_symmetrize(idx_, P_, trim=False)
+                return idx_
+
+            for _ in range(3):
+                idx_p = run_exact()
+            ts = []
+            for _ in range(args.exact_reps):
+                if l2_flush is not None:
+                    l2_flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                idx_p = run_exact()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            at.atsne_check()
+            med = sorted(ts)[len(ts) // 2]
+            entry = {"ms": round(med, 3), "points_per_s": round(world * N / (med / 1e3), 1)}
+            if ref_idx is None:
+                ref_idx = idx_p
+            else:
+                entry["recall_vs_fp32"] = round(at.atsne_knn_precision(idx_p, ref_idx)[1], 6)
+            exact_p[prec] = entry
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, Xh, labels)
@@ -420,7 +464,8 @@ def run_ours(args, world, rank, local, pg):
             "rho": round(rho, 5), "rho_after_refine": round(rho_refined, 5), "nnz_exact_P": nnz,
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
-            "roofline": roofline, "knn_tc_roofline": knn_line, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
+            "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line))

@@ -354,3 +354,27 @@ def test_mnist_shaped_full_size_sampled(at, precision):
     perm = np.argsort(key_t)
     assert np.array_equal(key_t[perm], key)
     assert np.array_equal(val[perm], val)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_gamma_clusters_full_size_sampled(at, precision):
+    # the TIMIT-scale workload at full size (N=10^6, D=128, continuous
+    # Gamma-distributed features in 50 clusters): all rows on the tensor cores,
+    # 48 sampled rows checked against the oracle one by one, their P rows too.
+    X = synth.gamma_clusters(seed=3)
+    Xd = to_dev(X)
+    idx, d2 = at.atsne_knn(Xd, 90, precision=precision)
+    at.atsne_check()
+    rows = synth.sample_rows(X.shape[0], 48, seed=31)
+    g_idx, g_d2 = idx.cpu().numpy()[rows], d2.cpu().numpy()[rows]
+    knn_parity(g_idx, g_d2, X, 90, queries=rows)
+    P, beta = at.atsne_calibrate_P(d2, 30.0)
+    o_idx, o_d2 = oracle.knn_exact(X, 90, queries=rows)
+    o_P, _, _, _ = oracle.calibrate(o_d2, 30.0)
+    same = np.all(np.sort(g_idx, 1) == np.sort(o_idx, 1), axis=1)
+    assert same.mean() > 0.9
+    g_P = P.cpu().numpy()[rows]
+    for r in np.flatnonzero(same):  # compared by neighbour index (near ties may swap places)
+        gp = g_P[r][np.argsort(g_idx[r])]
+        op = o_P[r][np.argsort(o_idx[r])]
+        assert np.abs(gp - op).max() <= 1e-5, r
