@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--queue-cap", type=int, default=0, help="forest queue capacity (0 = auto)")
     p.add_argument("--refine", type=int, default=2000, help="points in the refined selection")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--refine-batch-reps", type=int, default=3,
+                   help="timed runs of the batched refinement workload (0 = skip)")
     p.add_argument("--exact-reps", type=int, default=5,
                    help="timed runs of the exact path alone per precision (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -244,6 +246,52 @@ def recorded_traffic(kernel, workload):
     except OSError:
         return None
     return None
+
+
+def bench_refine_batch(at, torch, dev, stream, reps, peaks):
+    """Batched refinement on its own workload: a 500000 x 256 corpus of 100
+    Gaussian clusters (sigma 1, centres N(0, 4^2)) and 512 brushed selections
+    of 200..20000 points (log-uniform, 1-3 clusters each), refined in one call
+    (Sec. 4.3, 5.1.1). Median of `reps` CUDA-event timed calls after one warm-up;
+    value = selected points (with repeats) per second and union rows per second."""
+    from paper_1512_01655_gb300 import synth
+    X, labels = synth.gaussian_mixture(500_000, 256, n_centres=100, centre_sigma=4.0, seed=4,
+                                       return_labels=True)
+    subs = synth.refine_subsets(labels, 512, lo=200, hi=20000, seed=4)
+    N, D, k = X.shape[0], X.shape[1], K_NN
+    Xd = torch.from_numpy(X).to(dev)
+    lists = torch.from_numpy(np.concatenate(subs)).to(dev)
+    total = int(lists.numel())
+    idx = torch.zeros((N, k), dtype=torch.int32, device=dev)
+    d2 = torch.zeros((N, k), dtype=torch.float32, device=dev)
+    P = torch.zeros((N, k), dtype=torch.float32, device=dev)
+    beta = torch.zeros(N, dtype=torch.float32, device=dev)
+    rho = torch.zeros(N, dtype=torch.float32, device=dev)
+    ws = torch.empty(at.workspace_bytes(at.OP_REFINE_BATCH, N, D, k, total), dtype=torch.uint8,
+                     device=dev)
+    cnt = at.atsne_refine_batch(Xd, lists, PERPLEXITY, idx, d2, P, beta, rho, workspace=ws)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cnt = at.atsne_refine_batch(Xd, lists, PERPLEXITY, idx, d2, P, beta, rho, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    at.atsne_check()
+    ms = sorted(ts)[len(ts) // 2]
+    union = int(cnt.item())
+    flops = 2.0 * union * N * D
+    peak = peaks.get("bf16_tflops", 1900.0)
+    ach = flops / (ms / 1e3) / 1e12
+    return {"workload": "500000x256 fp32, 100 Gaussian clusters; 512 selections of 200..20000 points",
+            "selections": len(subs), "listed_points": total, "union_rows": union,
+            "ms": round(ms, 2), "listed_points_per_s": round(total / (ms / 1e3), 1),
+            "union_rows_per_s": round(union / (ms / 1e3), 1),
+            "tensor": {"achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s (algorithmic 2*U*N*D)",
+                       "frac": round(ach / peak, 4), "tensor_passes": 3}}
 
 
 def algorithmic_flops_knn(N, D):
@@ -440,6 +488,10 @@ def run_ours(args, world, rank, local, pg):
                 entry["recall_vs_fp32"] = round(at.atsne_knn_precision(idx_p, ref_idx)[1], 6)
             exact_p[prec] = entry
 
+    refine_batch = None
+    if args.refine_batch_reps > 0:
+        refine_batch = bench_refine_batch(at, torch, dev, stream, args.refine_batch_reps, peaks)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, Xh, labels)
@@ -465,6 +517,7 @@ def run_ours(args, world, rank, local, pg):
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
             "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
+            "refine_batch": refine_batch,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }

@@ -59,7 +59,8 @@ typedef enum {
     ATSNE_OP_SYMMETRIZE = 2,
     ATSNE_OP_REFINE = 3,
     ATSNE_OP_FOREST_BUILD = 4,
-    ATSNE_OP_FOREST_QUERY = 5
+    ATSNE_OP_FOREST_QUERY = 5,
+    ATSNE_OP_REFINE_BATCH = 6  /* S = total entries of the concatenated selections */
 } atsne_op;
 
 /* Options of the kNN step. atsne_knn_opts_default() fills the defaults. */
@@ -168,6 +169,27 @@ atsne_status atsne_refine_subset_noalloc(const float *X, int64_t N, int32_t D,
                                          const int32_t *subset, int64_t S, int32_t k,
                                          float perplexity, int32_t *idx, float *d2, float *P_cond,
                                          float *beta, float *rho, void *stream);
+
+/*
+ * Batched refinement, Sec. 4.3 and Sec. 5.1.1: many user selections (brushes,
+ * lenses) refined at once. `lists` holds the selections concatenated, `total`
+ * entries in [0, N) (device int32; duplicates within and across selections
+ * allowed). A refined row depends only on X and its point, so this equals
+ * atsne_refine_subset on every selection in any order, and each point of the
+ * union is computed once: the union is formed on the device (bitmap, then an
+ * ordered compaction) and refined by one exact kNN on the tensor cores, one
+ * bisection and one row scatter.
+ *  refined_count  device int64 receiving the size of the union (may be NULL).
+ *  lists may be NULL when total is 0 (nothing is refined).
+ * Stream-ordered, with no host synchronisation and no allocation: the call can
+ * be recorded into a CUDA graph and replayed (its workspace and arguments are
+ * then fixed). Workspace: atsne_workspace_bytes(ATSNE_OP_REFINE_BATCH, N, D, k,
+ * total, NULL). Errors as atsne_refine_subset.
+ */
+atsne_status atsne_refine_batch(const float *X, int64_t N, int32_t D, const int32_t *lists,
+                                int64_t total, int32_t k, float perplexity, int32_t *idx, float *d2,
+                                float *P_cond, float *beta, float *rho, int64_t *refined_count,
+                                void *workspace, size_t ws_bytes, void *stream);
 
 /*
  * Precision of approximate neighbourhoods, Eq. 9 (Sec. 4.1):

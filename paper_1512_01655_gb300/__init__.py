@@ -16,14 +16,15 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libatsne.so")
 ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPPORTED = range(6)
 KNN_EXACT, KNN_FOREST = 0, 1
 FP32, BF16_RERANK, FP32_CUDA_CORES = 0, 1, 2
-OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY = range(6)
+(OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY,
+ OP_REFINE_BATCH) = range(7)
 
 EXPORTED = (
     "atsne_knn_opts_default", "atsne_workspace_bytes", "atsne_knn", "atsne_calibrate_P",
     "atsne_symmetrize", "atsne_refine_subset", "atsne_knn_precision", "atsne_forest_layout",
     "atsne_forest_build", "atsne_forest_query", "atsne_check", "atsne_last_error",
     "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
-    "atsne_refine_subset_noalloc",
+    "atsne_refine_subset_noalloc", "atsne_refine_batch",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
@@ -75,6 +76,8 @@ def lib():
                                           _vp, _vp, _vp, _sz, _vp]
         L.atsne_refine_subset_noalloc.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp,
                                                   _vp, _vp, _vp, _vp, _vp]
+        L.atsne_refine_batch.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _vp, _vp,
+                                         _vp, _vp, _vp, _vp, _sz, _vp]
         L.atsne_knn_precision.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
                                           ctypes.POINTER(ForestLayout)]
@@ -202,6 +205,30 @@ def atsne_refine_subset(X, subset, perplexity, idx, d2, P_cond, beta=None, rho=N
     _raise(lib().atsne_refine_subset(_p(X), N, D, _p(subset), S, k, perplexity, _p(idx), _p(d2),
                                      _p(P_cond), _p(beta), _p(rho), _p(ws), ws.numel(),
                                      _stream(stream)))
+
+
+def atsne_refine_batch(X, lists, perplexity, idx, d2, P_cond, beta=None, rho=None, stream=None,
+                       workspace=None):
+    """Refinement of many selections at once (their union, each point once) --
+    Sec. 4.3, 5.1.1. `lists`: one int32 device tensor or a sequence of them
+    (concatenated here). Returns a device int64 tensor holding the union's size.
+    Pass a preallocated `workspace` (uint8, workspace_bytes(OP_REFINE_BATCH, N,
+    D, k, total)) to record the call into a CUDA graph without allocating."""
+    _dev(X, torch.float32, "X")
+    if not isinstance(lists, torch.Tensor):
+        lists = torch.cat([t.reshape(-1) for t in lists]) if len(lists) else \
+            torch.empty(0, dtype=torch.int32, device=X.device)
+    _dev(lists, torch.int32, "lists")
+    N, D = X.shape
+    k = idx.shape[1]
+    total = lists.shape[0]
+    ws = workspace if workspace is not None else \
+        _workspace(workspace_bytes(OP_REFINE_BATCH, N, D, k, total), X.device)
+    count = torch.zeros(1, dtype=torch.int64, device=X.device)
+    _raise(lib().atsne_refine_batch(_p(X), N, D, _p(lists), total, k, perplexity, _p(idx), _p(d2),
+                                    _p(P_cond), _p(beta), _p(rho), _p(count), _p(ws), ws.numel(),
+                                    _stream(stream)))
+    return count
 
 
 def atsne_refine_subset_noalloc(X, subset, perplexity, idx, d2, P_cond, beta=None, rho=None,

@@ -251,6 +251,19 @@ size_t refine_ws(Carver &c, int64_t N, int32_t D, int64_t S, int32_t k, int32_t 
     return c.bytes();
 }
 
+// Batched refinement: the union's rows (padded to min(N, total)), its bitmap,
+// then the refinement of that many rows.
+size_t refine_batch_ws(Carver &c, int64_t N, int32_t D, int64_t total, int32_t k, int32_t **rows,
+                       uint32_t **bitmap, int32_t **ti, float **td, float **tp, float **tb,
+                       TcPlan *plan, TcWs *tws) {
+    const int64_t rows_max = total < N ? total : N;
+    int32_t *r = c.take<int32_t>((size_t)(rows_max > 0 ? rows_max : 1));
+    uint32_t *b = c.take<uint32_t>((size_t)((N + 31) / 32));
+    if (rows) *rows = r;
+    if (bitmap) *bitmap = b;
+    return refine_ws(c, N, D, rows_max, k, ti, td, tp, tb, plan, tws);
+}
+
 }  // namespace
 }  // namespace atsne
 
@@ -292,6 +305,9 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
         return forest_build_workspace(c, N, D, o.trees, o.leaf_size, nullptr);
     case ATSNE_OP_FOREST_QUERY:
         return forest_query_workspace(c, N, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
+    case ATSNE_OP_REFINE_BATCH:
+        return refine_batch_ws(c, N, D, S, k, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                               nullptr, nullptr);
     default:
         return 0;
     }
@@ -392,6 +408,49 @@ atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int
     }
     if ((st = calibrate_launch(td, S, k, perplexity, 1e-5f, 200, tp, tb, stream))) return st;
     return refine_scatter_launch(subset, S, N, k, ti, td, tp, tb, idx, d2, P_cond, beta, rho, stream);
+}
+
+atsne_status atsne_refine_batch(const float *X, int64_t N, int32_t D, const int32_t *lists,
+                                int64_t total, int32_t k, float perplexity, int32_t *idx, float *d2,
+                                float *P_cond, float *beta, float *rho, int64_t *refined_count,
+                                void *workspace, size_t ws_bytes, void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_status st = validate_xk(X, N, D, k);
+    if (st) return st;
+    if ((!lists && total > 0) || !idx || !d2 || !P_cond)
+        return set_error(ATSNE_EINVAL, "refine batch: NULL pointer");
+    if (total < 0) return set_error(ATSNE_EINVAL, "refine batch: total=%lld < 0", (long long)total);
+    if (!(perplexity > 0.f) || !(perplexity < (float)k))
+        return set_error(ATSNE_EINVAL, "refine batch: perplexity=%g not in (0, k=%d)", (double)perplexity, k);
+    if (total == 0) {
+        if (refined_count) {
+            cudaError_t e = cudaMemsetAsync(refined_count, 0, sizeof(int64_t), stream);
+            if (e != cudaSuccess) return cuda_error(e, "refine batch: count");
+        }
+        return ATSNE_OK;
+    }
+    Carver c(workspace);
+    int32_t *rows, *ti;
+    uint32_t *bitmap;
+    float *td, *tp, *tb;
+    TcPlan plan;
+    TcWs tws;
+    refine_batch_ws(c, N, D, total, k, &rows, &bitmap, &ti, &td, &tp, &tb, &plan, &tws);
+    if (!workspace || ws_bytes < c.bytes())
+        return set_error(ATSNE_ENOMEM, "refine batch: workspace of %zu bytes, %zu needed", ws_bytes,
+                         c.bytes());
+    if ((st = check_base(workspace, "refine batch workspace"))) return st;
+    if ((st = check_indices(lists, total, N, stream))) return st;
+    const int64_t S = total < N ? total : N;
+    if ((st = union_launch(lists, total, N, bitmap, rows, S, refined_count, stream))) return st;
+    if (S >= REFINE_TC_MIN_ROWS && k <= 200) {  // the prep kernel checks X for non-finite values
+        if ((st = knn_exact_tc(X, N, D, rows, S, k, plan, tws, ti, td, stream))) return st;
+    } else {
+        if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
+        if ((st = knn_bruteforce(X, N, D, rows, S, k, ti, td, stream))) return st;
+    }
+    if ((st = calibrate_launch(td, S, k, perplexity, 1e-5f, 200, tp, tb, stream))) return st;
+    return refine_scatter_launch(rows, S, N, k, ti, td, tp, tb, idx, d2, P_cond, beta, rho, stream);
 }
 
 atsne_status atsne_knn_precision(const int32_t *idx_approx, const int32_t *idx_exact,

@@ -62,6 +62,8 @@ atsne_status symmetrize_launch(const int32_t *idx, const float *P, int64_t N, in
 // ---- precision / refine -----------------------------------------------------
 atsne_status precision_launch(const int32_t *a, const int32_t *e, int64_t rows, int k,
                               float *rho_i, double *rho_sum, cudaStream_t stream);
+atsne_status union_launch(const int32_t *lists, int64_t total, int64_t N, uint32_t *bitmap,
+                          int32_t *out, int64_t out_rows, int64_t *count, cudaStream_t stream);
 atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, int k, const int32_t *ti,
                                    const float *td, const float *tp, const float *tb, int32_t *idx,
                                    float *d2, float *P, float *beta, float *rho,

@@ -420,8 +420,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             const int64_t c0 = (int64_t)sp * p.cols_per_split;
             const int64_t c1 = min(p.N, c0 + p.cols_per_split);
             const int64_t row = (int64_t)rt * TC_BM + quarter * 32 + lane;
-            const bool qv = row < p.Q;
-            const int qid = qv ? (p.qlist ? p.qlist[row] : (int)row) : -1;
+            const int qraw = row < p.Q ? (p.qlist ? p.qlist[row] : (int)row) : -1;
+            const bool qv = qraw >= 0 && qraw < p.N;  // listed rows out of range are flagged by the caller
+            const int qid = qv ? qraw : -1;
             Cand *buf = qv ? p.cand + ((size_t)row * p.splits + sp) * p.cap : nullptr;
             float tau = qv ? INFINITY : -INFINITY;
             int cnt = 0, since = 0;

@@ -64,7 +64,82 @@ __global__ void refine_scatter_kernel(const int32_t *__restrict__ subset, int64_
     }
 }
 
+// The union of listed rows: one bit per corpus row.
+__global__ void mark_kernel(const int32_t *__restrict__ lists, int64_t total, int64_t N,
+                            uint32_t *__restrict__ bitmap) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t i = lists[e];
+    if (i < 0 || i >= N) return;  // flagged by the caller's index check
+    atomicOr(&bitmap[i >> 5], 1u << (i & 31));
+}
+
+// Ordered compaction of the bitmap by one block: thread t takes a contiguous
+// run of words, a block-wide exclusive scan of the runs' popcounts gives each
+// its output offset. The list is padded to out_rows with its first entry (a
+// padded row repeats that point's refinement and writes the same values), or
+// with -1 when no listed index was in range (such rows are never written).
+constexpr int UNION_THREADS = 1024;
+__global__ void __launch_bounds__(UNION_THREADS)
+union_compact_kernel(const uint32_t *__restrict__ bitmap, int64_t words, int32_t *__restrict__ out,
+                     int64_t out_rows, int64_t *__restrict__ count) {
+    __shared__ int64_t warp_tot[UNION_THREADS / 32];
+    __shared__ int64_t s_total;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t per = (words + UNION_THREADS - 1) / UNION_THREADS;
+    const int64_t w0 = tid * per, w1 = w0 + per < words ? w0 + per : words;
+    int64_t mine = 0;
+    for (int64_t q = w0; q < w1; ++q) mine += __popc(bitmap[q]);
+    int64_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t v = warp_tot[lane];
+        int64_t vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += t;
+        }
+        warp_tot[lane] = vi - v;  // exclusive prefix of the warps
+        if (lane == 31) s_total = vi;
+    }
+    __syncthreads();
+    int64_t pos = warp_tot[w] + incl - mine;
+    for (int64_t q = w0; q < w1; ++q) {
+        uint32_t b = bitmap[q];
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            if (pos < out_rows) out[pos] = (int32_t)(q * 32 + bit);
+            ++pos;
+        }
+    }
+    __syncthreads();
+    const int64_t n = s_total < out_rows ? s_total : out_rows;
+    const int32_t first = n > 0 ? out[0] : -1;  // -1: nothing valid listed (an error is flagged)
+    for (int64_t r = n + tid; r < out_rows; r += UNION_THREADS) out[r] = first;
+    if (tid == 0 && count) *count = s_total;
+}
+
 }  // namespace
+
+atsne_status union_launch(const int32_t *lists, int64_t total, int64_t N, uint32_t *bitmap,
+                          int32_t *out, int64_t out_rows, int64_t *count, cudaStream_t stream) {
+    const int64_t words = (N + 31) / 32;
+    cudaError_t e = cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)words, stream);
+    if (e != cudaSuccess) return cuda_error(e, "union memset");
+    if (total > 0)
+        ATSNE_TRY(launch_kernel("refine_mark", mark_kernel, ceil_div(total, 256), 256, 0, stream, lists,
+                                total, N, bitmap));
+    return launch_kernel("refine_union", union_compact_kernel, 1, UNION_THREADS, 0, stream,
+                         (const uint32_t *)bitmap, words, out, out_rows, count);
+}
 
 atsne_status precision_launch(const int32_t *a, const int32_t *e, int64_t rows, int k,
                               float *rho_i, double *rho_sum, cudaStream_t stream) {

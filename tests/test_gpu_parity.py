@@ -378,3 +378,101 @@ def test_gamma_clusters_full_size_sampled(at, precision):
         gp = g_P[r][np.argsort(g_idx[r])]
         op = o_P[r][np.argsort(o_idx[r])]
         assert np.abs(gp - op).max() <= 1e-5, r
+
+
+def _refine_state(at, X, k, perp):
+    Xd = to_dev(X)
+    idx, d2 = at.atsne_knn(Xd, k, method="forest", trees=2, checks=64)
+    P, beta = at.atsne_calibrate_P(d2, perp)
+    return Xd, [idx, d2, P, beta, torch.zeros(X.shape[0], dtype=torch.float32, device=DEV)]
+
+
+def test_refine_batch_equals_refining_each_selection(at):
+    X, labels = synth.gaussian_mixture(3000, 32, seed=8, return_labels=True)
+    Xd, base = _refine_state(at, X, 30, 10.0)
+    subs = synth.refine_subsets(labels, 6, lo=128, hi=700, seed=9)  # overlapping brushes
+    a = [t.clone() for t in base]
+    for sub in subs:
+        at.atsne_refine_subset(Xd, to_dev(sub), 10.0, *a)
+    b = [t.clone() for t in base]
+    cnt = at.atsne_refine_batch(Xd, [to_dev(s) for s in subs], 10.0, *b)
+    at.atsne_check()
+    union = np.unique(np.concatenate(subs))
+    assert int(cnt.item()) == union.size
+    ai, bi = a[0].cpu().numpy(), b[0].cpu().numpy()
+    assert np.array_equal(ai, bi)
+    for x, y in zip(a[1:], b[1:]):
+        assert torch.allclose(x, y, rtol=1e-6, atol=1e-7)
+    untouched = np.setdiff1d(np.arange(X.shape[0]), union)
+    assert np.array_equal(bi[untouched], base[0].cpu().numpy()[untouched])
+    assert np.all(b[4].cpu().numpy()[union] == 1.0)
+    knn_parity(bi[union], b[1].cpu().numpy()[union], X, 30, queries=union)
+
+
+def test_refine_batch_replays_from_a_cuda_graph(at):
+    X, labels = synth.gaussian_mixture(3000, 32, seed=8, return_labels=True)
+    Xd, base = _refine_state(at, X, 30, 10.0)
+    subs = synth.refine_subsets(labels, 5, lo=40, hi=900, seed=10)
+    lists = to_dev(np.concatenate(subs))
+    eager = [t.clone() for t in base]
+    at.atsne_refine_batch(Xd, lists, 10.0, *eager)
+    at.atsne_check()
+    state = [t.clone() for t in base]
+    ws = torch.empty(at.workspace_bytes(at.OP_REFINE_BATCH, 3000, 32, 30, lists.shape[0]),
+                     dtype=torch.uint8, device=DEV)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cnt = at.atsne_refine_batch(Xd, lists, 10.0, *state, workspace=ws)
+    for t, b0 in zip(state, base):  # capture records without running; reset to the base
+        t.copy_(b0)
+    g.replay()
+    torch.cuda.synchronize()
+    at.atsne_check()
+    assert int(cnt.item()) == np.unique(np.concatenate(subs)).size
+    for x, y in zip(eager, state):
+        assert torch.equal(x, y)
+
+
+def test_refine_batch_edge_cases(at):
+    X, labels = synth.gaussian_mixture(500, 8, seed=12, return_labels=True)
+    Xd, base = _refine_state(at, X, 10, 3.0)
+    st = [t.clone() for t in base]
+    cnt = at.atsne_refine_batch(Xd, [], 3.0, *st)  # nothing listed: nothing changes
+    assert int(cnt.item()) == 0
+    for x, y in zip(st, base):
+        assert torch.equal(x, y)
+    rep = np.array([7, 7, 7, 3, 499, 3], np.int32)  # duplicates, small batch (CUDA-core path)
+    cnt = at.atsne_refine_batch(Xd, to_dev(rep), 3.0, *st)
+    at.atsne_check()
+    assert int(cnt.item()) == 3
+    knn_parity(st[0].cpu().numpy()[[3, 7, 499]], st[1].cpu().numpy()[[3, 7, 499]], X, 10,
+               queries=np.array([3, 7, 499], np.int32))
+    with pytest.raises(at.AtsneError):
+        at.atsne_refine_batch(Xd, to_dev(np.array([1, 500], np.int32)), 3.0, *st)
+        at.atsne_check()
+
+
+def test_refine_batch_full_size_sampled(at):
+    # the batched-refinement workload at full size: a 500000 x 256 corpus of 100
+    # Gaussian clusters and 512 brushed selections of 200..20000 points, refined
+    # in one call; 32 sampled rows of the union checked against the oracle.
+    X, labels = synth.gaussian_mixture(500_000, 256, n_centres=100, centre_sigma=4.0, seed=4,
+                                       return_labels=True)
+    Xd = to_dev(X)
+    N, k = X.shape[0], 90
+    subs = synth.refine_subsets(labels, 512, lo=200, hi=20000, seed=4)
+    union = np.unique(np.concatenate(subs))
+    idx = torch.zeros((N, k), dtype=torch.int32, device=DEV)
+    d2 = torch.zeros((N, k), dtype=torch.float32, device=DEV)
+    P = torch.zeros((N, k), dtype=torch.float32, device=DEV)
+    beta = torch.zeros(N, dtype=torch.float32, device=DEV)
+    rho = torch.zeros(N, dtype=torch.float32, device=DEV)
+    cnt = at.atsne_refine_batch(Xd, [to_dev(s) for s in subs], 30.0, idx, d2, P, beta, rho)
+    at.atsne_check()
+    assert int(cnt.item()) == union.size
+    rows = union[synth.sample_rows(union.size, 32, seed=41)]
+    knn_parity(idx.cpu().numpy()[rows], d2.cpu().numpy()[rows], X, k, queries=rows.astype(np.int32))
+    assert np.all(rho.cpu().numpy()[union] == 1.0)
+    outside = np.setdiff1d(np.arange(N), union)
+    if outside.size:
+        assert not idx.cpu().numpy()[outside].any()
