@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--queue-cap", type=int, default=0, help="forest queue capacity (0 = auto)")
     p.add_argument("--refine", type=int, default=2000, help="points in the refined selection")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--kde-reps", type=int, default=5,
+                   help="timed renders of the density / approximation map (0 = skip)")
     p.add_argument("--refine-batch-reps", type=int, default=3,
                    help="timed runs of the batched refinement workload (0 = skip)")
     p.add_argument("--exact-reps", type=int, default=5,
@@ -246,6 +248,49 @@ def recorded_traffic(kernel, workload):
     except OSError:
         return None
     return None
+
+
+def bench_kde(at, torch, dev, stream, labels, rho_i, reps, clk, peaks):
+    """Density view, selected share, approximation map and lens (Sec. 5.2) of a
+    stand-in 2-D layout of the workload's points (synth.embedding_2d: the
+    optimiser is not part of this library), rho from the step's refined
+    precision, one label selected; 1024 x 1024 pixels over [-13, 13]^2,
+    h = 0.3, cutoff 4 h. Median of `reps` CUDA-event timed renders.
+    Work model: every point contributes to the pixels within cutoff * h,
+    about N * pi * (4h)^2 / pixel^2 Gaussian terms, one exp each; the bound is
+    the SFU exponential rate, 16 per clock per SM (152 SMs)."""
+    from paper_1512_01655_gb300 import synth
+    Y = torch.from_numpy(synth.embedding_2d(labels, seed=6)).to(dev)
+    sel = torch.from_numpy((labels == 3).astype(np.uint8)).to(dev)
+    W = H = 1024
+    x0 = y0 = -13.0
+    px = 26.0 / W
+    h, cut = 0.3, 4.0
+    args = (Y, x0, y0, px, W, H, h)
+    kw = dict(cutoff=cut, lens_k=2.0, rho=rho_i, selected=sel)
+    for _ in range(2):
+        at.atsne_kde_map(*args, **kw)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        at.atsne_kde_map(*args, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    at.atsne_check()
+    ms = sorted(ts)[len(ts) // 2]
+    N = int(Y.shape[0])
+    terms = N * np.pi * (cut * h) ** 2 / (px * px)
+    mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 16 * mhz * 1e6
+    ach = terms / (ms / 1e3)
+    return {"workload": "%d points (stand-in 2-D layout), %dx%d pixels, h=%.1f, cutoff %.0f h" % (N, W, H, h, cut),
+            "ms": round(ms, 3), "pixels_per_s": round(W * H / (ms / 1e3), 1),
+            "roofline": {"bound": "sfu", "achieved": round(ach / 1e12, 3), "peak": round(peak / 1e12, 3),
+                         "unit": "T Gaussian terms/s (model N*pi*(cutoff*h)^2/pixel^2)",
+                         "frac": round(ach / peak, 4)}}
 
 
 def bench_refine_batch(at, torch, dev, stream, reps, peaks):
@@ -488,6 +533,10 @@ def run_ours(args, world, rank, local, pg):
                 entry["recall_vs_fp32"] = round(at.atsne_knn_precision(idx_p, ref_idx)[1], 6)
             exact_p[prec] = entry
 
+    kde = None
+    if args.kde_reps > 0:
+        kde = bench_kde(at, torch, dev, stream, labels, rho_i, args.kde_reps, clk, peaks)
+
     refine_batch = None
     if args.refine_batch_reps > 0:
         refine_batch = bench_refine_batch(at, torch, dev, stream, args.refine_batch_reps, peaks)
@@ -517,7 +566,7 @@ def run_ours(args, world, rank, local, pg):
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
             "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
-            "refine_batch": refine_batch,
+            "refine_batch": refine_batch, "kde": kde,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }

@@ -74,7 +74,7 @@ typedef struct {
     int32_t queue_cap;     /* forest: capacity of the per-query priority queue; 0 (default)
                               = checks/2 rounded up to a power of two, within [256, 4096] */
     int32_t rerank_k;      /* exact tensor path: candidates kept per row and column split
-                              (0 = k + 38 for FP32, 2k for BF16) */
+                              (0 = k + 38 for FP32, 2k for BF16; at most 4096) */
     uint64_t seed;         /* forest: seed of the counter-based split choice */
 } atsne_knn_opts;
 
@@ -190,6 +190,32 @@ atsne_status atsne_refine_batch(const float *X, int64_t N, int32_t D, const int3
                                 int64_t total, int32_t k, float perplexity, int32_t *idx, float *d2,
                                 float *P_cond, float *beta, float *rho, int64_t *refined_count,
                                 void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Density-based view of a 2-D embedding and its approximation map, Sec. 5.2.
+ * For each pixel p of a width x height image (pixel (x, y) centred at
+ * (x0 + (x + 0.5) pixel, y0 + (y + 0.5) pixel), each an FP32 fused
+ * multiply-add rounded once; rows y outermost) and the
+ * Gaussian kernel G(d, h) = exp(-d^2 / (2 h^2)) / (2 pi h^2):
+ *   f = (1/N) sum_i G(|p - y_i|, h)                 Eq. 12, kernel density
+ *   s = sum_{i selected} G / sum_i G                Eq. 13, selected share
+ *   a = sum_i rho_i G / sum_i G                     Sec. 5.2.2, approximation
+ *   alpha = 1 - a^lens_k                            the Magic Lens (paper: k = 2)
+ * Eq. 13 and a(p,h) are printed with the normalisers 1/|S| and 1/sum rho_i;
+ * they are read as 1/N (the same as f's), which makes s and a the shares in
+ * [0, 1] that the text describes. Where no point reaches a pixel, s = 0 and
+ * a = 1. Points farther than cutoff * h from a pixel are left out of its sums;
+ * cutoff = 0 keeps every point.
+ *  Y         [N][2] fp32 embedding coordinates (device).
+ *  rho       [N] fp32 per-point precision (Eq. 9), or NULL for all 1.
+ *  selected  [N] uint8 (non-zero = selected), or NULL for none.
+ *  f_out, s_out, a_out, alpha_out: [height][width] fp32 (device); any may be NULL.
+ * No workspace. Errors: EINVAL (sizes, h <= 0, cutoff < 0, NULL Y), ECUDA.
+ */
+atsne_status atsne_kde_map(const float *Y, int64_t N, const float *rho, const uint8_t *selected,
+                           float x0, float y0, float pixel, int32_t width, int32_t height, float h,
+                           float cutoff, float lens_k, float *f_out, float *s_out, float *a_out,
+                           float *alpha_out, void *stream);
 
 /*
  * Precision of approximate neighbourhoods, Eq. 9 (Sec. 4.1):

@@ -44,6 +44,8 @@ def lib():
                                           _i32p, _i64p]
         L.oracle_forest_query.argtypes = [_f32p, _i64, _i32, _i32, _i32, _i32p, _f32p, _i32p,
                                           _i64p, _vp, _i64, _i32, _i32, _i32, _i32p, _f64p, _i64p]
+        L.oracle_kde.argtypes = [_f32p, _i64, _vp, _vp, _f64, _f64, _f64, _i32, _i32, _f64, _f64,
+                                 _f64, _f64p, _f64p, _f64p, _f64p]
         L.oracle_refine.argtypes = [_f32p, _i64, _i32, _i32p, _i64, _i32, _f64, _f64, _i32, _i32p,
                                     _f64p, _f64p, _f64p, _f64p]
         _lib = L
@@ -194,3 +196,17 @@ def refine(X, subset, k, perplexity, idx, d2, P, beta, rho, tol=1e-10, max_iter=
             raise TypeError("refine state arrays must be C-contiguous %s" % dt)
     _check(lib().oracle_refine(X, N, D, subset, subset.shape[0], k, float(perplexity), float(tol),
                                int(max_iter), idx, d2, P, beta, rho), "refine")
+
+
+def kde(Y, x0, y0, pixel, width, height, h, cutoff=4.0, k=2.0, rho=None, selected=None):
+    """Density view and approximation map, Eq. 12, Eq. 13, Sec. 5.2.2.
+    Returns f, s, a, alpha as float64 [height][width]."""
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    N = Y.shape[0]
+    r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float32)
+    sl = None if selected is None else np.ascontiguousarray(selected, dtype=np.uint8)
+    out = [np.empty((height, width), np.float64) for _ in range(4)]
+    _check(lib().oracle_kde(Y, N, None if r is None else r.ctypes.data_as(_vp),
+                            None if sl is None else sl.ctypes.data_as(_vp), x0, y0, pixel, width,
+                            height, h, cutoff, k, *out), "kde")
+    return tuple(out)

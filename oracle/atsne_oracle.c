@@ -21,6 +21,7 @@
  *   oracle_refine        Sec. 4.3 and Sec. 5.1.1: exact neighbourhood of the
  *                        selected points, new Gaussian, rho_i = 1
  *   oracle_precision     Eq. 9 (Sec. 4.1)
+ *   oracle_kde           Eq. 12, Eq. 13 and the approximation map of Sec. 5.2.2
  *
  * Readings taken where the paper is silent are stated at each function.
  * Compile with -ffp-contract=off: the forest's float decisions (split value,
@@ -659,4 +660,65 @@ int oracle_refine(const float *X, int64_t N, int32_t D, const int32_t *subset, i
     free(tp);
     free(tb);
     return rc;
+}
+
+
+/*
+ * Density view of a 2-D embedding and its approximation map (Sec. 5.2), per
+ * pixel p (centre x0 + (x + 0.5) pixel, y0 + (y + 0.5) pixel, an FP32 value
+ * like the embedding's coordinates: fma(x + 0.5, pixel, x0) rounded once), with
+ * G(d, h) = exp(-d^2 / (2 h^2)) / (2 pi h^2), the zero-mean Gaussian of
+ * standard deviation h in the plane:
+ *   f(p, h) = (1/N) sum_i G(|p - y_i|, h)                  Eq. 12
+ *   s(p, h) = sum_{i in S} G / sum_i G                     Eq. 13
+ *   a(p, h) = sum_i rho_i G / sum_i G                      Sec. 5.2.2
+ *   alpha   = 1 - a^k                                      Sec. 5.2.2 (Magic Lens)
+ * Reading: Eq. 13 and a(p,h) carry the normalisers 1/|S| and 1/sum rho_i; as
+ * printed a would exceed 1 wherever the local precision beats the mean, which
+ * the text rules out (a is between zero and one), and the fixed threshold 0.5
+ * on s would depend on |S|/N. Both normalisers are read as 1/N, f's own, so s
+ * is the selected share and a the precision-weighted mean of the kernel.
+ * Empty pixels (no point within reach): s = 0, a = 1. A point farther than
+ * cutoff * h from p is left out (cutoff = 0: none is). That test decides a
+ * membership, so it is taken in the GPU kernel's precision (FP32: centre
+ * fma(x + 0.5, pixel, x0), squared distance fma(dx, dx, dy * dy) against
+ * (cutoff * h)^2, each operation rounded once); the sums are FP64, in point
+ * order.
+ */
+int oracle_kde(const float *Y, int64_t N, const float *rho, const uint8_t *sel, double x0, double y0,
+               double pixel, int32_t W, int32_t H, double h, double cutoff, double k, double *f,
+               double *s, double *a, double *alpha)
+{
+    if (N < 1 || W < 1 || H < 1 || !(h > 0.0) || !(pixel > 0.0) || cutoff < 0.0) return 1;
+    const float rf = (float)cutoff * (float)h;
+    const float r2f = rf * rf;
+    const double norm = 1.0 / (2.0 * 3.14159265358979323846 * h * h);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int32_t y = 0; y < H; ++y) {
+        for (int32_t x = 0; x < W; ++x) {
+            const float pxf = fmaf((float)x + 0.5f, (float)pixel, (float)x0);
+            const float pyf = fmaf((float)y + 0.5f, (float)pixel, (float)y0);
+            const double px = (double)pxf, py = (double)pyf;
+            double F = 0.0, S = 0.0, R = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                if (cutoff > 0.0) {
+                    const float dxf = pxf - Y[2 * i], dyf = pyf - Y[2 * i + 1];
+                    const float dyy = dyf * dyf;
+                    if (fmaf(dxf, dxf, dyy) > r2f) continue;
+                }
+                const double dx = px - (double)Y[2 * i], dy = py - (double)Y[2 * i + 1];
+                const double d2 = dx * dx + dy * dy;
+                const double g = norm * exp(-d2 / (2.0 * h * h));
+                F += g;
+                if (sel && sel[i]) S += g;
+                R += (rho ? (double)rho[i] : 1.0) * g;
+            }
+            const int64_t o = (int64_t)y * W + x;
+            f[o] = F / (double)N;
+            s[o] = F > 0.0 ? S / F : 0.0;
+            a[o] = F > 0.0 ? R / F : 1.0;
+            alpha[o] = 1.0 - pow(a[o], k);
+        }
+    }
+    return 0;
 }

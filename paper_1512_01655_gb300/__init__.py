@@ -24,7 +24,7 @@ EXPORTED = (
     "atsne_symmetrize", "atsne_refine_subset", "atsne_knn_precision", "atsne_forest_layout",
     "atsne_forest_build", "atsne_forest_query", "atsne_check", "atsne_last_error",
     "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
-    "atsne_refine_subset_noalloc", "atsne_refine_batch",
+    "atsne_refine_subset_noalloc", "atsne_refine_batch", "atsne_kde_map",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
@@ -79,6 +79,8 @@ def lib():
         L.atsne_refine_batch.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _vp, _vp,
                                          _vp, _vp, _vp, _vp, _sz, _vp]
         L.atsne_knn_precision.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
+        L.atsne_kde_map.argtypes = [_vp, _i64, _vp, _vp, _f32, _f32, _f32, _i32, _i32, _f32, _f32,
+                                    _f32, _vp, _vp, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
                                           ctypes.POINTER(ForestLayout)]
         L.atsne_forest_build.argtypes = [_vp, _i64, _i32, ctypes.POINTER(KnnOpts), _vp, _sz, _vp,
@@ -229,6 +231,23 @@ def atsne_refine_batch(X, lists, perplexity, idx, d2, P_cond, beta=None, rho=Non
                                     _p(P_cond), _p(beta), _p(rho), _p(count), _p(ws), ws.numel(),
                                     _stream(stream)))
     return count
+
+
+def atsne_kde_map(Y, x0, y0, pixel, width, height, h, cutoff=4.0, lens_k=2.0, rho=None,
+                  selected=None, stream=None):
+    """Density view f (Eq. 12), selected share s (Eq. 13), approximation map a
+    and lens alpha (Sec. 5.2.2) of a 2-D embedding Y [N][2] on a width x height
+    image. Returns four float32 [height][width] device tensors."""
+    _dev(Y, torch.float32, "Y")
+    N = Y.shape[0]
+    if rho is not None:
+        _dev(rho, torch.float32, "rho")
+    if selected is not None:
+        selected = selected.to(torch.uint8)
+    out = [torch.empty((height, width), dtype=torch.float32, device=Y.device) for _ in range(4)]
+    _raise(lib().atsne_kde_map(_p(Y), N, _p(rho), _p(selected), x0, y0, pixel, width, height, h,
+                               cutoff, lens_k, *[_p(t) for t in out], _stream(stream)))
+    return tuple(out)
 
 
 def atsne_refine_subset_noalloc(X, subset, perplexity, idx, d2, P_cond, beta=None, rho=None,

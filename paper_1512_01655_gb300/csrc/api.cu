@@ -142,6 +142,8 @@ atsne_status validate_knn_opts(const atsne_knn_opts &o) {
     if (o.precision != ATSNE_FP32 && o.precision != ATSNE_BF16_RERANK &&
         o.precision != ATSNE_FP32_CUDA_CORES)
         return set_error(ATSNE_EINVAL, "knn: unknown precision %d", o.precision);
+    if (o.rerank_k < 0 || o.rerank_k > 4096)
+        return set_error(ATSNE_EINVAL, "knn: rerank_k=%d not in [0, 4096]", o.rerank_k);
     if (o.method == ATSNE_KNN_FOREST) {
         if (o.trees < 1 || o.trees > 64) return set_error(ATSNE_EINVAL, "forest: trees=%d not in [1,64]", o.trees);
         if (o.top_var_dims < 1 || o.top_var_dims > 8)
@@ -451,6 +453,20 @@ atsne_status atsne_refine_batch(const float *X, int64_t N, int32_t D, const int3
     }
     if ((st = calibrate_launch(td, S, k, perplexity, 1e-5f, 200, tp, tb, stream))) return st;
     return refine_scatter_launch(rows, S, N, k, ti, td, tp, tb, idx, d2, P_cond, beta, rho, stream);
+}
+
+atsne_status atsne_kde_map(const float *Y, int64_t N, const float *rho, const uint8_t *selected,
+                           float x0, float y0, float pixel, int32_t width, int32_t height, float h,
+                           float cutoff, float lens_k, float *f_out, float *s_out, float *a_out,
+                           float *alpha_out, void *stream) {
+    if (!Y) return set_error(ATSNE_EINVAL, "kde: Y is NULL");
+    if (N < 1 || N > INT32_MAX) return set_error(ATSNE_EINVAL, "kde: N=%lld", (long long)N);
+    if (width < 1 || height < 1 || !(pixel > 0.f) || !(h > 0.f) || !(cutoff >= 0.f) ||
+        !isfinite(x0) || !isfinite(y0) || !isfinite(lens_k))
+        return set_error(ATSNE_EINVAL, "kde: width=%d height=%d pixel=%g h=%g cutoff=%g", width, height,
+                         (double)pixel, (double)h, (double)cutoff);
+    return kde_launch(Y, N, rho, selected, x0, y0, pixel, width, height, h, cutoff, lens_k, f_out,
+                      s_out, a_out, alpha_out, static_cast<cudaStream_t>(stream));
 }
 
 atsne_status atsne_knn_precision(const int32_t *idx_approx, const int32_t *idx_exact,

@@ -62,6 +62,10 @@ atsne_status symmetrize_launch(const int32_t *idx, const float *P, int64_t N, in
 // ---- precision / refine -----------------------------------------------------
 atsne_status precision_launch(const int32_t *a, const int32_t *e, int64_t rows, int k,
                               float *rho_i, double *rho_sum, cudaStream_t stream);
+atsne_status kde_launch(const float *Y, int64_t N, const float *rho, const uint8_t *selected, float x0,
+                        float y0, float pixel, int W, int H, float h, float cutoff, float lens_k,
+                        float *f_out, float *s_out, float *a_out, float *alpha_out,
+                        cudaStream_t stream);
 atsne_status union_launch(const int32_t *lists, int64_t total, int64_t N, uint32_t *bitmap,
                           int32_t *out, int64_t out_rows, int64_t *count, cudaStream_t stream);
 atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, int k, const int32_t *ti,

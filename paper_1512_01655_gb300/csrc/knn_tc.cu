@@ -88,7 +88,8 @@ struct __align__(1024) TcSmem {
     // survivors are read back; between tiles the warp's first 256 words serve
     // the radix select of an exact compaction
     float tr[4][32 * 33];
-    uint16_t dhist[4][NBUCKET][32];  // per epilogue thread: buffered distances by bucket
+    // per epilogue thread: buffered distances by bucket, two 16-bit counts per word
+    uint32_t dhist[4][NBUCKET / 2][32];
     uint64_t full[TcCfg<PASSES>::STAGES];
     uint64_t empty[TcCfg<PASSES>::STAGES];
     uint64_t acc_full[2];
@@ -122,6 +123,11 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Shared-memory add whose result is not needed (no wait on it).
+__device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
 
 // Adds one to hist[bin] for every active lane; must be called by the whole
@@ -455,8 +461,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 if (b < NBUCKET) tau = fminf(tau, __uint_as_float((uint32_t)(gbase + b + 1) << 20) - nx);
             };
             if (gh) global_tau();
-            uint16_t *dh = &s.dhist[warp - 2][0][lane];
-            for (int bk = 0; bk < NBUCKET; ++bk) dh[bk * 32] = 0;
+            uint32_t *dh = &s.dhist[warp - 2][0][lane];
+            for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
             // corpus norms of the first tile of the unit, then one tile ahead
             float nyn[TC_BN / 32];
 #pragma unroll
@@ -515,24 +521,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     __syncwarp();  // the chunk's norms are read before the next chunk's
                     if (mask) {
                         // spill this row's keys to its own padded shared row and
-                        // walk its survivors: the warp pays the largest count of
-                        // any lane, not the union of survivor positions
+                        // walk its survivors, two per step (their shared loads
+                        // issue together): the warp pays the largest count of any
+                        // lane, not the union of survivor positions. Each survivor
+                        // is appended (key, column) to the row's buffer and counted
+                        // in its bucket by a fire-and-forget shared add.
 #pragma unroll
                         for (int j = 0; j < 32; ++j) mine[j] = kk[j];
                         const int colb = (int)ct + c * 32;
                         since += __popc(mask);
-                        do {
-                            const int j = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const float key = mine[j];
-                            buf[cnt++] = Cand{key, colb + j};
-                            int bk = (int)(__float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20) - (top - (NBUCKET - 1));
+                        auto append = [&](float key, int col) {
+                            buf[cnt++] = Cand{key, col};
+                            const uint32_t db = __float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20;
+                            int bk = (int)db - (top - (NBUCKET - 1));
                             bk = min(max(bk, 0), NBUCKET - 1);
-                            dh[bk * 32] += 1;
+                            red_add_shared(dh + (bk >> 1) * 32, 1u << ((bk & 1) * 16));
                             if (gh) {
-                                int gb = (int)(__float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20) - gbase;
+                                const int gb = (int)db - gbase;
                                 atomicAdd(gh + min(max(gb, 0), NBUCKET - 1), 1u);
                             }
+                        };
+                        do {
+                            const int j0 = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const int j1 = mask ? __ffs(mask) - 1 : -1;
+                            mask &= mask - 1;
+                            const float k0 = mine[j0];
+                            const float k1 = j1 >= 0 ? mine[j1] : 0.f;
+                            append(k0, colb + j0);
+                            if (j1 >= 0) append(k1, colb + j1);
                         } while (mask);
                     }
                 }
@@ -545,10 +562,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 }
                 // lower tau to the upper edge of the bucket holding the ksel-th distance
                 if (since >= 16 && cnt >= p.ksel) {
-                    int cum = 0, bk = 0;
-                    for (; bk < NBUCKET; ++bk) {
-                        cum += dh[bk * 32];
-                        if (cum >= p.ksel) break;
+                    uint32_t hw[NBUCKET / 2];
+#pragma unroll
+                    for (int bw = 0; bw < NBUCKET / 2; ++bw) hw[bw] = dh[bw * 32];
+                    int cum = 0, bk = NBUCKET;
+#pragma unroll
+                    for (int b2 = 0; b2 < NBUCKET; ++b2) {
+                        cum += (int)((hw[b2 >> 1] >> ((b2 & 1) * 16)) & 0xffffu);
+                        if (bk == NBUCKET && cum >= p.ksel) bk = b2;
                     }
                     if (bk < NBUCKET) {
                         const float edge =
@@ -597,12 +618,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 if ((compacted >> lane) & 1u) {
                     // re-base the buckets below the new tau and recount the kept entries
                     top = (int)(__float_as_uint(fmaxf(nx + tau, 1e-30f) * 1.0001f) >> 20) + 1;
-                    for (int bk = 0; bk < NBUCKET; ++bk) dh[bk * 32] = 0;
+                    for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
                     for (int i = 0; i < cnt; ++i) {
                         int bk = (int)(__float_as_uint(fmaxf(nx + buf[i].key, 1e-30f)) >> 20) -
                                  (top - (NBUCKET - 1));
                         bk = min(max(bk, 0), NBUCKET - 1);
-                        dh[bk * 32] += 1;
+                        dh[(bk >> 1) * 32] += 1u << ((bk & 1) * 16);
                     }
                     since = 0;
                 }
@@ -914,6 +935,8 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
     const double model = ks * (1.0 + log(fmax(1.0, ncol / ks)));
     int64_t cap = (int64_t)ceil(2.5 * model) + TC_BN;
     if (cap < 8 * ks + TC_BN) cap = 8 * ks + TC_BN;
+    // the epilogue's bucket counts are 16 bits and never exceed the buffer's size
+    if (cap > 65504) cap = 65504;
     pl.cap = (int)((cap + 31) / 32 * 32);
     return pl;
 }

@@ -17,6 +17,10 @@ these mixtures stand in for their shapes:
   x_d = s_{m,d} * Gamma(2, 1).
 * ``refine_subsets``: sizes log-uniform in [lo, hi], members drawn from one to
   three clusters (a brushed selection, Sec. 5.1.1).
+* ``embedding_2d``: a stand-in for a 2-D tSNE layout of labelled points (the
+  optimiser is not part of this library): cluster m centred on a circle of
+  radius 10 at angle 2 pi m / M, points spread N(0, diag(s_x^2, s_y^2)) with
+  s ~ U(0.5, 1.5) per cluster and axis.
 """
 import numpy as np
 
@@ -81,3 +85,16 @@ def sample_rows(N, n, seed=11):
     """A seeded sorted sample of n distinct row indices."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(N, size=min(n, N), replace=False)).astype(np.int32)
+
+
+def embedding_2d(labels, seed=6):
+    """A seeded 2-D layout of labelled points: cluster m on a circle of radius
+    10 at angle 2 pi m / M, anisotropic Gaussian spread U(0.5, 1.5) per axis."""
+    rng = np.random.default_rng(seed)
+    labels = np.asarray(labels)
+    M = int(labels.max()) + 1
+    ang = 2 * np.pi * np.arange(M) / M
+    centres = np.stack([10 * np.cos(ang), 10 * np.sin(ang)], axis=1)
+    spread = rng.uniform(0.5, 1.5, size=(M, 2))
+    Y = centres[labels] + spread[labels] * rng.normal(size=(labels.shape[0], 2))
+    return Y.astype(np.float32)

@@ -476,3 +476,39 @@ def test_refine_batch_full_size_sampled(at):
     outside = np.setdiff1d(np.arange(N), union)
     if outside.size:
         assert not idx.cpu().numpy()[outside].any()
+
+
+@pytest.mark.parametrize("cutoff", [4.0, 0.0])
+def test_kde_map_matches_oracle(at, cutoff):
+    labels = np.random.default_rng(13).integers(0, 6, size=3000)
+    Y = synth.embedding_2d(labels, seed=13)
+    rng = np.random.default_rng(14)
+    rho = rng.random(3000).astype(np.float32)
+    sel = (labels == 2).astype(np.uint8)
+    x0, y0, px, W, H, h = -13.0, -12.0, 0.25, 104, 90, 0.6
+    g = at.atsne_kde_map(to_dev(Y), x0, y0, px, W, H, h, cutoff=cutoff, lens_k=2.0,
+                         rho=to_dev(rho), selected=to_dev(sel))
+    o = oracle.kde(Y, x0, y0, px, W, H, h, cutoff=cutoff, k=2.0, rho=rho, selected=sel)
+    gf, gs, ga, gal = [t.cpu().numpy().astype(np.float64) for t in g]
+    of, os_, oa, oal = o
+    assert np.all(np.abs(gf - of) <= 1e-5 * np.abs(of) + 1e-12)
+    # shares compared where the density is not vanishing (FP32 sums of tiny terms)
+    live = of > 1e-9
+    assert live.mean() > 0.3
+    for u, v in ((gs, os_), (ga, oa), (gal, oal)):
+        assert np.abs(u - v)[live].max() <= 1e-5
+    dead = of == 0.0
+    assert np.all(gs[dead] == 0.0) and np.all(ga[dead] == 1.0)
+
+
+def test_kde_map_edges(at):
+    Y = to_dev(np.array([[0.0, 0.0]], np.float32))
+    f, s, a, al = at.atsne_kde_map(Y, -0.5, -0.5, 1.0, 1, 1, 1.0, cutoff=0.0)  # no rho, no selection
+    assert abs(f.item() - 1 / (2 * np.pi)) < 1e-6 and s.item() == 0.0 and a.item() == 1.0
+    assert al.item() == 0.0
+    for bad in (dict(h=0.0), dict(cutoff=-1.0), dict(width=0)):
+        kw = dict(x0=0.0, y0=0.0, pixel=1.0, width=4, height=4, h=1.0, cutoff=4.0)
+        kw.update(bad)
+        with pytest.raises(at.AtsneError):
+            at.atsne_kde_map(Y, kw["x0"], kw["y0"], kw["pixel"], kw["width"], kw["height"], kw["h"],
+                             cutoff=kw["cutoff"])
