@@ -11,8 +11,8 @@ workload (N=70000, D=784, integer values in [0, 255], ~80% zeros; perplexity
   refinement:     exact refinement of a brushed selection of P^A's rows, then
                   the CSR rebuild of Eq. 10                          (Sec. 4.3)
 value = N points / step time (whole job: N points per rank, summed over ranks).
-exact_P reports the exact path alone (kNN + beta + CSR P, N / time) in FP32 and
-in BF16+rerank, with the recall of BF16+rerank against FP32.
+exact_P reports the exact path alone (kNN + beta + CSR P, N / time) in FP32, in
+BF16+rerank and in FP8+rerank, with their recall against FP32.
 
 --impl reference times the FP64 CPU oracle (the plain restatement of the
 method the library is checked against) on the host cores, on a bounded sample
@@ -493,16 +493,16 @@ def run_ours(args, world, rank, local, pg):
         e2e = {"value": round(world * N * len(e2e_ms) / (e2e_total / 1e3), 1),
                "unit": "points/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # the exact path alone (kNN + beta + CSR P) in both precisions: the metric's
-    # FP32 vs BF16+rerank comparison. CUDA events on the launching stream, L2
+    # the exact path alone (kNN + beta + CSR P) in each precision: the metric's
+    # FP32 vs BF16+rerank comparison, and the FP8+rerank variant. CUDA events on the launching stream, L2
     # flushed before each run when the input alone does not exceed it, median of
-    # --exact-reps runs after 3 warm-ups; recall (Eq. 9) of BF16+rerank against
-    # FP32.
+    # --exact-reps runs after 3 warm-ups; recall (Eq. 9) of BF16+rerank and
+    # FP8+rerank against FP32.
     exact_p = None
     if args.exact_reps > 0:
         exact_p = {}
         ref_idx = None
-        for prec in ("fp32", "bf16"):
+        for prec in ("fp32", "bf16", "fp8"):
             o = at.knn_opts(method="exact", precision=prec)
 
             def run_exact():

@@ -49,7 +49,11 @@ typedef enum { ATSNE_KNN_EXACT = 0, ATSNE_KNN_FOREST = 1 } atsne_knn_method;
 typedef enum {
     ATSNE_FP32 = 0,            /* tensor cores, 3 BF16 passes (hi.hi + hi.lo + lo.hi) */
     ATSNE_BF16_RERANK = 1,     /* tensor cores, 1 BF16 pass, rerank_k candidates per row */
-    ATSNE_FP32_CUDA_CORES = 2  /* FP32 direct differences on the CUDA cores */
+    ATSNE_FP32_CUDA_CORES = 2, /* FP32 direct differences on the CUDA cores */
+    ATSNE_FP8_RERANK = 3       /* tensor cores, 1 FP8 (E4M3, per-row scale) pass; the
+                                  rerank_k (default 4k, at most 512) best keys per row
+                                  re-ranked in FP32, the k best returned: approximate,
+                                  no certificate (measure recall against FP32) */
 } atsne_precision;
 
 /* Operation codes for atsne_workspace_bytes(). */

@@ -31,6 +31,7 @@ struct TcWs {
     unsigned *gmax = nullptr;
     char *cand = nullptr, *meta = nullptr;
     unsigned *row_hist = nullptr;
+    float *scale = nullptr, *qscale = nullptr;  // FP8 row scales
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
 };
 TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k);

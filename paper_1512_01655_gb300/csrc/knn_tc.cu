@@ -63,8 +63,10 @@ constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int TC_EPI = 128;
 constexpr uint64_t WAIT_NS = 1000000000ull;
 constexpr int MERGE_WARPS = 4;
-constexpr int RCAP = 256;        // candidates re-ranked per row at most
+constexpr int RCAP = 256;        // candidates re-ranked per row at most (certified modes)
 constexpr int MSTAGE = 1024;     // keys below tau staged per row for the merge's select
+constexpr int RCAP_FP8 = 1024;   // FP8 mode: candidates re-ranked per row at most
+constexpr int MSTAGE_FP8 = 2048;
 constexpr int NBUCKET = 48;      // distance buckets per row: 6 octaves, 8 per octave
 
 struct Cand {
@@ -72,18 +74,23 @@ struct Cand {
     int32_t idx;
 };
 
+// PASSES: 1 = one BF16 pass, 3 = BF16 hi/lo in three passes, 8 = one FP8
+// (E4M3, per-row scale) pass. A k-block is one 128-byte swizzle row: 64 BF16
+// or 128 FP8 values, four MMAs (K = 16 or 32).
 template <int PASSES>
 struct TcCfg {
-    static constexpr int STAGES = PASSES == 1 ? 4 : 2;
-    static constexpr int A_BYTES = TC_BM * TC_BK * 2;
-    static constexpr int B_BYTES = TC_BN * TC_BK * 2;
-    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (PASSES == 1 ? 1 : 2);
+    static constexpr int STAGES = PASSES == 3 ? 2 : 4;
+    static constexpr int KE = PASSES == 8 ? 128 : TC_BK;  // elements per k-block
+    static constexpr int A_BYTES = TC_BM * 128;
+    static constexpr int B_BYTES = TC_BN * 128;
+    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (PASSES == 3 ? 2 : 1);
 };
 
 template <int PASSES>
 struct __align__(1024) TcSmem {
     unsigned char stage[TcCfg<PASSES>::STAGES][TcCfg<PASSES>::STAGE_BYTES];
     float ny[4][32];            // per epilogue warp: the chunk's corpus norms
+    float ms[4][32];            // FP8: the chunk's -2 * corpus row scales
     // per epilogue thread: one row of 32 keys (padded to 33) from which its
     // survivors are read back; between tiles the warp's first 256 words serve
     // the radix select of an exact compaction
@@ -103,6 +110,8 @@ struct __align__(1024) TcSmem {
 struct TcParams {
     CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;
     const float *nrm;      // [N] corpus ||x||^2
+    const float *scale;    // FP8: [N] corpus row scales (x ~ scale * q)
+    const float *qscale;   // FP8 with a query list: [Q] query row scales
     const unsigned *gmax;  // max ||x|| over the corpus (float bits)
     const int32_t *qlist;  // query row -> corpus index (nullptr: identity)
     int64_t Q, N;
@@ -262,6 +271,46 @@ knn_prep_kernel(const float *__restrict__ X, const int32_t *__restrict__ rows, i
     }
 }
 
+// FP8 copies: per row the scale s = max|x| / 448 (448 = largest E4M3 value;
+// s = 1 for a zero row) and the E4M3 bytes of x / s (round to nearest even),
+// zero-padded to Dp bytes; ||x||^2 and max ||x|| as in knn_prep_kernel.
+__global__ void __launch_bounds__(256)
+knn_prep_fp8_kernel(const float *__restrict__ X, const int32_t *__restrict__ rows, int64_t nrows,
+                    int64_t N, int D, int Dp, uint16_t *__restrict__ q8, float *__restrict__ scale,
+                    float *__restrict__ nrm, unsigned *__restrict__ gmax, int *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= nrows) return;
+    int64_t src = rows ? rows[r] : r;
+    if (src < 0 || src >= N) src = 0;  // flagged by the caller's index check
+    const float *x = X + src * D;
+    float m = 0.f, n = 0.f;
+    bool finite = true;
+    for (int d = lane; d < D; d += 32) {
+        const float v = x[d];
+        finite &= isfinite(v);
+        m = fmaxf(m, fabsf(v));
+        n = fmaf(v, v, n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    n = warp_sum(n);
+    if (!__all_sync(0xffffffffu, finite) && lane == 0) raise_status(status, DEV_NONFINITE);
+    const float sc = m > 0.f ? __fdiv_rn(m, 448.f) : 1.f;
+    uint16_t *out = q8 + r * (Dp >> 1);
+    for (int d = 2 * lane; d < Dp; d += 64) {
+        const float v0 = d < D ? x[d] : 0.f, v1 = d + 1 < D ? x[d + 1] : 0.f;
+        out[d >> 1] = cvt_e4m3x2(__fdiv_rn(v1, sc), __fdiv_rn(v0, sc));
+    }
+    if (lane == 0) {
+        scale[r] = sc;
+        if (nrm) {
+            nrm[r] = n;
+            atomicMax(&gmax[0], __float_as_uint(sqrtf(n)));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the fused contraction + filter kernel
 // ---------------------------------------------------------------------------
@@ -329,8 +378,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                         mbar_arrive_expect_tx(&s.full[stage], C::STAGE_BYTES);
                         armed[stage] = true;
                         armed_phase[stage] = phase;
-                        tma_load_2d(st, &p.tm_a_hi, kb * TC_BK, rt * TC_BM, &s.full[stage]);
-                        tma_load_2d(st + C::A_BYTES, &p.tm_b_hi, kb * TC_BK, (int)ct, &s.full[stage]);
+                        tma_load_2d(st, &p.tm_a_hi, kb * C::KE, rt * TC_BM, &s.full[stage]);
+                        tma_load_2d(st + C::A_BYTES, &p.tm_b_hi, kb * C::KE, (int)ct, &s.full[stage]);
                         if (PASSES == 3) {
                             tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.tm_a_lo, kb * TC_BK,
                                         rt * TC_BM, &s.full[stage]);
@@ -355,7 +404,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = idesc_bf16_f32(TC_BM, TC_BN);
+            const uint32_t idesc = PASSES == 8 ? idesc_e4m3_f32(TC_BM, TC_BN) : idesc_bf16_f32(TC_BM, TC_BN);
             int stage = 0, acc = 0;
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
@@ -381,9 +430,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                         const uint32_t a_lo = b_hi + C::B_BYTES;
                         const uint32_t b_lo = a_lo + C::A_BYTES;
 #pragma unroll
-                        for (int k = 0; k < TC_BK / 16; ++k) {
-                            mma_bf16(d, sw128_kmajor_desc(a_hi + 32 * k), sw128_kmajor_desc(b_hi + 32 * k),
-                                     idesc, (kb | k) != 0);
+                        for (int k = 0; k < 4; ++k) {  // 32 bytes of each row per MMA
+                            if (PASSES == 8)
+                                mma_e4m3(d, sw128_kmajor_desc(a_hi + 32 * k), sw128_kmajor_desc(b_hi + 32 * k),
+                                         idesc, (kb | k) != 0);
+                            else
+                                mma_bf16(d, sw128_kmajor_desc(a_hi + 32 * k), sw128_kmajor_desc(b_hi + 32 * k),
+                                         idesc, (kb | k) != 0);
                             if (PASSES == 3) {
                                 mma_bf16(d, sw128_kmajor_desc(a_hi + 32 * k),
                                          sw128_kmajor_desc(b_lo + 32 * k), idesc, 1u);
@@ -464,23 +517,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             uint32_t *dh = &s.dhist[warp - 2][0][lane];
             for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
             // corpus norms of the first tile of the unit, then one tile ahead
-            float nyn[TC_BN / 32];
+            float nyn[TC_BN / 32], msn[TC_BN / 32];
 #pragma unroll
             for (int q = 0; q < TC_BN / 32; ++q) {
                 const int64_t cc = c0 + q * 32 + lane;
                 nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
+                if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
             }
+            // FP8: x_i . x_j ~ s_i s_j (q_i . q_j); the row's scale, the
+            // columns' -2 s_j beside their norms
+            const float si = PASSES == 8 && qv ? (p.qscale ? p.qscale[row] : p.scale[qid]) : 1.f;
             float *nyw = s.ny[warp - 2];
+            float *msw = s.ms[warp - 2];
             float *mine = s.tr[warp - 2] + lane * 33;
             for (int64_t ct = c0; ct < c1; ct += TC_BN) {
-                float nyc[TC_BN / 32];  // lane l: columns l, l + 32, ... of this tile
+                float nyc[TC_BN / 32], msc[TC_BN / 32];  // lane l: columns l, l + 32, ... of this tile
 #pragma unroll
-                for (int q = 0; q < TC_BN / 32; ++q) nyc[q] = nyn[q];
+                for (int q = 0; q < TC_BN / 32; ++q) {
+                    nyc[q] = nyn[q];
+                    msc[q] = msn[q];
+                }
                 if (ct + TC_BN < c1) {
 #pragma unroll
                     for (int q = 0; q < TC_BN / 32; ++q) {
                         const int64_t cc = ct + TC_BN + q * 32 + lane;
                         nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
+                        if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
                     }
                 }
                 ok = mbar_wait(&s.acc_full[acc], acc_phase, &s.abort_flag, WAIT_NS);
@@ -500,19 +562,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     uint32_t r[32];
                     tmem_ld32(taddr + (uint32_t)(c * 32), r);
                     nyw[lane] = nyc[c];
+                    if (PASSES == 8) msw[lane] = msc[c];
                     tmem_ld_wait();
                     __syncwarp();
                     // branch-free filter: 32 keys, one survivor bit each
                     float kk[32];
                     uint32_t mask = 0;
                     const float4 *ny4 = reinterpret_cast<const float4 *>(nyw);
+                    if (PASSES == 8) {
+                        const float4 *ms4 = reinterpret_cast<const float4 *>(msw);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 n4 = ny4[q];
-                        kk[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), n4.x);
-                        kk[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), n4.y);
-                        kk[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), n4.z);
-                        kk[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), n4.w);
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 n4 = ny4[q], m4 = ms4[q];
+                            kk[4 * q + 0] = fmaf(__uint_as_float(r[4 * q + 0]) * si, m4.x, n4.x);
+                            kk[4 * q + 1] = fmaf(__uint_as_float(r[4 * q + 1]) * si, m4.y, n4.y);
+                            kk[4 * q + 2] = fmaf(__uint_as_float(r[4 * q + 2]) * si, m4.z, n4.z);
+                            kk[4 * q + 3] = fmaf(__uint_as_float(r[4 * q + 3]) * si, m4.w, n4.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 n4 = ny4[q];
+                            kk[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), n4.x);
+                            kk[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), n4.y);
+                            kk[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), n4.z);
+                            kk[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), n4.w);
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < 32; ++j) mask |= (kk[j] < tau ? 1u : 0u) << j;
@@ -650,7 +725,7 @@ struct MergeParams {
     int64_t Q, N;
     const int32_t *qlist;
     const float *X;
-    int D, k;
+    int D, k, ksel;
     const float *nrm;
     const float4 *stats;
     const unsigned *gmax;
@@ -673,13 +748,25 @@ __device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st
     return 2.f * drop + p.acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
 }
 
+// CERT (FP32 and BF16 modes): the k nearest, certified exact or sent to the
+// brute-force kernel. Otherwise (FP8 mode): the SEL = ksel best keys re-ranked
+// in FP32 and the k best of them kept, without a certificate. MST keys are
+// staged per row, RC candidates re-ranked at most.
+template <bool CERT, int RC, int MST>
+size_t merge_smem_bytes() {
+    return (size_t)MERGE_WARPS * (256 * 4 + MST * 8 + RC * 8);
+}
+
+template <bool CERT, int RC, int MST>
 __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams p) {
-    __shared__ uint32_t hist_s[MERGE_WARPS][256];
-    __shared__ float stage_k[MERGE_WARPS][MSTAGE];
-    __shared__ int stage_j[MERGE_WARPS][MSTAGE];
-    __shared__ float rd[MERGE_WARPS][RCAP];
-    __shared__ int rj[MERGE_WARPS][RCAP];
+    extern __shared__ __align__(16) unsigned char mg_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(mg_smem) + w * 256;
+    float *sk = reinterpret_cast<float *>(mg_smem + MERGE_WARPS * 1024) + w * MST;
+    int *sj = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 4)) + w * MST;
+    float *rdw = reinterpret_cast<float *>(mg_smem + MERGE_WARPS * (1024 + MST * 8)) + w * RC;
+    int *rjw = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 4)) + w * RC;
+    const int sel = CERT ? p.k : p.ksel;  // rank of the key that bounds the re-rank set
     const int64_t row = (int64_t)blockIdx.x * MERGE_WARPS + w;
     if (row >= p.Q) return;
     const int qid = p.qlist ? p.qlist[row] : (int)row;
@@ -702,7 +789,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         ovf |= __shfl_xor_sync(0xffffffffu, ovf, o);
         tau_min = fminf(tau_min, __shfl_xor_sync(0xffffffffu, tau_min, o));
     }
-    bool good = !ovf && total >= p.k && qid >= 0 && qid < p.N;
+    bool good = !ovf && total >= sel && qid >= 0 && qid < p.N;
     int nr = 0;
     if (good) {
         // One pass over the buffers stages every (key, index) at or below
@@ -710,11 +797,8 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         // smallest key theta lies among them, and every candidate the re-rank
         // takes (key <= theta + 2E) is staged; otherwise the buffers are
         // walked again.
-        const float E = row_error_bound(p, p.stats[qid]);
+        const float E = CERT ? row_error_bound(p, p.stats[qid]) : 0.f;
         const float slim = tau_min + 2.f * E;
-        uint32_t *hist = hist_s[w];
-        float *sk = stage_k[w];
-        int *sj = stage_j[w];
         int ns = 0, nlt = 0;
         for (int u0 = 0; u0 < S; u0 += 32) {
           const int cu = u0 + lane < S ? mt[u0 + lane].x : 0;  // the counts of 32 splits at once
@@ -737,11 +821,11 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
                 const unsigned m1 = __ballot_sync(0xffffffffu, t1);
                 const unsigned lt = lanemask_lt();
                 const int pos = ns + __popc(m0 & lt) + __popc(m1 & lt);
-                if (t0 && pos < MSTAGE) {
+                if (t0 && pos < MST) {
                     sk[pos] = e0.key;
                     sj[pos] = e0.idx;
                 }
-                if (t1 && pos + t0 < MSTAGE) {
+                if (t1 && pos + t0 < MST) {
                     sk[pos + t0] = e1.key;
                     sj[pos + t0] = e1.idx;
                 }
@@ -752,10 +836,10 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         nlt = (int)__reduce_add_sync(0xffffffffu, (unsigned)nlt);
         __syncwarp();
         int n_less = 0;
-        const bool staged = nlt >= p.k && ns <= MSTAGE;
+        const bool staged = nlt >= sel && ns <= MST;
         uint32_t prefix;
         if (staged) {
-            prefix = warp_select([&](int i) { return sk[i]; }, ns, p.k, hist, lane, n_less);
+            prefix = warp_select([&](int i) { return sk[i]; }, ns, sel, hist, lane, n_less);
         } else {
             prefix = warp_select_visit(
                 [&](auto fn) {
@@ -768,7 +852,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
                         }
                     }
                 },
-                p.k, hist, lane, n_less);
+                sel, hist, lane, n_less);
         }
         const float theta = key_of_bits(prefix);
         const float lim = theta + 2.f * E;
@@ -776,7 +860,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         auto take_batch = [&](bool take, int idx) {
             const unsigned tm = __ballot_sync(0xffffffffu, take);
             const int pos = nr + __popc(tm & lanemask_lt());
-            if (take && pos < RCAP) rj[w][pos] = idx;
+            if (take && pos < RC) rjw[pos] = idx;
             nr += __popc(tm);
         };
         if (staged) {
@@ -796,7 +880,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
                 }
             }
         }
-        if (nr > RCAP) good = false;
+        if (nr > RC) good = false;
         __syncwarp();
         if (good && nr >= p.k) {
             // exact FP32 direct-difference distances, four candidates at a time
@@ -807,7 +891,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
                 float a[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    xc[u] = t0 + u < nr ? p.X + (int64_t)rj[w][t0 + u] * p.D : nullptr;
+                    xc[u] = t0 + u < nr ? p.X + (int64_t)rjw[t0 + u] * p.D : nullptr;
                     a[u] = 0.f;
                 }
                 if (vec4) {
@@ -842,28 +926,32 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const float r = warp_sum(a[u]);
-                    if (lane == 0 && xc[u]) rd[w][t0 + u] = r;
+                    if (lane == 0 && xc[u]) rdw[t0 + u] = r;
                 }
             }
-            for (int t = nr + lane; t < RCAP; t += 32) {
-                rd[w][t] = INFINITY;
-                rj[w][t] = INT_MAX;
+            int ns2 = 32;
+            while (ns2 < nr) ns2 <<= 1;
+            for (int t = nr + lane; t < ns2; t += 32) {
+                rdw[t] = INFINITY;
+                rjw[t] = INT_MAX;
             }
             __syncwarp();
-            warp_bitonic_sort_smem(rd[w], rj[w], RCAP, lane);
-            const float dk = rd[w][p.k - 1];
-            const float nx = p.nrm[qid];
-            const float lb = nx + tau_min - E;
-            // certified: no point outside the buffers can be closer than dk
-            good = isinf(tau_min) || dk < lb * (1.f - 1e-6f);
+            warp_bitonic_sort_smem(rdw, rjw, ns2, lane);
+            if (CERT) {
+                const float dk = rdw[p.k - 1];
+                const float nx = p.nrm[qid];
+                const float lb = nx + tau_min - E;
+                // certified: no point outside the buffers can be closer than dk
+                good = isinf(tau_min) || dk < lb * (1.f - 1e-6f);
+            }
         } else {
             good = false;
         }
     }
     if (good) {
         for (int t = lane; t < p.k; t += 32) {
-            p.idx_out[row * p.k + t] = rj[w][t];
-            p.d2_out[row * p.k + t] = rd[w][t];
+            p.idx_out[row * p.k + t] = rjw[t];
+            p.d2_out[row * p.k + t] = rdw[t];
         }
     } else if (lane == 0) {
         p.flag_rows[atomicAdd(p.flag_count, 1)] = (int)row;
@@ -897,6 +985,20 @@ atsne_status make_bf16_map(CUtensorMap *m, const void *base, int64_t rows, int D
     return ATSNE_OK;
 }
 
+atsne_status make_u8_map(CUtensorMap *m, const void *base, int64_t rows, int Dp, int box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return set_error(ATSNE_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Dp};
+    cuuint32_t box[2] = {128u, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(ATSNE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ATSNE_OK;
+}
+
 template <int PASSES>
 size_t tc_smem_bytes() {
     return sizeof(TcSmem<PASSES>) + 1024;
@@ -904,13 +1006,15 @@ size_t tc_smem_bytes() {
 static_assert(sizeof(TcSmem<1>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
 static_assert(NBUCKET % 4 == 0, "row histograms are read as uint4");
 static_assert(sizeof(TcSmem<3>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
+static_assert(sizeof(TcSmem<8>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
 
 }  // namespace
 
 TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) {
     TcPlan pl;
-    pl.passes = precision == ATSNE_FP32 ? 3 : 1;
-    pl.Dp = ((D + TC_BK - 1) / TC_BK) * TC_BK;
+    pl.passes = precision == ATSNE_FP32 ? 3 : precision == ATSNE_FP8_RERANK ? 8 : 1;
+    const int ke = pl.passes == 8 ? 128 : TC_BK;  // elements per 128-byte row
+    pl.Dp = ((D + ke - 1) / ke) * ke;
     pl.row_tiles = (int)((Q + TC_BM - 1) / TC_BM);
     const int64_t col_tiles = (N + TC_BN - 1) / TC_BN;
     // (row tile, column split) units: one split per row tile when the row tiles
@@ -924,7 +1028,8 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
     const int64_t tiles_per = (col_tiles + S - 1) / S;
     pl.cols_per_split = (int)(tiles_per * TC_BN);
     pl.splits = (int)((N + pl.cols_per_split - 1) / pl.cols_per_split);
-    int ks = rerank_k > 0 ? rerank_k : (pl.passes == 3 ? k + 38 : 2 * k);
+    int ks = rerank_k > 0 ? rerank_k : (pl.passes == 3 ? k + 38 : pl.passes == 8 ? 4 * k : 2 * k);
+    if (pl.passes == 8 && ks > RCAP_FP8 / 2) ks = RCAP_FP8 / 2;
     if (ks < k) ks = k;
     pl.ksel = ks;
     // A streaming top-ksel over n columns in random order admits about
@@ -943,10 +1048,13 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
 
 size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcPlan &pl, TcWs *ws) {
     TcWs w;
-    w.hi = c.take<uint16_t>((size_t)N * pl.Dp);
-    w.lo = pl.passes == 3 ? c.take<uint16_t>((size_t)N * pl.Dp) : nullptr;
-    w.qhi = list ? c.take<uint16_t>((size_t)Q * pl.Dp) : nullptr;
-    w.qlo = (list && pl.passes == 3) ? c.take<uint16_t>((size_t)Q * pl.Dp) : nullptr;
+    const size_t per = pl.passes == 8 ? (size_t)pl.Dp / 2 : (size_t)pl.Dp;  // 16-bit words per row
+    w.hi = c.take<uint16_t>((size_t)N * per);
+    w.lo = pl.passes == 3 ? c.take<uint16_t>((size_t)N * per) : nullptr;
+    w.qhi = list ? c.take<uint16_t>((size_t)Q * per) : nullptr;
+    w.qlo = (list && pl.passes == 3) ? c.take<uint16_t>((size_t)Q * per) : nullptr;
+    w.scale = pl.passes == 8 ? c.take<float>((size_t)N) : nullptr;
+    w.qscale = (list && pl.passes == 8) ? c.take<float>((size_t)Q) : nullptr;
     w.nrm = c.take<float>((size_t)N);
     w.stats = c.take<float>((size_t)N * 4);
     w.gmax = c.take<unsigned>(4);
@@ -968,25 +1076,43 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     if (e == cudaSuccess && w.row_hist)
         e = cudaMemsetAsync(w.row_hist, 0, (size_t)Q * NBUCKET * sizeof(unsigned), stream);
     if (e != cudaSuccess) return cuda_error(e, "knn_tc memset");
-    auto *hi = reinterpret_cast<__nv_bfloat16 *>(w.hi);
-    auto *lo = reinterpret_cast<__nv_bfloat16 *>(w.lo);
-    ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
-                            (const int32_t *)nullptr, N, N, D, pl.Dp, pl.passes, hi, lo, w.nrm,
-                            reinterpret_cast<float4 *>(w.stats), w.gmax, status));
+    const bool fp8 = pl.passes == 8;
     const void *a_hi = w.hi, *a_lo = w.lo;
-    if (qlist) {
-        ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(Q * 32, 256), 256, 0, stream, X,
-                                qlist, Q, N, D, pl.Dp, pl.passes,
-                                reinterpret_cast<__nv_bfloat16 *>(w.qhi),
-                                reinterpret_cast<__nv_bfloat16 *>(w.qlo), (float *)nullptr,
-                                (float4 *)nullptr, (unsigned *)nullptr, status));
-        a_hi = w.qhi;
-        a_lo = w.qlo;
+    if (fp8) {
+        ATSNE_TRY(launch_kernel("knn_prep", knn_prep_fp8_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
+                                (const int32_t *)nullptr, N, N, D, pl.Dp, w.hi, w.scale, w.nrm, w.gmax,
+                                status));
+        if (qlist) {
+            ATSNE_TRY(launch_kernel("knn_prep", knn_prep_fp8_kernel, ceil_div(Q * 32, 256), 256, 0, stream,
+                                    X, qlist, Q, N, D, pl.Dp, w.qhi, w.qscale, (float *)nullptr,
+                                    (unsigned *)nullptr, status));
+            a_hi = w.qhi;
+        }
+    } else {
+        auto *hi = reinterpret_cast<__nv_bfloat16 *>(w.hi);
+        auto *lo = reinterpret_cast<__nv_bfloat16 *>(w.lo);
+        ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
+                                (const int32_t *)nullptr, N, N, D, pl.Dp, pl.passes, hi, lo, w.nrm,
+                                reinterpret_cast<float4 *>(w.stats), w.gmax, status));
+        if (qlist) {
+            ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(Q * 32, 256), 256, 0, stream, X,
+                                    qlist, Q, N, D, pl.Dp, pl.passes,
+                                    reinterpret_cast<__nv_bfloat16 *>(w.qhi),
+                                    reinterpret_cast<__nv_bfloat16 *>(w.qlo), (float *)nullptr,
+                                    (float4 *)nullptr, (unsigned *)nullptr, status));
+            a_hi = w.qhi;
+            a_lo = w.qlo;
+        }
     }
     TcParams p;
     memset(&p, 0, sizeof(p));
-    ATSNE_TRY(make_bf16_map(&p.tm_a_hi, a_hi, qlist ? Q : N, pl.Dp, TC_BM));
-    ATSNE_TRY(make_bf16_map(&p.tm_b_hi, w.hi, N, pl.Dp, TC_BN));
+    if (fp8) {
+        ATSNE_TRY(make_u8_map(&p.tm_a_hi, a_hi, qlist ? Q : N, pl.Dp, TC_BM));
+        ATSNE_TRY(make_u8_map(&p.tm_b_hi, w.hi, N, pl.Dp, TC_BN));
+    } else {
+        ATSNE_TRY(make_bf16_map(&p.tm_a_hi, a_hi, qlist ? Q : N, pl.Dp, TC_BM));
+        ATSNE_TRY(make_bf16_map(&p.tm_b_hi, w.hi, N, pl.Dp, TC_BN));
+    }
     if (pl.passes == 3) {
         ATSNE_TRY(make_bf16_map(&p.tm_a_lo, a_lo, qlist ? Q : N, pl.Dp, TC_BM));
         ATSNE_TRY(make_bf16_map(&p.tm_b_lo, w.lo, N, pl.Dp, TC_BN));
@@ -994,12 +1120,14 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         p.tm_a_lo = p.tm_a_hi;
         p.tm_b_lo = p.tm_b_hi;
     }
+    p.scale = w.scale;
+    p.qscale = qlist ? w.qscale : nullptr;
     p.nrm = w.nrm;
     p.gmax = w.gmax;
     p.qlist = qlist;
     p.Q = Q;
     p.N = N;
-    p.KB = pl.Dp / TC_BK;
+    p.KB = pl.Dp / (fp8 ? 128 : TC_BK);
     p.splits = pl.splits;
     p.cols_per_split = pl.cols_per_split;
     p.row_tiles = pl.row_tiles;
@@ -1016,6 +1144,11 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         e = cudaFuncSetAttribute(knn_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "knn_tc attribute");
         ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<3>, grid, TC_THREADS, smem, stream, p));
+    } else if (fp8) {
+        const size_t smem = tc_smem_bytes<8>();
+        e = cudaFuncSetAttribute(knn_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "knn_tc attribute");
+        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<8>, grid, TC_THREADS, smem, stream, p));
     } else {
         const size_t smem = tc_smem_bytes<1>();
         e = cudaFuncSetAttribute(knn_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1041,8 +1174,19 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     m.d2_out = d2_out;
     m.flag_rows = w.flag_rows;
     m.flag_count = w.flag_count;
-    ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel, ceil_div(Q, MERGE_WARPS), MERGE_WARPS * 32,
-                            0, stream, m));
+    m.ksel = pl.ksel;
+    if (fp8) {
+        const size_t ms = merge_smem_bytes<false, RCAP_FP8, MSTAGE_FP8>();
+        e = cudaFuncSetAttribute(knn_merge_kernel<false, RCAP_FP8, MSTAGE_FP8>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
+        if (e != cudaSuccess) return cuda_error(e, "knn_tc_merge attribute");
+        ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<false, RCAP_FP8, MSTAGE_FP8>,
+                                ceil_div(Q, MERGE_WARPS), MERGE_WARPS * 32, ms, stream, m));
+    } else {
+        const size_t ms = merge_smem_bytes<true, RCAP, MSTAGE>();
+        ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<true, RCAP, MSTAGE>,
+                                ceil_div(Q, MERGE_WARPS), MERGE_WARPS * 32, ms, stream, m));
+    }
     return knn_bruteforce_rows(X, N, D, qlist, w.flag_rows, w.flag_count, Q, k, idx_out, d2_out, stream);
 }
 

@@ -512,3 +512,31 @@ def test_kde_map_edges(at):
         with pytest.raises(at.AtsneError):
             at.atsne_kde_map(Y, kw["x0"], kw["y0"], kw["pixel"], kw["width"], kw["height"], kw["h"],
                              cutoff=kw["cutoff"])
+
+
+def _sq_dists(X, rows, idx):
+    Xd = X.astype(np.float64)
+    return np.stack([((Xd[idx[i]] - Xd[r]) ** 2).sum(1) for i, r in enumerate(rows)])
+
+
+@pytest.mark.parametrize("kind", ["mnist", "gauss"])
+def test_knn_fp8_rerank_recall_and_exact_distances(at, kind):
+    # FP8 (E4M3, per-row scale) keys select 4k candidates, re-ranked in FP32:
+    # approximate, so the test measures recall against the oracle, and checks
+    # that every returned distance is the FP32 direct difference of its pair.
+    if kind == "mnist":
+        X = synth.sparse_prototypes(N=6000, seed=2)
+    else:
+        X = synth.gaussian_mixture(4000, 64, seed=1)
+    idx, d2 = at.atsne_knn(to_dev(X), 90, precision="fp8")
+    at.atsne_check()
+    rows = synth.sample_rows(X.shape[0], 200, seed=51)
+    o_idx, o_d2 = oracle.knn_exact(X, 90, queries=rows)
+    g_idx, g_d2 = idx.cpu().numpy()[rows], d2.cpu().numpy()[rows]
+    recall = np.mean([len(set(g_idx[i]) & set(o_idx[i])) / 90 for i in range(len(rows))])
+    print("fp8 recall", kind, recall)
+    assert recall >= 0.99
+    exact = _sq_dists(X, rows, g_idx)
+    assert np.all(np.abs(g_d2 - exact) <= 1e-5 * exact + 1e-3)
+    assert np.all(np.diff(g_d2, axis=1) >= 0)
+    assert np.all(g_idx != rows[:, None])
