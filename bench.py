@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--queue-cap", type=int, default=0, help="forest queue capacity (0 = auto)")
     p.add_argument("--refine", type=int, default=2000, help="points in the refined selection")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--serve-max", type=int, default=2_000_000,
+                   help="serving session: corpus size at which it ends (0 = skip)")
     p.add_argument("--kde-reps", type=int, default=5,
                    help="timed renders of the density / approximation map (0 = skip)")
     p.add_argument("--refine-batch-reps", type=int, default=3,
@@ -248,6 +250,63 @@ def recorded_traffic(kernel, workload):
     except OSError:
         return None
     return None
+
+
+def bench_serving(at, torch, dev, n_max, seed=5):
+    """Serving (Sec. 5.3.1 insertions, Sec. 4.3 refinements) with continuous
+    batching: log-normal D = 50 points in 30 clusters, a corpus growing from
+    100000 rows to n_max, BF16+rerank kNN, 4 stream slots, admission by free
+    HBM. One request sequence (half inserts of log-uniform 1000..50000 points,
+    half refinements of log-uniform 500..50000 existing rows brushed from 1-3
+    clusters, until the corpus is full) is served twice on a fresh server:
+    closed loop (every request arriving at once) for the capacity, then open
+    loop with Poisson arrivals offering 70% of that capacity in points/s
+    (inter-arrival time exponential with mean size / rate). Latency = the
+    completion of a request's state commit minus its arrival."""
+    from paper_1512_01655_gb300 import synth
+    from paper_1512_01655_gb300.serve import Request, Server
+    X, labels = synth.lognormal_clusters(n_max, 50, seed=seed, return_labels=True)
+    N0 = 100_000
+    rng = np.random.default_rng(seed + 1)
+    seq, n = [], N0  # (kind, payload), in arrival order
+    while n < n_max:
+        if rng.random() < 0.5:
+            b = min(int(np.exp(rng.uniform(np.log(1000), np.log(50000)))), n_max - n)
+            seq.append(("insert", (n, n + b)))
+            n += b
+        else:
+            sz = int(np.exp(rng.uniform(np.log(500), np.log(50000))))
+            cl = rng.choice(30, size=int(rng.integers(1, 4)), replace=False)
+            pool = np.flatnonzero(np.isin(labels[:n], cl))
+            seq.append(("refine", np.sort(rng.choice(pool, size=min(sz, pool.size),
+                                                     replace=False)).astype(np.int32)))
+
+    def requests(arrivals):
+        out = []
+        for j, ((kind, pay), t) in enumerate(zip(seq, arrivals)):
+            if kind == "insert":
+                out.append(Request(j, "insert", t, points=X[pay[0]:pay[1]]))
+            else:
+                out.append(Request(j, "refine", t, rows=pay))
+        return out
+
+    sizes = np.array([(p[1] - p[0]) if k == "insert" else len(p) for k, p in seq], np.float64)
+    srv = Server(X[:N0], capacity=n_max, k=K_NN, perplexity=PERPLEXITY, precision="bf16", slots=4)
+    _, closed = srv.run(requests(np.zeros(len(seq))))
+    del srv
+    torch.cuda.empty_cache()
+    rate = 0.7 * closed["points_per_s"]
+    arr = np.cumsum(rng.exponential(sizes / rate))
+    srv = Server(X[:N0], capacity=n_max, k=K_NN, perplexity=PERPLEXITY, precision="bf16", slots=4)
+    _, opened = srv.run(requests(arr))
+    at.atsne_check()
+    out = {"workload": "log-normal D=50, 30 clusters; corpus %d -> %d rows; %d requests; BF16+rerank; "
+                       "4 slots" % (N0, srv.N, len(seq)),
+           "capacity_points_per_s": closed["points_per_s"], "offered_points_per_s": round(rate, 1)}
+    out.update(opened)
+    del srv
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_kde(at, torch, dev, stream, labels, rho_i, reps, clk, peaks):
@@ -533,6 +592,10 @@ def run_ours(args, world, rank, local, pg):
                 entry["recall_vs_fp32"] = round(at.atsne_knn_precision(idx_p, ref_idx)[1], 6)
             exact_p[prec] = entry
 
+    serving = None
+    if args.serve_max > 0 and world == 1:
+        serving = bench_serving(at, torch, dev, args.serve_max)
+
     kde = None
     if args.kde_reps > 0:
         kde = bench_kde(at, torch, dev, stream, labels, rho_i, args.kde_reps, clk, peaks)
@@ -566,7 +629,7 @@ def run_ours(args, world, rank, local, pg):
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
             "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
-            "refine_batch": refine_batch, "kde": kde,
+            "refine_batch": refine_batch, "kde": kde, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }

@@ -64,7 +64,9 @@ typedef enum {
     ATSNE_OP_REFINE = 3,
     ATSNE_OP_FOREST_BUILD = 4,
     ATSNE_OP_FOREST_QUERY = 5,
-    ATSNE_OP_REFINE_BATCH = 6  /* S = total entries of the concatenated selections */
+    ATSNE_OP_REFINE_BATCH = 6, /* S = total entries of the concatenated selections */
+    ATSNE_OP_KNN_CROSS = 7,    /* N = corpus rows, S = query rows */
+    ATSNE_OP_KNN_CROSS_RADIUS = 8  /* as KNN_CROSS, with per-row radii */
 } atsne_op;
 
 /* Options of the kNN step. atsne_knn_opts_default() fills the defaults. */
@@ -194,6 +196,70 @@ atsne_status atsne_refine_batch(const float *X, int64_t N, int32_t D, const int3
                                 int64_t total, int32_t k, float perplexity, int32_t *idx, float *d2,
                                 float *P_cond, float *beta, float *rho, int64_t *refined_count,
                                 void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * atsne_knn for listed rows (method EXACT) with optional per-row bounds:
+ * hint_d2 [S] (device, or NULL) holds for each listed row an upper bound of
+ * its k-th nearest squared distance, e.g. its current d2[i][k-1] when the row
+ * lists k real points (Sec. 4.3's refinement of an approximate row). The
+ * tensor-core filter starts from it instead of from +inf; the result is the
+ * same exact neighbourhood whatever the bounds (a wrong one costs time only:
+ * its rows fail the certificate and take the brute-force kernel).
+ * Workspace: atsne_workspace_bytes(ATSNE_OP_KNN, N, D, k, S, opts).
+ */
+atsne_status atsne_knn_rows(const float *X, int64_t N, int32_t D, const int32_t *queries, int64_t S,
+                            int32_t k, const atsne_knn_opts *opts, const float *hint_d2,
+                            int32_t *idx_out, float *d2_out, void *workspace, size_t ws_bytes,
+                            void *stream);
+
+/*
+ * k nearest rows of Xc for each row of Xq, Eq. 8 across two point sets; no
+ * point is excluded. Insertion (Sec. 5.3.1) uses it for the candidates of
+ * the existing points among the inserted ones. Output row r belongs to
+ * Xq[r], indices are rows of Xc, sorted by (d^2, index).
+ *  Xq [Nq][D], Xc [Nc][D] fp32 (device, finite); 1 <= k <= Nc.
+ *  opts: the exact method's precision (FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK).
+ *  radius_d2  NULL, or [Nq] fp32 squared radii: row r then lists only the rows
+ *             of Xc with d^2 < radius_d2[r] among its k nearest, the rest of
+ *             the row (-1, +inf). With the radius of each existing point's
+ *             farthest neighbour (its cached d_i^Max), this is Eq. 11's test
+ *             (Sec. 5.3.1) in O(Nq * Nc) without a top-k per row; on the tensor
+ *             cores it is exact (the filter is widened by the key error bound
+ *             and every candidate is re-ranked in FP32).
+ * Workspace: atsne_workspace_bytes(radius_d2 ? ATSNE_OP_KNN_CROSS_RADIUS :
+ * ATSNE_OP_KNN_CROSS, Nc, D, k, Nq, opts).
+ */
+atsne_status atsne_knn_cross(const float *Xq, int64_t Nq, const float *Xc, int64_t Nc, int32_t D,
+                             int32_t k, const atsne_knn_opts *opts, const float *radius_d2,
+                             int32_t *idx_out, float *d2_out, void *workspace, size_t ws_bytes,
+                             void *stream);
+
+/*
+ * Insertion of new points into existing neighbourhoods, Eq. 11 (Sec. 5.3.1),
+ * for a batch: row i of idx/d2 ([rows][k], sorted by (d^2, index)) becomes the
+ * k smallest of its list and its kc candidates (cand_idx + index_offset,
+ * cand_d2: [rows][kc], sorted, e.g. atsne_knn_cross against the new points).
+ * A candidate enters exactly when it is closer than the row's farthest
+ * neighbour d_i^Max (ties go to the listed point, whose index is smaller), and
+ * takes the place of the farthest ones. changed [rows] uint8 (may be NULL)
+ * receives 1 for a row whose list changed. rho is not touched (insertion does
+ * not lower the precision); re-run atsne_calibrate_P on the changed rows.
+ */
+atsne_status atsne_merge_neighbors(int32_t *idx, float *d2, int64_t rows, int32_t k,
+                                   const int32_t *cand_idx, const float *cand_d2, int32_t kc,
+                                   int32_t index_offset, uint8_t *changed, void *stream);
+
+/*
+ * Writes S computed rows into the state: row rows[s] of idx/d2/P_cond ([N][k])
+ * receives row s of ti/td/tp ([S][k]), beta[rows[s]] = tb[s] and rho[rows[s]] =
+ * 1 (an exactly computed neighbourhood, Sec. 4.3). Entries of rows outside
+ * [0, N) are skipped. beta, rho and tb may be NULL. This is the write step of a
+ * refinement or an insertion, for callers that compute rows on one stream and
+ * commit them on another.
+ */
+atsne_status atsne_commit_rows(const int32_t *rows, int64_t S, int64_t N, int32_t k, const int32_t *ti,
+                               const float *td, const float *tp, const float *tb, int32_t *idx,
+                               float *d2, float *P_cond, float *beta, float *rho, void *stream);
 
 /*
  * Density-based view of a 2-D embedding and its approximation map, Sec. 5.2.

@@ -46,6 +46,7 @@ def lib():
                                           _i64p, _vp, _i64, _i32, _i32, _i32, _i32p, _f64p, _i64p]
         L.oracle_kde.argtypes = [_f32p, _i64, _vp, _vp, _f64, _f64, _f64, _i32, _i32, _f64, _f64,
                                  _f64, _f64p, _f64p, _f64p, _f64p]
+        L.oracle_knn_cross.argtypes = [_f32p, _i64, _f32p, _i64, _i32, _i32, _i32p, _f64p]
         L.oracle_refine.argtypes = [_f32p, _i64, _i32, _i32p, _i64, _i32, _f64, _f64, _i32, _i32p,
                                     _f64p, _f64p, _f64p, _f64p]
         _lib = L
@@ -210,3 +211,14 @@ def kde(Y, x0, y0, pixel, width, height, h, cutoff=4.0, k=2.0, rho=None, selecte
                             None if sl is None else sl.ctypes.data_as(_vp), x0, y0, pixel, width,
                             height, h, cutoff, k, *out), "kde")
     return tuple(out)
+
+
+def knn_cross(Xq, Xc, k):
+    """The k nearest rows of Xc for each row of Xq (Eq. 8 across two sets)."""
+    Xq = np.ascontiguousarray(Xq, dtype=np.float32)
+    Xc = np.ascontiguousarray(Xc, dtype=np.float32)
+    idx = np.empty((Xq.shape[0], k), np.int32)
+    d2 = np.empty((Xq.shape[0], k), np.float64)
+    _check(lib().oracle_knn_cross(Xq, Xq.shape[0], Xc, Xc.shape[0], Xq.shape[1], k, idx, d2),
+           "knn_cross")
+    return idx, d2

@@ -22,6 +22,7 @@
  *                        selected points, new Gaussian, rho_i = 1
  *   oracle_precision     Eq. 9 (Sec. 4.1)
  *   oracle_kde           Eq. 12, Eq. 13 and the approximation map of Sec. 5.2.2
+ *   oracle_knn_cross     Eq. 8 across two point sets (insertion, Sec. 5.3.1)
  *
  * Readings taken where the paper is silent are stated at each function.
  * Compile with -ffp-contract=off: the forest's float decisions (split value,
@@ -719,6 +720,27 @@ int oracle_kde(const float *Y, int64_t N, const float *rho, const uint8_t *sel, 
             a[o] = F > 0.0 ? R / F : 1.0;
             alpha[o] = 1.0 - pow(a[o], k);
         }
+    }
+    return 0;
+}
+
+
+/*
+ * The k nearest rows of Xc for each row of Xq (Eq. 8 with the query set apart
+ * from the corpus, as insertion needs in Sec. 5.3.1): FP64 direct differences,
+ * no point excluded, order (d^2, index).
+ */
+int oracle_knn_cross(const float *Xq, int64_t Nq, const float *Xc, int64_t Nc, int32_t D, int32_t k,
+                     int32_t *idx, double *d2)
+{
+    if (k < 1 || k > Nc) return 1;
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int64_t q = 0; q < Nq; ++q) {
+        double *bd = d2 + q * k;
+        int32_t *bj = idx + q * k;
+        int cnt = 0;
+        for (int64_t j = 0; j < Nc; ++j)
+            best_insert(bd, bj, k, &cnt, sq_dist(Xq + q * D, Xc + j * D, D), (int32_t)j);
     }
     return 0;
 }

@@ -17,14 +17,16 @@ ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPP
 KNN_EXACT, KNN_FOREST = 0, 1
 FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK = 0, 1, 2, 3
 (OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY,
- OP_REFINE_BATCH) = range(7)
+ OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS) = range(9)
 
 EXPORTED = (
     "atsne_knn_opts_default", "atsne_workspace_bytes", "atsne_knn", "atsne_calibrate_P",
     "atsne_symmetrize", "atsne_refine_subset", "atsne_knn_precision", "atsne_forest_layout",
     "atsne_forest_build", "atsne_forest_query", "atsne_check", "atsne_last_error",
     "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
-    "atsne_refine_subset_noalloc", "atsne_refine_batch", "atsne_kde_map",
+    "atsne_refine_subset_noalloc", "atsne_refine_batch", "atsne_kde_map", "atsne_knn_cross",
+    "atsne_knn_rows",
+    "atsne_merge_neighbors", "atsne_commit_rows",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
@@ -79,6 +81,13 @@ def lib():
         L.atsne_refine_batch.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _vp, _vp,
                                          _vp, _vp, _vp, _vp, _sz, _vp]
         L.atsne_knn_precision.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
+        L.atsne_knn_cross.argtypes = [_vp, _i64, _vp, _i64, _i32, _i32, ctypes.POINTER(KnnOpts),
+                                      _vp, _vp, _vp, _vp, _sz, _vp]
+        L.atsne_knn_rows.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, ctypes.POINTER(KnnOpts), _vp,
+                                     _vp, _vp, _vp, _sz, _vp]
+        L.atsne_merge_neighbors.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _i32, _vp, _vp]
+        L.atsne_commit_rows.argtypes = [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                        _vp, _vp, _vp]
         L.atsne_kde_map.argtypes = [_vp, _i64, _vp, _vp, _f32, _f32, _f32, _i32, _i32, _f32, _f32,
                                     _f32, _vp, _vp, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
@@ -166,12 +175,13 @@ def atsne_knn(X, k, queries=None, opts=None, stream=None, **kw):
     return idx, d2
 
 
-def atsne_calibrate_P(d2, perplexity, tol=0.0, max_iter=0, stream=None):
-    """Conditional rows P_{j|i} and beta by bisection -- Eq. 3-4 over N_i."""
+def atsne_calibrate_P(d2, perplexity, tol=0.0, max_iter=0, stream=None, P_out=None, beta_out=None):
+    """Conditional rows P_{j|i} and beta by bisection -- Eq. 3-4 over N_i.
+    P_out / beta_out: contiguous tensors to write into (else new ones)."""
     _dev(d2, torch.float32, "d2")
     rows, k = d2.shape
-    P = torch.empty_like(d2)
-    beta = torch.empty(rows, dtype=torch.float32, device=d2.device)
+    P = torch.empty_like(d2) if P_out is None else P_out
+    beta = torch.empty(rows, dtype=torch.float32, device=d2.device) if beta_out is None else beta_out
     _raise(lib().atsne_calibrate_P(_p(d2), rows, k, perplexity, tol, max_iter, _p(P), _p(beta),
                                    _stream(stream)))
     return P, beta
@@ -232,6 +242,64 @@ def atsne_refine_batch(X, lists, perplexity, idx, d2, P_cond, beta=None, rho=Non
                                     _p(P_cond), _p(beta), _p(rho), _p(count), _p(ws), ws.numel(),
                                     _stream(stream)))
     return count
+
+
+def atsne_knn_rows(X, queries, k, hint_d2=None, opts=None, stream=None, **kw):
+    """Exact kNN of the listed rows, with optional per-row upper bounds of the
+    k-th squared distance (hint_d2 [S]) that seed the filter."""
+    _dev(X, torch.float32, "X")
+    _dev(queries, torch.int32, "queries")
+    N, D = X.shape
+    S = queries.shape[0]
+    o = opts or knn_opts(**kw)
+    if hint_d2 is not None:
+        _dev(hint_d2, torch.float32, "hint_d2")
+    idx = torch.empty((S, k), dtype=torch.int32, device=X.device)
+    d2 = torch.empty((S, k), dtype=torch.float32, device=X.device)
+    ws = _workspace(workspace_bytes(OP_KNN, N, D, k, S, o), X.device)
+    _raise(lib().atsne_knn_rows(_p(X), N, D, _p(queries), S, k, ctypes.byref(o), _p(hint_d2),
+                                _p(idx), _p(d2), _p(ws), ws.numel(), _stream(stream)))
+    return idx, d2
+
+
+def atsne_knn_cross(Xq, Xc, k, opts=None, stream=None, workspace=None, radius_d2=None, **kw):
+    """The k nearest rows of Xc for each row of Xq (Eq. 8 across two sets);
+    with radius_d2 [Nq] only those strictly inside each row's squared radius
+    (the rest of the row -1 / +inf)."""
+    _dev(Xq, torch.float32, "Xq")
+    _dev(Xc, torch.float32, "Xc")
+    Nq, D = Xq.shape
+    Nc = Xc.shape[0]
+    o = opts or knn_opts(**kw)
+    if radius_d2 is not None:
+        _dev(radius_d2, torch.float32, "radius_d2")
+    idx = torch.empty((Nq, k), dtype=torch.int32, device=Xq.device)
+    d2 = torch.empty((Nq, k), dtype=torch.float32, device=Xq.device)
+    op = OP_KNN_CROSS if radius_d2 is None else OP_KNN_CROSS_RADIUS
+    ws = workspace if workspace is not None else \
+        _workspace(workspace_bytes(op, Nc, D, k, Nq, o), Xq.device)
+    _raise(lib().atsne_knn_cross(_p(Xq), Nq, _p(Xc), Nc, D, k, ctypes.byref(o), _p(radius_d2),
+                                 _p(idx), _p(d2), _p(ws), ws.numel(), _stream(stream)))
+    return idx, d2
+
+
+def atsne_merge_neighbors(idx, d2, cand_idx, cand_d2, index_offset, changed=None, stream=None):
+    """Insert candidates into the first cand_idx.shape[0] rows of idx/d2 in
+    place (Eq. 11, Sec. 5.3.1); returns the uint8 changed-row flags."""
+    rows, kc = cand_idx.shape
+    k = idx.shape[1]
+    if changed is None:
+        changed = torch.empty(rows, dtype=torch.uint8, device=idx.device)
+    _raise(lib().atsne_merge_neighbors(_p(idx), _p(d2), rows, k, _p(cand_idx), _p(cand_d2), kc,
+                                       int(index_offset), _p(changed), _stream(stream)))
+    return changed
+
+
+def atsne_commit_rows(rows, ti, td, tp, tb, idx, d2, P_cond, beta=None, rho=None, stream=None):
+    """Write computed rows into the state (rho := 1 on them) -- Sec. 4.3."""
+    S, k = ti.shape
+    _raise(lib().atsne_commit_rows(_p(rows), S, idx.shape[0], k, _p(ti), _p(td), _p(tp), _p(tb),
+                                   _p(idx), _p(d2), _p(P_cond), _p(beta), _p(rho), _stream(stream)))
 
 
 def atsne_kde_map(Y, x0, y0, pixel, width, height, h, cutoff=4.0, lens_k=2.0, rho=None,

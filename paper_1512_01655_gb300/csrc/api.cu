@@ -236,15 +236,18 @@ atsne_status check_base(const void *p, const char *what) {
 constexpr int64_t REFINE_TC_MIN_ROWS = 128;
 
 size_t refine_ws(Carver &c, int64_t N, int32_t D, int64_t S, int32_t k, int32_t **ti, float **td,
-                 float **tp, float **tb, TcPlan *plan = nullptr, TcWs *tws = nullptr) {
+                 float **tp, float **tb, TcPlan *plan = nullptr, TcWs *tws = nullptr,
+                 float **hint = nullptr) {
     int32_t *a = c.take<int32_t>((size_t)S * k);
     float *b = c.take<float>((size_t)S * k);
     float *p = c.take<float>((size_t)S * k);
     float *q = c.take<float>((size_t)(S > 0 ? S : 1));
+    float *h = c.take<float>((size_t)(S > 0 ? S : 1));
     if (ti) *ti = a;
     if (td) *td = b;
     if (tp) *tp = p;
     if (tb) *tb = q;
+    if (hint) *hint = h;
     if (S >= REFINE_TC_MIN_ROWS && k <= 200) {
         const TcPlan pl = tc_plan(N, D, S, k, ATSNE_FP32, 0);
         if (plan) *plan = pl;
@@ -253,17 +256,29 @@ size_t refine_ws(Carver &c, int64_t N, int32_t D, int64_t S, int32_t k, int32_t 
     return c.bytes();
 }
 
+// kNN of Nq rows of another array among Nc corpus rows.
+size_t cross_ws(Carver &c, int64_t Nq, int64_t Nc, int32_t D, int32_t k, const atsne_knn_opts &o,
+                bool radius, TcPlan *plan, TcWs *tws) {
+    if (exact_on_tensor_cores(o, k) && Nq > 0 && !(radius && o.precision == ATSNE_FP8_RERANK)) {
+        TcPlan pl = tc_plan(Nc, D, Nq, k, o.precision, o.rerank_k);
+        if (radius) pl.cap = RADIUS_CAP;  // only the points inside the radius are buffered
+        if (plan) *plan = pl;
+        tc_workspace(c, Nc, D, Nq, true, pl, tws);
+    }
+    return c.bytes();
+}
+
 // Batched refinement: the union's rows (padded to min(N, total)), its bitmap,
 // then the refinement of that many rows.
 size_t refine_batch_ws(Carver &c, int64_t N, int32_t D, int64_t total, int32_t k, int32_t **rows,
                        uint32_t **bitmap, int32_t **ti, float **td, float **tp, float **tb,
-                       TcPlan *plan, TcWs *tws) {
+                       TcPlan *plan, TcWs *tws, float **hint = nullptr) {
     const int64_t rows_max = total < N ? total : N;
     int32_t *r = c.take<int32_t>((size_t)(rows_max > 0 ? rows_max : 1));
     uint32_t *b = c.take<uint32_t>((size_t)((N + 31) / 32));
     if (rows) *rows = r;
     if (bitmap) *bitmap = b;
-    return refine_ws(c, N, D, rows_max, k, ti, td, tp, tb, plan, tws);
+    return refine_ws(c, N, D, rows_max, k, ti, td, tp, tb, plan, tws, hint);
 }
 
 }  // namespace
@@ -307,6 +322,10 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
         return forest_build_workspace(c, N, D, o.trees, o.leaf_size, nullptr);
     case ATSNE_OP_FOREST_QUERY:
         return forest_query_workspace(c, N, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
+    case ATSNE_OP_KNN_CROSS:
+        return cross_ws(c, S, N, D, k, o, false, nullptr, nullptr);
+    case ATSNE_OP_KNN_CROSS_RADIUS:
+        return cross_ws(c, S, N, D, k, o, true, nullptr, nullptr);
     case ATSNE_OP_REFINE_BATCH:
         return refine_batch_ws(c, N, D, S, k, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                nullptr, nullptr);
@@ -394,16 +413,21 @@ atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int
     if (S == 0) return ATSNE_OK;
     Carver c(workspace);
     int32_t *ti;
-    float *td, *tp, *tb;
+    float *td, *tp, *tb, *hint;
     TcPlan plan;
     TcWs tws;
-    refine_ws(c, N, D, S, k, &ti, &td, &tp, &tb, &plan, &tws);
+    refine_ws(c, N, D, S, k, &ti, &td, &tp, &tb, &plan, &tws, &hint);
     if (!workspace || ws_bytes < c.bytes())
         return set_error(ATSNE_ENOMEM, "refine: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
     if ((st = check_base(workspace, "refine workspace"))) return st;
     if ((st = check_indices(subset, S, N, stream))) return st;
     if (S >= REFINE_TC_MIN_ROWS && k <= 200) {  // the prep kernel checks X for non-finite values
-        if ((st = knn_exact_tc(X, N, D, subset, S, k, plan, tws, ti, td, stream))) return st;
+        // the rows' current k-th distances seed the threshold (a row that lists
+        // k real points bounds its exact k-th distance; the certificate keeps
+        // the result exact whatever the bound)
+        if ((st = gather_hint_launch(subset, S, N, k, d2, hint, stream))) return st;
+        if ((st = knn_exact_tc(X, N, D, subset, S, k, plan, tws, ti, td, stream, nullptr, nullptr, hint)))
+            return st;
     } else {
         if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
         if ((st = knn_bruteforce(X, N, D, subset, S, k, ti, td, stream))) return st;
@@ -434,10 +458,10 @@ atsne_status atsne_refine_batch(const float *X, int64_t N, int32_t D, const int3
     Carver c(workspace);
     int32_t *rows, *ti;
     uint32_t *bitmap;
-    float *td, *tp, *tb;
+    float *td, *tp, *tb, *hint;
     TcPlan plan;
     TcWs tws;
-    refine_batch_ws(c, N, D, total, k, &rows, &bitmap, &ti, &td, &tp, &tb, &plan, &tws);
+    refine_batch_ws(c, N, D, total, k, &rows, &bitmap, &ti, &td, &tp, &tb, &plan, &tws, &hint);
     if (!workspace || ws_bytes < c.bytes())
         return set_error(ATSNE_ENOMEM, "refine batch: workspace of %zu bytes, %zu needed", ws_bytes,
                          c.bytes());
@@ -446,13 +470,108 @@ atsne_status atsne_refine_batch(const float *X, int64_t N, int32_t D, const int3
     const int64_t S = total < N ? total : N;
     if ((st = union_launch(lists, total, N, bitmap, rows, S, refined_count, stream))) return st;
     if (S >= REFINE_TC_MIN_ROWS && k <= 200) {  // the prep kernel checks X for non-finite values
-        if ((st = knn_exact_tc(X, N, D, rows, S, k, plan, tws, ti, td, stream))) return st;
+        if ((st = gather_hint_launch(rows, S, N, k, d2, hint, stream))) return st;
+        if ((st = knn_exact_tc(X, N, D, rows, S, k, plan, tws, ti, td, stream, nullptr, nullptr, hint)))
+            return st;
     } else {
         if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
         if ((st = knn_bruteforce(X, N, D, rows, S, k, ti, td, stream))) return st;
     }
     if ((st = calibrate_launch(td, S, k, perplexity, 1e-5f, 200, tp, tb, stream))) return st;
     return refine_scatter_launch(rows, S, N, k, ti, td, tp, tb, idx, d2, P_cond, beta, rho, stream);
+}
+
+atsne_status atsne_knn_rows(const float *X, int64_t N, int32_t D, const int32_t *queries, int64_t S,
+                            int32_t k, const atsne_knn_opts *opts, const float *hint_d2,
+                            int32_t *idx_out, float *d2_out, void *workspace, size_t ws_bytes,
+                            void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_status st = validate_xk(X, N, D, k);
+    if (st) return st;
+    const atsne_knn_opts o = opts_or_default(opts);
+    if ((st = validate_knn_opts(o))) return st;
+    if (o.method != ATSNE_KNN_EXACT) return set_error(ATSNE_EINVAL, "knn rows: exact method only");
+    if (!queries || !idx_out || !d2_out) return set_error(ATSNE_EINVAL, "knn rows: NULL pointer");
+    if (S < 0) return set_error(ATSNE_EINVAL, "knn rows: S=%lld < 0", (long long)S);
+    if (S == 0) return ATSNE_OK;
+    Carver c(workspace);
+    void *forest = nullptr, *sub = nullptr;
+    size_t sub_bytes = 0;
+    TcPlan plan;
+    TcWs tws;
+    knn_ws(c, N, D, k, S, o, &forest, &sub, &sub_bytes, &plan, &tws);
+    if (c.bytes() > 0 && (!workspace || ws_bytes < c.bytes()))
+        return set_error(ATSNE_ENOMEM, "knn rows: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    if ((st = check_base(workspace, "knn rows workspace"))) return st;
+    if ((st = check_indices(queries, S, N, stream))) return st;
+    if (exact_on_tensor_cores(o, k))
+        return knn_exact_tc(X, N, D, queries, S, k, plan, tws, idx_out, d2_out, stream, nullptr, nullptr,
+                            hint_d2);
+    if ((st = check_finite(X, N * (int64_t)D, stream))) return st;
+    return knn_bruteforce(X, N, D, queries, S, k, idx_out, d2_out, stream);
+}
+
+atsne_status atsne_knn_cross(const float *Xq, int64_t Nq, const float *Xc, int64_t Nc, int32_t D,
+                             int32_t k, const atsne_knn_opts *opts, const float *radius_d2,
+                             int32_t *idx_out, float *d2_out, void *workspace, size_t ws_bytes,
+                             void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    const atsne_knn_opts o = opts_or_default(opts);
+    atsne_status st = validate_knn_opts(o);
+    if (st) return st;
+    if (o.method != ATSNE_KNN_EXACT) return set_error(ATSNE_EINVAL, "knn cross: exact method only");
+    if (!Xq || !Xc || !idx_out || !d2_out) return set_error(ATSNE_EINVAL, "knn cross: NULL pointer");
+    if (Nq < 0 || Nq > INT32_MAX || Nc < 1 || Nc > INT32_MAX || D < 1 || k < 1 || (int64_t)k > Nc)
+        return set_error(ATSNE_EINVAL, "knn cross: Nq=%lld Nc=%lld D=%d k=%d", (long long)Nq,
+                         (long long)Nc, D, k);
+    if (Nq == 0) return ATSNE_OK;
+    Carver c(workspace);
+    TcPlan plan;
+    TcWs tws;
+    cross_ws(c, Nq, Nc, D, k, o, radius_d2 != nullptr, &plan, &tws);
+    if (c.bytes() > 0 && (!workspace || ws_bytes < c.bytes()))
+        return set_error(ATSNE_ENOMEM, "knn cross: workspace of %zu bytes, %zu needed", ws_bytes, c.bytes());
+    if ((st = check_base(workspace, "knn cross workspace"))) return st;
+    // radius mode needs the certified keys: the FP8 variant takes the CUDA-core path
+    const bool tc = exact_on_tensor_cores(o, k) && !(radius_d2 && o.precision == ATSNE_FP8_RERANK);
+    if (tc)  // both prep kernels check their rows for non-finite values
+        return knn_exact_tc(Xc, Nc, D, nullptr, Nq, k, plan, tws, idx_out, d2_out, stream, Xq, radius_d2);
+    if ((st = check_finite(Xc, Nc * (int64_t)D, stream))) return st;
+    if ((st = check_finite(Xq, Nq * (int64_t)D, stream))) return st;
+    if ((st = knn_bruteforce_rows(Xc, Nc, D, nullptr, nullptr, nullptr, Nq, k, idx_out, d2_out, stream,
+                                  Xq)))
+        return st;
+    return radius_d2 ? radius_filter_launch(idx_out, d2_out, Nq, k, radius_d2, stream) : ATSNE_OK;
+}
+
+atsne_status atsne_merge_neighbors(int32_t *idx, float *d2, int64_t rows, int32_t k,
+                                   const int32_t *cand_idx, const float *cand_d2, int32_t kc,
+                                   int32_t index_offset, uint8_t *changed, void *stream) {
+    if (rows < 0 || k < 1 || kc < 0) return set_error(ATSNE_EINVAL, "merge neighbors: rows=%lld k=%d kc=%d",
+                                                      (long long)rows, k, kc);
+    if (rows == 0 || kc == 0) {
+        if (rows > 0 && changed) {
+            cudaError_t e = cudaMemsetAsync(changed, 0, (size_t)rows, static_cast<cudaStream_t>(stream));
+            if (e != cudaSuccess) return cuda_error(e, "merge neighbors");
+        }
+        return ATSNE_OK;
+    }
+    if (!idx || !d2 || !cand_idx || !cand_d2) return set_error(ATSNE_EINVAL, "merge neighbors: NULL pointer");
+    return merge_neighbors_launch(idx, d2, rows, k, cand_idx, cand_d2, kc, index_offset, changed,
+                                  static_cast<cudaStream_t>(stream));
+}
+
+atsne_status atsne_commit_rows(const int32_t *rows, int64_t S, int64_t N, int32_t k, const int32_t *ti,
+                               const float *td, const float *tp, const float *tb, int32_t *idx,
+                               float *d2, float *P_cond, float *beta, float *rho, void *stream) {
+    if (S < 0 || N < 1 || k < 1) return set_error(ATSNE_EINVAL, "commit rows: S=%lld N=%lld k=%d",
+                                                  (long long)S, (long long)N, k);
+    if (S == 0) return ATSNE_OK;
+    if (!rows || !ti || !td || !tp || !idx || !d2 || !P_cond)
+        return set_error(ATSNE_EINVAL, "commit rows: NULL pointer");
+    if (!tb) beta = nullptr;
+    return refine_scatter_launch(rows, S, N, k, ti, td, tp, tb, idx, d2, P_cond, beta, rho,
+                                 static_cast<cudaStream_t>(stream));
 }
 
 atsne_status atsne_kde_map(const float *Y, int64_t N, const float *rho, const uint8_t *selected,

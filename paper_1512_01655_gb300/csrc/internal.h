@@ -19,7 +19,8 @@ atsne_status knn_bruteforce(const float *X, int64_t N, int D, const int32_t *qli
 // The rows listed in rows_list[0 .. *rows_count) (device count, at most nq).
 atsne_status knn_bruteforce_rows(const float *X, int64_t N, int D, const int32_t *qlist,
                                  const int32_t *rows_list, const int32_t *rows_count, int64_t nq,
-                                 int k, int32_t *idx_out, float *d2_out, cudaStream_t stream);
+                                 int k, int32_t *idx_out, float *d2_out, cudaStream_t stream,
+                                 const float *Xq = nullptr);
 
 // Tensor-core exact kNN: plan (tile split, candidate capacity) and workspace.
 struct TcPlan {
@@ -32,13 +33,21 @@ struct TcWs {
     char *cand = nullptr, *meta = nullptr;
     unsigned *row_hist = nullptr;
     float *scale = nullptr, *qscale = nullptr;  // FP8 row scales
+    float *qnrm = nullptr, *qstats = nullptr;   // queries from another array: norms, error stats
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
 };
 TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k);
 size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcPlan &pl, TcWs *ws);
+// Xq != nullptr: the Q queries are the rows of Xq (another array), none excluded.
+// radius != nullptr (with Xq): only neighbours with d^2 < radius[row] are kept,
+// the row padded with (-1, +inf); the plan's cap is then RADIUS_CAP.
+constexpr int RADIUS_CAP = 256;
+atsne_status radius_filter_launch(int32_t *idx, float *d2, int64_t rows, int k, const float *radius,
+                                  cudaStream_t stream);
 atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist, int64_t Q, int k,
                           const TcPlan &pl, const TcWs &w, int32_t *idx_out, float *d2_out,
-                          cudaStream_t stream);
+                          cudaStream_t stream, const float *Xq = nullptr,
+                          const float *radius = nullptr, const float *hint = nullptr);
 
 // ---- calibrate ------------------------------------------------------------
 size_t calibrate_smem_bytes(int k);
@@ -67,6 +76,11 @@ atsne_status kde_launch(const float *Y, int64_t N, const float *rho, const uint8
                         float y0, float pixel, int W, int H, float h, float cutoff, float lens_k,
                         float *f_out, float *s_out, float *a_out, float *alpha_out,
                         cudaStream_t stream);
+atsne_status gather_hint_launch(const int32_t *rows, int64_t S, int64_t N, int k, const float *d2,
+                                float *hint, cudaStream_t stream);
+atsne_status merge_neighbors_launch(int32_t *idx, float *d2, int64_t rows, int k, const int32_t *cidx,
+                                    const float *cd2, int kc, int32_t offset, uint8_t *changed,
+                                    cudaStream_t stream);
 atsne_status union_launch(const int32_t *lists, int64_t total, int64_t N, uint32_t *bitmap,
                           int32_t *out, int64_t out_rows, int64_t *count, cudaStream_t stream);
 atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, int k, const int32_t *ti,

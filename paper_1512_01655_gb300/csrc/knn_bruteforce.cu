@@ -24,15 +24,19 @@ constexpr int BF_DC = 32;       // dimensions per slice
 constexpr int BF_THREADS = 256;
 
 // Work item s (0 <= s < nq, or < *rows_count when rows_list is given) is output
-// row r = rows_list ? rows_list[s] : s, whose query point is qlist ? qlist[r] : r.
-// CTAs stride over blocks of 32 work items.
+// row r = rows_list ? rows_list[s] : s, whose query point is qlist ? qlist[r] : r
+// of X, or, with Xq (queries against another corpus), row r of Xq, with no
+// point excluded. CTAs stride over blocks of 32 work items.
 template <int KCAP>
 __global__ void __launch_bounds__(BF_THREADS)
 knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
                       const int32_t *__restrict__ qlist, int64_t nq,
                       const int32_t *__restrict__ rows_list, const int32_t *__restrict__ rows_count,
-                      int k, int32_t *__restrict__ idx_out, float *__restrict__ d2_out) {
+                      int k, int32_t *__restrict__ idx_out, float *__restrict__ d2_out,
+                      const float *__restrict__ Xq) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const bool cross = Xq != nullptr;
+    const float *QX = cross ? Xq : X;
     float *Qs = reinterpret_cast<float *>(smem_raw);      // [QB][DC+1]
     float *Cs = Qs + BF_QB * (BF_DC + 1);                 // [CB][DC+1]
     float *Dt = Cs + BF_CB * (BF_DC + 1);                 // [QB][CB+1]
@@ -53,9 +57,9 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
         int q = -1;
         if (s < n_items) {
             r = rows_list ? rows_list[s] : s;
-            q = qlist ? qlist[r] : (int)r;
+            q = cross ? (int)r : (qlist ? qlist[r] : (int)r);
         }
-        qid[tid] = (q >= 0 && q < N) ? q : -1;  // out-of-range queries are flagged by the caller
+        qid[tid] = (q >= 0 && (cross || q < N)) ? q : -1;  // out-of-range queries are flagged by the caller
         orow[tid] = r;
         thr_d[tid] = INFINITY;
         thr_j[tid] = INT_MAX;
@@ -76,7 +80,7 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
             for (int t = tid; t < BF_QB * BF_DC; t += BF_THREADS) {
                 int r = t / BF_DC, c = t - r * BF_DC;
                 int q = qid[r];
-                Qs[r * (BF_DC + 1) + c] = (q >= 0 && d0 + c < D) ? X[(int64_t)q * D + d0 + c] : 0.f;
+                Qs[r * (BF_DC + 1) + c] = (q >= 0 && d0 + c < D) ? QX[(int64_t)q * D + d0 + c] : 0.f;
             }
             for (int t = tid; t < BF_CB * BF_DC; t += BF_THREADS) {
                 int r = t / BF_DC, c = t - r * BF_DC;
@@ -109,7 +113,7 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
             for (int h = 0; h < 2; ++h) {
                 const int c = lane + 32 * h;
                 const int64_t j = c0 + c;
-                const bool valid = j < N && j != q;
+                const bool valid = j < N && (cross || j != q);
                 const float cd = valid ? Dt[r * (BF_CB + 1) + c] : INFINITY;
                 const int cj = valid ? (int)j : INT_MAX;
                 unsigned ball = __ballot_sync(0xffffffffu, pair_less(cd, cj, md, mj));
@@ -166,7 +170,7 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
 template <int KCAP>
 atsne_status launch_bf(const float *X, int64_t N, int D, const int32_t *qlist, int64_t nq,
                        const int32_t *rows_list, const int32_t *rows_count, int k,
-                       int32_t *idx_out, float *d2_out, cudaStream_t stream) {
+                       int32_t *idx_out, float *d2_out, cudaStream_t stream, const float *Xq) {
     const size_t smem = sizeof(float) * (BF_QB * (BF_DC + 1) + BF_CB * (BF_DC + 1) +
                                          BF_QB * (BF_CB + 1) + BF_QB * KCAP) +
                         sizeof(int) * BF_QB * KCAP;
@@ -180,7 +184,7 @@ atsne_status launch_bf(const float *X, int64_t N, int D, const int32_t *qlist, i
     const int grid = rows_count ? (int)hmin(2 * num_sms(), ceil_div(nq, BF_QB)) : ceil_div(nq, BF_QB);
     return launch_kernel(rows_count ? "knn_fallback" : "knn_bruteforce", knn_bruteforce_kernel<KCAP>,
                          grid, BF_THREADS, smem, stream, X, N, D, qlist, nq, rows_list, rows_count,
-                         k, idx_out, d2_out);
+                         k, idx_out, d2_out, Xq);
 }
 
 }  // namespace
@@ -192,11 +196,12 @@ atsne_status knn_bruteforce(const float *X, int64_t N, int D, const int32_t *qli
 
 atsne_status knn_bruteforce_rows(const float *X, int64_t N, int D, const int32_t *qlist,
                                  const int32_t *rows_list, const int32_t *rows_count, int64_t nq,
-                                 int k, int32_t *idx_out, float *d2_out, cudaStream_t stream) {
+                                 int k, int32_t *idx_out, float *d2_out, cudaStream_t stream,
+                                 const float *Xq) {
     if (nq <= 0) return ATSNE_OK;
-    if (k <= 128) return launch_bf<128>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream);
-    if (k <= 256) return launch_bf<256>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream);
-    if (k <= 512) return launch_bf<512>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream);
+    if (k <= 128) return launch_bf<128>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream, Xq);
+    if (k <= 256) return launch_bf<256>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream, Xq);
+    if (k <= 512) return launch_bf<512>(X, N, D, qlist, nq, rows_list, rows_count, k, idx_out, d2_out, stream, Xq);
     return set_error(ATSNE_EUNSUPPORTED, "knn: k=%d above the supported maximum of 512", k);
 }
 

@@ -112,6 +112,12 @@ struct TcParams {
     const float *nrm;      // [N] corpus ||x||^2
     const float *scale;    // FP8: [N] corpus row scales (x ~ scale * q)
     const float *qscale;   // FP8 with a query list: [Q] query row scales
+    const float *qnrm;     // queries from another array: [Q] their ||x||^2 (no self exclusion)
+    const float *radius;   // radius mode: [Q] squared radius per query row (else nullptr)
+    const float *hint;     // [Q] upper bounds of each query row's k-th squared distance (or nullptr)
+    const float4 *qst;     // queries from another array: their error statistics
+    const float4 *st;      // corpus rows' error statistics (for listed queries)
+    float acc_coef;        // FP32 accumulation term of the key error bound
     const unsigned *gmax;  // max ||x|| over the corpus (float bits)
     const int32_t *qlist;  // query row -> corpus index (nullptr: identity)
     int64_t Q, N;
@@ -265,9 +271,11 @@ knn_prep_kernel(const float *__restrict__ X, const int32_t *__restrict__ rows, i
         nrm[r] = n;
         const float a = sqrtf(n), e = sqrtf(res), l = sqrtf(l2);
         stats[r] = make_float4(a, e, l, 0.f);
-        atomicMax(&gmax[0], __float_as_uint(a));
-        atomicMax(&gmax[1], __float_as_uint(e));
-        atomicMax(&gmax[2], __float_as_uint(l));
+        if (gmax) {  // corpus rows only
+            atomicMax(&gmax[0], __float_as_uint(a));
+            atomicMax(&gmax[1], __float_as_uint(e));
+            atomicMax(&gmax[2], __float_as_uint(l));
+        }
     }
 }
 
@@ -304,16 +312,28 @@ knn_prep_fp8_kernel(const float *__restrict__ X, const int32_t *__restrict__ row
     }
     if (lane == 0) {
         scale[r] = sc;
-        if (nrm) {
-            nrm[r] = n;
-            atomicMax(&gmax[0], __float_as_uint(sqrtf(n)));
-        }
+        if (nrm) nrm[r] = n;
+        if (gmax) atomicMax(&gmax[0], __float_as_uint(sqrtf(n)));
     }
 }
 
 // ---------------------------------------------------------------------------
 // the fused contraction + filter kernel
 // ---------------------------------------------------------------------------
+// Bound on |estimated - true| key (= squared distance - ||x_i||^2) for query
+// row statistics st = (||x||, residual norm of its BF16 copy, norm of its low
+// part) against any corpus point (gmax: the corpus maxima of the same): the
+// terms the BF16 copies drop (Cauchy-Schwarz on the residual norms), the FP32
+// accumulation of the products, and the FP32 norms.
+__device__ __forceinline__ float key_error_bound(float4 st, const unsigned *gmax, float acc_coef) {
+    const float amax = __uint_as_float(gmax[0]);
+    const float rmax = __uint_as_float(gmax[1]);
+    const float lmax = __uint_as_float(gmax[2]);
+    const float a = st.x, r = st.y, l = st.z;
+    const float drop = l * lmax + r * amax + a * rmax;
+    return 2.f * drop + acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
+}
+
 template <int PASSES>
 __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_constant__ TcParams p) {
     using C = TcCfg<PASSES>;
@@ -479,14 +499,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             const int64_t c0 = (int64_t)sp * p.cols_per_split;
             const int64_t c1 = min(p.N, c0 + p.cols_per_split);
             const int64_t row = (int64_t)rt * TC_BM + quarter * 32 + lane;
-            const int qraw = row < p.Q ? (p.qlist ? p.qlist[row] : (int)row) : -1;
-            const bool qv = qraw >= 0 && qraw < p.N;  // listed rows out of range are flagged by the caller
+            const bool cross = p.qnrm != nullptr;  // queries from another array than the corpus
+            const int qraw = row < p.Q ? (cross ? (int)row : (p.qlist ? p.qlist[row] : (int)row)) : -1;
+            const bool qv = qraw >= 0 && (cross || qraw < p.N);  // listed rows out of range are flagged by the caller
             const int qid = qv ? qraw : -1;
             Cand *buf = qv ? p.cand + ((size_t)row * p.splits + sp) * p.cap : nullptr;
             float tau = qv ? INFINITY : -INFINITY;
-            int cnt = 0, since = 0;
+            int cnt = 0, since = 0, rovf = 0;
+            // radius mode: a fixed threshold, the row's squared radius as a key
+            // widened by twice the key error bound, so that no point inside the
+            // radius is filtered out; no top-k bookkeeping
+            const bool rmode = p.radius != nullptr;
             // distance buckets (8 per octave) below t0 = (||x|| + max||y||)^2 >= d
-            const float nx = qv ? p.nrm[qid] : 0.f;
+            const float nx = qv ? (cross ? p.qnrm[row] : p.nrm[qid]) : 0.f;
             const float ai = sqrtf(nx), amax = __uint_as_float(p.gmax[0]);
             int top = (int)(__float_as_uint((ai + amax) * (ai + amax) * 1.0001f + 1e-30f) >> 20);
             // With column splits, every split of a row also counts its buffered
@@ -514,6 +539,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 if (b < NBUCKET) tau = fminf(tau, __uint_as_float((uint32_t)(gbase + b + 1) << 20) - nx);
             };
             if (gh) global_tau();
+            if ((rmode || (p.hint && PASSES != 8)) && qv) {  // FP8 keys carry no error bound
+                // the radius (or the hint, an upper bound of the k-th squared
+                // distance) as a key threshold, widened by twice the key error
+                // bound so that no point inside is filtered out
+                const float rad = rmode ? p.radius[row] : p.hint[row];
+                if (isfinite(rad))
+                    tau = fminf(tau, rad - nx +
+                                         2.f * key_error_bound(cross ? p.qst[row] : p.st[qid], p.gmax,
+                                                               p.acc_coef) +
+                                         1e-6f * (fabsf(rad) + nx));
+            }
             uint32_t *dh = &s.dhist[warp - 2][0][lane];
             for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
             // corpus norms of the first tile of the unit, then one tile ahead
@@ -556,7 +592,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 }
                 fence_after_sync();
                 const uint32_t taddr = tbase + lane_base + (uint32_t)(acc * TC_BN);
-                const int self_off = qid - (int)ct;  // the query's own column, if in this tile
+                // the query's own column, if in this tile (none for another array's queries)
+                const int self_off = cross ? INT_MIN / 2 : qid - (int)ct;
 #pragma unroll
                 for (int c = 0; c < TC_BN / 32; ++c) {
                     uint32_t r[32];
@@ -606,6 +643,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                         const int colb = (int)ct + c * 32;
                         since += __popc(mask);
                         auto append = [&](float key, int col) {
+                            if (rmode) {  // no compaction: a full buffer sends the row to the fallback
+                                if (cnt < p.cap)
+                                    buf[cnt++] = Cand{key, col};
+                                else
+                                    rovf = 1;
+                                return;
+                            }
                             buf[cnt++] = Cand{key, col};
                             const uint32_t db = __float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20;
                             int bk = (int)db - (top - (NBUCKET - 1));
@@ -635,6 +679,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     acc = 0;
                     acc_phase ^= 1u;
                 }
+                if (rmode) continue;  // the threshold is fixed
                 // lower tau to the upper edge of the bucket holding the ksel-th distance
                 if (since >= 16 && cnt >= p.ksel) {
                     uint32_t hw[NBUCKET / 2];
@@ -705,7 +750,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             }
             if (!ok) break;
             if (qv)
-                p.meta[(size_t)row * p.splits + sp] = make_int4(cnt, __float_as_int(tau), 0, 0);
+                p.meta[(size_t)row * p.splits + sp] = make_int4(cnt, __float_as_int(tau), rovf, 0);
         }
     }
 
@@ -728,6 +773,9 @@ struct MergeParams {
     int D, k, ksel;
     const float *nrm;
     const float4 *stats;
+    const float *Xq;        // queries from another array (row r = Xq[r]), else nullptr
+    const float *qnrm;
+    const float4 *qstats;
     const unsigned *gmax;
     float acc_coef;        // (passes * Dp / 16 + 8) * 2^-21
     int32_t *idx_out;
@@ -740,12 +788,7 @@ struct MergeParams {
 // the terms the BF16 copies drop (Cauchy-Schwarz on the residual norms), the
 // FP32 accumulation of the products, and the FP32 norms.
 __device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st) {
-    const float amax = __uint_as_float(p.gmax[0]);
-    const float rmax = __uint_as_float(p.gmax[1]);
-    const float lmax = __uint_as_float(p.gmax[2]);
-    const float a = st.x, r = st.y, l = st.z;
-    const float drop = l * lmax + r * amax + a * rmax;
-    return 2.f * drop + p.acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
+    return key_error_bound(st, p.gmax, p.acc_coef);
 }
 
 // CERT (FP32 and BF16 modes): the k nearest, certified exact or sent to the
@@ -769,7 +812,8 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
     const int sel = CERT ? p.k : p.ksel;  // rank of the key that bounds the re-rank set
     const int64_t row = (int64_t)blockIdx.x * MERGE_WARPS + w;
     if (row >= p.Q) return;
-    const int qid = p.qlist ? p.qlist[row] : (int)row;
+    const bool cross = p.Xq != nullptr;
+    const int qid = cross ? (int)row : (p.qlist ? p.qlist[row] : (int)row);
     const int S = p.splits;
     const Cand *cb = p.cand + (size_t)row * S * p.cap;
     const int4 *mt = p.meta + (size_t)row * S;
@@ -789,7 +833,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         ovf |= __shfl_xor_sync(0xffffffffu, ovf, o);
         tau_min = fminf(tau_min, __shfl_xor_sync(0xffffffffu, tau_min, o));
     }
-    bool good = !ovf && total >= sel && qid >= 0 && qid < p.N;
+    bool good = !ovf && total >= sel && qid >= 0 && (cross || qid < p.N);
     int nr = 0;
     if (good) {
         // One pass over the buffers stages every (key, index) at or below
@@ -797,7 +841,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         // smallest key theta lies among them, and every candidate the re-rank
         // takes (key <= theta + 2E) is staged; otherwise the buffers are
         // walked again.
-        const float E = CERT ? row_error_bound(p, p.stats[qid]) : 0.f;
+        const float E = CERT ? row_error_bound(p, cross ? p.qstats[row] : p.stats[qid]) : 0.f;
         const float slim = tau_min + 2.f * E;
         int ns = 0, nlt = 0;
         for (int u0 = 0; u0 < S; u0 += 32) {
@@ -884,8 +928,9 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         __syncwarp();
         if (good && nr >= p.k) {
             // exact FP32 direct-difference distances, four candidates at a time
-            const float *xq = p.X + (int64_t)qid * p.D;
-            const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0;
+            const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (int64_t)qid * p.D;
+            const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
+                              (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
             for (int t0 = 0; t0 < nr; t0 += 4) {
                 const float *xc[4];
                 float a[4];
@@ -939,7 +984,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
             warp_bitonic_sort_smem(rdw, rjw, ns2, lane);
             if (CERT) {
                 const float dk = rdw[p.k - 1];
-                const float nx = p.nrm[qid];
+                const float nx = cross ? p.qnrm[row] : p.nrm[qid];
                 const float lb = nx + tau_min - E;
                 // certified: no point outside the buffers can be closer than dk
                 good = isinf(tau_min) || dk < lb * (1.f - 1e-6f);
@@ -955,6 +1000,84 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         }
     } else if (lane == 0) {
         p.flag_rows[atomicAdd(p.flag_count, 1)] = (int)row;
+    }
+}
+
+// Radius mode (queries from another array): every buffered candidate is
+// re-ranked by FP32 direct differences, the ones strictly inside the row's
+// squared radius are kept in (d^2, index) order, the first k written and the
+// rest of the row padded with (-1, +inf). Rows whose buffers overflowed, or
+// that hold more than RCAP candidates, go to the brute-force kernel (then
+// radius_filter_kernel applies the same rule).
+__global__ void __launch_bounds__(MERGE_WARPS * 32) radius_merge_kernel(MergeParams p, const float *radius) {
+    __shared__ float rd_s[MERGE_WARPS][RCAP];
+    __shared__ int rj_s[MERGE_WARPS][RCAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * MERGE_WARPS + w;
+    if (row >= p.Q) return;
+    float *rdw = rd_s[w];
+    int *rjw = rj_s[w];
+    const int S = p.splits;
+    const Cand *cb = p.cand + (size_t)row * S * p.cap;
+    const int4 *mt = p.meta + (size_t)row * S;
+    int total = 0, ovf = 0;
+    for (int u = lane; u < S; u += 32) {
+        const int4 m = mt[u];
+        total += m.x;
+        ovf |= m.z;
+    }
+    total = (int)__reduce_add_sync(0xffffffffu, (unsigned)total);
+    ovf = (int)__reduce_or_sync(0xffffffffu, (unsigned)ovf);
+    if (ovf || total > RCAP) {
+        if (lane == 0) p.flag_rows[atomicAdd(p.flag_count, 1)] = (int)row;
+        return;
+    }
+    int nr = 0;
+    for (int u = 0; u < S; ++u) {
+        const int c = mt[u].x;
+        const Cand *b = cb + (size_t)u * p.cap;
+        for (int i = lane; i < c; i += 32) rjw[nr + i] = b[i].idx;
+        nr += c;
+    }
+    __syncwarp();
+    const float *xq = p.Xq + (int64_t)row * p.D;
+    for (int t = 0; t < nr; ++t) {
+        const float *xc = p.X + (int64_t)rjw[t] * p.D;
+        float a = 0.f;
+        for (int d = lane; d < p.D; d += 32) {
+            const float df = xq[d] - xc[d];
+            a = fmaf(df, df, a);
+        }
+        a = warp_sum(a);
+        if (lane == 0) rdw[t] = a;
+    }
+    __syncwarp();
+    const float rad = radius[row];
+    int ns2 = 32;
+    while (ns2 < nr) ns2 <<= 1;
+    for (int t = lane; t < ns2; t += 32) {
+        if (t >= nr || !(rdw[t] < rad)) {
+            rdw[t] = INFINITY;
+            rjw[t] = INT_MAX;
+        }
+    }
+    __syncwarp();
+    warp_bitonic_sort_smem(rdw, rjw, ns2, lane);
+    for (int t = lane; t < p.k; t += 32) {
+        const bool in = t < ns2 && rjw[t] != INT_MAX;
+        p.idx_out[row * p.k + t] = in ? rjw[t] : -1;
+        p.d2_out[row * p.k + t] = in ? rdw[t] : INFINITY;
+    }
+}
+
+// Entries at or beyond the row's squared radius become (-1, +inf); rows are
+// sorted, so they form a suffix.
+__global__ void radius_filter_kernel(int32_t *idx, float *d2, int64_t rows, int k, const float *radius) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * k) return;
+    if (!(d2[e] < radius[e / k])) {
+        d2[e] = INFINITY;
+        idx[e] = -1;
     }
 }
 
@@ -1010,6 +1133,13 @@ static_assert(sizeof(TcSmem<8>) + 1024 <= 232448, "tensor kNN shared memory abov
 
 }  // namespace
 
+atsne_status radius_filter_launch(int32_t *idx, float *d2, int64_t rows, int k, const float *radius,
+                                  cudaStream_t stream) {
+    if (rows <= 0) return ATSNE_OK;
+    return launch_kernel("radius_filter", radius_filter_kernel, ceil_div(rows * k, 256), 256, 0, stream,
+                         idx, d2, rows, k, radius);
+}
+
 TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) {
     TcPlan pl;
     pl.passes = precision == ATSNE_FP32 ? 3 : precision == ATSNE_FP8_RERANK ? 8 : 1;
@@ -1055,6 +1185,8 @@ size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcP
     w.qlo = (list && pl.passes == 3) ? c.take<uint16_t>((size_t)Q * per) : nullptr;
     w.scale = pl.passes == 8 ? c.take<float>((size_t)N) : nullptr;
     w.qscale = (list && pl.passes == 8) ? c.take<float>((size_t)Q) : nullptr;
+    w.qnrm = list ? c.take<float>((size_t)Q) : nullptr;  // queries from another array
+    w.qstats = list ? c.take<float>((size_t)Q * 4) : nullptr;
     w.nrm = c.take<float>((size_t)N);
     w.stats = c.take<float>((size_t)N * 4);
     w.gmax = c.take<unsigned>(4);
@@ -1069,7 +1201,7 @@ size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcP
 
 atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist, int64_t Q, int k,
                           const TcPlan &pl, const TcWs &w, int32_t *idx_out, float *d2_out,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, const float *Xq, const float *radius, const float *hint) {
     int *status = device_status_word();
     cudaError_t e = cudaMemsetAsync(w.gmax, 0, 4 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.flag_count, 0, sizeof(int32_t), stream);
@@ -1082,7 +1214,12 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         ATSNE_TRY(launch_kernel("knn_prep", knn_prep_fp8_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
                                 (const int32_t *)nullptr, N, N, D, pl.Dp, w.hi, w.scale, w.nrm, w.gmax,
                                 status));
-        if (qlist) {
+        if (Xq) {
+            ATSNE_TRY(launch_kernel("knn_prep", knn_prep_fp8_kernel, ceil_div(Q * 32, 256), 256, 0, stream,
+                                    Xq, (const int32_t *)nullptr, Q, Q, D, pl.Dp, w.qhi, w.qscale, w.qnrm,
+                                    (unsigned *)nullptr, status));
+            a_hi = w.qhi;
+        } else if (qlist) {
             ATSNE_TRY(launch_kernel("knn_prep", knn_prep_fp8_kernel, ceil_div(Q * 32, 256), 256, 0, stream,
                                     X, qlist, Q, N, D, pl.Dp, w.qhi, w.qscale, (float *)nullptr,
                                     (unsigned *)nullptr, status));
@@ -1094,7 +1231,15 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
                                 (const int32_t *)nullptr, N, N, D, pl.Dp, pl.passes, hi, lo, w.nrm,
                                 reinterpret_cast<float4 *>(w.stats), w.gmax, status));
-        if (qlist) {
+        if (Xq) {
+            ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(Q * 32, 256), 256, 0, stream, Xq,
+                                    (const int32_t *)nullptr, Q, Q, D, pl.Dp, pl.passes,
+                                    reinterpret_cast<__nv_bfloat16 *>(w.qhi),
+                                    reinterpret_cast<__nv_bfloat16 *>(w.qlo), w.qnrm,
+                                    reinterpret_cast<float4 *>(w.qstats), (unsigned *)nullptr, status));
+            a_hi = w.qhi;
+            a_lo = w.qlo;
+        } else if (qlist) {
             ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(Q * 32, 256), 256, 0, stream, X,
                                     qlist, Q, N, D, pl.Dp, pl.passes,
                                     reinterpret_cast<__nv_bfloat16 *>(w.qhi),
@@ -1107,21 +1252,27 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     TcParams p;
     memset(&p, 0, sizeof(p));
     if (fp8) {
-        ATSNE_TRY(make_u8_map(&p.tm_a_hi, a_hi, qlist ? Q : N, pl.Dp, TC_BM));
+        ATSNE_TRY(make_u8_map(&p.tm_a_hi, a_hi, (qlist || Xq) ? Q : N, pl.Dp, TC_BM));
         ATSNE_TRY(make_u8_map(&p.tm_b_hi, w.hi, N, pl.Dp, TC_BN));
     } else {
-        ATSNE_TRY(make_bf16_map(&p.tm_a_hi, a_hi, qlist ? Q : N, pl.Dp, TC_BM));
+        ATSNE_TRY(make_bf16_map(&p.tm_a_hi, a_hi, (qlist || Xq) ? Q : N, pl.Dp, TC_BM));
         ATSNE_TRY(make_bf16_map(&p.tm_b_hi, w.hi, N, pl.Dp, TC_BN));
     }
     if (pl.passes == 3) {
-        ATSNE_TRY(make_bf16_map(&p.tm_a_lo, a_lo, qlist ? Q : N, pl.Dp, TC_BM));
+        ATSNE_TRY(make_bf16_map(&p.tm_a_lo, a_lo, (qlist || Xq) ? Q : N, pl.Dp, TC_BM));
         ATSNE_TRY(make_bf16_map(&p.tm_b_lo, w.lo, N, pl.Dp, TC_BN));
     } else {
         p.tm_a_lo = p.tm_a_hi;
         p.tm_b_lo = p.tm_b_hi;
     }
     p.scale = w.scale;
-    p.qscale = qlist ? w.qscale : nullptr;
+    p.qscale = (qlist || Xq) ? w.qscale : nullptr;
+    p.qnrm = Xq ? w.qnrm : nullptr;
+    p.radius = radius;
+    p.hint = hint;
+    p.qst = reinterpret_cast<const float4 *>(w.qstats);
+    p.st = reinterpret_cast<const float4 *>(w.stats);
+    p.acc_coef = (float)((pl.passes * pl.Dp / 16 + 8) * (1.0 / (1 << 21)));
     p.nrm = w.nrm;
     p.gmax = w.gmax;
     p.qlist = qlist;
@@ -1168,6 +1319,9 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     m.k = k;
     m.nrm = w.nrm;
     m.stats = reinterpret_cast<const float4 *>(w.stats);
+    m.Xq = Xq;
+    m.qnrm = w.qnrm;
+    m.qstats = reinterpret_cast<const float4 *>(w.qstats);
     m.gmax = w.gmax;
     m.acc_coef = (float)((pl.passes * pl.Dp / 16 + 8) * (1.0 / (1 << 21)));
     m.idx_out = idx_out;
@@ -1175,6 +1329,14 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     m.flag_rows = w.flag_rows;
     m.flag_count = w.flag_count;
     m.ksel = pl.ksel;
+    if (radius) {
+        ATSNE_TRY(launch_kernel("knn_tc_merge", radius_merge_kernel, ceil_div(Q, MERGE_WARPS),
+                                MERGE_WARPS * 32, 0, stream, m, radius));
+        ATSNE_TRY(knn_bruteforce_rows(X, N, D, qlist, w.flag_rows, w.flag_count, Q, k, idx_out, d2_out,
+                                      stream, Xq));
+        return launch_kernel("radius_filter", radius_filter_kernel, ceil_div(Q * k, 256), 256, 0, stream,
+                             idx_out, d2_out, Q, k, radius);
+    }
     if (fp8) {
         const size_t ms = merge_smem_bytes<false, RCAP_FP8, MSTAGE_FP8>();
         e = cudaFuncSetAttribute(knn_merge_kernel<false, RCAP_FP8, MSTAGE_FP8>,
@@ -1187,7 +1349,8 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<true, RCAP, MSTAGE>,
                                 ceil_div(Q, MERGE_WARPS), MERGE_WARPS * 32, ms, stream, m));
     }
-    return knn_bruteforce_rows(X, N, D, qlist, w.flag_rows, w.flag_count, Q, k, idx_out, d2_out, stream);
+    return knn_bruteforce_rows(X, N, D, qlist, w.flag_rows, w.flag_count, Q, k, idx_out, d2_out, stream,
+                               Xq);
 }
 
 }  // namespace atsne

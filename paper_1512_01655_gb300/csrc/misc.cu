@@ -127,7 +127,89 @@ union_compact_kernel(const uint32_t *__restrict__ bitmap, int64_t words, int32_t
     if (tid == 0 && count) *count = s_total;
 }
 
+// Insertion of new points into existing neighbourhoods (Eq. 11, Sec. 5.3.1),
+// for a batch: row i keeps the k smallest of its list and its kc candidates
+// (indices + offset) under the (d^2, index) order. A candidate ties with the
+// farthest listed point only at a larger index, so it enters exactly when it
+// is strictly closer (Eq. 11's "<"). One warp per row; changed[i] = 1 if the
+// list changed.
+__global__ void __launch_bounds__(128)
+merge_neighbors_kernel(int32_t *__restrict__ idx, float *__restrict__ d2, int64_t rows, int k,
+                       const int32_t *__restrict__ cidx, const float *__restrict__ cd2, int kc,
+                       int32_t offset, uint8_t *__restrict__ changed) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= rows) return;
+    int32_t *ri = idx + r * k;
+    float *rd = d2 + r * k;
+    const int32_t *ci = cidx + r * kc;
+    const float *cd = cd2 + r * kc;
+    // both lists are sorted; candidate t belongs to the k smallest of the
+    // union when fewer than k entries precede it: its t predecessors among
+    // the candidates and the listed entries below it (binary search). The
+    // entering candidates are therefore a prefix of length m.
+    int m = 0;
+    for (int t = lane; t < kc; t += 32) {
+        const float d = cd[t];
+        const int32_t j = ci[t] + offset;
+        int lo = 0, hi = k;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (rd[mid] < d || (rd[mid] == d && ri[mid] < j))
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        m += (t + lo < k) ? 1 : 0;
+    }
+    m = (int)__reduce_add_sync(0xffffffffu, (unsigned)m);
+    if (lane == 0 && changed) changed[r] = m > 0;
+    if (m == 0) return;
+    // lane 0 merges from the back: the k - m first listed entries and the m
+    // first candidates; position o is written after every entry it held was read
+    if (lane == 0) {
+        int a = k - m - 1, b = m - 1;
+        for (int o = k - 1; o >= 0 && b >= 0; --o) {
+            const bool take_b = a < 0 || cd[b] > rd[a] || (cd[b] == rd[a] && ci[b] + offset > ri[a]);
+            if (take_b) {
+                rd[o] = cd[b];
+                ri[o] = ci[b] + offset;
+                --b;
+            } else {
+                rd[o] = rd[a];
+                ri[o] = ri[a];
+                --a;
+            }
+        }
+    }
+}
+
+// hint[s] = d2[rows[s]][k-1]: a listed row's current k-th squared distance,
+// an upper bound of its exact one when the row lists k real points.
+__global__ void gather_hint_kernel(const int32_t *__restrict__ rows, int64_t S, int64_t N, int k,
+                                   const float *__restrict__ d2, float *__restrict__ hint) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t i = rows[s];
+    hint[s] = (i >= 0 && i < N) ? d2[i * k + k - 1] : INFINITY;
+}
+
 }  // namespace
+
+atsne_status gather_hint_launch(const int32_t *rows, int64_t S, int64_t N, int k, const float *d2,
+                                float *hint, cudaStream_t stream) {
+    if (S <= 0) return ATSNE_OK;
+    return launch_kernel("gather_hint", gather_hint_kernel, ceil_div(S, 256), 256, 0, stream, rows, S, N,
+                         k, d2, hint);
+}
+
+atsne_status merge_neighbors_launch(int32_t *idx, float *d2, int64_t rows, int k, const int32_t *cidx,
+                                    const float *cd2, int kc, int32_t offset, uint8_t *changed,
+                                    cudaStream_t stream) {
+    if (rows <= 0) return ATSNE_OK;
+    return launch_kernel("merge_neighbors", merge_neighbors_kernel, ceil_div(rows * 32, 128), 128, 0,
+                         stream, idx, d2, rows, k, cidx, cd2, kc, offset, changed);
+}
 
 atsne_status union_launch(const int32_t *lists, int64_t total, int64_t N, uint32_t *bitmap,
                           int32_t *out, int64_t out_rows, int64_t *count, cudaStream_t stream) {

@@ -1,0 +1,218 @@
+"""Serving: a growing corpus and its neighbourhood state kept on one GPU, with
+insert requests (Sec. 5.3.1) and refinement requests (Sec. 4.3, Sec. 5.1.1)
+processed by continuous batching.
+
+A request is admitted, in arrival order, as soon as a stream slot is free and
+its device memory fits in the free HBM. Its computation runs on its own stream
+and overlaps the other admitted requests. Its write to the shared state (the
+commit) is enqueued at admission on one state stream, so commits apply in
+arrival order. A computation reads only rows of X, and rows of X are never
+rewritten: an insert appends rows, and every request admitted after it waits
+for that copy. Hence every request's result is the same alone and in the mix.
+
+Insert of B points as rows [N, N + B):
+  compute  the new rows' k nearest among X[:N + B] (exact) and their Gaussians
+           (Eq. 3-4); for the existing rows, the new points inside their
+           current radius d_i^Max (atsne_knn_cross with radii, kc = min(k, B)).
+  commit   write the new rows (rho = 1); merge the candidates into the
+           existing rows (Eq. 11); re-calibrate the existing rows.
+Refine of S listed rows:
+  compute  their k nearest among the current rows (the filter seeded with each
+           row's current k-th distance) and their Gaussians.
+  commit   write the rows (rho = 1).
+"""
+import collections
+import time
+
+import numpy as np
+import torch
+
+from . import (OP_KNN, OP_KNN_CROSS_RADIUS, atsne_calibrate_P, atsne_commit_rows, atsne_knn,
+               atsne_knn_cross, atsne_knn_rows, atsne_merge_neighbors, knn_opts, workspace_bytes)
+
+
+class Request:
+    """kind "insert" (points: float32 [B][D] host array) or "refine" (rows:
+    int32 [S] host array of existing rows); arrival in seconds."""
+
+    def __init__(self, rid, kind, arrival, points=None, rows=None):
+        self.rid, self.kind, self.arrival = rid, kind, float(arrival)
+        self.points, self.rows = points, rows
+        self.admitted = self.done = None
+        self.first_row = None
+
+    @property
+    def size(self):
+        return len(self.points) if self.kind == "insert" else len(self.rows)
+
+
+class Server:
+    def __init__(self, X0, capacity, k=90, perplexity=30.0, precision="fp32", slots=4,
+                 reserve_bytes=1 << 30, device="cuda"):
+        self.dev = torch.device(device)
+        N0, D = X0.shape
+        if N0 < k + 1 or capacity < N0:
+            raise ValueError("need k + 1 <= N0 <= capacity")
+        self.k, self.perp, self.D, self.cap = k, float(perplexity), D, capacity
+        self.opts = knn_opts(method="exact", precision=precision)
+        f32, i32 = torch.float32, torch.int32
+        self.X = torch.empty((capacity, D), dtype=f32, device=self.dev)
+        self.X[:N0].copy_(torch.from_numpy(np.ascontiguousarray(X0, dtype=np.float32)))
+        self.idx = torch.zeros((capacity, k), dtype=i32, device=self.dev)
+        self.d2 = torch.zeros((capacity, k), dtype=f32, device=self.dev)
+        self.P = torch.zeros((capacity, k), dtype=f32, device=self.dev)
+        self.beta = torch.zeros(capacity, dtype=f32, device=self.dev)
+        self.rho = torch.zeros(capacity, dtype=f32, device=self.dev)
+        i, d = atsne_knn(self.X[:N0], k, opts=self.opts)
+        self.idx[:N0].copy_(i)
+        self.d2[:N0].copy_(d)
+        atsne_calibrate_P(self.d2[:N0], self.perp, P_out=self.P[:N0], beta_out=self.beta[:N0])
+        self.rho[:N0] = 1.0
+        self.N = N0
+        torch.cuda.synchronize(self.dev)
+        self.state = torch.cuda.Stream(self.dev)
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        self.free = list(range(slots))
+        self.reserve = reserve_bytes
+        self.x_ready = None
+        self.inflight = []
+
+    # ---- admission ----
+    def need_bytes(self, req):
+        k, D, N = self.k, self.D, self.N
+        n = req.size
+        if req.kind == "insert":
+            ws = workspace_bytes(OP_KNN, N + n, D, k, n, self.opts)
+            if N > 0:
+                kc = min(k, n)
+                ws += workspace_bytes(OP_KNN_CROSS_RADIUS, n, D, kc, N, self.opts) + N * (kc * 8 + 5)
+        else:
+            ws = workspace_bytes(OP_KNN, N, D, k, n, self.opts)
+        return ws + n * (k * 12 + 8) + (1 << 20)
+
+    def free_bytes(self):
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        return free + torch.cuda.memory_reserved(self.dev) - torch.cuda.memory_allocated(self.dev)
+
+    def fits(self, req):
+        if req.kind == "insert" and self.N + req.size > self.cap:
+            raise ValueError("insert beyond the corpus capacity")
+        return self.need_bytes(req) + self.reserve <= self.free_bytes()
+
+    def admit(self, req, now):
+        slot = self.free.pop(0)
+        s = self.streams[slot]
+        keep = []
+        with torch.cuda.stream(s):
+            if self.x_ready is not None:
+                s.wait_event(self.x_ready)
+            N0 = self.N
+            if req.kind == "insert":
+                B = req.size
+                host = torch.from_numpy(np.ascontiguousarray(req.points, dtype=np.float32)).pin_memory()
+                self.X[N0:N0 + B].copy_(host, non_blocking=True)
+                self.x_ready = torch.cuda.Event()
+                self.x_ready.record(s)
+                rows = torch.arange(N0, N0 + B, dtype=torch.int32, device=self.dev)
+                ti, td = atsne_knn(self.X[:N0 + B], self.k, queries=rows, opts=self.opts, stream=s)
+                tp, tb = atsne_calibrate_P(td, self.perp, stream=s)
+                cand = None
+                if N0 > 0:
+                    # the existing rows' radii d_i^Max, taken on the state stream
+                    # after the earlier commits (a radius only ever shrinks)
+                    with torch.cuda.stream(self.state):
+                        radius = self.d2[:N0, self.k - 1].contiguous()
+                        snap = torch.cuda.Event()
+                        snap.record(self.state)
+                    radius.record_stream(s)
+                    s.wait_event(snap)
+                    kc = min(self.k, B)
+                    cand = atsne_knn_cross(self.X[:N0], self.X[N0:N0 + B], kc, opts=self.opts, stream=s,
+                                           radius_d2=radius)
+                    keep.append(radius)
+                self.N = N0 + B
+                req.first_row = N0
+                keep += [host, rows, ti, td, tp, tb] + (list(cand) if cand else [])
+            else:
+                rows = torch.from_numpy(np.ascontiguousarray(req.rows, dtype=np.int32)).to(self.dev)
+                # the rows' current k-th distances (taken after the earlier
+                # commits) seed the exact search's filter
+                with torch.cuda.stream(self.state):
+                    hint = self.d2[:, self.k - 1].index_select(0, rows.long())
+                    snap = torch.cuda.Event()
+                    snap.record(self.state)
+                hint.record_stream(s)
+                s.wait_event(snap)
+                ti, td = atsne_knn_rows(self.X[:N0], rows, self.k, hint_d2=hint, opts=self.opts, stream=s)
+                keep.append(hint)
+                tp, tb = atsne_calibrate_P(td, self.perp, stream=s)
+                cand = None
+                keep += [rows, ti, td, tp, tb]
+            computed = torch.cuda.Event()
+            computed.record(s)
+        st = self.state
+        with torch.cuda.stream(st):
+            st.wait_event(computed)
+            atsne_commit_rows(rows, ti, td, tp, tb, self.idx, self.d2, self.P, self.beta, self.rho,
+                              stream=st)
+            if cand is not None:
+                atsne_merge_neighbors(self.idx[:N0], self.d2[:N0], cand[0], cand[1], N0, stream=st)
+                atsne_calibrate_P(self.d2[:N0], self.perp, stream=st, P_out=self.P[:N0],
+                                  beta_out=self.beta[:N0])
+            done = torch.cuda.Event()
+            done.record(st)
+        for t in keep:
+            if t.is_cuda:
+                t.record_stream(st)
+        req.admitted = now
+        self.inflight.append((req, slot, done, keep))
+
+    # ---- the loop ----
+    def run(self, requests, clock=time.perf_counter, idle_sleep=2e-4):
+        """Serve `requests` (arrival times in seconds from the start); returns
+        them with admitted/done times and a summary."""
+        pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        served = []
+        t0 = clock()
+        while pending or self.inflight:
+            now = clock() - t0
+            progress = False
+            for item in list(self.inflight):
+                req, slot, done, _ = item
+                if done.query():
+                    req.done = clock() - t0
+                    self.inflight.remove(item)
+                    self.free.append(slot)
+                    served.append(req)
+                    progress = True
+            while pending and pending[0].arrival <= now and self.free:
+                if not self.fits(pending[0]):
+                    if not self.inflight:
+                        raise MemoryError("request %d does not fit in free device memory"
+                                          % pending[0].rid)
+                    break
+                self.admit(pending.popleft(), clock() - t0)
+                progress = True
+            if not progress:
+                time.sleep(idle_sleep)
+        torch.cuda.synchronize(self.dev)
+        return served, summarize(served)
+
+
+def summarize(served):
+    if not served:
+        return {}
+    lat = np.array([r.done - r.arrival for r in served])
+    pts = sum(r.size for r in served)
+    span = max(r.done for r in served) - min(r.arrival for r in served)
+    out = {"requests": len(served), "points": int(pts), "seconds": round(span, 4),
+           "points_per_s": round(pts / span, 1) if span > 0 else None,
+           "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+           "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
+    for kind in ("insert", "refine"):
+        lk = np.array([r.done - r.arrival for r in served if r.kind == kind])
+        if lk.size:
+            out[kind] = {"requests": int(lk.size),
+                         "p50_ms": round(float(np.percentile(lk, 50)) * 1e3, 3),
+                         "p99_ms": round(float(np.percentile(lk, 99)) * 1e3, 3)}
+    return out

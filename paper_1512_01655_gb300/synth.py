@@ -17,6 +17,9 @@ these mixtures stand in for their shapes:
   x_d = s_{m,d} * Gamma(2, 1).
 * ``refine_subsets``: sizes log-uniform in [lo, hi], members drawn from one to
   three clusters (a brushed selection, Sec. 5.1.1).
+* ``lognormal_clusters``: the IMU-stream-shaped serving workload (Sec. 8 of the
+  paper streams IMU records): D = 50, 30 clusters, mu_{m,d} ~ N(0, 1),
+  x_d = exp(mu_{m,d} + N(0, 1)).
 * ``embedding_2d``: a stand-in for a 2-D tSNE layout of labelled points (the
   optimiser is not part of this library): cluster m centred on a circle of
   radius 10 at angle 2 pi m / M, points spread N(0, diag(s_x^2, s_y^2)) with
@@ -98,3 +101,15 @@ def embedding_2d(labels, seed=6):
     spread = rng.uniform(0.5, 1.5, size=(M, 2))
     Y = centres[labels] + spread[labels] * rng.normal(size=(labels.shape[0], 2))
     return Y.astype(np.float32)
+
+
+def lognormal_clusters(N, D=50, n_clusters=30, seed=5, return_labels=False, chunk=262144):
+    """Log-normal features in clusters: x_d = exp(mu_{m,d} + N(0, 1)), mu ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    mu = rng.normal(size=(n_clusters, D))
+    labels = rng.integers(0, n_clusters, size=N)
+    X = np.empty((N, D), np.float32)
+    for s in range(0, N, chunk):
+        e = min(N, s + chunk)
+        X[s:e] = np.exp(mu[labels[s:e]] + rng.normal(size=(e - s, D))).astype(np.float32)
+    return (X, labels) if return_labels else X

@@ -1,0 +1,160 @@
+"""Serving (insertion, Eq. 11 / Sec. 5.3.1; refinement, Sec. 4.3): the
+primitives against the oracle, the served state against the oracle's exact
+neighbourhoods of the grown corpus, and the same state whether requests run
+alone or overlapped in the mix."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1512_01655_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def at():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1512_01655_gb300 as pkg
+    return pkg
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_cuda"])
+def test_knn_cross_matches_oracle(at, precision):
+    rng = np.random.default_rng(21)
+    Xq = synth.gaussian_mixture(700, 24, seed=22)
+    Xc = synth.gaussian_mixture(1500, 24, seed=23)
+    for k in (1, 17, 90):
+        idx, d2 = at.atsne_knn_cross(to_dev(Xq), to_dev(Xc), k, precision=precision)
+        at.atsne_check()
+        o_idx, o_d2 = oracle.knn_cross(Xq, Xc, k + 1 if k < 1500 else k)
+        g_idx, g_d2 = idx.cpu().numpy(), d2.cpu().numpy()
+        gap = (o_d2[:, k] - o_d2[:, k - 1]) / o_d2[:, k]
+        clear = gap > 1e-4
+        for r in np.flatnonzero(clear):
+            assert set(g_idx[r]) == set(o_idx[r, :k]), r
+        assert np.allclose(g_d2, o_d2[:, :k], rtol=1e-5, atol=1e-5)
+    _ = rng
+
+
+def test_merge_neighbors_rule(at):
+    # rows of 6 sorted neighbours; candidates enter only when strictly closer
+    # than the farthest, ties go to the listed (smaller) index
+    k = 6
+    d = np.array([[1, 2, 3, 4, 5, 6], [1, 2, 3, 4, 5, 6], [1, 1, 1, 1, 1, 1]], np.float32)
+    i = np.array([[10, 11, 12, 13, 14, 15], [10, 11, 12, 13, 14, 15], [1, 2, 3, 4, 5, 6]], np.int32)
+    cd = np.array([[0.5, 3.5, 9.0], [6.0, 7.0, 8.0], [0.5, 1.0, 1.0]], np.float32)
+    ci = np.array([[0, 1, 2], [0, 1, 2], [0, 1, 2]], np.int32)
+    idx, d2 = to_dev(i), to_dev(d)
+    ch = at.atsne_merge_neighbors(idx, d2, to_dev(ci), to_dev(cd), 100).cpu().numpy()
+    assert list(ch) == [1, 0, 1]
+    assert idx.cpu().numpy().tolist() == [[100, 10, 11, 12, 101, 13], [10, 11, 12, 13, 14, 15],
+                                          [100, 1, 2, 3, 4, 5]]
+    assert d2.cpu().numpy().tolist()[0] == [0.5, 1, 2, 3, 3.5, 4]
+    # random rows against numpy's k smallest of the union
+    rng = np.random.default_rng(24)
+    R, k, kc = 300, 20, 7
+    d = np.sort(rng.random((R, k)).astype(np.float32), axis=1)
+    i = rng.permutation(R * k).reshape(R, k).astype(np.int32)
+    cd = np.sort(rng.random((R, kc)).astype(np.float32) * 0.8, axis=1)
+    ci = np.tile(np.arange(kc, dtype=np.int32), (R, 1))
+    idx, d2 = to_dev(i), to_dev(d)
+    at.atsne_merge_neighbors(idx, d2, to_dev(ci), to_dev(cd), 10**6)
+    for r in range(R):
+        pairs = sorted(list(zip(d[r], i[r])) + list(zip(cd[r], ci[r] + 10**6)))[:k]
+        assert idx.cpu().numpy()[r].tolist() == [p[1] for p in pairs]
+
+
+def _requests(at, X0, extra, seed):
+    from paper_1512_01655_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    reqs, n, pos = [], X0.shape[0], 0
+    for rid, size in enumerate([400, 250, 600, 300, 500]):
+        if rid % 2 == 0:
+            reqs.append(Request(rid, "insert", 0.0, points=extra[pos:pos + size]))
+            n += size
+            pos += size
+        else:
+            reqs.append(Request(rid, "refine", 0.0, rows=np.sort(rng.choice(n, size, replace=False)).astype(np.int32)))
+    return reqs, pos
+
+
+def test_served_state_is_the_exact_state_of_the_grown_corpus(at):
+    from paper_1512_01655_gb300.serve import Server
+    Xall = synth.gaussian_mixture(3500, 16, seed=25)
+    X0, extra = Xall[:2000], Xall[2000:]
+    srv = Server(X0, capacity=3500, k=30, perplexity=10.0, precision="fp32", slots=3)
+    reqs, used = _requests(at, X0, extra, seed=26)
+    srv.run(reqs)
+    at.atsne_check()
+    N = srv.N
+    assert N == 2000 + used
+    Xf = Xall[:N]
+    assert np.array_equal(srv.X[:N].cpu().numpy(), Xf)
+    o_idx, o_d2 = oracle.knn_exact(Xf, 31)
+    g_idx, g_d2 = srv.idx[:N].cpu().numpy(), srv.d2[:N].cpu().numpy()
+    clear = (o_d2[:, 30] - o_d2[:, 29]) / o_d2[:, 30] > 1e-4
+    bad = [r for r in np.flatnonzero(clear) if set(g_idx[r]) != set(o_idx[r, :30])]
+    assert not bad, bad[:5]
+    assert np.allclose(g_d2, o_d2[:, :30], rtol=1e-5, atol=1e-4)
+    o_P, _, _, _ = oracle.calibrate(o_d2[:, :30], 10.0)
+    same = np.all(np.sort(g_idx, 1) == np.sort(o_idx[:, :30], 1), axis=1)
+    gP = srv.P[:N].cpu().numpy()
+    for r in np.flatnonzero(same)[::7]:
+        assert np.abs(gP[r][np.argsort(g_idx[r])] - o_P[r][np.argsort(o_idx[r, :30])]).max() <= 1e-5
+    assert np.all(srv.rho[:N].cpu().numpy() == 1.0)
+
+
+def test_same_state_alone_and_in_the_mix(at):
+    from paper_1512_01655_gb300.serve import Server
+    Xall = synth.gaussian_mixture(3500, 16, seed=27)
+    X0, extra = Xall[:2000], Xall[2000:]
+    states = []
+    for slots, spread in ((1, None), (4, 0.0), (3, 0.003)):
+        srv = Server(X0, capacity=3500, k=30, perplexity=10.0, precision="bf16", slots=slots)
+        reqs, _ = _requests(at, X0, extra, seed=28)
+        if slots == 1:  # alone: each request admitted after the previous one finished
+            served = []
+            for r in reqs:
+                s, _ = srv.run([r])
+                served += s
+        else:  # in the mix: all at once, or arriving a few ms apart
+            for j, r in enumerate(reqs):
+                r.arrival = 0.0 if not spread else j * spread
+            served, summary = srv.run(reqs)
+            assert summary["requests"] == len(reqs)
+        at.atsne_check()
+        N = srv.N
+        states.append([t[:N].cpu().numpy() for t in (srv.X, srv.idx, srv.d2, srv.P, srv.beta, srv.rho)])
+    for other in states[1:]:
+        for a, b in zip(states[0], other):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_cuda"])
+def test_knn_cross_radius_keeps_exactly_the_points_inside(at, precision):
+    Xq = synth.gaussian_mixture(800, 24, seed=31)
+    Xc = synth.gaussian_mixture(1200, 24, seed=32)
+    k = 40
+    o_idx, o_d2 = oracle.knn_cross(Xq, Xc, k)
+    # radii between the 5th and 30th nearest distances, some rows with none inside
+    rng = np.random.default_rng(33)
+    pick = rng.integers(5, 30, size=800)
+    rad = o_d2[np.arange(800), pick].astype(np.float32) * np.float32(0.999)
+    rad[::17] = 0.0
+    idx, d2 = at.atsne_knn_cross(to_dev(Xq), to_dev(Xc), k, precision=precision, radius_d2=to_dev(rad))
+    at.atsne_check()
+    g_idx, g_d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    for r in range(800):
+        inside = o_idx[r][o_d2[r] < rad[r] * (1 - 1e-5)]
+        maybe = o_idx[r][o_d2[r] < rad[r] * (1 + 1e-5)]
+        got = g_idx[r][g_idx[r] >= 0]
+        assert set(inside) <= set(got) <= set(maybe), r
+        assert np.all(np.isinf(g_d2[r][g_idx[r] < 0]))
+        assert np.all(g_d2[r][g_idx[r] >= 0] < rad[r])
