@@ -334,6 +334,21 @@ __device__ __forceinline__ float key_error_bound(float4 st, const unsigned *gmax
     return 2.f * drop + acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
 }
 
+// The same bound over the corpus points of norm at most amax_cap only (a
+// point farther in norm than sqrt(d) from the query is farther than sqrt(d)
+// in distance). Their residuals are capped by the BF16 rounding bound:
+// ||x - hi|| <= 2^-9 ||x|| and ||lo|| <= 2^-8 ||x|| (round to nearest, 8
+// significand bits), plus a tiny absolute term for subnormal values.
+__device__ __forceinline__ float key_error_bound_capped(float4 st, const unsigned *gmax, float acc_coef,
+                                                        float amax_cap) {
+    const float amax = fminf(__uint_as_float(gmax[0]), amax_cap);
+    const float rmax = fminf(__uint_as_float(gmax[1]), 0x1p-9f * amax + 1e-30f);
+    const float lmax = fminf(__uint_as_float(gmax[2]), 0x1p-8f * amax + 1e-30f);
+    const float a = st.x, r = st.y, l = st.z;
+    const float drop = l * lmax + r * amax + a * rmax;
+    return 2.f * drop + acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
+}
+
 template <int PASSES>
 __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_constant__ TcParams p) {
     using C = TcCfg<PASSES>;
@@ -544,12 +559,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 // distance) as a key threshold, widened by twice the key error
                 // bound so that no point inside is filtered out
                 const float rad = rmode ? p.radius[row] : p.hint[row];
-                if (isfinite(rad))
-                    tau = fminf(tau, rad - nx +
-                                         2.f * key_error_bound(cross ? p.qst[row] : p.st[qid], p.gmax,
-                                                               p.acc_coef) +
-                                         1e-6f * (fabsf(rad) + nx));
+                if (isfinite(rad)) {
+                    // the points that must pass lie within sqrt(rad) of the
+                    // query, so their norms are at most ||x|| + sqrt(rad)
+                    const float4 qs = cross ? p.qst[row] : p.st[qid];
+                    const float widen =
+                        2.f * key_error_bound_capped(qs, p.gmax, p.acc_coef,
+                                                     qs.x + sqrtf(fmaxf(rad, 0.f)) * (1.f + 1e-6f) + 1e-30f) +
+                        1e-6f * (fabsf(rad) + nx);
+                    tau = fminf(tau, rad - nx + widen);
+                    // the distance grid then only needs to reach the bound
+                    const int ht = (int)(__float_as_uint(fmaxf(rad + widen, 1e-30f) * 1.0001f) >> 20) + 1;
+                    if (ht < top) top = ht;
+                }
             }
+            bool rebased = rmode || (p.hint && PASSES != 8);
+            float dmx = 0.f;  // largest buffered distance, for the first re-anchoring of the grid
             uint32_t *dh = &s.dhist[warp - 2][0][lane];
             for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
             // corpus norms of the first tile of the unit, then one tile ahead
@@ -651,10 +676,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                                 return;
                             }
                             buf[cnt++] = Cand{key, col};
-                            const uint32_t db = __float_as_uint(fmaxf(nx + key, 1e-30f)) >> 20;
+                            const float dd = nx + key;
+                            dmx = fmaxf(dmx, dd);
+                            const uint32_t db = __float_as_uint(fmaxf(dd, 1e-30f)) >> 20;
                             int bk = (int)db - (top - (NBUCKET - 1));
-                            bk = min(max(bk, 0), NBUCKET - 1);
-                            red_add_shared(dh + (bk >> 1) * 32, 1u << ((bk & 1) * 16));
+                            if (bk < NBUCKET) {  // distances above the grid are not counted
+                                bk = max(bk, 0);
+                                red_add_shared(dh + (bk >> 1) * 32, 1u << ((bk & 1) * 16));
+                            }
                             if (gh) {
                                 const int gb = (int)db - gbase;
                                 atomicAdd(gh + min(max(gb, 0), NBUCKET - 1), 1u);
@@ -680,6 +709,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     acc_phase ^= 1u;
                 }
                 if (rmode) continue;  // the threshold is fixed
+                // With column splits (few query rows), once ksel distances are
+                // buffered the grid is re-anchored just above the largest of them
+                // and recounted: the first grid reaches the largest distance any
+                // point could have, which heavy-tailed norms put many octaves
+                // above the neighbourhood, and a split's short stream would not
+                // reach the exact compaction that otherwise re-anchors it.
+                if (!rebased && p.splits > 1 && cnt >= p.ksel) {
+                    rebased = true;
+                    const int nt = (int)(__float_as_uint(fmaxf(dmx, 1e-30f) * 1.0001f) >> 20) + 1;
+                    if (nt < top) {
+                        top = nt;
+                        for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
+                        for (int i = 0; i < cnt; ++i) {
+                            int bk = (int)(__float_as_uint(fmaxf(nx + buf[i].key, 1e-30f)) >> 20) -
+                                     (top - (NBUCKET - 1));
+                            if (bk < NBUCKET) {
+                                bk = max(bk, 0);
+                                dh[(bk >> 1) * 32] += 1u << ((bk & 1) * 16);
+                            }
+                        }
+                        since = 16;
+                    }
+                }
                 // lower tau to the upper edge of the bucket holding the ksel-th distance
                 if (since >= 16 && cnt >= p.ksel) {
                     uint32_t hw[NBUCKET / 2];
@@ -742,9 +794,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     for (int i = 0; i < cnt; ++i) {
                         int bk = (int)(__float_as_uint(fmaxf(nx + buf[i].key, 1e-30f)) >> 20) -
                                  (top - (NBUCKET - 1));
-                        bk = min(max(bk, 0), NBUCKET - 1);
-                        dh[(bk >> 1) * 32] += 1u << ((bk & 1) * 16);
+                        if (bk < NBUCKET) {
+                            bk = max(bk, 0);
+                            dh[(bk >> 1) * 32] += 1u << ((bk & 1) * 16);
+                        }
                     }
+                    rebased = true;
                     since = 0;
                 }
             }
@@ -837,12 +892,12 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
     int nr = 0;
     if (good) {
         // One pass over the buffers stages every (key, index) at or below
-        // tau_min + 2E. When at least k keys lie below tau_min, the k-th
-        // smallest key theta lies among them, and every candidate the re-rank
-        // takes (key <= theta + 2E) is staged; otherwise the buffers are
-        // walked again.
+        // tau_min. When at least sel keys lie below tau_min, the sel-th
+        // smallest key theta lies among them and is selected there; otherwise
+        // the buffers are walked again. Re-rank bands reaching above tau_min
+        // are collected from the buffers.
         const float E = CERT ? row_error_bound(p, cross ? p.qstats[row] : p.stats[qid]) : 0.f;
-        const float slim = tau_min + 2.f * E;
+        const float slim = tau_min;  // the select needs no key above tau_min
         int ns = 0, nlt = 0;
         for (int u0 = 0; u0 < S; u0 += 32) {
           const int cu = u0 + lane < S ? mt[u0 + lane].x : 0;  // the counts of 32 splits at once
@@ -899,44 +954,45 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
                 sel, hist, lane, n_less);
         }
         const float theta = key_of_bits(prefix);
-        const float lim = theta + 2.f * E;
-        // collect the re-rank set
+        // the re-rank set, collected in two bands of keys: (-inf, theta] then
+        // (theta, lim]
         auto take_batch = [&](bool take, int idx) {
             const unsigned tm = __ballot_sync(0xffffffffu, take);
             const int pos = nr + __popc(tm & lanemask_lt());
             if (take && pos < RC) rjw[pos] = idx;
             nr += __popc(tm);
         };
-        if (staged) {
-            for (int base = 0; base < ns; base += 32) {
-                const int i = base + lane;
-                take_batch(i < ns && sk[i] <= lim, i < ns ? sj[i] : -1);
-            }
-        } else {
-            for (int u = 0; u < S; ++u) {
-                const int c = mt[u].x;
-                const Cand *b = cb + (size_t)u * p.cap;
-                for (int base = 0; base < c; base += 32) {
+        auto collect = [&](float lo, float hi) {  // keys in (lo, hi]
+            if (staged && hi <= slim) {  // all staged: every key up to slim was
+                for (int base = 0; base < ns; base += 32) {
                     const int i = base + lane;
-                    Cand e{INFINITY, -1};
-                    if (i < c) e = b[i];
-                    take_batch(i < c && e.key <= lim, e.idx);
+                    const bool in = i < ns && sk[i] > lo && sk[i] <= hi;
+                    take_batch(in, i < ns ? sj[i] : -1);
+                }
+            } else {
+                for (int u = 0; u < S; ++u) {
+                    const int c = mt[u].x;
+                    const Cand *b = cb + (size_t)u * p.cap;
+                    for (int base = 0; base < c; base += 32) {
+                        const int i = base + lane;
+                        Cand e{INFINITY, -1};
+                        if (i < c) e = b[i];
+                        take_batch(i < c && e.key > lo && e.key <= hi, e.idx);
+                    }
                 }
             }
-        }
-        if (nr > RC) good = false;
-        __syncwarp();
-        if (good && nr >= p.k) {
-            // exact FP32 direct-difference distances, four candidates at a time
-            const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (int64_t)qid * p.D;
-            const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
-                              (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
-            for (int t0 = 0; t0 < nr; t0 += 4) {
+        };
+        // exact FP32 direct-difference distances of rjw[from, to), four at a time
+        const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (int64_t)qid * p.D;
+        const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
+                          (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
+        auto rerank = [&](int from, int to) {
+            for (int t0 = from; t0 < to; t0 += 4) {
                 const float *xc[4];
                 float a[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    xc[u] = t0 + u < nr ? p.X + (int64_t)rjw[t0 + u] * p.D : nullptr;
+                    xc[u] = t0 + u < to ? p.X + (int64_t)rjw[t0 + u] * p.D : nullptr;
                     a[u] = 0.f;
                 }
                 if (vec4) {
@@ -974,6 +1030,35 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
                     if (lane == 0 && xc[u]) rdw[t0 + u] = r;
                 }
             }
+        };
+        collect(-INFINITY, theta);
+        const int nr1 = nr;
+        float Ec = E;  // the key error bound the band and the certificate use
+        if (nr1 > RC) good = false;
+        __syncwarp();
+        if (good && CERT) {
+            // the candidates at or below theta are sel >= k real points: the
+            // largest of their exact distances bounds the k-th nearest one, so
+            // only points of norm at most ||x|| + sqrt(that) can be nearer, and
+            // the bound is taken over those points only
+            rerank(0, nr1);
+            __syncwarp();
+            float dk0 = 0.f;
+            for (int t = lane; t < nr1; t += 32) dk0 = fmaxf(dk0, rdw[t]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dk0 = fmaxf(dk0, __shfl_xor_sync(0xffffffffu, dk0, o));
+            const float4 st = cross ? p.qstats[row] : p.stats[qid];
+            Ec = fminf(E, key_error_bound_capped(st, p.gmax, p.acc_coef,
+                                                  st.x + sqrtf(dk0) * (1.f + 1e-6f) + 1e-30f));
+            collect(theta, theta + 2.f * Ec);
+            if (nr > RC) good = false;
+            __syncwarp();
+            if (good) rerank(nr1, nr);
+        } else if (good) {
+            rerank(0, nr1);
+        }
+        __syncwarp();
+        if (good && nr >= p.k) {
             int ns2 = 32;
             while (ns2 < nr) ns2 <<= 1;
             for (int t = nr + lane; t < ns2; t += 32) {
@@ -985,7 +1070,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
             if (CERT) {
                 const float dk = rdw[p.k - 1];
                 const float nx = cross ? p.qnrm[row] : p.nrm[qid];
-                const float lb = nx + tau_min - E;
+                const float lb = nx + tau_min - Ec;
                 // certified: no point outside the buffers can be closer than dk
                 good = isinf(tau_min) || dk < lb * (1.f - 1e-6f);
             }
