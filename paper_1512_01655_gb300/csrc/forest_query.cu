@@ -19,6 +19,19 @@
 //      (FP32 direct differences, float4 loads when D % 4 == 0) and keeps the k
 //      best in shared memory under the (distance, index) order.
 // Warps fetch queries from a global counter; the grid is sized by occupancy.
+//
+// Cut-off (all-rows mode). Popped keys never decrease (a descent adds squares to
+// the popped key), so the search pops its entries in key order and stops at some
+// last key K. Leaving out every push with key > C does not change which entries
+// at or below C are popped, nor their order: an entry's fate in the bounded queue
+// (kept or evicted) depends only on the entries below it, and the queue's minimum
+// is the same while it holds any entry at or below C. So a search run with a
+// cut-off C that reaches its budget is the search without one, and most pushes
+// (and nearly all evictions) are skipped. A search that runs dry under its
+// cut-off is run again without one. The queries are taken in the leaf order of
+// tree 0; every FQ_SEED_GAP-th one (a seed, handed out first) runs without a
+// cut-off and records its K, and the others take FQ_CUT_FACTOR times the larger
+// K of the seeds on either side (neighbouring leaves: similar densities).
 #include <float.h>
 #include <limits.h>
 
@@ -32,6 +45,8 @@ constexpr int FQ_WARPS = 4;
 constexpr int FQ_MAX_SLOTS = 4096;  // warps of the persistent grid (one seen bitmap each)
 constexpr int FQ_KCAP = 128;
 constexpr int SUB_DEPTH = 5;        // levels fetched per descent round (31 nodes, one per lane)
+constexpr int FQ_SEED_GAP = 32;     // one seed query per this many, in tree-0 leaf order
+constexpr float FQ_CUT_FACTOR = 3.f;
 
 struct FqArgs {
     const float *X;
@@ -54,6 +69,8 @@ struct FqArgs {
     int32_t *marked;   // [slots][mark_cap]
     int64_t mark_cap;
     int *next_query;
+    float *kseed;      // [n_seeds] last popped key of each seed (NaN until written)
+    int64_t n_seeds;
 };
 
 __device__ __forceinline__ uint64_t qpack(float key, int tree, int node) {
@@ -209,7 +226,7 @@ __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool vali
 }
 
 // Descend tree `tr` from node v (queue key `key`) to a leaf, pushing the far
-// child of every node passed; returns the leaf index. Each round covers up to
+// child of every node passed whose key is at most `cut`; returns the leaf index. Each round covers up to
 // five levels: lane j < 31 loads node j of the five-level subtree below the
 // current node and compares the query with its split, a ballot of the
 // outcomes gives the path, and lane j < (levels) pushes the far child of the
@@ -218,7 +235,7 @@ __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool vali
 // leaf's point (-1 if empty). Node ids fit in 26 bits.
 template <bool PT>
 __device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueue &q, int tr, int v,
-                                       float key, int lane, int &pt) {
+                                       float key, float cut, int lane, int &pt) {
     const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
     const float *sv = A.split_val + (int64_t)tr * A.n_int;
     const int32_t *lpt = A.leaf_pt + ((int64_t)tr << A.h);
@@ -252,7 +269,7 @@ __device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueu
         const float pk = __shfl_sync(FULL, fk, my_c);
         const int pn = __shfl_sync(FULL, node, my_c);
         const uint64_t e = qpack(pk, tr, ((lm >> my_c) & 1u) ? 2 * pn + 2 : 2 * pn + 1);
-        cq_push_lanes(q, e, lane < d && !isinf(pk), lane);
+        cq_push_lanes(q, e, lane < d && !isinf(pk) && pk <= cut, lane);
         const int o = c + 1 - (1 << d);  // offset of the reached node on its level
         if (PT && last) pt = __shfl_sync(FULL, lp, o);
         v = ((v + 1) << d) - 1 + o;
@@ -282,9 +299,27 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
         if (lane == 0) s = atomicAdd(A.next_query, 1);
         s = __shfl_sync(0xffffffffu, s, 0);
         if (s >= A.nq) break;
-        // all-rows mode walks the points in the leaf order of tree 0, so warps
-        // running at the same time search neighbouring points (shared rows in L2)
-        if (!A.qlist) s = A.perm[s];
+        float cut = INFINITY;
+        int64_t seed = -1;
+        if (!A.qlist) {
+            // all-rows mode walks the points in the leaf order of tree 0, so warps
+            // running at the same time search neighbouring points (shared rows in
+            // L2): the seeds first, then the positions between them
+            int64_t pos;
+            if (s < A.n_seeds) {
+                seed = s;
+                pos = s * FQ_SEED_GAP;
+            } else {
+                const int64_t j = s - A.n_seeds;
+                pos = j / (FQ_SEED_GAP - 1) * FQ_SEED_GAP + j % (FQ_SEED_GAP - 1) + 1;
+                const int64_t a = pos / FQ_SEED_GAP;
+                const float ka = __ldcg(A.kseed + a);
+                const float kb = a + 1 < A.n_seeds ? __ldcg(A.kseed + a + 1) : ka;
+                // a seed still running reads NaN: no cut-off
+                if (ka >= 0.f && kb >= 0.f) cut = FQ_CUT_FACTOR * fmaxf(ka, kb);
+            }
+            s = A.perm[pos];
+        }
         const int64_t qi = A.qlist ? A.qlist[s] : s;
         if (qi < 0 || qi >= A.N) continue;  // flagged by the caller's index check
         const float *xq = A.X + qi * A.D;
@@ -293,92 +328,115 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
             td[t] = INFINITY;
             tj[t] = INT_MAX;
         }
-        if (lane == 0) {
-            atomicOr(&seen[qi >> 5], 1u << (qi & 31));
-            marked[0] = (int32_t)qi;
-        }
-        int64_t n_marked = 1, evaluated = 0;
+        int64_t n_marked, evaluated;
+        float kfin = 0.f;  // key of the last pop whose leaf was scanned
         ColQueue q;
-        cq_init(q, qcol, A.qcap, lane);
-        __syncwarp();
-
-        // ---- phase 1: traversal ----
-        auto scan_leaf = [&](int tr, int m) {
-            const int s0 = A.leaf_ofs[m];
-            const int cnt = A.leaf_ofs[m + 1] - s0;
-            const int32_t *pt = A.perm + (int64_t)tr * A.N + s0;
-            for (int b = 0; b < cnt; b += 32) {
-                const int q = b + lane;
-                int32_t p = -1;
-                bool fresh = false;
-                if (q < cnt) {
-                    p = pt[q];
-                    fresh = !((__ldcg(&seen[p >> 5]) >> (p & 31)) & 1u);
-                }
-                const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-                if (fresh) {
-                    atomicOr(&seen[p >> 5], 1u << (p & 31));
-                    marked[n_marked + __popc(fm & ((1u << lane) - 1u))] = p;
-                }
-                n_marked += __popc(fm);
-                evaluated += __popc(fm);
-                __syncwarp();
+        // ---- phase 1: traversal (a second time, without cut-off, if the first ran dry) ----
+        for (;;) {
+            if (lane == 0) {
+                atomicOr(&seen[qi >> 5], 1u << (qi & 31));
+                marked[0] = (int32_t)qi;
             }
-        };
-        if (A.leaf_size == 1) {
-            // one point per leaf: the seen test of step i is resolved after the
-            // descent of step i + 1 (descents never read the bitmap; a step made
-            // past the stopping point only adds queue entries that are not used)
-            int pend_p = -1;
-            uint32_t pend_w = 0;
-            auto resolve = [&]() {
-                if (pend_p >= 0 && !((pend_w >> (pend_p & 31)) & 1u)) {
-                    if (lane == 0) {
-                        atomicOr(&seen[pend_p >> 5], 1u << (pend_p & 31));
-                        marked[n_marked] = pend_p;
+            n_marked = 1;
+            evaluated = 0;
+            cq_init(q, qcol, A.qcap, lane);
+            __syncwarp();
+
+            auto scan_leaf = [&](int tr, int m) {
+                const int s0 = A.leaf_ofs[m];
+                const int cnt = A.leaf_ofs[m + 1] - s0;
+                const int32_t *pt = A.perm + (int64_t)tr * A.N + s0;
+                for (int b = 0; b < cnt; b += 32) {
+                    const int q = b + lane;
+                    int32_t p = -1;
+                    bool fresh = false;
+                    if (q < cnt) {
+                        p = pt[q];
+                        fresh = !((__ldcg(&seen[p >> 5]) >> (p & 31)) & 1u);
                     }
-                    ++n_marked;
-                    ++evaluated;
+                    const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+                    if (fresh) {
+                        atomicOr(&seen[p >> 5], 1u << (p & 31));
+                        marked[n_marked + __popc(fm & ((1u << lane) - 1u))] = p;
+                    }
+                    n_marked += __popc(fm);
+                    evaluated += __popc(fm);
+                    __syncwarp();
                 }
-                pend_p = -1;
             };
-            for (int t = 0;;) {
-                int hp_ = -1;
-                if (t < A.T) {
-                    descend<true>(A, qv, q, t, 0, 0.f, lane, hp_);
-                    ++t;
-                } else {
-                    if (q.n == 0) break;
+            if (A.leaf_size == 1) {
+                // one point per leaf: the seen test of step i is resolved after the
+                // descent of step i + 1 (descents never read the bitmap; a step made
+                // past the stopping point only adds queue entries that are not used)
+                int pend_p = -1, pending = 0;
+                uint32_t pend_w = 0;
+                float pend_key = 0.f;
+                auto resolve = [&]() {
+                    if (pending) kfin = pend_key;
+                    pending = 0;
+                    if (pend_p >= 0 && !((pend_w >> (pend_p & 31)) & 1u)) {
+                        if (lane == 0) {
+                            atomicOr(&seen[pend_p >> 5], 1u << (pend_p & 31));
+                            marked[n_marked] = pend_p;
+                        }
+                        ++n_marked;
+                        ++evaluated;
+                    }
+                    pend_p = -1;
+                };
+                for (int t = 0;;) {
+                    int hp_ = -1;
+                    float key = 0.f;
+                    if (t < A.T) {
+                        descend<true>(A, qv, q, t, 0, 0.f, cut, lane, hp_);
+                        ++t;
+                    } else {
+                        if (q.n == 0) break;
+                        const uint64_t e = cq_pop(q, lane);
+                        key = __uint_as_float((uint32_t)(e >> 32));
+                        const int tr = (int)((e >> 26) & 63u);
+                        const int v = (int)(e & ((1u << 26) - 1u));
+                        descend<true>(A, qv, q, tr, v, key, cut, lane, hp_);
+                    }
+                    // the word is loaded now and only read at the next step
+                    uint32_t hw = hp_ >= 0 ? __ldcg(&seen[hp_ >> 5]) : 0u;
+                    const int prev = pend_p;
+                    resolve();
+                    __syncwarp();
+                    if (evaluated >= need) break;
+                    if (hp_ >= 0 && hp_ == prev) hw |= 1u << (prev & 31);
+                    pend_p = hp_;
+                    pend_w = hw;
+                    pend_key = key;
+                    pending = 1;
+                }
+                resolve();
+                __syncwarp();
+            } else {
+                int unused;
+                for (int t = 0; t < A.T && evaluated < need; ++t) {
+                    scan_leaf(t, descend<false>(A, qv, q, t, 0, 0.f, cut, lane, unused));
+                    kfin = 0.f;
+                }
+                while (evaluated < need && q.n > 0) {
                     const uint64_t e = cq_pop(q, lane);
                     const float key = __uint_as_float((uint32_t)(e >> 32));
                     const int tr = (int)((e >> 26) & 63u);
                     const int v = (int)(e & ((1u << 26) - 1u));
-                    descend<true>(A, qv, q, tr, v, key, lane, hp_);
+                    scan_leaf(tr, descend<false>(A, qv, q, tr, v, key, cut, lane, unused));
+                    kfin = key;
                 }
-                // the word is loaded now and only read at the next step
-                uint32_t hw = hp_ >= 0 ? __ldcg(&seen[hp_ >> 5]) : 0u;
-                const int prev = pend_p;
-                resolve();
-                __syncwarp();
-                if (evaluated >= need) break;
-                if (hp_ >= 0 && hp_ == prev) hw |= 1u << (prev & 31);
-                pend_p = hp_;
-                pend_w = hw;
             }
-            resolve();
+            if (evaluated >= need || isinf(cut)) break;
+            // the cut-off left too few entries: clear this attempt's marks, search again
+            for (int64_t u = lane; u < n_marked; u += 32) {
+                const int32_t p = marked[u];
+                atomicAnd(&seen[p >> 5], ~(1u << (p & 31)));
+            }
             __syncwarp();
-        } else {
-            int unused;
-            for (int t = 0; t < A.T && evaluated < need; ++t)
-                scan_leaf(t, descend<false>(A, qv, q, t, 0, 0.f, lane, unused));
-            while (evaluated < need && q.n > 0) {
-                const uint64_t e = cq_pop(q, lane);
-                const float key = __uint_as_float((uint32_t)(e >> 32));
-                const int tr = (int)((e >> 26) & 63u);
-                const int v = (int)(e & ((1u << 26) - 1u));
-                scan_leaf(tr, descend<false>(A, qv, q, tr, v, key, lane, unused));
-            }
+            cut = INFINITY;
         }
+        if (seed >= 0 && lane == 0) A.kseed[seed] = kfin;
         // the queue ran dry with fewer than k points: lowest-index unseen points
         for (int64_t b = 0; evaluated < A.k && b < A.N; b += 32) {
             const int64_t p = b + lane;
@@ -507,7 +565,8 @@ size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int check
     a.seen = c.take<uint32_t>((size_t)FQ_MAX_SLOTS * a.words);
     a.marked = c.take<int32_t>((size_t)FQ_MAX_SLOTS * a.mark_cap);
     a.next_query = c.take<int>(1);
-    (void)nq;
+    a.n_seeds = (nq + FQ_SEED_GAP - 1) / FQ_SEED_GAP;
+    a.kseed = c.take<float>((size_t)a.n_seeds + 1);
     if (ws_out) *static_cast<FqArgs *>(ws_out) = a;
     return c.bytes();
 }
@@ -539,6 +598,8 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
                                ceil_div(nq, FQ_WARPS));
     e = cudaMemsetAsync(a.seen, 0, sizeof(uint32_t) * (size_t)grid * FQ_WARPS * a.words, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.next_query, 0, sizeof(int), stream);
+    if (e == cudaSuccess)  // 0xff bytes: NaN, a seed not yet searched
+        e = cudaMemsetAsync(a.kseed, 0xff, sizeof(float) * (size_t)(a.n_seeds + 1), stream);
     if (e != cudaSuccess) return cuda_error(e, "forest query memset");
     a.X = X;
     a.N = f.N;

@@ -242,6 +242,48 @@ def test_forest_full_budget_is_exact(at):
     assert torch.all(ev == 599)
 
 
+def test_forest_query_cutoff_is_exact(at):
+    # In all-rows mode most queries search under a cut-off taken from seed
+    # queries (pushes above it skipped, a search that runs dry repeated without
+    # it); a query list searches without one. Both give the same lists bit for
+    # bit; 30000 queries are several waves of warps, so most queries start after
+    # their seeds have finished and take the cut-off.
+    X = synth.sparse_prototypes(N=30000, D=784, seed=12)
+    Xd = to_dev(X)
+    f = at.atsne_forest_build(Xd, trees=4, leaf_size=1, seed=3)
+    a = at.atsne_forest_query(Xd, f, 90, checks=1024)
+    rows = torch.arange(X.shape[0], dtype=torch.int32, device=DEV)
+    b = at.atsne_forest_query(Xd, f, 90, checks=1024, queries=rows)
+    at.atsne_check()
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+    # a small queue (evictions decide what is popped) and a multi-point leaf
+    for leaf, qcap in ((1, 128), (4, 256)):
+        f = at.atsne_forest_build(Xd, trees=2, leaf_size=leaf, seed=4)
+        a = at.atsne_forest_query(Xd, f, 90, checks=512, queue_cap=qcap)
+        b = at.atsne_forest_query(Xd, f, 90, checks=512, queue_cap=qcap, queries=rows)
+        for u, v in zip(a, b):
+            assert torch.equal(u, v)
+
+
+def test_forest_mnist_shaped_full_size_sampled(at):
+    # the benchmark's forest launch (N=70000, D=784, T=4, V=5, checks=1024,
+    # queue 512): the forest compared whole, the search on 64 sampled rows the
+    # oracle runs one by one (same visiting order: same evaluated counts)
+    X = synth.sparse_prototypes(seed=2)
+    Xd = to_dev(X)
+    f, o = forest_compare(at, X, 4, 1, 7)
+    idx, d2, ev = at.atsne_forest_query(Xd, f, 90, checks=1024)
+    at.atsne_check()
+    rows = synth.sample_rows(X.shape[0], 64, seed=23)
+    o_idx, o_d2, o_ev = oracle.forest_query(X, o, 90, 1024, queries=rows)
+    assert np.array_equal(ev.cpu().numpy()[rows], o_ev)
+    gi = idx.cpu().numpy()[rows]
+    same = np.array([set(gi[r]) == set(o_idx[r]) for r in range(len(rows))])
+    assert same.mean() > 0.95
+    assert np.abs(d2.cpu().numpy()[rows] - o_d2).max() <= 1e-5 * max(1.0, o_d2.max())
+
+
 def test_knn_forest_method_matches_build_then_query(at):
     X = synth.gaussian_mixture(1200, 16, seed=6)
     Xd = to_dev(X)
