@@ -152,6 +152,24 @@ __device__ __forceinline__ void warp_bitonic_sort_smem(K *key, V *val, int n, in
     }
 }
 
+// Asynchronous global -> shared copies (cp.async): 4 or 16 bytes per call,
+// completed in commit-group order; a thread's wait covers its own copies.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { cp_async_wait<1>(); }
+__device__ __forceinline__ void cp_async_wait0() { cp_async_wait<0>(); }
+
 #endif  // __CUDACC__
 
 }  // namespace atsne

@@ -170,19 +170,6 @@ __global__ void iota_kernel(int32_t *perm, int64_t N, int T) {
 constexpr int ACC_SLICE = 1024;         // columns per slice (256 threads x 4)
 constexpr int ACC_TILE_FLOATS = 12288;  // floats per tile buffer (48 KB)
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 struct SliceGeom {
     int W, Wp, TP;  // columns, padded row length (multiple of 4), rows per tile

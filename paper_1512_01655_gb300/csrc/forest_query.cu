@@ -3,8 +3,9 @@
 // of `checks` distinct points has been evaluated.
 //
 // The visiting order never depends on distances (no pruning by the current
-// k-th distance), so each query runs in two phases inside one warp:
-//   1. traversal: queue pops, descents and de-duplication only. A descent
+// k-th distance), so the search runs as two kernels, one warp per query in each:
+//   1. traversal (forest_traverse_kernel): queue pops, descents and
+//      de-duplication only. A descent
 //      round covers five levels below the current node: each lane loads one
 //      of the 31 subtree nodes and compares the query with its split, one
 //      ballot gives the path, and the far children along it are pushed, so a
@@ -14,11 +15,17 @@
 //      node). The queue is spread over the 32 lanes (ColQueue): pops and
 //      evictions take a warp-wide min or max reduction and one
 //      warp-cooperative column rescan, insertions one store. The points
-//      collected are appended to a per-warp list in the workspace.
-//   2. evaluation: the warp streams the collected points' rows eight at a time
-//      (FP32 direct differences, float4 loads when D % 4 == 0) and keeps the k
-//      best in shared memory under the (distance, index) order.
-// Warps fetch queries from a global counter; the grid is sized by occupancy.
+//      collected are written to the query's list in the workspace.
+//   2. evaluation (forest_dist_kernel): the warp streams the listed points'
+//      rows eight at a time (float4 loads into registers when D % 4 == 0, two
+//      pieces of each row in flight; built for 32 warps per SM, so that enough
+//      bytes are in flight to cover the L2 latency), takes FP32 direct
+//      differences, reduces the eight rows at once (nine shuffles), and keeps
+//      the k best under the (distance, index) order in a buffer of FD_BUF
+//      pairs: new candidates below the current k-th pair are appended, and a
+//      full buffer is sorted and cut back to k.
+// The queries go in chunks (the lists of a chunk fit in FQ_MARK_BUDGET bytes);
+// traversal warps fetch queries from a global counter.
 //
 // Cut-off (all-rows mode). Popped keys never decrease (a descent adds squares to
 // the popped key), so the search pops its entries in key order and stops at some
@@ -42,8 +49,11 @@ namespace atsne {
 namespace {
 
 constexpr int FQ_WARPS = 4;
-constexpr int FQ_MAX_SLOTS = 4096;  // warps of the persistent grid (one seen bitmap each)
-constexpr int FQ_KCAP = 128;
+constexpr int FQ_MAX_SLOTS = 4096;  // traversal warps of the persistent grid (one seen bitmap each)
+constexpr int FQ_KCAP = 128;        // largest k
+constexpr int64_t FQ_MARK_BUDGET = int64_t(1) << 30;  // bytes of point lists per chunk
+constexpr int FD_MAX_WARPS = 4;     // distance kernel: warps per block (fewer for very long rows)
+constexpr int FD_BUF = 256;         // (distance, index) pairs per distance warp
 constexpr int SUB_DEPTH = 5;        // levels fetched per descent round (31 nodes, one per lane)
 constexpr int FQ_SEED_GAP = 32;     // one seed query per this many, in tree-0 leaf order
 constexpr float FQ_CUT_FACTOR = 3.f;
@@ -60,17 +70,28 @@ struct FqArgs {
     const int32_t *leaf_pt;
     int leaf_size;
     const int32_t *qlist;
-    int64_t nq;
-    int32_t *idx_out;
-    float *d2_out;
+    int64_t w0, nw;    // work items of this chunk: leaf positions of tree 0, or list entries
     int64_t *evaluated_out;
     uint32_t *seen;    // [slots][words]
     int64_t words;
-    int32_t *marked;   // [slots][mark_cap]
+    int32_t *marked;   // [nw][mark_cap] points collected (entry 0: the query itself)
+    int32_t *n_marked; // [nw] entries of each list (0: no list)
     int64_t mark_cap;
     int *next_query;
-    float *kseed;      // [n_seeds] last popped key of each seed (NaN until written)
-    int64_t n_seeds;
+    float *kseed;      // last popped key of each seed (NaN until written)
+    int64_t chunk;     // work items per chunk (a multiple of FQ_SEED_GAP)
+};
+
+struct FdArgs {
+    const float *X;
+    int D, k;
+    bool list_mode;
+    int64_t w0, nw;
+    const int32_t *marked;
+    const int32_t *n_marked;
+    int64_t mark_cap;
+    int32_t *idx_out;
+    float *d2_out;
 };
 
 __device__ __forceinline__ uint64_t qpack(float key, int tree, int node) {
@@ -277,57 +298,60 @@ __device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueu
     return v - n_int;
 }
 
-__global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
+__global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArgs A) {
     extern __shared__ __align__(16) unsigned char fq_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const size_t heap_b = (size_t)((A.qcap + 31) >> 5) * 32 * 8;
     const size_t q_b = ((size_t)A.D * 4 + 15) & ~size_t(15);
-    unsigned char *base = fq_smem + w * (heap_b + q_b + FQ_KCAP * 8);
+    unsigned char *base = fq_smem + w * (heap_b + q_b);
     uint64_t *qcol = reinterpret_cast<uint64_t *>(base);
     float *qv = reinterpret_cast<float *>(base + heap_b);
-    float *td = reinterpret_cast<float *>(base + heap_b + q_b);
-    int *tj = reinterpret_cast<int *>(td + FQ_KCAP);
 
     const int slot = blockIdx.x * FQ_WARPS + w;
     uint32_t *seen = A.seen + (int64_t)slot * A.words;
-    int32_t *marked = A.marked + (int64_t)slot * A.mark_cap;
     const int64_t need = A.checks > A.k ? A.checks : A.k;
-    const bool vec4 = (A.D & 3) == 0 && (reinterpret_cast<uintptr_t>(A.X) & 15) == 0;
 
     for (;;) {
-        int64_t s = 0;
-        if (lane == 0) s = atomicAdd(A.next_query, 1);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= A.nq) break;
+        int64_t c = 0;
+        if (lane == 0) c = atomicAdd(A.next_query, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= A.nw) break;
         float cut = INFINITY;
-        int64_t seed = -1;
+        int64_t seed = -1, t, qi, row;
         if (!A.qlist) {
             // all-rows mode walks the points in the leaf order of tree 0, so warps
             // running at the same time search neighbouring points (shared rows in
-            // L2): the seeds first, then the positions between them
-            int64_t pos;
-            if (s < A.n_seeds) {
-                seed = s;
-                pos = s * FQ_SEED_GAP;
+            // L2): the chunk's seeds first, then the positions between them
+            const int64_t ns = (A.nw + FQ_SEED_GAP - 1) / FQ_SEED_GAP;
+            if (c < ns) {
+                t = c * FQ_SEED_GAP;
             } else {
-                const int64_t j = s - A.n_seeds;
-                pos = j / (FQ_SEED_GAP - 1) * FQ_SEED_GAP + j % (FQ_SEED_GAP - 1) + 1;
-                const int64_t a = pos / FQ_SEED_GAP;
+                const int64_t j = c - ns;
+                t = j / (FQ_SEED_GAP - 1) * FQ_SEED_GAP + j % (FQ_SEED_GAP - 1) + 1;
+            }
+            const int64_t wpos = A.w0 + t, a = wpos / FQ_SEED_GAP;
+            if (t % FQ_SEED_GAP == 0) {
+                seed = a;
+            } else {
                 const float ka = __ldcg(A.kseed + a);
-                const float kb = a + 1 < A.n_seeds ? __ldcg(A.kseed + a + 1) : ka;
+                // the seed after the chunk's last block belongs to the next chunk
+                const float kb = (a + 1) * FQ_SEED_GAP < A.w0 + A.nw ? __ldcg(A.kseed + a + 1) : ka;
                 // a seed still running reads NaN: no cut-off
                 if (ka >= 0.f && kb >= 0.f) cut = FQ_CUT_FACTOR * fmaxf(ka, kb);
             }
-            s = A.perm[pos];
+            qi = row = A.perm[wpos];
+        } else {
+            t = c;
+            row = A.w0 + c;
+            qi = A.qlist[row];
         }
-        const int64_t qi = A.qlist ? A.qlist[s] : s;
-        if (qi < 0 || qi >= A.N) continue;  // flagged by the caller's index check
+        int32_t *marked = A.marked + t * A.mark_cap;
+        if (qi < 0 || qi >= A.N) {  // flagged by the caller's index check
+            if (lane == 0) A.n_marked[t] = 0;
+            continue;
+        }
         const float *xq = A.X + qi * A.D;
         for (int d = lane; d < A.D; d += 32) qv[d] = xq[d];
-        for (int t = lane; t < FQ_KCAP; t += 32) {
-            td[t] = INFINITY;
-            tj[t] = INT_MAX;
-        }
         int64_t n_marked, evaluated;
         float kfin = 0.f;  // key of the last pop whose leaf was scanned
         ColQueue q;
@@ -461,86 +485,10 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
             __syncwarp();
         }
 
-        // ---- phase 2: distances of the collected points, k best kept ----
-        float md = INFINITY;
-        int mj = INT_MAX, mp = 0;
-        auto insert = [&](float dist, int p) {
-            if (!pair_less(dist, p, md, mj)) return;
-            if (lane == 0) {
-                td[mp] = dist;
-                tj[mp] = p;
-            }
-            __syncwarp();
-            float bd = -INFINITY;
-            int bj = INT_MIN, bp = 0;
-            for (int u = lane; u < A.k; u += 32) {
-                if (pair_less(bd, bj, td[u], tj[u])) {
-                    bd = td[u];
-                    bj = tj[u];
-                    bp = u;
-                }
-            }
-            warp_argmax_pair(bd, bj, bp);
-            md = bd;
-            mj = bj;
-            mp = bp;
-            __syncwarp();
-        };
-        for (int64_t b0 = 1; b0 < n_marked; b0 += 32) {
-            const int64_t nb = n_marked - b0 < 32 ? n_marked - b0 : 32;
-            const int my = lane < nb ? marked[b0 + lane] : -1;
-            for (int g = 0; g < nb; g += 8) {
-                int pj[8];
-                float acc[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    pj[u] = __shfl_sync(0xffffffffu, my, (g + u) & 31);
-                    if (g + u >= nb) pj[u] = -1;
-                    acc[u] = 0.f;
-                }
-                if (vec4) {
-                    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
-                    for (int d = lane; d < (A.D >> 2); d += 32) {
-                        const float4 qq = q4[d];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            if (pj[u] < 0) continue;
-                            const float4 xv = reinterpret_cast<const float4 *>(A.X + (int64_t)pj[u] * A.D)[d];
-                            float df = qq.x - xv.x;
-                            acc[u] = fmaf(df, df, acc[u]);
-                            df = qq.y - xv.y;
-                            acc[u] = fmaf(df, df, acc[u]);
-                            df = qq.z - xv.z;
-                            acc[u] = fmaf(df, df, acc[u]);
-                            df = qq.w - xv.w;
-                            acc[u] = fmaf(df, df, acc[u]);
-                        }
-                    }
-                } else {
-                    for (int d = lane; d < A.D; d += 32) {
-                        const float qq = qv[d];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            if (pj[u] < 0) continue;
-                            const float df = qq - A.X[(int64_t)pj[u] * A.D + d];
-                            acc[u] = fmaf(df, df, acc[u]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float dist = warp_sum(acc[u]);
-                    if (pj[u] >= 0) insert(dist, pj[u]);
-                }
-            }
+        if (lane == 0) {
+            A.n_marked[t] = (int32_t)n_marked;
+            if (A.evaluated_out) A.evaluated_out[row] = evaluated;
         }
-
-        warp_bitonic_sort_smem(td, tj, FQ_KCAP, lane);
-        for (int t = lane; t < A.k; t += 32) {
-            A.idx_out[s * A.k + t] = tj[t];
-            A.d2_out[s * A.k + t] = td[t];
-        }
-        if (lane == 0 && A.evaluated_out) A.evaluated_out[s] = evaluated;
         for (int64_t u = lane; u < n_marked; u += 32) {
             const int32_t p = marked[u];
             atomicAnd(&seen[p >> 5], ~(1u << (p & 31)));
@@ -549,9 +497,169 @@ __global__ void __launch_bounds__(FQ_WARPS * 32) forest_query_kernel(FqArgs A) {
     }
 }
 
+// Sums of eight rows' partial sums over the warp with nine shuffles: each lane
+// ends with the total of row ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 +
+// ((lane >> 2) & 1) (four lanes per row).
+__device__ __forceinline__ float warp_sum8(float (&v)[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float send = b4 ? v[u] : v[u + 4];
+        const float keep = b4 ? v[u + 4] : v[u];
+        v[u] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const float send = b3 ? v[u] : v[u + 2];
+        const float keep = b3 ? v[u + 2] : v[u];
+        v[u] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+    const float send = b2 ? v[0] : v[1];
+    float r = (b2 ? v[1] : v[0]) + __shfl_xor_sync(FULL, send, 4);
+    r += __shfl_xor_sync(FULL, r, 2);
+    r += __shfl_xor_sync(FULL, r, 1);
+    return r;
+}
+
+// Distances of each query to its listed points (entry 0, the query, left out)
+// and the k best under the (distance, index) order, written sorted.
+template <bool VEC>
+__global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArgs A) {
+    extern __shared__ __align__(16) unsigned char fd_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int Dp = (A.D + 3) & ~3;
+    float *qv = reinterpret_cast<float *>(fd_smem) + (size_t)w * Dp;
+    float *bd = reinterpret_cast<float *>(fd_smem + (size_t)nwarp * Dp * 4) + w * FD_BUF;
+    int *bj = reinterpret_cast<int *>(bd + (size_t)nwarp * FD_BUF);
+    const int D = A.D, D4 = D >> 2, k = A.k;
+    const int64_t stride = (int64_t)gridDim.x * nwarp;
+
+    for (int64_t t = (int64_t)blockIdx.x * nwarp + w; t < A.nw; t += stride) {
+        const int n = A.n_marked[t];
+        if (n == 0) continue;
+        const int32_t *list = A.marked + t * A.mark_cap;
+        const int32_t qi = list[0];
+        const int64_t row = A.list_mode ? A.w0 + t : qi;
+        const float *xq = A.X + (int64_t)qi * D;
+        for (int d = lane; d < D; d += 32) qv[d] = xq[d];
+        for (int u = lane; u < FD_BUF; u += 32) {
+            bd[u] = INFINITY;
+            bj[u] = INT_MAX;
+        }
+        __syncwarp();
+        const int nr = n - 1;
+        int fill = 0;
+        bool sorted = false;
+        float thr_d = INFINITY;
+        int thr_j = INT_MAX;
+        auto sort_cut = [&]() {
+            for (int u = fill + lane; u < FD_BUF; u += 32) {
+                bd[u] = INFINITY;
+                bj[u] = INT_MAX;
+            }
+            __syncwarp();
+            warp_bitonic_sort_smem(bd, bj, FD_BUF, lane);
+            fill = k;
+            sorted = true;
+            thr_d = bd[k - 1];
+            thr_j = bj[k - 1];
+        };
+        int my = 0;
+        for (int b0 = 0; b0 < nr; b0 += 8) {
+            if ((b0 & 31) == 0) my = b0 + lane < nr ? list[1 + b0 + lane] : 0;
+            int pj[8];
+            float acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                pj[u] = __shfl_sync(FULL, my, (b0 + u) & 31);
+                if (b0 + u >= nr) pj[u] = pj[0];  // a valid row, its sum unused
+                acc[u] = 0.f;
+            }
+            if (VEC) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+#pragma unroll 2
+                for (int c = lane; c < D4; c += 32) {
+                    const float4 qq = q4[c];
+                    float4 xv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        xv[u] = __ldg(reinterpret_cast<const float4 *>(A.X + (int64_t)pj[u] * D) + c);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        float df = qq.x - xv[u].x;
+                        acc[u] = fmaf(df, df, acc[u]);
+                        df = qq.y - xv[u].y;
+                        acc[u] = fmaf(df, df, acc[u]);
+                        df = qq.z - xv[u].z;
+                        acc[u] = fmaf(df, df, acc[u]);
+                        df = qq.w - xv[u].w;
+                        acc[u] = fmaf(df, df, acc[u]);
+                    }
+                }
+            } else {
+                for (int c = lane; c < D; c += 32) {
+                    const float qq = qv[c];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float df = qq - __ldg(A.X + (int64_t)pj[u] * D + c);
+                        acc[u] = fmaf(df, df, acc[u]);
+                    }
+                }
+            }
+            const float dist = warp_sum8(acc, lane);
+            const int u = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+            const bool own = (lane & 3) == 0 && b0 + u < nr;
+            const int p = __shfl_sync(FULL, my, (b0 + u) & 31);
+            const bool cand = own && pair_less(dist, p, thr_d, thr_j);
+            const unsigned m = __ballot_sync(FULL, cand);
+            if (m) {
+                if (cand) {
+                    const int pos = fill + __popc(m & ((1u << lane) - 1u));
+                    bd[pos] = dist;
+                    bj[pos] = p;
+                }
+                fill += __popc(m);
+                sorted = false;
+                __syncwarp();
+                if (fill + 8 > FD_BUF) sort_cut();
+            }
+        }
+        if (!sorted) sort_cut();
+        for (int u = lane; u < k; u += 32) {
+            A.idx_out[row * k + u] = bj[u];
+            A.d2_out[row * k + u] = bd[u];
+        }
+        __syncwarp();
+    }
+}
+
 size_t fq_smem_bytes(int D, int qcap) {
-    return FQ_WARPS * ((size_t)((qcap + 31) >> 5) * 32 * 8 + (((size_t)D * 4 + 15) & ~size_t(15)) +
-                       FQ_KCAP * 8);
+    return FQ_WARPS * ((size_t)((qcap + 31) >> 5) * 32 * 8 + (((size_t)D * 4 + 15) & ~size_t(15)));
+}
+
+size_t fd_warp_bytes(int D) { return (size_t)((D + 3) & ~3) * 4 + FD_BUF * 8; }
+
+template <bool VEC>
+atsne_status fd_launch_v(const FdArgs &a, int warps, cudaStream_t stream) {
+    const size_t smem = warps * fd_warp_bytes(a.D);
+    cudaError_t e = cudaFuncSetAttribute(forest_dist_kernel<VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "forest distances attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forest_dist_kernel<VEC>, warps * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int grid = (int)hmin((int64_t)per_sm * num_sms(), ceil_div(a.nw, warps));
+    return launch_kernel("forest_dist", forest_dist_kernel<VEC>, grid, warps * 32, smem, stream, a);
+}
+
+int64_t fq_mark_cap(int k, int checks, int leaf_size) {
+    const int64_t need = checks > k ? checks : k;
+    return need + leaf_size + k + 1;
+}
+int64_t fq_chunk(int64_t nq, int64_t mark_cap) {
+    int64_t c = FQ_MARK_BUDGET / (mark_cap * 4) / FQ_SEED_GAP * FQ_SEED_GAP;
+    if (c < FQ_SEED_GAP) c = FQ_SEED_GAP;
+    return nq < c ? (nq > 0 ? nq : 1) : c;
 }
 
 }  // namespace
@@ -560,13 +668,13 @@ size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int check
                               void *ws_out) {
     FqArgs a{};
     a.words = (N + 31) / 32;
-    const int64_t need = checks > k ? checks : k;
-    a.mark_cap = need + leaf_size + k + 1;
+    a.mark_cap = fq_mark_cap(k, checks, leaf_size);
+    a.chunk = fq_chunk(nq, a.mark_cap);
     a.seen = c.take<uint32_t>((size_t)FQ_MAX_SLOTS * a.words);
-    a.marked = c.take<int32_t>((size_t)FQ_MAX_SLOTS * a.mark_cap);
+    a.marked = c.take<int32_t>((size_t)a.chunk * a.mark_cap);
+    a.n_marked = c.take<int32_t>((size_t)a.chunk);
     a.next_query = c.take<int>(1);
-    a.n_seeds = (nq + FQ_SEED_GAP - 1) / FQ_SEED_GAP;
-    a.kseed = c.take<float>((size_t)a.n_seeds + 1);
+    a.kseed = c.take<float>((size_t)(nq / FQ_SEED_GAP) + 2);
     if (ws_out) *static_cast<FqArgs *>(ws_out) = a;
     return c.bytes();
 }
@@ -583,23 +691,26 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     FqArgs a;
     forest_query_workspace(c, f.N, nq, k, checks, f.leaf_size, &a);
     if (c.bytes() > ws_bytes) return set_error(ATSNE_ENOMEM, "forest query: workspace too small");
+    if (nq == 0) return ATSNE_OK;
     const size_t smem = fq_smem_bytes(f.D, qcap);
     if (smem > 227 * 1024)
         return set_error(ATSNE_EUNSUPPORTED,
                          "forest query: queue_cap %d with D=%d needs %zu B of shared memory", qcap, f.D,
                          smem);
-    cudaError_t e = cudaFuncSetAttribute(forest_query_kernel,
+    const int fd_warps = (int)hmin(FD_MAX_WARPS, (int64_t)(227 * 1024 / fd_warp_bytes(f.D)));
+    if (fd_warps < 1)
+        return set_error(ATSNE_EUNSUPPORTED, "forest query: rows of D=%d do not fit in shared memory", f.D);
+    cudaError_t e = cudaFuncSetAttribute(forest_traverse_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "forest query attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forest_query_kernel, FQ_WARPS * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forest_traverse_kernel, FQ_WARPS * 32, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     const int grid = (int)hmin(hmin((int64_t)per_sm * num_sms(), FQ_MAX_SLOTS / FQ_WARPS),
-                               ceil_div(nq, FQ_WARPS));
+                               ceil_div(hmin(nq, a.chunk), FQ_WARPS));
     e = cudaMemsetAsync(a.seen, 0, sizeof(uint32_t) * (size_t)grid * FQ_WARPS * a.words, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.next_query, 0, sizeof(int), stream);
     if (e == cudaSuccess)  // 0xff bytes: NaN, a seed not yet searched
-        e = cudaMemsetAsync(a.kseed, 0xff, sizeof(float) * (size_t)(a.n_seeds + 1), stream);
+        e = cudaMemsetAsync(a.kseed, 0xff, sizeof(float) * (size_t)(nq / FQ_SEED_GAP + 2), stream);
     if (e != cudaSuccess) return cuda_error(e, "forest query memset");
     a.X = X;
     a.N = f.N;
@@ -617,11 +728,30 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     a.leaf_pt = f.leaf_pt;
     a.leaf_size = f.leaf_size;
     a.qlist = qlist;
-    a.nq = nq;
-    a.idx_out = idx_out;
-    a.d2_out = d2_out;
     a.evaluated_out = evaluated_out;
-    return launch_kernel("forest_query", forest_query_kernel, grid, FQ_WARPS * 32, smem, stream, a);
+    FdArgs b;
+    b.X = X;
+    b.D = f.D;
+    b.k = k;
+    b.list_mode = qlist != nullptr;
+    b.marked = a.marked;
+    b.n_marked = a.n_marked;
+    b.mark_cap = a.mark_cap;
+    b.idx_out = idx_out;
+    b.d2_out = d2_out;
+    const bool vec = (f.D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    for (int64_t w0 = 0; w0 < nq; w0 += a.chunk) {
+        a.w0 = b.w0 = w0;
+        a.nw = b.nw = hmin(a.chunk, nq - w0);
+        e = cudaMemsetAsync(a.next_query, 0, sizeof(int), stream);
+        if (e != cudaSuccess) return cuda_error(e, "forest query memset");
+        atsne_status st = launch_kernel("forest_traverse", forest_traverse_kernel, grid, FQ_WARPS * 32,
+                                        smem, stream, a);
+        if (st != ATSNE_OK) return st;
+        st = vec ? fd_launch_v<true>(b, fd_warps, stream) : fd_launch_v<false>(b, fd_warps, stream);
+        if (st != ATSNE_OK) return st;
+    }
+    return ATSNE_OK;
 }
 
 }  // namespace atsne
