@@ -234,11 +234,45 @@ __device__ __forceinline__ void cq_push(ColQueue &q, uint64_t x, int lane) {
     if (x > q.hmax) q.hmax = x;
 }
 
-// Pushes the entries of the lanes with `valid` set, in lane order. With no
-// pop in between, the queue ends up holding the same set in any order; when
-// it is full at the start, entries at or above the bound are rejected at once.
+// Pushes the entries of the lanes with `valid` set. With no pop in between,
+// the queue ends up holding the same set in any order; when it is full at the
+// start, entries at or above the bound are rejected at once. When the queue
+// has room for all of them in distinct columns they are stored at once, else
+// one by one in lane order.
 __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool valid, int lane) {
     unsigned m = __ballot_sync(FULL, valid && (q.n < q.cap || e < q.hmax));
+    if (!m) return;
+    const int np = __popc(m);
+    const unsigned room = __ballot_sync(FULL, q.cnt < q.lcap);
+    if (q.n + np <= q.cap && __popc(room) >= np) {
+        // the r-th pushing lane's entry goes to the r-th column with room,
+        // counting from column q.rr: one store per column, all at once
+        const unsigned rot = __funnelshift_r(room, room, q.rr);
+        const int my = (lane - q.rr) & 31;
+        const int rho = __popc(rot & ((1u << my) - 1u));
+        const bool take = ((rot >> my) & 1u) && rho < np;
+        unsigned mm = m;
+        for (int i = 0; i < rho && i < np; ++i) mm &= mm - 1u;
+        const int src = take ? __ffs(mm) - 1 : 0;
+        const uint64_t x = __shfl_sync(FULL, e, src);
+        if (take) {
+            q.col[lane * q.stride + q.cnt] = x;
+            if (x < q.mn) {
+                q.mn = x;
+                q.mns = q.cnt;
+            }
+            if (x > q.mx) {
+                q.mx = x;
+                q.mxs = q.cnt;
+            }
+            ++q.cnt;
+        }
+        q.rr = (q.rr + np) & 31;
+        q.n += np;
+        const uint64_t hm = warp_max_u64(take ? x : 0ull);
+        if (hm > q.hmax) q.hmax = hm;
+        return;
+    }
     while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1;
