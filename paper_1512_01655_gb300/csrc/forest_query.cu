@@ -12,10 +12,11 @@
 //      17-level descent costs four memory round trips and no serial
 //      level-by-level walk. Queue entries are 64-bit words (key bits << 32 |
 //      tree << 26 | node), so one integer compare orders them by (key, tree,
-//      node). The queue is spread over the 32 lanes (ColQueue): pops and
-//      evictions take a warp-wide min or max reduction and one
-//      warp-cooperative column rescan, insertions one store. The points
-//      collected are written to the query's list in the workspace.
+//      node). The queue is spread over the 32 lanes (ColQueue), each lane
+//      keeping its column sorted: pops and evictions take one warp-wide min
+//      or max reduction and one load by the owning lane, insertions a short
+//      shift inside one column. The points collected are written to the
+//      query's list in the workspace.
 //   2. evaluation (forest_dist_kernel): the warp streams the listed points'
 //      rows eight at a time (float4 loads into registers when D % 4 == 0, two
 //      pieces of each row in flight; built for 32 warps per SM, so that enough
@@ -112,123 +113,95 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
 }
 
 // Bounded min-queue of distinct packed entries, spread over 32 columns in
-// shared memory (lane l owns col[l * stride ...], filled in slots 0..cnt-1).
-// Each lane keeps its column's count, minimum and maximum (and their slots) in
-// registers; the warp keeps the total and an upper bound of the maximum.
-//   pop:    the minimum over the lanes' minima; its column is closed up and
-//           rescanned by the whole warp.
-//   push:   into a column with room (round robin), or, when the queue is full,
-//           in place of the maximum if smaller, that column then rescanned.
-// All lanes call each operation with the same arguments. As entries are
-// distinct, the queue holds the same set as any bounded min-queue that evicts
-// its maximum, given the same pushes and pops.
+// shared memory. Lane l owns column l (col[l * stride ...]) and keeps it
+// sorted, largest first, in a circular buffer of `stride` slots starting at
+// its head slot h; its count, minimum (the tail) and maximum (the head) live
+// in registers. Every lane reads and writes only its own column.
+//   pop:    the minimum over the lanes' minima (one warp reduction); the owner
+//           drops its tail and loads the next one.
+//   push:   into a column with room (round robin): the owner moves its
+//           entries below the new one a slot toward the tail and stores it.
+//   evict:  when the queue is full, the maximum over the lanes' maxima (one
+//           warp reduction) is dropped by its owner (head advanced), unless
+//           the new entry is larger, which is dropped instead.
+// As entries are distinct, the queue holds the same set as any bounded
+// min-queue that evicts its maximum, given the same pushes and pops.
 struct ColQueue {
-    uint64_t *col;
+    uint64_t *col;    // this lane's column
     int stride, cap;
-    int lcap, cnt;    // this lane's column: capacity, entries
+    int lcap, cnt, h; // this lane's column: capacity, entries, head slot
     uint64_t mn, mx;  // this lane's minimum (~0 if empty) and maximum (0 if empty)
-    int mns, mxs;     // their slots
     int n;            // entries held (warp-uniform)
     uint64_t hmax;    // upper bound of the maximum held (warp-uniform)
     int rr;           // next column tried by an insertion (warp-uniform)
 };
 
 __device__ __forceinline__ void cq_init(ColQueue &q, uint64_t *col, int cap, int lane) {
-    q.col = col;
-    q.cap = cap;
     q.stride = (cap + 31) >> 5;
+    q.col = col + lane * q.stride;
+    q.cap = cap;
     q.lcap = (cap - lane + 31) >> 5;
     q.cnt = 0;
+    q.h = 0;
     q.mn = ~0ull;
     q.mx = 0;
-    q.mns = q.mxs = -1;
     q.n = 0;
     q.hmax = 0;
     q.rr = 0;
 }
 
-// Lane w's column minimum (MIN) or maximum and its slot, found by the whole warp.
-template <bool MIN>
-__device__ __forceinline__ void cq_rescan(ColQueue &q, int w, int lane) {
-    const int c = __shfl_sync(FULL, q.cnt, w);
-    const uint64_t *cw = q.col + w * q.stride;
-    uint64_t best = MIN ? ~0ull : 0ull;
-    int bs = -1;
-    for (int s = lane; s < c; s += 32) {
-        const uint64_t e = cw[s];
-        if (MIN ? e < best : e > best) {
-            best = e;
-            bs = s;
-        }
+__device__ __forceinline__ int cq_wrap(const ColQueue &q, int i) { return i >= q.stride ? i - q.stride : i; }
+
+// Stores x in this lane's column (which has room), keeping it sorted.
+__device__ __forceinline__ void cq_insert(ColQueue &q, uint64_t x) {
+    int i = q.cnt;
+    while (i > 0) {
+        const uint64_t y = q.col[cq_wrap(q, q.h + i - 1)];
+        if (y > x) break;
+        q.col[cq_wrap(q, q.h + i)] = y;
+        --i;
     }
-    const uint64_t g = MIN ? warp_min_u64(best) : warp_max_u64(best);
-    const unsigned hit = __ballot_sync(FULL, bs >= 0 && best == g);
-    const int slot = hit ? __shfl_sync(FULL, bs, __ffs(hit) - 1) : -1;
-    if (lane == w) {
-        if (MIN) {
-            q.mn = hit ? g : ~0ull;
-            q.mns = slot;
-        } else {
-            q.mx = hit ? g : 0ull;
-            q.mxs = slot;
-        }
-    }
+    q.col[cq_wrap(q, q.h + i)] = x;
+    ++q.cnt;
+    if (x < q.mn) q.mn = x;
+    if (x > q.mx) q.mx = x;
 }
 
 __device__ __forceinline__ uint64_t cq_pop(ColQueue &q, int lane) {
     const uint64_t top = warp_min_u64(q.mn);
-    const int w = __ffs(__ballot_sync(FULL, q.cnt > 0 && q.mn == top)) - 1;
-    if (lane == w) {
-        uint64_t *cw = q.col + w * q.stride;
-        const int last = q.cnt - 1, hole = q.mns;
-        if (hole != last) cw[hole] = cw[last];
-        if (q.mxs == last) q.mxs = hole;
-        q.cnt = last;
-        if (last == 0) {
+    if (q.cnt > 0 && q.mn == top) {  // one lane: entries are distinct
+        --q.cnt;
+        if (q.cnt > 0) {
+            q.mn = q.col[cq_wrap(q, q.h + q.cnt - 1)];
+        } else {
+            q.mn = ~0ull;
             q.mx = 0;
-            q.mxs = -1;
         }
     }
-    __syncwarp();
-    cq_rescan<true>(q, w, lane);
     --q.n;
     return top;
 }
 
+// One entry (the same in all lanes).
 __device__ __forceinline__ void cq_push(ColQueue &q, uint64_t x, int lane) {
     if (q.n == q.cap) {
         if (x >= q.hmax) return;
         const uint64_t m = warp_max_u64(q.mx);
-        q.hmax = m;
+        q.hmax = m;  // stays an upper bound after the eviction
         if (x >= m) return;
-        const int w = __ffs(__ballot_sync(FULL, q.cnt > 0 && q.mx == m)) - 1;
-        if (lane == w) {
-            q.col[w * q.stride + q.mxs] = x;
-            if (x < q.mn) {
-                q.mn = x;
-                q.mns = q.mxs;
-            }
+        if (q.cnt > 0 && q.mx == m) {  // the owner of the maximum drops it and takes x
+            q.h = cq_wrap(q, q.h + 1);
+            --q.cnt;
+            q.mx = q.cnt > 0 ? q.col[q.h] : 0ull;
+            if (q.cnt == 0) q.mn = ~0ull;
+            cq_insert(q, x);
         }
-        __syncwarp();
-        cq_rescan<false>(q, w, lane);
-        q.hmax = warp_max_u64(q.mx);
         return;
     }
     const unsigned nf = __ballot_sync(FULL, q.cnt < q.lcap);
     const unsigned rot = __funnelshift_r(nf, nf, q.rr);
     const int t = (q.rr + __ffs(rot) - 1) & 31;
-    if (lane == t) {
-        q.col[t * q.stride + q.cnt] = x;
-        if (x < q.mn) {
-            q.mn = x;
-            q.mns = q.cnt;
-        }
-        if (x > q.mx) {
-            q.mx = x;
-            q.mxs = q.cnt;
-        }
-        ++q.cnt;
-    }
+    if (lane == t) cq_insert(q, x);
     q.rr = (t + 1) & 31;
     ++q.n;
     if (x > q.hmax) q.hmax = x;
@@ -236,9 +209,9 @@ __device__ __forceinline__ void cq_push(ColQueue &q, uint64_t x, int lane) {
 
 // Pushes the entries of the lanes with `valid` set. With no pop in between,
 // the queue ends up holding the same set in any order; when it is full at the
-// start, entries at or above the bound are rejected at once. When the queue
-// has room for all of them in distinct columns they are stored at once, else
-// one by one in lane order.
+// start, entries at or above the bound are rejected at once. When the queue has room
+// for all of them in distinct columns they are inserted at once (each by the
+// owner of its column), else one by one in lane order.
 __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool valid, int lane) {
     unsigned m = __ballot_sync(FULL, valid && (q.n < q.cap || e < q.hmax));
     if (!m) return;
@@ -246,31 +219,18 @@ __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool vali
     const unsigned room = __ballot_sync(FULL, q.cnt < q.lcap);
     if (q.n + np <= q.cap && __popc(room) >= np) {
         // the r-th pushing lane's entry goes to the r-th column with room,
-        // counting from column q.rr: one store per column, all at once
+        // counting from column q.rr
         const unsigned rot = __funnelshift_r(room, room, q.rr);
         const int my = (lane - q.rr) & 31;
         const int rho = __popc(rot & ((1u << my) - 1u));
         const bool take = ((rot >> my) & 1u) && rho < np;
         unsigned mm = m;
         for (int i = 0; i < rho && i < np; ++i) mm &= mm - 1u;
-        const int src = take ? __ffs(mm) - 1 : 0;
-        const uint64_t x = __shfl_sync(FULL, e, src);
-        if (take) {
-            q.col[lane * q.stride + q.cnt] = x;
-            if (x < q.mn) {
-                q.mn = x;
-                q.mns = q.cnt;
-            }
-            if (x > q.mx) {
-                q.mx = x;
-                q.mxs = q.cnt;
-            }
-            ++q.cnt;
-        }
+        const uint64_t x = __shfl_sync(FULL, e, take ? __ffs(mm) - 1 : 0);
+        if (take) cq_insert(q, x);
         q.rr = (q.rr + np) & 31;
         q.n += np;
-        const uint64_t hm = warp_max_u64(take ? x : 0ull);
-        if (hm > q.hmax) q.hmax = hm;
+        q.hmax = ~0ull;  // unknown until the next eviction
         return;
     }
     while (m) {
@@ -305,8 +265,9 @@ __device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueu
         bool left = false;
         float fk = INFINITY;
         if (lane < (1 << d) - 1) {
+            // lane = node (lane + 1 - 2^j) of level j below v, j = floor(log2(lane + 1))
             const int j = 31 - __clz(lane + 1);
-            node = ((v + 1) << j) - 1 + (lane + 1 - (1 << j));
+            node = ((v + 1) << j) + lane - (1 << j);
             const float qd = qv[sd[node]];
             const float val = sv[node];
             left = qd < val;
@@ -316,10 +277,12 @@ __device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueu
         if (PT && last && lane < (1 << d)) lp = lpt[((v + 1) << d) - 1 + lane - n_int];
         const unsigned lm = __ballot_sync(FULL, left);
         int c = 0, my_c = 0;
-#pragma unroll 1
-        for (int j = 0; j < d; ++j) {
-            if (lane == j) my_c = c;
-            c = ((lm >> c) & 1u) ? 2 * c + 1 : 2 * c + 2;
+#pragma unroll
+        for (int j = 0; j < SUB_DEPTH; ++j) {
+            if (j < d) {
+                if (lane == j) my_c = c;
+                c = 2 * c + 2 - (int)((lm >> c) & 1u);
+            }
         }
         const float pk = __shfl_sync(FULL, fk, my_c);
         const int pn = __shfl_sync(FULL, node, my_c);
