@@ -77,9 +77,13 @@ struct Cand {
 // PASSES: 1 = one BF16 pass, 3 = BF16 hi/lo in three passes, 8 = one FP8
 // (E4M3, per-row scale) pass. A k-block is one 128-byte swizzle row: 64 BF16
 // or 128 FP8 values, four MMAs (K = 16 or 32).
+// With PASSES = 3 and every low half zero (data exact in BF16, e.g. 8-bit
+// integers) the two correction passes add exact zeros: the kernel then skips
+// them and runs the same shared memory as MAX_STAGES single-pass stages.
 template <int PASSES>
 struct TcCfg {
     static constexpr int STAGES = PASSES == 3 ? 2 : 4;
+    static constexpr int MAX_STAGES = 4;
     static constexpr int KE = PASSES == 8 ? 128 : TC_BK;  // elements per k-block
     static constexpr int A_BYTES = TC_BM * 128;
     static constexpr int B_BYTES = TC_BN * 128;
@@ -97,8 +101,8 @@ struct __align__(1024) TcSmem {
     float tr[4][32 * 33];
     // per epilogue thread: buffered distances by bucket, two 16-bit counts per word
     uint32_t dhist[4][NBUCKET / 2][32];
-    uint64_t full[TcCfg<PASSES>::STAGES];
-    uint64_t empty[TcCfg<PASSES>::STAGES];
+    uint64_t full[TcCfg<PASSES>::MAX_STAGES];
+    uint64_t empty[TcCfg<PASSES>::MAX_STAGES];
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint64_t drain;
@@ -119,6 +123,8 @@ struct TcParams {
     const float4 *st;      // corpus rows' error statistics (for listed queries)
     float acc_coef;        // FP32 accumulation term of the key error bound
     const unsigned *gmax;  // max ||x|| over the corpus (float bits)
+    const unsigned *lo_max;  // max norm of the corpus' BF16 low halves (float bits), or nullptr
+                             // when the queries' low halves are not covered by it
     const int32_t *qlist;  // query row -> corpus index (nullptr: identity)
     int64_t Q, N;
     int KB;                // Dp / 64
@@ -356,9 +362,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
     const uint32_t pad = (1024u - (smem_u32(tc_raw) & 1023u)) & 1023u;
     TcSmem<PASSES> &s = *reinterpret_cast<TcSmem<PASSES> *>(tc_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // three passes unless every low half is zero; then single-pass stages
+    const bool lo_on = PASSES == 3 && !(p.lo_max && *p.lo_max == 0u);
+    const int nst = PASSES == 3 && !lo_on ? C::MAX_STAGES : C::STAGES;
+    const int sbytes = PASSES == 3 && !lo_on ? C::STAGE_BYTES / 2 : C::STAGE_BYTES;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < C::STAGES; ++i) {
+        for (int i = 0; i < C::MAX_STAGES; ++i) {
             mbar_init(&s.full[i], 1);
             mbar_init(&s.empty[i], 1);
         }
@@ -396,9 +406,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            uint32_t armed_phase[C::STAGES];
-            bool armed[C::STAGES];
-            for (int i = 0; i < C::STAGES; ++i) armed[i] = false;
+            uint32_t armed_phase[C::MAX_STAGES];
+            bool armed[C::MAX_STAGES];
+            for (int i = 0; i < C::MAX_STAGES; ++i) armed[i] = false;
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
                 const int rt = u % p.row_tiles, sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
@@ -409,19 +419,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                             ok = false;
                             break;
                         }
-                        unsigned char *st = s.stage[stage];
-                        mbar_arrive_expect_tx(&s.full[stage], C::STAGE_BYTES);
+                        unsigned char *st = &s.stage[0][0] + stage * sbytes;
+                        mbar_arrive_expect_tx(&s.full[stage], sbytes);
                         armed[stage] = true;
                         armed_phase[stage] = phase;
                         tma_load_2d(st, &p.tm_a_hi, kb * C::KE, rt * TC_BM, &s.full[stage]);
                         tma_load_2d(st + C::A_BYTES, &p.tm_b_hi, kb * C::KE, (int)ct, &s.full[stage]);
-                        if (PASSES == 3) {
+                        if (PASSES == 3 && lo_on) {
                             tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.tm_a_lo, kb * TC_BK,
                                         rt * TC_BM, &s.full[stage]);
                             tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &p.tm_b_lo, kb * TC_BK,
                                         (int)ct, &s.full[stage]);
                         }
-                        if (++stage == C::STAGES) {
+                        if (++stage == nst) {
                             stage = 0;
                             phase ^= 1u;
                         }
@@ -432,7 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 s.abort_flag = 1;
                 raise_status(p.status, DEV_TIMEOUT);
                 // let the copies already issued land before the CTA exits
-                for (int i = 0; i < C::STAGES; ++i)
+                for (int i = 0; i < nst; ++i)
                     if (armed[i]) mbar_wait(&s.full[i], armed_phase[i], &s.zero, WAIT_NS);
             }
         }
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                             break;
                         }
                         fence_after_sync();
-                        const uint32_t a_hi = smem_u32(s.stage[stage]);
+                        const uint32_t a_hi = smem_u32(&s.stage[0][0] + stage * sbytes);
                         const uint32_t b_hi = a_hi + C::A_BYTES;
                         const uint32_t a_lo = b_hi + C::B_BYTES;
                         const uint32_t b_lo = a_lo + C::A_BYTES;
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                             else
                                 mma_bf16(d, sw128_kmajor_desc(a_hi + 32 * k), sw128_kmajor_desc(b_hi + 32 * k),
                                          idesc, (kb | k) != 0);
-                            if (PASSES == 3) {
+                            if (PASSES == 3 && lo_on) {
                                 mma_bf16(d, sw128_kmajor_desc(a_hi + 32 * k),
                                          sw128_kmajor_desc(b_lo + 32 * k), idesc, 1u);
                                 mma_bf16(d, sw128_kmajor_desc(a_lo + 32 * k),
@@ -480,7 +490,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                             }
                         }
                         mma_commit(&s.empty[stage]);
-                        if (++stage == C::STAGES) {
+                        if (++stage == nst) {
                             stage = 0;
                             phase ^= 1u;
                         }
@@ -1360,6 +1370,8 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     p.acc_coef = (float)((pl.passes * pl.Dp / 16 + 8) * (1.0 / (1 << 21)));
     p.nrm = w.nrm;
     p.gmax = w.gmax;
+    // queries that are corpus rows have the corpus' low halves
+    p.lo_max = pl.passes == 3 && !Xq ? w.gmax + 2 : nullptr;
     p.qlist = qlist;
     p.Q = Q;
     p.N = N;
