@@ -225,6 +225,7 @@ def default_queue_cap(checks):
 TRAFFIC_SOURCES = {
     "forest_traverse": ["forest_query.cu", "common.cuh", "internal.h"],
     "forest_dist": ["forest_query.cu", "common.cuh", "internal.h"],
+    "forest_dist_u8": ["forest_query.cu", "common.cuh", "internal.h"],
     "knn_tc": ["knn_tc.cu", "tc_ptx.cuh", "common.cuh", "internal.h"],
 }
 
@@ -449,7 +450,7 @@ def run_ours(args, world, rank, local, pg):
     total_ms = sum(step_ms)
     per_kernel = {}
     for name in ["knn_bruteforce", "knn_tc", "knn_tc_merge", "calibrate_beta", "forest_traverse",
-                 "forest_dist", "forest_choose", "forest_partial", "forest_sort_smem", "forest_sort_global",
+                 "forest_dist", "forest_dist_u8", "forest_u8_prep", "forest_choose", "forest_partial", "forest_sort_smem", "forest_sort_global",
                  "sym_scatter", "sym_count", "sym_sort_rows", "sym_sort_tails", "knn_prep"]:
         n, ms = at.profile_read(name)
         if n:
@@ -471,9 +472,10 @@ def run_ours(args, world, rank, local, pg):
     # roofline of the dominant kernel; the forest search is one step made of two
     # launches (traversal, then the distances of the points it collected), taken
     # together against the bytes the search must gather
-    cand = {k_: v["ms"] for k_, v in per_kernel.items() if k_ not in ("forest_traverse", "forest_dist")}
-    if "forest_traverse" in per_kernel and "forest_dist" in per_kernel:
-        cand["forest_query"] = per_kernel["forest_traverse"]["ms"] + per_kernel["forest_dist"]["ms"]
+    fparts = ("forest_u8_prep", "forest_traverse", "forest_dist", "forest_dist_u8")
+    cand = {k_: v["ms"] for k_, v in per_kernel.items() if k_ not in fparts}
+    if "forest_traverse" in per_kernel:
+        cand["forest_query"] = sum(per_kernel[k_]["ms"] for k_ in fparts if k_ in per_kernel)
     dom = max(cand.items(), key=lambda kv: kv[1])[0] if cand else None
     roofline = None
     peaks = {}
@@ -504,27 +506,34 @@ def run_ours(args, world, rank, local, pg):
                     "traffic": None, "tensor_passes": mult,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
     elif dom == "forest_query":
-        # gather-bound: every evaluated point's row (D floats) is read once per
+        # gather-bound: every evaluated point's row (D values) is read once per
         # query, plus the query row and the k (index, distance) outputs; with one
-        # point per leaf exactly max(checks, k) points are evaluated per query
+        # point per leaf exactly max(checks, k) points are evaluated per query.
+        # Rows are gathered as bytes when every value is an integer in [0, 255]
+        # (the distance kernel then reads the byte copy), else as FP32.
         need = max(args.checks, K_NN)
-        per_launch = N * ((need + 1) * D * 4 + K_NN * 8)
-        tr, di = per_kernel["forest_traverse"], per_kernel["forest_dist"]
-        avg_ms = (tr["ms"] + di["ms"]) / tr["launches"]
+        Xd = pipe.X
+        u8 = D <= 2048 and bool(((Xd >= 0) & (Xd <= 255) & (Xd == torch.round(Xd))).all())
+        vb = 1 if u8 else 4
+        per_launch = N * ((need + 1) * D * vb + K_NN * 8)
+        tr = per_kernel["forest_traverse"]
+        di = per_kernel["forest_dist_u8" if u8 else "forest_dist"]
+        avg_ms = sum(per_kernel[k_]["ms"] for k_ in fparts if k_ in per_kernel) / tr["launches"]
         ach = per_launch / (avg_ms / 1e3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
+        dname = "forest_dist_u8" if u8 else "forest_dist"
         t_tr, t_di = (recorded_traffic("forest_traverse", args.workload),
-                      recorded_traffic("forest_dist", args.workload))
-        roofline = {"kernel": "forest_query (forest_traverse + forest_dist)", "bound": "hbm",
+                      recorded_traffic(dname, args.workload))
+        roofline = {"kernel": "forest_query (forest_traverse + %s)" % dname, "bound": "hbm",
                     "achieved": round(ach, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(ach / peak, 4),
                     "traffic": t_tr + t_di if t_tr is not None and t_di is not None else None,
-                    "algorithmic_bytes_per_launch": per_launch,
+                    "algorithmic_bytes_per_launch": per_launch, "row_bytes_per_value": vb,
                     "parts": {
                         "forest_traverse": {"ms": round(tr["ms"] / tr["launches"], 3),
                                             "traffic": t_tr,
                                             "bound": "latency (queue and tree walk)"},
-                        "forest_dist": {"ms": round(di["ms"] / di["launches"], 3),
+                        dname: {"ms": round(di["ms"] / di["launches"], 3),
                                         "traffic": t_di,
                                         "achieved": round(per_launch / (di["ms"] / di["launches"] / 1e3)
                                                           / 1e9, 1),

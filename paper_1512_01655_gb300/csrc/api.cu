@@ -215,7 +215,7 @@ size_t knn_ws(Carver &c, int64_t N, int32_t D, int32_t k, int64_t S, const atsne
         if (forest) *forest = f;
         Carver b(nullptr), q(nullptr);
         const size_t bb = forest_build_workspace(b, N, D, o.trees, o.leaf_size, nullptr);
-        const size_t qb = forest_query_workspace(q, N, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
+        const size_t qb = forest_query_workspace(q, N, D, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
         const size_t need = bb > qb ? bb : qb;
         char *w = c.take<char>(need);
         if (sub_ws) *sub_ws = w;
@@ -321,7 +321,7 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
     case ATSNE_OP_FOREST_BUILD:
         return forest_build_workspace(c, N, D, o.trees, o.leaf_size, nullptr);
     case ATSNE_OP_FOREST_QUERY:
-        return forest_query_workspace(c, N, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
+        return forest_query_workspace(c, N, D, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
     case ATSNE_OP_KNN_CROSS:
         return cross_ws(c, S, N, D, k, o, false, nullptr, nullptr);
     case ATSNE_OP_KNN_CROSS_RADIUS:

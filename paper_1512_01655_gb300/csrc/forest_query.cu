@@ -55,6 +55,8 @@ constexpr int FQ_KCAP = 128;        // largest k
 constexpr int64_t FQ_MARK_BUDGET = int64_t(1) << 30;  // bytes of point lists per chunk
 constexpr int FD_MAX_WARPS = 4;     // distance kernel: warps per block (fewer for very long rows)
 constexpr int FD_BUF = 256;         // (distance, index) pairs per distance warp
+constexpr int FD_U8_PIECES = 4;     // byte rows: 16-byte pieces per lane at most (D <= 2048)
+enum { FD_F32 = 0, FD_F32V = 1, FD_U8 = 2 };
 constexpr int SUB_DEPTH = 5;        // levels fetched per descent round (31 nodes, one per lane)
 constexpr int FQ_SEED_GAP = 32;     // one seed query per this many, in tree-0 leaf order
 constexpr float FQ_CUT_FACTOR = 3.f;
@@ -85,6 +87,10 @@ struct FqArgs {
 
 struct FdArgs {
     const float *X;
+    const uint8_t *xu8;      // X as bytes ([N][Dp16]) when every value is an integer in [0, 255]
+    const uint32_t *nx8;     // their exact squared norms
+    const unsigned *u8_bad;  // nonzero: some value is not such an integer (FP32 rows used)
+    int Dp16;
     int D, k;
     bool list_mode;
     int64_t w0, nw;
@@ -497,31 +503,70 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArg
 // Sums of eight rows' partial sums over the warp with nine shuffles: each lane
 // ends with the total of row ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 +
 // ((lane >> 2) & 1) (four lanes per row).
-__device__ __forceinline__ float warp_sum8(float (&v)[8], int lane) {
+template <typename T>
+__device__ __forceinline__ T warp_sum8(T (&v)[8], int lane) {
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const float send = b4 ? v[u] : v[u + 4];
-        const float keep = b4 ? v[u + 4] : v[u];
+        const T send = b4 ? v[u] : v[u + 4];
+        const T keep = b4 ? v[u + 4] : v[u];
         v[u] = keep + __shfl_xor_sync(FULL, send, 16);
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-        const float send = b3 ? v[u] : v[u + 2];
-        const float keep = b3 ? v[u + 2] : v[u];
+        const T send = b3 ? v[u] : v[u + 2];
+        const T keep = b3 ? v[u + 2] : v[u];
         v[u] = keep + __shfl_xor_sync(FULL, send, 8);
     }
-    const float send = b2 ? v[0] : v[1];
-    float r = (b2 ? v[1] : v[0]) + __shfl_xor_sync(FULL, send, 4);
+    const T send = b2 ? v[0] : v[1];
+    T r = (b2 ? v[1] : v[0]) + __shfl_xor_sync(FULL, send, 4);
     r += __shfl_xor_sync(FULL, r, 2);
     r += __shfl_xor_sync(FULL, r, 1);
     return r;
 }
 
+// Byte copy of X (rows padded to Dp16 bytes with zeros) and the rows' exact
+// squared norms; *bad is raised if any value is not an integer in [0, 255]
+// (then the copy is not used). One warp per row, four values per lane.
+__global__ void __launch_bounds__(256) fq_u8_prep_kernel(const float *__restrict__ X, int64_t N, int D,
+                                                         int Dp16, uint8_t *__restrict__ xu8,
+                                                         uint32_t *__restrict__ nx8, unsigned *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= N) return;
+    const float *x = X + r * D;
+    uint32_t *out = reinterpret_cast<uint32_t *>(xu8 + r * Dp16);
+    uint32_t sq = 0;
+    bool ok = true;
+    for (int d4 = 4 * lane; d4 < Dp16; d4 += 128) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float v = d4 + i < D ? x[d4 + i] : 0.f;
+            ok &= v >= 0.f && v <= 255.f && v == rintf(v);  // false for NaN
+            const uint32_t b = ok ? (uint32_t)v : 0u;
+            word |= b << (8 * i);
+            sq += b * b;
+        }
+        out[d4 >> 2] = word;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
+    if (!__all_sync(FULL, ok) && lane == 0) atomicOr(bad, 1u);
+    if (lane == 0) nx8[r] = sq;
+}
+
 // Distances of each query to its listed points (entry 0, the query, left out)
 // and the k best under the (distance, index) order, written sorted.
-template <bool VEC>
+// MODE: FD_F32 / FD_F32V (FP32 rows, scalar or float4 loads) or FD_U8 (byte
+// rows, QP 16-byte pieces per lane). The host launches an FP32 and, where byte
+// rows are possible, a byte instantiation; each returns at once unless the
+// prep kernel's verdict (every value an integer in [0, 255] or not) selects it.
+template <int MODE, int QP>
 __global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArgs A) {
+    constexpr bool U8 = MODE == FD_U8, VEC = MODE == FD_F32V;
+    const bool u8_ok = A.xu8 != nullptr && *A.u8_bad == 0u;
+    if (U8 != u8_ok) return;
     extern __shared__ __align__(16) unsigned char fd_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int Dp = (A.D + 3) & ~3;
@@ -530,6 +575,7 @@ __global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArg
     int *bj = reinterpret_cast<int *>(bd + (size_t)nwarp * FD_BUF);
     const int D = A.D, D4 = D >> 2, k = A.k;
     const int64_t stride = (int64_t)gridDim.x * nwarp;
+    const int C16 = A.Dp16 >> 4;  // 16-byte pieces per byte row
 
     for (int64_t t = (int64_t)blockIdx.x * nwarp + w; t < A.nw; t += stride) {
         const int n = A.n_marked[t];
@@ -538,7 +584,19 @@ __global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArg
         const int32_t qi = list[0];
         const int64_t row = A.list_mode ? A.w0 + t : qi;
         const float *xq = A.X + (int64_t)qi * D;
-        for (int d = lane; d < D; d += 32) qv[d] = xq[d];
+        uint4 qb[QP];
+        int nq8 = 0;
+        if constexpr (U8) {
+#pragma unroll
+            for (int j = 0; j < QP; ++j) {
+                const int c = lane + 32 * j;
+                qb[j] = c < C16 ? reinterpret_cast<const uint4 *>(A.xu8 + (int64_t)qi * A.Dp16)[c]
+                                : make_uint4(0u, 0u, 0u, 0u);
+            }
+            nq8 = (int)A.nx8[qi];
+        } else {
+            for (int d = lane; d < D; d += 32) qv[d] = xq[d];
+        }
         for (int u = lane; u < FD_BUF; u += 32) {
             bd[u] = INFINITY;
             bj[u] = INT_MAX;
@@ -572,7 +630,32 @@ __global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArg
                 if (b0 + u >= nr) pj[u] = pj[0];  // a valid row, its sum unused
                 acc[u] = 0.f;
             }
-            if (VEC) {
+            int dot8 = 0;
+            if constexpr (U8) {
+                // |q - x|^2 = |q|^2 + |x|^2 - 2 q.x, every term an exact integer
+                // (below 2^31 for D <= 2048)
+                unsigned dp[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) dp[u] = 0u;
+#pragma unroll
+                for (int j = 0; j < QP; ++j) {
+                    const int c = lane + 32 * j;
+                    if (c < C16) {
+                        uint4 xv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            xv[u] = __ldg(reinterpret_cast<const uint4 *>(A.xu8 + (int64_t)pj[u] * A.Dp16) + c);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            dp[u] = __dp4a(xv[u].x, qb[j].x, dp[u]);
+                            dp[u] = __dp4a(xv[u].y, qb[j].y, dp[u]);
+                            dp[u] = __dp4a(xv[u].z, qb[j].z, dp[u]);
+                            dp[u] = __dp4a(xv[u].w, qb[j].w, dp[u]);
+                        }
+                    }
+                }
+                dot8 = (int)warp_sum8(dp, lane);
+            } else if constexpr (VEC) {
                 const float4 *q4 = reinterpret_cast<const float4 *>(qv);
 #pragma unroll 2
                 for (int c = lane; c < D4; c += 32) {
@@ -603,10 +686,14 @@ __global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArg
                     }
                 }
             }
-            const float dist = warp_sum8(acc, lane);
             const int u = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
             const bool own = (lane & 3) == 0 && b0 + u < nr;
             const int p = __shfl_sync(FULL, my, (b0 + u) & 31);
+            float dist;
+            if constexpr (U8)
+                dist = (float)(nq8 + (int)A.nx8[p] - 2 * dot8);
+            else
+                dist = warp_sum8(acc, lane);
             const bool cand = own && pair_less(dist, p, thr_d, thr_j);
             const unsigned m = __ballot_sync(FULL, cand);
             if (m) {
@@ -636,17 +723,18 @@ size_t fq_smem_bytes(int D, int qcap) {
 
 size_t fd_warp_bytes(int D) { return (size_t)((D + 3) & ~3) * 4 + FD_BUF * 8; }
 
-template <bool VEC>
-atsne_status fd_launch_v(const FdArgs &a, int warps, cudaStream_t stream) {
+template <int MODE, int QP>
+atsne_status fd_launch_t(const FdArgs &a, int warps, cudaStream_t stream) {
     const size_t smem = warps * fd_warp_bytes(a.D);
-    cudaError_t e = cudaFuncSetAttribute(forest_dist_kernel<VEC>,
+    cudaError_t e = cudaFuncSetAttribute(forest_dist_kernel<MODE, QP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "forest distances attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forest_dist_kernel<VEC>, warps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forest_dist_kernel<MODE, QP>, warps * 32, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     const int grid = (int)hmin((int64_t)per_sm * num_sms(), ceil_div(a.nw, warps));
-    return launch_kernel("forest_dist", forest_dist_kernel<VEC>, grid, warps * 32, smem, stream, a);
+    return launch_kernel(MODE == FD_U8 ? "forest_dist_u8" : "forest_dist", forest_dist_kernel<MODE, QP>, grid,
+                         warps * 32, smem, stream, a);
 }
 
 int64_t fq_mark_cap(int k, int checks, int leaf_size) {
@@ -659,10 +747,19 @@ int64_t fq_chunk(int64_t nq, int64_t mark_cap) {
     return nq < c ? (nq > 0 ? nq : 1) : c;
 }
 
-}  // namespace
+struct FqU8 {
+    uint8_t *xu8 = nullptr;
+    uint32_t *nx8 = nullptr;
+    unsigned *bad = nullptr;
+    int Dp16 = 0;
+};
+// Byte rows are used up to D = 2048 (16-byte pieces per lane in registers;
+// exact int32 distances).
+bool fq_u8_ok(int D) { return D <= 32 * 16 * FD_U8_PIECES; }
 
-size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int checks, int leaf_size,
-                              void *ws_out) {
+// Workspace layout of one search (sizing when c has no base).
+size_t fq_workspace(Carver &c, int64_t N, int D, int64_t nq, int k, int checks, int leaf_size, FqArgs *ws_out,
+                    FqU8 *u8_out) {
     FqArgs a{};
     a.words = (N + 31) / 32;
     a.mark_cap = fq_mark_cap(k, checks, leaf_size);
@@ -672,8 +769,23 @@ size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int check
     a.n_marked = c.take<int32_t>((size_t)a.chunk);
     a.next_query = c.take<int>(1);
     a.kseed = c.take<float>((size_t)(nq / FQ_SEED_GAP) + 2);
-    if (ws_out) *static_cast<FqArgs *>(ws_out) = a;
+    FqU8 u{};
+    if (fq_u8_ok(D)) {
+        u.Dp16 = (D + 15) & ~15;
+        u.xu8 = c.take<uint8_t>((size_t)N * u.Dp16);
+        u.nx8 = c.take<uint32_t>((size_t)N);
+        u.bad = c.take<unsigned>(1);
+    }
+    if (ws_out) *ws_out = a;
+    if (u8_out) *u8_out = u;
     return c.bytes();
+}
+
+}  // namespace
+
+size_t forest_query_workspace(Carver &c, int64_t N, int D, int64_t nq, int k, int checks, int leaf_size,
+                              void *ws_out) {
+    return fq_workspace(c, N, D, nq, k, checks, leaf_size, static_cast<FqArgs *>(ws_out), nullptr);
 }
 
 atsne_status forest_query_launch(const float *X, const ForestView &f, const int32_t *qlist,
@@ -686,7 +798,8 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
                          f.depth, f.trees);
     Carver c(ws_base);
     FqArgs a;
-    forest_query_workspace(c, f.N, nq, k, checks, f.leaf_size, &a);
+    FqU8 u8;
+    fq_workspace(c, f.N, f.D, nq, k, checks, f.leaf_size, &a, &u8);
     if (c.bytes() > ws_bytes) return set_error(ATSNE_ENOMEM, "forest query: workspace too small");
     if (nq == 0) return ATSNE_OK;
     const size_t smem = fq_smem_bytes(f.D, qcap);
@@ -736,6 +849,16 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     b.mark_cap = a.mark_cap;
     b.idx_out = idx_out;
     b.d2_out = d2_out;
+    b.xu8 = u8.xu8;
+    b.nx8 = u8.nx8;
+    b.u8_bad = u8.bad;
+    b.Dp16 = u8.Dp16;
+    if (u8.xu8) {
+        e = cudaMemsetAsync(u8.bad, 0, sizeof(unsigned), stream);
+        if (e != cudaSuccess) return cuda_error(e, "forest query memset");
+        ATSNE_TRY(launch_kernel("forest_u8_prep", fq_u8_prep_kernel, ceil_div(f.N * 32, 256), 256, 0, stream,
+                                X, f.N, f.D, u8.Dp16, u8.xu8, u8.nx8, u8.bad));
+    }
     const bool vec = (f.D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     for (int64_t w0 = 0; w0 < nq; w0 += a.chunk) {
         a.w0 = b.w0 = w0;
@@ -745,8 +868,14 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
         atsne_status st = launch_kernel("forest_traverse", forest_traverse_kernel, grid, FQ_WARPS * 32,
                                         smem, stream, a);
         if (st != ATSNE_OK) return st;
-        st = vec ? fd_launch_v<true>(b, fd_warps, stream) : fd_launch_v<false>(b, fd_warps, stream);
+        // the FP32 and byte instantiations; the prep kernel's verdict picks one
+        st = vec ? fd_launch_t<FD_F32V, 1>(b, fd_warps, stream) : fd_launch_t<FD_F32, 1>(b, fd_warps, stream);
         if (st != ATSNE_OK) return st;
+        if (b.xu8) {
+            st = b.Dp16 <= 32 * 16 * 2 ? fd_launch_t<FD_U8, 2>(b, fd_warps, stream)
+                                       : fd_launch_t<FD_U8, FD_U8_PIECES>(b, fd_warps, stream);
+            if (st != ATSNE_OK) return st;
+        }
     }
     return ATSNE_OK;
 }

@@ -105,7 +105,7 @@ size_t forest_layout(int64_t N, int trees, int leaf_size, atsne_forest_layout_t 
 size_t forest_build_workspace(Carver &c, int64_t N, int D, int trees, int leaf_size, void *ws_out);
 atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_base, size_t ws_bytes,
                                  cudaStream_t stream);
-size_t forest_query_workspace(Carver &c, int64_t N, int64_t nq, int k, int checks, int leaf_size,
+size_t forest_query_workspace(Carver &c, int64_t N, int D, int64_t nq, int k, int checks, int leaf_size,
                               void *ws_out);
 atsne_status forest_query_launch(const float *X, const ForestView &f, const int32_t *qlist,
                                  int64_t nq, int k, int checks, int qcap, int32_t *idx_out,
