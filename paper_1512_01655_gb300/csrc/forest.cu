@@ -405,51 +405,48 @@ choose_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ pe
 }
 
 // Nodes of at most SMALL_NODE points: one warp per node; lane l accumulates
-// the dimensions l, l + 32, ... (eight at a time, two points' loads in flight
-// together, in point order) and keeps its top eight.
-constexpr int SMALL_NODE = 64;
+// the dimensions l, l + 32, ... (four at a time, four points' loads in flight
+// together, accumulated in point order) and keeps its top eight.
+constexpr int SMALL_NODE = 128;
 constexpr int SMALL_WARPS = 8;
 
-// Columns d0 + lane + 32 j (j < 8) over the node's points; FULL: all 256 in range.
+// Columns d0 + lane + 32 j (j < 4) over the node's points; FULL: all 128 in range.
 template <bool FULL>
 __device__ __forceinline__ void small_group(const float *__restrict__ X, int D, int d0, int lane, int cnt,
-                                            int p0, int p1, float n, Top8 &tp) {
-    float4 a[8];
+                                            const int (&pp)[4], float n, Top8 &tp) {
+    // columns d0 + lane + 32 j (j < 4); four points per step, accumulated in point order
+    float4 a[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = 0; q < cnt; q += 2) {
-        const int pa = __shfl_sync(0xffffffffu, q < 32 ? p0 : p1, q & 31);
-        const int pb = __shfl_sync(0xffffffffu, q + 1 < 32 ? p0 : p1, (q + 1) & 31);
-        const float *ra = X + (int64_t)pa * D + d0 + lane;
-        const float *rb = X + (int64_t)pb * D + d0 + lane;
-        float xa[8], xb[8];
-        if (q + 1 < cnt) {
+    for (int j = 0; j < 4; ++j) a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < cnt; q += 4) {
+        float x[4][4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const bool in = FULL || d0 + lane + 32 * j < D;
-                xa[j] = in ? __ldg(ra + 32 * j) : 0.f;
-                xb[j] = in ? __ldg(rb + 32 * j) : 0.f;
+        for (int i = 0; i < 4; ++i) {
+            const int qq = q + i;
+            const int sel = qq >> 5;
+            const int pv = sel == 0 ? pp[0] : sel == 1 ? pp[1] : sel == 2 ? pp[2] : pp[3];
+            const int p = __shfl_sync(0xffffffffu, pv, qq & 31);
+            const float *r = X + (int64_t)p * D + d0 + lane;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                x[i][j] = qq < cnt && (FULL || d0 + lane + 32 * j < D) ? __ldg(r + 32 * j) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (q + i < cnt) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc_point(a[j], x[i][j]);
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                acc_point(a[j], xa[j]);
-                acc_point(a[j], xb[j]);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) xa[j] = (FULL || d0 + lane + 32 * j < D) ? __ldg(ra + 32 * j) : 0.f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc_point(a[j], xa[j]);
         }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 4; ++j) {
         const int d = d0 + lane + 32 * j;
         if (FULL || d < D) top8_insert(tp, spread_of(a[j], n), d);
     }
 }
 
-__global__ void __launch_bounds__(SMALL_WARPS * 32)
+__global__ void __launch_bounds__(SMALL_WARPS * 32, 3)
 choose_small_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
                     const int32_t *__restrict__ leaf_ofs, int h, int l, int V, uint64_t seed,
                     int32_t *__restrict__ split_dim, float *__restrict__ split_val, int64_t n_int) {
@@ -471,14 +468,15 @@ choose_small_kernel(const float *__restrict__ X, int D, const int32_t *__restric
     const float n = (float)(hi - lo);
     const int cnt = (int)(hi - lo);
     const int32_t *pt = perm + (int64_t)t * N;
-    // the node's points, lane r holding points r and r + 32
-    const int p0 = lane < cnt ? pt[lo + lane] : 0;
-    const int p1 = lane + 32 < cnt ? pt[lo + lane + 32] : 0;
+    // the node's points, lane r holding points r, r + 32, r + 64 and r + 96
+    int pp[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pp[i] = lane + 32 * i < cnt ? pt[lo + lane + 32 * i] : 0;
     Top8 tp;
     top8_init(tp);
     int d0 = 0;
-    for (; d0 + 256 <= D; d0 += 256) small_group<true>(X, D, d0, lane, cnt, p0, p1, n, tp);
-    if (d0 < D) small_group<false>(X, D, d0, lane, cnt, p0, p1, n, tp);
+    for (; d0 + 128 <= D; d0 += 128) small_group<true>(X, D, d0, lane, cnt, pp, n, tp);
+    if (d0 < D) small_group<false>(X, D, d0, lane, cnt, pp, n, tp);
     const int dim = choose_from_top8(tp, nV, seed, t, v);
     if (lane == 0) {
         split_dim[(int64_t)t * n_int + v] = dim;
