@@ -254,11 +254,76 @@ __device__ void acc_slice(const float *__restrict__ X, int D, const int32_t *__r
     }
 }
 
+// ---- 8-bit integer data: exact integer sums from the byte copy of X ----
+// n * s2 - s1^2 exactly; the byte path runs only for N <= 2^18, so every term
+// stays below 2^53 (and the FP64 sums of the definition are exact as well).
+__device__ __forceinline__ uint64_t spread_exact(uint64_t s1, uint64_t s2, uint64_t n) { return n * s2 - s1 * s1; }
+
+// Integer sums s1 (of x) and s2 (of x^2) of columns [d0, d0 + W) of the byte
+// rows of points pt[b..e) (at most 65536 points, so s2 < 2^32): thread t takes
+// columns d0 + 4t .. d0 + 4t + 3 (one 32-bit word per row). The rows stream
+// through the same tile memory as acc_slice, in 16-byte pieces (cp.async).
+__device__ void acc_slice_u8(const uint8_t *__restrict__ xu8, int Dp16, const int32_t *__restrict__ pt,
+                             int64_t b, int64_t e, int d0, const SliceGeom &g, int W, float *tile_f,
+                             uint32_t (&s1)[4], uint32_t (&s2)[4]) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s1[i] = s2[i] = 0u;
+    uint8_t *tile = reinterpret_cast<uint8_t *>(tile_f);
+    const int Wb = (W + 15) & ~15;  // bytes per tile row (the padding is the next columns or zeros)
+    int TPb = g.TP * g.Wp * 4 / Wb;
+    if (TPb > 64) TPb = 64;
+    const int64_t n = e - b;
+    const int64_t nt = (n + TPb - 1) / TPb;
+    const int per = Wb >> 4;  // 16-byte pieces per row
+    auto issue = [&](int64_t k) {
+        uint8_t *buf = tile + (k & 1) * TPb * Wb;
+        const int64_t q0 = b + k * TPb;
+        const int rows = (int)(e - q0 < TPb ? e - q0 : TPb);
+        const int step = nth / per > 0 ? nth / per : 1;
+        for (int c0 = 0; c0 < per; c0 += nth) {
+            const int c = c0 + (per >= nth ? tid : tid % per);
+            const int r0 = per >= nth ? 0 : tid / per;
+            if (c >= per || r0 >= step) continue;
+            for (int r = r0; r < rows; r += step)
+                cp_async16(reinterpret_cast<float *>(buf + r * Wb + 16 * c),
+                           reinterpret_cast<const float *>(xu8 + (int64_t)pt[q0 + r] * Dp16 + d0 + 16 * c));
+        }
+        cp_async_commit();
+    };
+    const int c4 = 4 * tid;
+    if (nt > 0) issue(0);
+    for (int64_t k = 0; k < nt; ++k) {
+        if (k + 1 < nt) {
+            issue(k + 1);
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        __syncthreads();
+        const uint8_t *buf = tile + (k & 1) * TPb * Wb + c4;
+        const int rows = (int)(e - (b + k * TPb) < TPb ? e - (b + k * TPb) : TPb);
+        if (c4 < W) {
+            for (int r = 0; r < rows; ++r) {
+                const uint32_t w = *reinterpret_cast<const uint32_t *>(buf + r * Wb);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t x = (w >> (8 * i)) & 0xffu;
+                    s1[i] += x;
+                    s2[i] += x * x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Partial sums over CHUNK-point pieces of big nodes: grid (chunks, nodes, trees).
 __global__ void __launch_bounds__(256)
 partial_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
                const int32_t *__restrict__ leaf_ofs, int h, int l, int chunks,
-               float4 *__restrict__ part) {
+               float4 *__restrict__ part, const uint8_t *__restrict__ xu8, int Dp16,
+               const unsigned *__restrict__ u8_bad) {
     extern __shared__ __align__(16) float acc_tile[];
     const int ch = blockIdx.x, m = blockIdx.y, t = blockIdx.z;
     int64_t lo, hi;
@@ -267,6 +332,19 @@ partial_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ p
     const int32_t *pt = perm + (int64_t)t * N;
     float4 *out = part + (((int64_t)t * gridDim.y + m) * chunks + ch) * D;
     const SliceGeom g = slice_geom(D);
+    if (xu8 && *u8_bad == 0u) {  // byte rows: integer (s1, s2) in the first two words
+        for (int d0 = 0; d0 < D; d0 += g.W) {
+            const int W = D - d0 < g.W ? D - d0 : g.W;
+            uint32_t s1[4], s2[4];
+            acc_slice_u8(xu8, Dp16, pt, b, e, d0, g, W, acc_tile, s1, s2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = 4 * threadIdx.x + i;
+                if (c < W) out[d0 + c] = make_float4(__uint_as_float(s1[i]), __uint_as_float(s2[i]), 0.f, 0.f);
+            }
+        }
+        return;
+    }
     for (int d0 = 0; d0 < D; d0 += g.W) {
         const int W = D - d0 < g.W ? D - d0 : g.W;
         float4 a[4];
@@ -282,24 +360,41 @@ partial_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ p
 // ---- top-V dimensions by spread ----
 // Each lane keeps its best eight (spread, dim) pairs in registers, sorted by
 // spread_greater; V rounds of a warp-wide argmax over the lanes' heads then
-// give the V best in order.
-struct Top8 {
-    float2 s[8];
+// give the V best in order. The spread is a float pair (hi, lo) or, for 8-bit
+// integer data, the exact integer n * sum x^2 - (sum x)^2.
+template <typename K>
+struct TopN {
+    K s[8];
     int d[8];
 };
-__device__ __forceinline__ void top8_init(Top8 &t) {
+using Top8 = TopN<float2>;
+using Top8u = TopN<uint64_t>;
+__device__ __forceinline__ bool spread_greater(uint64_t a, int da, uint64_t b, int db) {
+    if (a != b) return a > b;
+    return da < db;
+}
+__device__ __forceinline__ void key_lowest(float2 &k) { k = make_float2(-INFINITY, -INFINITY); }
+__device__ __forceinline__ void key_lowest(uint64_t &k) { k = 0ull; }  // empty slots carry dim INT_MAX
+__device__ __forceinline__ float2 shfl_xor_key(float2 k, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, k.x, o), __shfl_xor_sync(0xffffffffu, k.y, o));
+}
+__device__ __forceinline__ uint64_t shfl_xor_key(uint64_t k, int o) { return __shfl_xor_sync(0xffffffffu, k, o); }
+
+template <typename K>
+__device__ __forceinline__ void top8_init(TopN<K> &t) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        t.s[r] = make_float2(-INFINITY, -INFINITY);
+        key_lowest(t.s[r]);
         t.d[r] = INT_MAX;
     }
 }
-__device__ __forceinline__ void top8_insert(Top8 &t, float2 s, int d) {
+template <typename K>
+__device__ __forceinline__ void top8_insert(TopN<K> &t, K s, int d) {
     if (!spread_greater(s, d, t.s[7], t.d[7])) return;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         if (spread_greater(s, d, t.s[r], t.d[r])) {
-            const float2 ts = t.s[r];
+            const K ts = t.s[r];
             const int td = t.d[r];
             t.s[r] = s;
             t.d[r] = d;
@@ -310,20 +405,20 @@ __device__ __forceinline__ void top8_insert(Top8 &t, float2 s, int d) {
 }
 // The split dimension of node v of tree t: one of the V best (counter-based
 // draw). Whole warp; returns it on every lane.
-__device__ __forceinline__ int choose_from_top8(Top8 &t, int nV, uint64_t seed, int tree, int64_t v) {
+template <typename K>
+__device__ __forceinline__ int choose_from_top8(TopN<K> &t, int nV, uint64_t seed, int tree, int64_t v) {
     const uint64_t rr = splitmix64_at(seed, ((uint64_t)tree << 32) + (uint64_t)v + 1u);
     const int want = (int)(rr % (uint64_t)nV);
     int pick = 0;
     for (int r = 0; r < nV; ++r) {
-        float2 best = t.s[0];
+        K best = t.s[0];
         int bd = t.d[0];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float ox = __shfl_xor_sync(0xffffffffu, best.x, o);
-            const float oy = __shfl_xor_sync(0xffffffffu, best.y, o);
+            const K ok = shfl_xor_key(best, o);
             const int od = __shfl_xor_sync(0xffffffffu, bd, o);
-            if (od != INT_MAX && (bd == INT_MAX || spread_greater(make_float2(ox, oy), od, best, bd))) {
-                best = make_float2(ox, oy);
+            if (od != INT_MAX && (bd == INT_MAX || spread_greater(ok, od, best, bd))) {
+                best = ok;
                 bd = od;
             }
         }
@@ -334,7 +429,7 @@ __device__ __forceinline__ int choose_from_top8(Top8 &t, int nV, uint64_t seed, 
                 t.s[q] = t.s[q + 1];
                 t.d[q] = t.d[q + 1];
             }
-            t.s[7] = make_float2(-INFINITY, -INFINITY);
+            key_lowest(t.s[7]);
             t.d[7] = INT_MAX;
         }
     }
@@ -354,7 +449,8 @@ __global__ void __launch_bounds__(256)
 choose_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
               const int32_t *__restrict__ leaf_ofs, int h, int l, int chunks,
               const float4 *__restrict__ part, int V, uint64_t seed, int32_t *__restrict__ split_dim,
-              float *__restrict__ split_val, int64_t n_int) {
+              float *__restrict__ split_val, int64_t n_int, const uint8_t *__restrict__ xu8, int Dp16,
+              const unsigned *__restrict__ u8_bad) {
     extern __shared__ __align__(16) float acc_tile[];
     const SliceGeom g = slice_geom(D);
     float2 *spread = reinterpret_cast<float2 *>(acc_tile + 2 * g.TP * g.Wp);  // [D]
@@ -372,6 +468,45 @@ choose_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ pe
     }
     const float n = (float)(hi - lo);
     const int32_t *pt = perm + (int64_t)t * N;
+    if (xu8 && *u8_bad == 0u) {  // byte rows: exact integer spreads
+        uint64_t *sp = reinterpret_cast<uint64_t *>(spread);
+        const uint64_t nn = (uint64_t)(hi - lo);
+        if (chunks > 1) {
+            for (int d = threadIdx.x; d < D; d += blockDim.x) {
+                uint64_t s1 = 0, s2 = 0;
+                const float4 *src = part + ((int64_t)t * gridDim.x + m) * chunks * D + d;
+                for (int c = 0; c < chunks; ++c) {
+                    const float4 q = src[(int64_t)c * D];
+                    s1 += __float_as_uint(q.x);
+                    s2 += __float_as_uint(q.y);
+                }
+                sp[d] = spread_exact(s1, s2, nn);
+            }
+        } else {
+            for (int d0 = 0; d0 < D; d0 += g.W) {
+                const int W = D - d0 < g.W ? D - d0 : g.W;
+                uint32_t s1[4], s2[4];
+                acc_slice_u8(xu8, Dp16, pt, lo, hi, d0, g, W, acc_tile, s1, s2);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = 4 * threadIdx.x + i;
+                    if (c < W) sp[d0 + c] = spread_exact(s1[i], s2[i], nn);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            Top8u tp;
+            top8_init(tp);
+            for (int d = threadIdx.x; d < D; d += 32) top8_insert(tp, sp[d], d);
+            const int dim = choose_from_top8(tp, nV, seed, t, v);
+            if (threadIdx.x == 0) {
+                split_dim[(int64_t)t * n_int + v] = dim;
+                split_val[(int64_t)t * n_int + v] = INFINITY;
+            }
+        }
+        return;
+    }
     if (chunks > 1) {
         for (int d = threadIdx.x; d < D; d += blockDim.x) {
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -446,10 +581,46 @@ __device__ __forceinline__ void small_group(const float *__restrict__ X, int D, 
     }
 }
 
+// Byte rows: lane l takes columns g0 + 8 l .. g0 + 8 l + 7 of each 256-column
+// group (one 8-byte load per point), exact integer sums, four points per step.
+__device__ __forceinline__ void small_group_u8(const uint8_t *__restrict__ xu8, int Dp16, int D, int g0, int lane,
+                                               int cnt, const int (&pp)[4], uint64_t n, Top8u &tp) {
+    uint32_t s1[8], s2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s1[j] = s2[j] = 0u;
+    const int c0 = g0 + 8 * lane;
+    const bool in = c0 < Dp16;
+    for (int q = 0; q < cnt; q += 4) {
+        uint2 x[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int qq = q + i;
+            const int sel = qq >> 5;
+            const int pv = sel == 0 ? pp[0] : sel == 1 ? pp[1] : sel == 2 ? pp[2] : pp[3];
+            const int p = __shfl_sync(0xffffffffu, pv, qq & 31);
+            x[i] = qq < cnt && in ? __ldg(reinterpret_cast<const uint2 *>(xu8 + (int64_t)p * Dp16 + c0))
+                                  : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t b = ((j < 4 ? x[i].x : x[i].y) >> (8 * (j & 3))) & 0xffu;
+                s1[j] += b;
+                s2[j] += b * b;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (c0 + j < D) top8_insert(tp, spread_exact(s1[j], s2[j], n), c0 + j);
+}
+
 __global__ void __launch_bounds__(SMALL_WARPS * 32, 3)
 choose_small_kernel(const float *__restrict__ X, int D, const int32_t *__restrict__ perm, int64_t N,
                     const int32_t *__restrict__ leaf_ofs, int h, int l, int V, uint64_t seed,
-                    int32_t *__restrict__ split_dim, float *__restrict__ split_val, int64_t n_int) {
+                    int32_t *__restrict__ split_dim, float *__restrict__ split_val, int64_t n_int,
+                    const uint8_t *__restrict__ xu8, int Dp16, const unsigned *__restrict__ u8_bad) {
     const int lane = threadIdx.x & 31;
     const int64_t m = (int64_t)blockIdx.x * SMALL_WARPS + (threadIdx.x >> 5);
     const int t = blockIdx.y;
@@ -472,6 +643,17 @@ choose_small_kernel(const float *__restrict__ X, int D, const int32_t *__restric
     int pp[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) pp[i] = lane + 32 * i < cnt ? pt[lo + lane + 32 * i] : 0;
+    if (xu8 && *u8_bad == 0u) {  // byte rows: exact integer spreads
+        Top8u tu;
+        top8_init(tu);
+        for (int g0 = 0; g0 < D; g0 += 256) small_group_u8(xu8, Dp16, D, g0, lane, cnt, pp, (uint64_t)cnt, tu);
+        const int dim = choose_from_top8(tu, nV, seed, t, v);
+        if (lane == 0) {
+            split_dim[(int64_t)t * n_int + v] = dim;
+            split_val[(int64_t)t * n_int + v] = INFINITY;
+        }
+        return;
+    }
     Top8 tp;
     top8_init(tp);
     int d0 = 0;
@@ -608,7 +790,13 @@ struct BuildWs {
     uint64_t *keys;
     float4 *part;
     int64_t key_count;  // per launch (all trees)
+    uint8_t *xu8;       // byte copy of X (N <= 2^18), else nullptr
+    unsigned *u8_bad;
+    int Dp16;
 };
+
+// The byte path (8-bit integer data) needs the partial sums exact: N <= 2^18.
+constexpr int64_t BUILD_U8_MAX_N = int64_t(1) << 18;
 
 int64_t pow2_at_least(int64_t x) {
     int64_t p = 1;
@@ -638,6 +826,13 @@ size_t forest_build_workspace(Carver &c, int64_t N, int D, int trees, int leaf_s
         if (ch > 1 && (((int64_t)1 << l) * ch) > max_parts) max_parts = ((int64_t)1 << l) * ch;
     }
     w.part = c.take<float4>((size_t)trees * (size_t)max_parts * D);
+    w.xu8 = nullptr;
+    w.u8_bad = nullptr;
+    w.Dp16 = (D + 15) & ~15;
+    if (N <= BUILD_U8_MAX_N) {
+        w.xu8 = c.take<uint8_t>((size_t)N * w.Dp16);
+        w.u8_bad = c.take<unsigned>(1);
+    }
     if (ws_out) *static_cast<BuildWs *>(ws_out) = w;
     return c.bytes();
 }
@@ -653,6 +848,11 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
                             256, 0, stream, f.N, h, f.leaf_ofs));
     ATSNE_TRY(launch_kernel("forest_iota", iota_kernel, ceil_div(f.N * T, 256), 256, 0, stream, f.perm,
                             f.N, T));
+    if (w.xu8) {  // 8-bit integer data: the spreads from a byte copy, exactly
+        cudaError_t eb = cudaMemsetAsync(w.u8_bad, 0, sizeof(unsigned), stream);
+        if (eb != cudaSuccess) return cuda_error(eb, "forest build memset");
+        ATSNE_TRY(u8_copy_launch("forest_u8_prep", X, f.N, f.D, w.Dp16, w.xu8, nullptr, w.u8_bad, stream));
+    }
     const SliceGeom sg = slice_geom(f.D);
     const size_t tile_smem = sizeof(float) * 2 * (size_t)sg.TP * sg.Wp;
     const size_t choose_smem = tile_smem + sizeof(float2) * (size_t)f.D;
@@ -672,17 +872,19 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
         if (chunks > 1)
             ATSNE_TRY(launch_kernel("forest_partial", partial_kernel, dim3(chunks, (unsigned)nodes, T),
                                     acc_threads(f.D), tile_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h,
-                                    l, chunks, w.part));
+                                    l, chunks, w.part, (const uint8_t *)w.xu8, w.Dp16,
+                                    (const unsigned *)w.u8_bad));
         if (nmax <= SMALL_NODE)
             ATSNE_TRY(launch_kernel("forest_choose", choose_small_kernel,
                                     dim3((unsigned)ceil_div(nodes, SMALL_WARPS), T), SMALL_WARPS * 32, 0,
                                     stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, f.top_var_dims,
-                                    f.seed, f.split_dim, f.split_val, f.n_internal));
+                                    f.seed, f.split_dim, f.split_val, f.n_internal, (const uint8_t *)w.xu8,
+                                    w.Dp16, (const unsigned *)w.u8_bad));
         else
             ATSNE_TRY(launch_kernel("forest_choose", choose_kernel, dim3((unsigned)nodes, T),
                                     acc_threads(f.D), choose_smem, stream, X, f.D, f.perm, f.N, f.leaf_ofs, h, l, chunks,
                                     w.part, f.top_var_dims, f.seed, f.split_dim, f.split_val,
-                                    f.n_internal));
+                                    f.n_internal, (const uint8_t *)w.xu8, w.Dp16, (const unsigned *)w.u8_bad));
         const int64_t P = pow2_at_least(nmax);
         const int64_t total = nodes * P * T;
         ATSNE_TRY(launch_kernel("forest_keys", keys_kernel, ceil_div(total, 256), 256, 0, stream, X,

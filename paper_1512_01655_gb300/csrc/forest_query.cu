@@ -525,37 +525,6 @@ __device__ __forceinline__ T warp_sum8(T (&v)[8], int lane) {
     return r;
 }
 
-// Byte copy of X (rows padded to Dp16 bytes with zeros) and the rows' exact
-// squared norms; *bad is raised if any value is not an integer in [0, 255]
-// (then the copy is not used). One warp per row, four values per lane.
-__global__ void __launch_bounds__(256) fq_u8_prep_kernel(const float *__restrict__ X, int64_t N, int D,
-                                                         int Dp16, uint8_t *__restrict__ xu8,
-                                                         uint32_t *__restrict__ nx8, unsigned *bad) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (r >= N) return;
-    const float *x = X + r * D;
-    uint32_t *out = reinterpret_cast<uint32_t *>(xu8 + r * Dp16);
-    uint32_t sq = 0;
-    bool ok = true;
-    for (int d4 = 4 * lane; d4 < Dp16; d4 += 128) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float v = d4 + i < D ? x[d4 + i] : 0.f;
-            ok &= v >= 0.f && v <= 255.f && v == rintf(v);  // false for NaN
-            const uint32_t b = ok ? (uint32_t)v : 0u;
-            word |= b << (8 * i);
-            sq += b * b;
-        }
-        out[d4 >> 2] = word;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
-    if (!__all_sync(FULL, ok) && lane == 0) atomicOr(bad, 1u);
-    if (lane == 0) nx8[r] = sq;
-}
-
 // Distances of each query to its listed points (entry 0, the query, left out)
 // and the k best under the (distance, index) order, written sorted.
 // MODE: FD_F32 / FD_F32V (FP32 rows, scalar or float4 loads) or FD_U8 (byte
@@ -856,8 +825,7 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     if (u8.xu8) {
         e = cudaMemsetAsync(u8.bad, 0, sizeof(unsigned), stream);
         if (e != cudaSuccess) return cuda_error(e, "forest query memset");
-        ATSNE_TRY(launch_kernel("forest_u8_prep", fq_u8_prep_kernel, ceil_div(f.N * 32, 256), 256, 0, stream,
-                                X, f.N, f.D, u8.Dp16, u8.xu8, u8.nx8, u8.bad));
+        ATSNE_TRY(u8_copy_launch("forest_u8_prep", X, f.N, f.D, u8.Dp16, u8.xu8, u8.nx8, u8.bad, stream));
     }
     const bool vec = (f.D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     for (int64_t w0 = 0; w0 < nq; w0 += a.chunk) {

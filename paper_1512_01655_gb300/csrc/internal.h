@@ -83,6 +83,11 @@ atsne_status merge_neighbors_launch(int32_t *idx, float *d2, int64_t rows, int k
                                     cudaStream_t stream);
 atsne_status union_launch(const int32_t *lists, int64_t total, int64_t N, uint32_t *bitmap,
                           int32_t *out, int64_t out_rows, int64_t *count, cudaStream_t stream);
+// Byte copy xu8[N][Dp16] of X (zero padded) and, if nx8 is given, the rows'
+// exact squared norms; *bad (cleared by the caller) is raised unless every value
+// is an integer in [0, 255].
+atsne_status u8_copy_launch(const char *name, const float *X, int64_t N, int D, int Dp16, uint8_t *xu8,
+                            uint32_t *nx8, unsigned *bad, cudaStream_t stream);
 atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, int k, const int32_t *ti,
                                    const float *td, const float *tp, const float *tb, int32_t *idx,
                                    float *d2, float *P, float *beta, float *rho,

@@ -1,4 +1,5 @@
-// Small kernels: precision rho (Eq. 9) and the row scatter of a refinement.
+// Small kernels: precision rho (Eq. 9), the row scatter of a refinement, and the
+// byte copy of 8-bit integer data.
 #include "common.cuh"
 #include "internal.h"
 
@@ -194,6 +195,37 @@ __global__ void gather_hint_kernel(const int32_t *__restrict__ rows, int64_t S, 
     hint[s] = (i >= 0 && i < N) ? d2[i * k + k - 1] : INFINITY;
 }
 
+// Byte copy of X (rows padded to Dp16 bytes with zeros) and, if nx8 is given,
+// the rows' exact squared norms; *bad is raised if any value is not an integer
+// in [0, 255] (then the copy is not used). One warp per row, four values per lane.
+__global__ void __launch_bounds__(256) u8_copy_kernel(const float *__restrict__ X, int64_t N, int D,
+                                                         int Dp16, uint8_t *__restrict__ xu8,
+                                                         uint32_t *__restrict__ nx8, unsigned *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= N) return;
+    const float *x = X + r * D;
+    uint32_t *out = reinterpret_cast<uint32_t *>(xu8 + r * Dp16);
+    uint32_t sq = 0;
+    bool ok = true;
+    for (int d4 = 4 * lane; d4 < Dp16; d4 += 128) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float v = d4 + i < D ? x[d4 + i] : 0.f;
+            ok &= v >= 0.f && v <= 255.f && v == rintf(v);  // false for NaN
+            const uint32_t b = ok ? (uint32_t)v : 0u;
+            word |= b << (8 * i);
+            sq += b * b;
+        }
+        out[d4 >> 2] = word;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(bad, 1u);
+    if (lane == 0 && nx8) nx8[r] = sq;
+}
+
 }  // namespace
 
 atsne_status gather_hint_launch(const int32_t *rows, int64_t S, int64_t N, int k, const float *d2,
@@ -245,6 +277,12 @@ atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, 
     if (S <= 0) return ATSNE_OK;
     return launch_kernel("refine_scatter", refine_scatter_kernel, ceil_div(S * k, 256), 256, 0,
                          stream, subset, S, N, k, ti, td, tp, tb, idx, d2, P, beta, rho);
+}
+
+atsne_status u8_copy_launch(const char *name, const float *X, int64_t N, int D, int Dp16, uint8_t *xu8,
+                            uint32_t *nx8, unsigned *bad, cudaStream_t stream) {
+    return launch_kernel(name, u8_copy_kernel, ceil_div(N * 32, 256), 256, 0, stream, X, N, D, Dp16, xu8, nx8,
+                         bad);
 }
 
 }  // namespace atsne
