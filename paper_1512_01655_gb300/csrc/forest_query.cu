@@ -223,6 +223,16 @@ __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool vali
     if (!m) return;
     const int np = __popc(m);
     const unsigned room = __ballot_sync(FULL, q.cnt < q.lcap);
+    if (np == 1 && q.n < q.cap) {  // the common case: one entry, into the next column with room
+        const uint64_t x = __shfl_sync(FULL, e, __ffs(m) - 1);
+        const unsigned rot = __funnelshift_r(room, room, q.rr);
+        const int t = (q.rr + __ffs(rot) - 1) & 31;
+        if (lane == t) cq_insert(q, x);
+        q.rr = (t + 1) & 31;
+        ++q.n;
+        if (x > q.hmax) q.hmax = x;
+        return;
+    }
     if (q.n + np <= q.cap && __popc(room) >= np) {
         // the r-th pushing lane's entry goes to the r-th column with room,
         // counting from column q.rr
