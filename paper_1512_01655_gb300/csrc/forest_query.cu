@@ -26,7 +26,10 @@
 //      pairs: new candidates below the current k-th pair are appended, and a
 //      full buffer is sorted and cut back to k.
 // The queries go in chunks (the lists of a chunk fit in FQ_MARK_BUDGET bytes);
-// traversal warps fetch queries from a global counter.
+// traversal warps fetch queries from a global counter. On 8-bit integer data
+// (a byte copy of X with a device flag, written first) the traversal holds the
+// query as bytes (more warps per SM) and the distances come from the byte rows;
+// the FP32 variants are launched too and return at once.
 //
 // Cut-off (all-rows mode). Popped keys never decrease (a descent adds squares to
 // the popped key), so the search pops its entries in key order and stops at some
@@ -41,6 +44,7 @@
 // cut-off and records its K, and the others take FQ_CUT_FACTOR times the larger
 // K of the seeds on either side (neighbouring leaves: similar densities).
 #include <float.h>
+#include <type_traits>
 #include <limits.h>
 
 #include "common.cuh"
@@ -50,7 +54,7 @@ namespace atsne {
 namespace {
 
 constexpr int FQ_WARPS = 4;
-constexpr int FQ_MAX_SLOTS = 4096;  // traversal warps of the persistent grid (one seen bitmap each)
+constexpr int FQ_MAX_SLOTS = 5120;  // traversal warps of the persistent grid (one seen bitmap each)
 constexpr int FQ_KCAP = 128;        // largest k
 constexpr int64_t FQ_MARK_BUDGET = int64_t(1) << 30;  // bytes of point lists per chunk
 constexpr int FD_MAX_WARPS = 4;     // distance kernel: warps per block (fewer for very long rows)
@@ -83,6 +87,9 @@ struct FqArgs {
     int *next_query;
     float *kseed;      // last popped key of each seed (NaN until written)
     int64_t chunk;     // work items per chunk (a multiple of FQ_SEED_GAP)
+    const uint8_t *xu8;      // byte copy of X, when every value is an integer in [0, 255]
+    const unsigned *u8_bad;
+    int Dp16;
 };
 
 struct FdArgs {
@@ -264,8 +271,8 @@ __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool vali
 // path's node on level j. With PT (one point per leaf) the last round also
 // fetches the points of the subtree's leaves and `pt` returns the reached
 // leaf's point (-1 if empty). Node ids fit in 26 bits.
-template <bool PT>
-__device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueue &q, int tr, int v,
+template <bool PT, typename QT>
+__device__ __forceinline__ int descend(const FqArgs &A, const QT *qv, ColQueue &q, int tr, int v,
                                        float key, float cut, int lane, int &pt) {
     const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
     const float *sv = A.split_val + (int64_t)tr * A.n_int;
@@ -284,7 +291,7 @@ __device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueu
             // lane = node (lane + 1 - 2^j) of level j below v, j = floor(log2(lane + 1))
             const int j = 31 - __clz(lane + 1);
             node = ((v + 1) << j) + lane - (1 << j);
-            const float qd = qv[sd[node]];
+            const float qd = (float)qv[sd[node]];
             const float val = sv[node];
             left = qd < val;
             const float diff = __fsub_rn(qd, val);
@@ -311,14 +318,20 @@ __device__ __forceinline__ int descend(const FqArgs &A, const float *qv, ColQueu
     return v - n_int;
 }
 
-__global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArgs A) {
+// QB: the query held as bytes (8-bit integer data: the same values, a quarter
+// of the shared memory, so more warps fit); the host launches both variants and
+// the byte copy's device flag lets one of them run.
+template <bool QB>
+__global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_kernel(FqArgs A) {
+    using QT = typename std::conditional<QB, uint8_t, float>::type;
+    if (QB != (A.xu8 != nullptr && *A.u8_bad == 0u)) return;
     extern __shared__ __align__(16) unsigned char fq_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const size_t heap_b = (size_t)((A.qcap + 31) >> 5) * 32 * 8;
-    const size_t q_b = ((size_t)A.D * 4 + 15) & ~size_t(15);
+    const size_t q_b = QB ? (size_t)A.Dp16 : ((size_t)A.D * 4 + 15) & ~size_t(15);
     unsigned char *base = fq_smem + w * (heap_b + q_b);
     uint64_t *qcol = reinterpret_cast<uint64_t *>(base);
-    float *qv = reinterpret_cast<float *>(base + heap_b);
+    QT *qv = reinterpret_cast<QT *>(base + heap_b);
 
     const int slot = blockIdx.x * FQ_WARPS + w;
     uint32_t *seen = A.seen + (int64_t)slot * A.words;
@@ -363,8 +376,13 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArg
             if (lane == 0) A.n_marked[t] = 0;
             continue;
         }
-        const float *xq = A.X + qi * A.D;
-        for (int d = lane; d < A.D; d += 32) qv[d] = xq[d];
+        if constexpr (QB) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(A.xu8 + qi * A.Dp16);
+            for (int d = lane; d < (A.Dp16 >> 2); d += 32) reinterpret_cast<uint32_t *>(qv)[d] = src[d];
+        } else {
+            const float *xq = A.X + qi * A.D;
+            for (int d = lane; d < A.D; d += 32) qv[d] = xq[d];
+        }
         int64_t n_marked, evaluated;
         float kfin = 0.f;  // key of the last pop whose leaf was scanned
         ColQueue q;
@@ -425,7 +443,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArg
                     int hp_ = -1;
                     float key = 0.f;
                     if (t < A.T) {
-                        descend<true>(A, qv, q, t, 0, 0.f, cut, lane, hp_);
+                        descend<true, QT>(A, qv, q, t, 0, 0.f, cut, lane, hp_);
                         ++t;
                     } else {
                         if (q.n == 0) break;
@@ -433,7 +451,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArg
                         key = __uint_as_float((uint32_t)(e >> 32));
                         const int tr = (int)((e >> 26) & 63u);
                         const int v = (int)(e & ((1u << 26) - 1u));
-                        descend<true>(A, qv, q, tr, v, key, cut, lane, hp_);
+                        descend<true, QT>(A, qv, q, tr, v, key, cut, lane, hp_);
                     }
                     // the word is loaded now and only read at the next step
                     uint32_t hw = hp_ >= 0 ? __ldcg(&seen[hp_ >> 5]) : 0u;
@@ -452,7 +470,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArg
             } else {
                 int unused;
                 for (int t = 0; t < A.T && evaluated < need; ++t) {
-                    scan_leaf(t, descend<false>(A, qv, q, t, 0, 0.f, cut, lane, unused));
+                    scan_leaf(t, descend<false, QT>(A, qv, q, t, 0, 0.f, cut, lane, unused));
                     kfin = 0.f;
                 }
                 while (evaluated < need && q.n > 0) {
@@ -460,7 +478,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, 7) forest_traverse_kernel(FqArg
                     const float key = __uint_as_float((uint32_t)(e >> 32));
                     const int tr = (int)((e >> 26) & 63u);
                     const int v = (int)(e & ((1u << 26) - 1u));
-                    scan_leaf(tr, descend<false>(A, qv, q, tr, v, key, cut, lane, unused));
+                    scan_leaf(tr, descend<false, QT>(A, qv, q, tr, v, key, cut, lane, unused));
                     kfin = key;
                 }
             }
@@ -696,8 +714,9 @@ __global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArg
     }
 }
 
-size_t fq_smem_bytes(int D, int qcap) {
-    return FQ_WARPS * ((size_t)((qcap + 31) >> 5) * 32 * 8 + (((size_t)D * 4 + 15) & ~size_t(15)));
+size_t fq_smem_bytes(int D, int qcap, bool qb) {
+    return FQ_WARPS * ((size_t)((qcap + 31) >> 5) * 32 * 8 +
+                       (qb ? (size_t)((D + 15) & ~15) : (((size_t)D * 4 + 15) & ~size_t(15))));
 }
 
 size_t fd_warp_bytes(int D) { return (size_t)((D + 3) & ~3) * 4 + FD_BUF * 8; }
@@ -781,7 +800,7 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     fq_workspace(c, f.N, f.D, nq, k, checks, f.leaf_size, &a, &u8);
     if (c.bytes() > ws_bytes) return set_error(ATSNE_ENOMEM, "forest query: workspace too small");
     if (nq == 0) return ATSNE_OK;
-    const size_t smem = fq_smem_bytes(f.D, qcap);
+    const size_t smem = fq_smem_bytes(f.D, qcap, false);
     if (smem > 227 * 1024)
         return set_error(ATSNE_EUNSUPPORTED,
                          "forest query: queue_cap %d with D=%d needs %zu B of shared memory", qcap, f.D,
@@ -789,15 +808,23 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     const int fd_warps = (int)hmin(FD_MAX_WARPS, (int64_t)(227 * 1024 / fd_warp_bytes(f.D)));
     if (fd_warps < 1)
         return set_error(ATSNE_EUNSUPPORTED, "forest query: rows of D=%d do not fit in shared memory", f.D);
-    cudaError_t e = cudaFuncSetAttribute(forest_traverse_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem_b = fq_smem_bytes(f.D, qcap, true);
+    auto grid_of = [&](auto kern, size_t sm, int &grid) -> cudaError_t {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FQ_WARPS * 32, sm);
+        if (err != cudaSuccess || per_sm < 1) per_sm = 1;
+        grid = (int)hmin(hmin((int64_t)per_sm * num_sms(), FQ_MAX_SLOTS / FQ_WARPS),
+                         ceil_div(hmin(nq, a.chunk), FQ_WARPS));
+        return cudaSuccess;
+    };
+    int grid = 0, grid_b = 0;
+    cudaError_t e = grid_of(forest_traverse_kernel<false>, smem, grid);
+    if (e == cudaSuccess && u8.xu8) e = grid_of(forest_traverse_kernel<true>, smem_b, grid_b);
     if (e != cudaSuccess) return cuda_error(e, "forest query attribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forest_traverse_kernel, FQ_WARPS * 32, smem);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    const int grid = (int)hmin(hmin((int64_t)per_sm * num_sms(), FQ_MAX_SLOTS / FQ_WARPS),
-                               ceil_div(hmin(nq, a.chunk), FQ_WARPS));
-    e = cudaMemsetAsync(a.seen, 0, sizeof(uint32_t) * (size_t)grid * FQ_WARPS * a.words, stream);
+    const int grid_max = grid > grid_b ? grid : grid_b;
+    e = cudaMemsetAsync(a.seen, 0, sizeof(uint32_t) * (size_t)grid_max * FQ_WARPS * a.words, stream);
     if (e == cudaSuccess)  // 0xff bytes: NaN, a seed not yet searched
         e = cudaMemsetAsync(a.kseed, 0xff, sizeof(float) * (size_t)(nq / FQ_SEED_GAP + 2), stream);
     if (e != cudaSuccess) return cuda_error(e, "forest query memset");
@@ -818,6 +845,9 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     a.leaf_size = f.leaf_size;
     a.qlist = qlist;
     a.evaluated_out = evaluated_out;
+    a.xu8 = u8.xu8;
+    a.u8_bad = u8.bad;
+    a.Dp16 = u8.Dp16;
     FdArgs b;
     b.X = X;
     b.D = f.D;
@@ -843,8 +873,11 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
         a.nw = b.nw = hmin(a.chunk, nq - w0);
         e = cudaMemsetAsync(a.next_query, 0, sizeof(int), stream);
         if (e != cudaSuccess) return cuda_error(e, "forest query memset");
-        atsne_status st = launch_kernel("forest_traverse", forest_traverse_kernel, grid, FQ_WARPS * 32,
+        atsne_status st = launch_kernel("forest_traverse", forest_traverse_kernel<false>, grid, FQ_WARPS * 32,
                                         smem, stream, a);
+        if (st == ATSNE_OK && u8.xu8)
+            st = launch_kernel("forest_traverse_u8", forest_traverse_kernel<true>, grid_b, FQ_WARPS * 32, smem_b,
+                               stream, a);
         if (st != ATSNE_OK) return st;
         // the FP32 and byte instantiations; the prep kernel's verdict picks one
         st = vec ? fd_launch_t<FD_F32V, 1>(b, fd_warps, stream) : fd_launch_t<FD_F32, 1>(b, fd_warps, stream);
