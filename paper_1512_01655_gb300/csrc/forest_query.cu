@@ -226,7 +226,11 @@ __device__ __forceinline__ void cq_push(ColQueue &q, uint64_t x, int lane) {
 // for all of them in distinct columns they are inserted at once (each by the
 // owner of its column), else one by one in lane order.
 __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool valid, int lane) {
-    unsigned m = __ballot_sync(FULL, valid && (q.n < q.cap || e < q.hmax));
+    unsigned m;
+    if (q.n < q.cap)
+        m = __ballot_sync(FULL, valid);
+    else
+        m = __ballot_sync(FULL, valid && e < q.hmax);
     if (!m) return;
     const int np = __popc(m);
     const unsigned room = __ballot_sync(FULL, q.cnt < q.lcap);
@@ -274,8 +278,9 @@ __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool vali
 template <bool PT, typename QT>
 __device__ __forceinline__ int descend(const FqArgs &A, const QT *qv, ColQueue &q, int tr, int v,
                                        float key, float cut, int lane, int &pt) {
-    const int32_t *sd = A.split_dim + (int64_t)tr * A.n_int;
-    const float *sv = A.split_val + (int64_t)tr * A.n_int;
+    const int64_t tb = (int64_t)tr * A.n_int;
+    const int32_t *sd = A.split_dim + tb;
+    const float *sv = A.split_val + tb;
     const int32_t *lpt = A.leaf_pt + ((int64_t)tr << A.h);
     const int n_int = (int)A.n_int;
     pt = -1;
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
 
     const int slot = blockIdx.x * FQ_WARPS + w;
     uint32_t *seen = A.seen + (int64_t)slot * A.words;
-    const int64_t need = A.checks > A.k ? A.checks : A.k;
+    const int need = A.checks > A.k ? A.checks : A.k;
 
     for (;;) {
         int64_t c = 0;
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
             const float *xq = A.X + qi * A.D;
             for (int d = lane; d < A.D; d += 32) qv[d] = xq[d];
         }
-        int64_t n_marked, evaluated;
+        int n_marked, evaluated;  // at most mark_cap
         float kfin = 0.f;  // key of the last pop whose leaf was scanned
         ColQueue q;
         // ---- phase 1: traversal (a second time, without cut-off, if the first ran dry) ----
