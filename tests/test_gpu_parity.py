@@ -266,6 +266,30 @@ def test_forest_query_cutoff_is_exact(at):
             assert torch.equal(u, v)
 
 
+@pytest.mark.parametrize("spoil", [None, 100.5, 300.0, -1.0])
+def test_byte_paths_follow_the_data(at, spoil):
+    # The forest build and search read a byte copy of X only when every value is
+    # an integer in [0, 255] (a device flag); one value outside that set sends
+    # the whole call to the FP32 kernels. Either way the forest equals the
+    # oracle's and the search visits the same points.
+    X = synth.sparse_prototypes(N=4000, D=784, seed=14)
+    if spoil is not None:
+        X = X.copy()
+        X[1234, 300] = spoil
+    f, o = forest_compare(at, X, 4, 1, 5)
+    idx, d2, ev = at.atsne_forest_query(to_dev(X), f, 90, checks=512)
+    at.atsne_check()
+    o_idx, o_d2, o_ev = oracle.forest_query(X, o, 90, 512)
+    assert np.array_equal(ev.cpu().numpy(), o_ev)
+    gi = idx.cpu().numpy()
+    same = np.array([set(gi[r]) == set(o_idx[r]) for r in range(X.shape[0])])
+    assert same.mean() > 0.99
+    assert np.abs(d2.cpu().numpy() - o_d2).max() <= 1e-5 * max(1.0, o_d2.max())
+    # the exact path on the same data (one tensor pass when every value is exact in BF16)
+    e_idx, e_d2 = at.atsne_knn(to_dev(X), 90)
+    knn_parity(e_idx.cpu().numpy(), e_d2.cpu().numpy(), X, 90)
+
+
 def test_forest_mnist_shaped_full_size_sampled(at):
     # the benchmark's forest launch (N=70000, D=784, T=4, V=5, checks=1024,
     # queue 512): the forest compared whole, the search on 64 sampled rows the
