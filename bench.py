@@ -182,17 +182,30 @@ class Pipeline:
         self.exact_opts = at.knn_opts(method="exact", precision=args.precision)
         self.forest_opts = at.knn_opts(method="forest", trees=args.trees, checks=args.checks,
                                        leaf_size=1, seed=7, queue_cap=args.queue_cap)
+        # the approximate path runs on its own stream beside the exact one: the
+        # two are independent until rho, and their kernels are bound by different
+        # units (integer issue and latency for the forest, tensor pipe and
+        # gathers for the exact kNN)
+        self.side = torch.cuda.Stream(device=dev)
 
     def step(self):
+        import torch
         at, X = self.at, self.X
-        # exact P
+        main = torch.cuda.current_stream()
+        side = self.side
+        side.wait_stream(main)
+        # approximate P^A (side stream)
+        with torch.cuda.stream(side):
+            forest = at.atsne_forest_build(X, opts=self.forest_opts, stream=side)
+            idx_a, d2_a, _ = at.atsne_forest_query(X, forest, K_NN, stream=side)
+            P_a, beta_a = at.atsne_calibrate_P(d2_a, PERPLEXITY, stream=side)
+        # exact P (main stream)
         idx_e, d2_e = at.atsne_knn(X, K_NN, opts=self.exact_opts)
         P_e, _ = at.atsne_calibrate_P(d2_e, PERPLEXITY)
         csr_e = at.atsne_symmetrize(idx_e, P_e, trim=False)
-        # approximate P^A
-        forest = at.atsne_forest_build(X, opts=self.forest_opts)
-        idx_a, d2_a, _ = at.atsne_forest_query(X, forest, K_NN)
-        P_a, beta_a = at.atsne_calibrate_P(d2_a, PERPLEXITY)
+        main.wait_stream(side)
+        for t in (idx_a, d2_a, P_a, beta_a):
+            t.record_stream(main)
         # precision of the approximate neighbourhoods (Eq. 9), before refinement
         rho_i, rho_sum = self._precision(idx_a, idx_e)
         self.rho_sum = rho_sum
