@@ -49,6 +49,8 @@ def lib():
         L.oracle_knn_cross.argtypes = [_f32p, _i64, _f32p, _i64, _i32, _i32, _i32p, _f64p]
         L.oracle_refine.argtypes = [_f32p, _i64, _i32, _i32p, _i64, _i32, _f64, _f64, _i32, _i32p,
                                     _f64p, _f64p, _f64p, _f64p]
+        L.oracle_delete.argtypes = [_f32p, _i64, _i32, _i32p, _i64, _i32, _f64, _f64, _i32, _i32p,
+                                    _f64p, _f64p, _f64p, _f64p, ctypes.POINTER(_i64)]
         _lib = L
     return _lib
 
@@ -222,3 +224,19 @@ def knn_cross(Xq, Xc, k):
     _check(lib().oracle_knn_cross(Xq, Xq.shape[0], Xc, Xc.shape[0], Xq.shape[1], k, idx, d2),
            "knn_cross")
     return idx, d2
+
+
+def delete(X, rows, k, perplexity, idx, d2, P, beta, rho, tol=1e-10, max_iter=200):
+    """Deletion of the listed points, Sec. 5.3.2, on copies of the state:
+    returns (X, idx, d2, P, beta, rho) over the N - R remaining points."""
+    X = np.array(X, dtype=np.float32, order="C", copy=True)
+    N, D = X.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    st = [np.array(a, dtype=dt, order="C", copy=True)
+          for a, dt in ((idx, np.int32), (d2, np.float64), (P, np.float64), (beta, np.float64),
+                        (rho, np.float64))]
+    n = _i64(0)
+    _check(lib().oracle_delete(X, N, D, rows, rows.shape[0], k, float(perplexity), float(tol),
+                               int(max_iter), *st, ctypes.byref(n)), "delete")
+    n = n.value
+    return (X[:n],) + tuple(a[:n] for a in st)

@@ -23,6 +23,8 @@
  *   oracle_precision     Eq. 9 (Sec. 4.1)
  *   oracle_kde           Eq. 12, Eq. 13 and the approximation map of Sec. 5.2.2
  *   oracle_knn_cross     Eq. 8 across two point sets (insertion, Sec. 5.3.1)
+ *   oracle_delete        Sec. 5.3.2: points leave every neighbourhood, rho_i
+ *                        falls by 1/k per point removed, rows renumbered
  *
  * Readings taken where the paper is silent are stated at each function.
  * Compile with -ffp-contract=off: the forest's float decisions (split value,
@@ -137,6 +139,10 @@ int oracle_knn_exact(const float *X, int64_t N, int32_t D, const int32_t *querie
  * hi is infinite, else midpoint), otherwise lower it to the midpoint with lo.
  * Stop when |H - ln mu| < tol or after max_iter evaluations; the outputs are
  * the p_j, beta and exp(H) of the last evaluation.
+ * A distance of +inf marks an absent neighbour (a neighbourhood left with
+ * fewer than k points by a deletion, Sec. 5.3.2): it is outside N_i, so it
+ * takes no part in the sums and gets p = 0. A row with no neighbour at all
+ * gets p = 0, beta = 0, perplexity 0 and no iteration.
  */
 int oracle_calibrate(const double *d2, int64_t rows, int32_t k, double perplexity, double tol,
                      int32_t max_iter, double *P_out, double *beta_out, double *perp_out,
@@ -148,15 +154,26 @@ int oracle_calibrate(const double *d2, int64_t rows, int32_t k, double perplexit
     for (int64_t r = 0; r < rows; ++r) {
         const double *d = d2 + r * k;
         double *p = P_out + r * k;
-        double dmin = d[0];
-        for (int32_t j = 1; j < k; ++j)
+        double dmin = INFINITY;
+        for (int32_t j = 0; j < k; ++j)
             if (d[j] < dmin) dmin = d[j];
+        if (isinf(dmin)) {  /* no neighbour */
+            for (int32_t j = 0; j < k; ++j) p[j] = 0.0;
+            if (beta_out) beta_out[r] = 0.0;
+            if (perp_out) perp_out[r] = 0.0;
+            if (iters_out) iters_out[r] = 0;
+            continue;
+        }
         double beta = 1.0, lo = 0.0, hi = INFINITY, H = 0.0, Z = 0.0;
         int32_t it;
         for (it = 1;; ++it) {
             double ws = 0.0;
             Z = 0.0;
             for (int32_t j = 0; j < k; ++j) {
+                if (isinf(d[j])) {  /* absent */
+                    p[j] = 0.0;
+                    continue;
+                }
                 double s = d[j] - dmin;
                 double w = exp(-beta * s);
                 p[j] = w;
@@ -206,20 +223,21 @@ int oracle_symmetrize(const int32_t *idx, const double *P, int64_t N, int32_t k,
                       int64_t *row_ptr, int32_t *col, double *val, int64_t *nnz_out)
 {
     if (!idx || !P || !row_ptr || !col || !val || N < 1 || k < 1) return 1;
-    int64_t M = 2 * N * (int64_t)k;
-    trip_t *t = (trip_t *)malloc(sizeof(trip_t) * (size_t)M);
+    int64_t M = 0;
+    trip_t *t = (trip_t *)malloc(sizeof(trip_t) * (size_t)(2 * N * (int64_t)k));
     if (!t) return 2;
     const double scale = 1.0 / (2.0 * (double)N);
     for (int64_t i = 0; i < N; ++i)
         for (int32_t a = 0; a < k; ++a) {
             int32_t j = idx[i * k + a];
+            if (j == -1) continue;  /* an absent neighbour (Sec. 5.3.2) */
             if (j < 0 || j >= N || j == i) {
                 free(t);
                 return 1;
             }
             double v = P[i * k + a] * scale;
-            t[2 * (i * k + a)] = (trip_t){i, j, v};
-            t[2 * (i * k + a) + 1] = (trip_t){j, (int32_t)i, v};
+            t[M++] = (trip_t){i, j, v};
+            t[M++] = (trip_t){j, (int32_t)i, v};
         }
     qsort(t, (size_t)M, sizeof(trip_t), trip_cmp);
     int64_t nnz = 0;
@@ -253,7 +271,7 @@ int oracle_precision(const int32_t *idx_a, const int32_t *idx_e, int64_t rows, i
         int64_t hits = 0;
         for (int32_t a = 0; a < k; ++a)
             for (int32_t e = 0; e < k; ++e)
-                if (idx_a[r * k + a] == idx_e[r * k + e]) {
+                if (idx_a[r * k + a] >= 0 && idx_a[r * k + a] == idx_e[r * k + e]) {
                     hits++;
                     break;
                 }
@@ -663,6 +681,72 @@ int oracle_refine(const float *X, int64_t N, int32_t D, const int32_t *subset, i
     return rc;
 }
 
+
+/*
+ * Deletion of points, Sec. 5.3.2. Each point of del (R distinct rows in
+ * [0, N)) leaves every neighbourhood that holds it: the row keeps its other
+ * entries in their order and ends with an absent entry (index -1, distance
+ * +inf) per point removed, and rho_i falls by 1/k per point removed (not
+ * below 0; the paper ignores the missing (K+1)-th neighbour instead of
+ * searching it). The deleted rows go away: the remaining points keep their
+ * order and are numbered 0..N-R-1 (X's rows and every index follow). Reading:
+ * P_{j|i} is defined over N_i (Eq. 3, Eq. 4), so every remaining row's
+ * Gaussian is calibrated again over its remaining neighbours. Arrays are
+ * updated in place; *N_out = N - R. Returns 1 on an index out of range or
+ * listed twice.
+ */
+int oracle_delete(float *X, int64_t N, int32_t D, const int32_t *del, int64_t R, int32_t k,
+                  double perplexity, double tol, int32_t max_iter, int32_t *idx, double *d2, double *P,
+                  double *beta, double *rho, int64_t *N_out)
+{
+    if (!X || N < 1 || D < 1 || k < 1 || R < 0 || (R > 0 && !del) || !idx || !d2 || !P) return 1;
+    unsigned char *dead = (unsigned char *)calloc((size_t)N, 1);
+    int64_t *newid = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!dead || !newid) {
+        free(dead);
+        free(newid);
+        return 2;
+    }
+    int rc = 0;
+    for (int64_t r = 0; r < R && !rc; ++r) {
+        if (del[r] < 0 || del[r] >= N || dead[del[r]]) rc = 1;
+        else dead[del[r]] = 1;
+    }
+    if (!rc) {
+        int64_t n = 0;
+        for (int64_t i = 0; i < N; ++i) newid[i] = dead[i] ? -1 : n++;
+        for (int64_t i = 0; i < N; ++i) {  /* newid[i] <= i: rows move down in order */
+            if (dead[i]) continue;
+            const int64_t ni = newid[i];
+            memmove(X + ni * D, X + i * D, sizeof(float) * (size_t)D);
+            int32_t c = 0, removed = 0;
+            for (int32_t a = 0; a < k; ++a) {
+                const int32_t j = idx[i * k + a];
+                if (j >= 0 && dead[j]) {
+                    removed++;
+                    continue;
+                }
+                if (j < 0) continue;  /* already absent */
+                idx[ni * k + c] = (int32_t)newid[j];
+                d2[ni * k + c] = d2[i * k + a];
+                c++;
+            }
+            for (; c < k; ++c) {
+                idx[ni * k + c] = -1;
+                d2[ni * k + c] = INFINITY;
+            }
+            if (rho) {
+                const double v = rho[i] - (double)removed / (double)k;
+                rho[ni] = v > 0.0 ? v : 0.0;
+            }
+        }
+        *N_out = n;
+        rc = oracle_calibrate(d2, n, k, perplexity, tol, max_iter, P, beta, NULL, NULL);
+    }
+    free(dead);
+    free(newid);
+    return rc;
+}
 
 /*
  * Density view of a 2-D embedding and its approximation map (Sec. 5.2), per
