@@ -155,8 +155,21 @@ int oracle_calibrate(const double *d2, int64_t rows, int32_t k, double perplexit
         const double *d = d2 + r * k;
         double *p = P_out + r * k;
         double dmin = INFINITY;
-        for (int32_t j = 0; j < k; ++j)
+        int32_t present = 0;
+        for (int32_t j = 0; j < k; ++j) {
             if (d[j] < dmin) dmin = d[j];
+            present += !isinf(d[j]);
+        }
+        if (present > 0 && (double)present <= perplexity) {
+            /* H over n present neighbours is at most log n, attained only at
+             * beta = 0: the target log(perplexity) >= log n is met in the
+             * limit beta -> 0, the uniform distribution over N_i */
+            for (int32_t j = 0; j < k; ++j) p[j] = isinf(d[j]) ? 0.0 : 1.0 / present;
+            if (beta_out) beta_out[r] = 0.0;
+            if (perp_out) perp_out[r] = (double)present;
+            if (iters_out) iters_out[r] = 0;
+            continue;
+        }
         if (isinf(dmin)) {  /* no neighbour */
             for (int32_t j = 0; j < k; ++j) p[j] = 0.0;
             if (beta_out) beta_out[r] = 0.0;

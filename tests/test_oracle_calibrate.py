@@ -74,3 +74,23 @@ def test_shift_invariance(oracle_mod):
     P1, b1, _, _ = oracle_mod.calibrate(d2, 10.0)
     P2, b2, _, _ = oracle_mod.calibrate(d2 + 1000.0, 10.0)
     assert np.allclose(P1, P2, atol=1e-9) and np.allclose(b1, b2, rtol=1e-9)
+
+
+def test_rows_at_most_perplexity_neighbours_are_uniform(oracle_mod):
+    # over n present neighbours H <= ln n, with equality only at beta = 0, so a
+    # target ln(mu) >= ln n is met only in the limit beta -> 0: P = 1/n on N_i
+    rng = np.random.default_rng(4)
+    d2 = np.sort(rng.uniform(0.5, 9.0, size=(3, 8)), axis=1)
+    d2[1, 5:] = np.inf   # 5 present
+    d2[2, 3:] = np.inf   # 3 present
+    for mu in (5.0, 6.5):
+        P, beta, perp, _ = oracle_mod.calibrate(d2, mu)
+        assert np.all(P[1, :5] == 0.2) and np.all(P[1, 5:] == 0.0) and beta[1] == 0.0
+        assert np.all(P[2, :3] == 1.0 / 3) and beta[2] == 0.0 and perp[2] == 3.0
+    # the limit: just below mu = n the bisection's row tends to the uniform one
+    dev = []
+    for eps in (1e-2, 1e-4, 1e-6):
+        P, beta, _, _ = oracle_mod.calibrate(d2[1:2], 5.0 - eps)
+        assert beta[0] > 0
+        dev.append(np.abs(P[0, :5] - 0.2).max())
+    assert dev[0] > dev[1] > dev[2] and dev[2] < 1e-2
