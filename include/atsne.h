@@ -66,7 +66,8 @@ typedef enum {
     ATSNE_OP_FOREST_QUERY = 5,
     ATSNE_OP_REFINE_BATCH = 6, /* S = total entries of the concatenated selections */
     ATSNE_OP_KNN_CROSS = 7,    /* N = corpus rows, S = query rows */
-    ATSNE_OP_KNN_CROSS_RADIUS = 8  /* as KNN_CROSS, with per-row radii */
+    ATSNE_OP_KNN_CROSS_RADIUS = 8, /* as KNN_CROSS, with per-row radii */
+    ATSNE_OP_DELETE = 9            /* N = rows before the deletion, D, k */
 } atsne_op;
 
 /* Options of the kNN step. atsne_knn_opts_default() fills the defaults. */
@@ -115,12 +116,18 @@ atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *quer
  * over the kNN support of Eq. 8: for each row, beta = 1/(2 sigma^2) is found by
  * bisection so that exp(H) = perplexity (H in nats, equal to Eq. 4's base-2
  * form), and P_cond[r][j] = exp(-beta d2[r][j]) / sum_l exp(-beta d2[r][l]).
- *  d2         [rows][k] fp32 squared distances (any order; finite, >= 0).
+ *  d2         [rows][k] fp32 squared distances (any order; >= 0). +inf marks an
+ *             absent neighbour (a row shortened by atsne_delete_rows): it takes
+ *             no part in the sums and gets P 0. NaN or a negative value raises
+ *             the device status.
  *  perplexity 0 < perplexity < k.   tol: stop when |H - ln perplexity| < tol
  *  (<= 0 selects 1e-5).  max_iter: bisection steps (<= 0 selects 200).
  *  P_cond_out [rows][k] fp32 (rows sum to 1), beta_out [rows] fp32 (may be NULL).
  * Rows whose target is unreachable (k equal distances, or at least
  * `perplexity` neighbours tied at the smallest distance) end at max_iter.
+ * A row of n present neighbours with n <= perplexity (its entropy is at most
+ * ln n, reached only at beta = 0) takes the bisection's limit: beta = 0 and
+ * P = 1/n on the present entries; a row with none gets P 0 and beta 0.
  */
 atsne_status atsne_calibrate_P(const float *d2, int64_t rows, int32_t k, float perplexity,
                                float tol, int32_t max_iter, float *P_cond_out, float *beta_out,
@@ -248,6 +255,26 @@ atsne_status atsne_knn_cross(const float *Xq, int64_t Nq, const float *Xc, int64
 atsne_status atsne_merge_neighbors(int32_t *idx, float *d2, int64_t rows, int32_t k,
                                    const int32_t *cand_idx, const float *cand_d2, int32_t kc,
                                    int32_t index_offset, uint8_t *changed, void *stream);
+
+/*
+ * Deletion of points, Sec. 5.3.2, for a batch: rows ([R], distinct, in
+ * [0, N)) leave the state. Every neighbourhood that holds one of them loses it:
+ * the row keeps its other entries in order and ends with one absent entry
+ * (index -1, distance +inf, P 0) per point removed, and rho falls by 1/k per
+ * point removed (not below 0): the paper leaves the (K+1)-th neighbour
+ * unsearched. The remaining points keep their order and become rows
+ * 0..N-R-1: X ([N][D]), idx/d2/P_cond ([N][k]), beta and rho ([N]) are
+ * compacted in place and every index renumbered. Every remaining row's Gaussian
+ * is then calibrated again over its remaining neighbours (Eq. 3, Eq. 4 over
+ * N_i; bisection as atsne_calibrate_P with its default tolerance), which the
+ * absent entries do not enter. Later insertions fill absent entries first (their
+ * d_i^Max is +inf). An index out of range or listed twice raises the device
+ * status (ATSNE_EINVAL from atsne_check) and leaves the state unspecified.
+ * Workspace: atsne_workspace_bytes(ATSNE_OP_DELETE, N, D, k, 0, NULL).
+ */
+atsne_status atsne_delete_rows(const int32_t *rows, int64_t R, float *X, int64_t N, int32_t D, int32_t k,
+                               float perplexity, int32_t *idx, float *d2, float *P_cond, float *beta,
+                               float *rho, void *workspace, size_t ws_bytes, void *stream);
 
 /*
  * Writes S computed rows into the state: row rows[s] of idx/d2/P_cond ([N][k])

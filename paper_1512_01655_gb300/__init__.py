@@ -17,7 +17,7 @@ ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPP
 KNN_EXACT, KNN_FOREST = 0, 1
 FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK = 0, 1, 2, 3
 (OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY,
- OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS) = range(9)
+ OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS, OP_DELETE) = range(10)
 
 EXPORTED = (
     "atsne_knn_opts_default", "atsne_workspace_bytes", "atsne_knn", "atsne_calibrate_P",
@@ -26,7 +26,7 @@ EXPORTED = (
     "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
     "atsne_refine_subset_noalloc", "atsne_refine_batch", "atsne_kde_map", "atsne_knn_cross",
     "atsne_knn_rows",
-    "atsne_merge_neighbors", "atsne_commit_rows",
+    "atsne_merge_neighbors", "atsne_commit_rows", "atsne_delete_rows",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
@@ -88,6 +88,8 @@ def lib():
         L.atsne_merge_neighbors.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _i32, _vp, _vp]
         L.atsne_commit_rows.argtypes = [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         _vp, _vp, _vp]
+        L.atsne_delete_rows.argtypes = [_vp, _i64, _vp, _i64, _i32, _i32, _f32, _vp, _vp, _vp, _vp,
+                                        _vp, _vp, _sz, _vp]
         L.atsne_kde_map.argtypes = [_vp, _i64, _vp, _vp, _f32, _f32, _f32, _i32, _i32, _f32, _f32,
                                     _f32, _vp, _vp, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
@@ -300,6 +302,23 @@ def atsne_commit_rows(rows, ti, td, tp, tb, idx, d2, P_cond, beta=None, rho=None
     S, k = ti.shape
     _raise(lib().atsne_commit_rows(_p(rows), S, idx.shape[0], k, _p(ti), _p(td), _p(tp), _p(tb),
                                    _p(idx), _p(d2), _p(P_cond), _p(beta), _p(rho), _stream(stream)))
+
+
+def atsne_delete_rows(X, rows, perplexity, idx, d2, P_cond, beta=None, rho=None, N=None, stream=None,
+                      workspace=None):
+    """Deletion of the listed points (Sec. 5.3.2), in place over the first N
+    rows (default: all): they leave every neighbourhood (an absent entry, index
+    -1, per point removed; rho -= 1/k each), the remaining rows move up in order
+    with every index renumbered, and their Gaussians are calibrated again.
+    Returns the new number of rows."""
+    _dev(X, torch.float32, "X")
+    _dev(rows, torch.int32, "rows")
+    N = X.shape[0] if N is None else int(N)
+    D, k, R = X.shape[1], idx.shape[1], rows.shape[0]
+    ws = workspace if workspace is not None else _workspace(workspace_bytes(OP_DELETE, N, D, k, 0), X.device)
+    _raise(lib().atsne_delete_rows(_p(rows), R, _p(X), N, D, k, perplexity, _p(idx), _p(d2), _p(P_cond),
+                                   _p(beta), _p(rho), _p(ws), ws.numel(), _stream(stream)))
+    return N - R
 
 
 def atsne_kde_map(Y, x0, y0, pixel, width, height, h, cutoff=4.0, lens_k=2.0, rho=None,

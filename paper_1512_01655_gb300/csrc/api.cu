@@ -324,6 +324,8 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
         return forest_query_workspace(c, N, D, S > 0 ? S : N, k, o.checks, o.leaf_size, nullptr);
     case ATSNE_OP_KNN_CROSS:
         return cross_ws(c, S, N, D, k, o, false, nullptr, nullptr);
+    case ATSNE_OP_DELETE:
+        return delete_workspace(c, N, D, k, nullptr);
     case ATSNE_OP_KNN_CROSS_RADIUS:
         return cross_ws(c, S, N, D, k, o, true, nullptr, nullptr);
     case ATSNE_OP_REFINE_BATCH:
@@ -380,6 +382,25 @@ atsne_status atsne_calibrate_P(const float *d2, int64_t rows, int32_t k, float p
     if (max_iter <= 0) max_iter = 200;
     return calibrate_launch(d2, rows, k, perplexity, tol, max_iter, P_cond_out, beta_out,
                             static_cast<cudaStream_t>(stream));
+}
+
+atsne_status atsne_delete_rows(const int32_t *rows, int64_t R, float *X, int64_t N, int32_t D, int32_t k,
+                               float perplexity, int32_t *idx, float *d2, float *P_cond, float *beta,
+                               float *rho, void *workspace, size_t ws_bytes, void *stream) {
+    if (!X || !idx || !d2 || !P_cond || (R > 0 && !rows))
+        return set_error(ATSNE_EINVAL, "delete: NULL pointer");
+    if (N < 1 || N > INT32_MAX || D < 1 || k < 1 || R < 0 || R > N)
+        return set_error(ATSNE_EINVAL, "delete: N=%lld D=%d k=%d R=%lld", (long long)N, D, k, (long long)R);
+    if (!(perplexity > 0.f) || !(perplexity < (float)k))
+        return set_error(ATSNE_EINVAL, "delete: perplexity=%g not in (0, k=%d)", (double)perplexity, k);
+    if (calibrate_smem_bytes(k) > 227 * 1024) return set_error(ATSNE_EUNSUPPORTED, "delete: k=%d too large", k);
+    if (atsne_status st = check_base(workspace, "delete workspace")) return st;
+    Carver c(workspace);
+    DeleteWs w;
+    delete_workspace(c, N, D, k, &w);
+    if (ws_bytes < c.bytes()) return set_error(ATSNE_ENOMEM, "delete: workspace too small");
+    return delete_launch(rows, R, X, N, D, k, perplexity, idx, d2, P_cond, beta, rho, w,
+                         static_cast<cudaStream_t>(stream));
 }
 
 atsne_status atsne_symmetrize(const int32_t *idx, const float *P_cond, int64_t N, int32_t k,

@@ -10,6 +10,10 @@
 // halves the bracket exactly as the definition prescribes: start beta = 1,
 // double while no upper bound is known, then bisect.
 //
+// A distance of +inf marks an absent neighbour (a neighbourhood shortened by a
+// deletion, Sec. 5.3.2): it is outside N_i, takes no part in the sums and gets
+// P = 0; a row without any neighbour gets P = 0 and beta = 0.
+//
 // Arithmetic: FP32 throughout. GB300 runs FP64 at 1/64 of the FP32 rate, and
 // the parity bound for P (1e-5 absolute) needs H only to about 1e-6, which the
 // 90-term FP32 sums give with a wide margin; the stopping tolerance defaults to
@@ -25,8 +29,8 @@ namespace {
 constexpr int CAL_THREADS = 128;
 
 __global__ void __launch_bounds__(CAL_THREADS)
-calibrate_kernel(const float *__restrict__ d2, int64_t rows, int k, float target, float tol,
-                 int max_iter, float *__restrict__ P, float *__restrict__ beta_out, int *status) {
+calibrate_kernel(const float *__restrict__ d2, int64_t rows, int k, float perplexity, float target,
+                 float tol, int max_iter, float *__restrict__ P, float *__restrict__ beta_out, int *status) {
     extern __shared__ float sm[];
     const int stride = k | 1;
     const int64_t r0 = (int64_t)blockIdx.x * CAL_THREADS;
@@ -40,22 +44,31 @@ calibrate_kernel(const float *__restrict__ d2, int64_t rows, int k, float target
 
     if ((int)threadIdx.x < nr) {
         float *row = sm + threadIdx.x * stride;
-        float dmin = row[0];
-        bool finite = true;
+        float dmin = INFINITY;
+        bool valid = true;
+        int present = 0;
         for (int j = 0; j < k; ++j) {
             float v = row[j];
-            finite &= isfinite(v) && v >= 0.f;
+            valid &= v >= 0.f;  // NaN and negative distances are errors; +inf is absent
             dmin = fminf(dmin, v);
+            present += v < INFINITY;
         }
-        if (!finite) raise_status(status, DEV_NONFINITE);
-        for (int j = 0; j < k; ++j) row[j] -= dmin;  // s_j
+        if (!valid) raise_status(status, DEV_NONFINITE);
+        if (dmin < INFINITY)
+            for (int j = 0; j < k; ++j) row[j] -= dmin;  // s_j (+inf stays +inf)
 
+        // the entropy over n present neighbours is at most log n, reached only
+        // at beta = 0: when n <= perplexity the bisection's limit is beta = 0,
+        // a uniform row, which is taken directly
+        const bool flat = present > 0 && (float)present <= perplexity;
         float beta = 1.f, lo = 0.f, hi = INFINITY, bf = 1.f, Z = 1.f;
-        for (int it = 1;; ++it) {
+        if (flat) bf = 0.f, Z = (float)present;
+        for (int it = 1; dmin < INFINITY && !flat; ++it) {
             bf = fminf(beta, FLT_MAX);
             float z = 0.f, ws = 0.f;
             for (int j = 0; j < k; ++j) {
                 const float s = row[j];
+                if (s == INFINITY) continue;  // absent
                 const float w = expf(-bf * s);
                 z += w;
                 ws = fmaf(w, s, ws);
@@ -71,8 +84,9 @@ calibrate_kernel(const float *__restrict__ d2, int64_t rows, int k, float target
                 beta = 0.5f * (lo + beta);
             }
         }
-        const float inv = 1.f / Z;
-        for (int j = 0; j < k; ++j) row[j] = expf(-bf * row[j]) * inv;
+        if (dmin == INFINITY) bf = 0.f;  // no neighbour
+        const float inv = dmin < INFINITY ? 1.f / Z : 0.f;
+        for (int j = 0; j < k; ++j) row[j] = row[j] == INFINITY ? 0.f : expf(-bf * row[j]) * inv;
         if (beta_out) beta_out[r0 + threadIdx.x] = bf;
     }
     __syncthreads();
@@ -99,7 +113,7 @@ atsne_status calibrate_launch(const float *d2, int64_t rows, int k, float perple
         attr = smem;
     }
     return launch_kernel("calibrate_beta", calibrate_kernel, ceil_div(rows, CAL_THREADS),
-                         CAL_THREADS, smem, stream, d2, rows, k, logf(perplexity), tol, max_iter, P,
+                         CAL_THREADS, smem, stream, d2, rows, k, perplexity, logf(perplexity), tol, max_iter, P,
                          beta, device_status_word());
 }
 

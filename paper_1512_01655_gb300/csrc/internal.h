@@ -58,7 +58,7 @@ atsne_status calibrate_launch(const float *d2, int64_t rows, int k, float perple
 struct SymWs {
     int32_t *scol = nullptr;
     float *sval = nullptr;
-    int32_t *rev = nullptr, *cursor = nullptr, *long_rows = nullptr, *n_long = nullptr;
+    int32_t *rev = nullptr, *cursor = nullptr, *long_rows = nullptr, *n_long = nullptr, *own = nullptr;
     int64_t *scan = nullptr;
 };
 size_t scan_partials_count(int64_t n);
@@ -83,6 +83,17 @@ atsne_status merge_neighbors_launch(int32_t *idx, float *d2, int64_t rows, int k
                                     cudaStream_t stream);
 atsne_status union_launch(const int32_t *lists, int64_t total, int64_t N, uint32_t *bitmap,
                           int32_t *out, int64_t out_rows, int64_t *count, cudaStream_t stream);
+// Deletion (Sec. 5.3.2): scratch of one call.
+struct DeleteWs {
+    int32_t *dead = nullptr;
+    int64_t *before = nullptr, *total = nullptr, *scan = nullptr;
+    float *X = nullptr, *d2 = nullptr, *beta = nullptr, *rho = nullptr;
+    int32_t *idx = nullptr;
+};
+size_t delete_workspace(Carver &c, int64_t N, int D, int k, DeleteWs *ws);
+atsne_status delete_launch(const int32_t *rows, int64_t R, float *X, int64_t N, int D, int k, float perplexity,
+                           int32_t *idx, float *d2, float *P, float *beta, float *rho, const DeleteWs &w,
+                           cudaStream_t stream);
 // Byte copy xu8[N][Dp16] of X (zero padded) and, if nx8 is given, the rows'
 // exact squared norms; *bad (cleared by the caller) is raised unless every value
 // is an integer in [0, 255].

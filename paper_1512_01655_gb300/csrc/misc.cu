@@ -24,7 +24,7 @@ precision_kernel(const int32_t *__restrict__ a, const int32_t *__restrict__ e, i
         for (int t = lane; t < k; t += 32) {
             const int j = a[r * k + t];
             bool found = false;
-            for (int u = 0; u < k; ++u) found |= (row[u] == j);
+            for (int u = 0; u < k; ++u) found |= j >= 0 && row[u] == j;  // -1: absent
             hits += found;
         }
 #pragma unroll
@@ -226,6 +226,62 @@ __global__ void __launch_bounds__(256) u8_copy_kernel(const float *__restrict__ 
     if (lane == 0 && nx8) nx8[r] = sq;
 }
 
+// ---- deletion (Sec. 5.3.2) ----
+// dead[j] = 1 for every listed row; a row out of range or listed twice raises
+// the status word.
+__global__ void delete_mark_kernel(const int32_t *__restrict__ rows, int64_t R, int64_t N,
+                                   int32_t *__restrict__ dead, int *status) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int32_t j = rows[r];
+    if (j < 0 || j >= N) {
+        raise_status(status, DEV_MALFORMED);
+        return;
+    }
+    if (atomicExch(&dead[j], 1) != 0) raise_status(status, DEV_MALFORMED);
+}
+
+// One warp per row i that stays: its new row i - before[i] receives X's row,
+// the entries that stay (renumbered j - before[j], in their order), absent
+// entries (-1, +inf) for the rest, beta, and rho less 1/k per entry removed.
+__global__ void __launch_bounds__(256)
+delete_compact_kernel(const float *__restrict__ X, int64_t N, int D, int k, const int32_t *__restrict__ dead,
+                      const int64_t *__restrict__ before, const int32_t *__restrict__ idx,
+                      const float *__restrict__ d2, const float *__restrict__ beta,
+                      const float *__restrict__ rho, float *__restrict__ Xo, int32_t *__restrict__ io,
+                      float *__restrict__ d2o, float *__restrict__ bo, float *__restrict__ ro) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N || dead[i]) return;
+    const int64_t ni = i - before[i];
+    for (int d = lane; d < D; d += 32) Xo[ni * D + d] = X[i * D + d];
+    int c = 0, removed = 0;
+    for (int t0 = 0; t0 < k; t0 += 32) {
+        const int t = t0 + lane;
+        const int32_t j = t < k ? idx[i * k + t] : -1;
+        const bool gone = j >= 0 && dead[j];
+        const bool stays = j >= 0 && !gone;
+        removed += gone;
+        const unsigned m = __ballot_sync(0xffffffffu, stays);
+        if (stays) {
+            const int pos = c + __popc(m & ((1u << lane) - 1u));
+            io[ni * k + pos] = (int32_t)(j - before[j]);
+            d2o[ni * k + pos] = d2[i * k + t];
+        }
+        c += __popc(m);
+    }
+    for (int t = c + lane; t < k; t += 32) {
+        io[ni * k + t] = -1;
+        d2o[ni * k + t] = INFINITY;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) removed += __shfl_xor_sync(0xffffffffu, removed, o);
+    if (lane == 0) {
+        if (beta) bo[ni] = beta[i];
+        if (rho) ro[ni] = fmaxf(0.f, rho[i] - (float)removed / (float)k);
+    }
+}
+
 }  // namespace
 
 atsne_status gather_hint_launch(const int32_t *rows, int64_t S, int64_t N, int k, const float *d2,
@@ -277,6 +333,48 @@ atsne_status refine_scatter_launch(const int32_t *subset, int64_t S, int64_t N, 
     if (S <= 0) return ATSNE_OK;
     return launch_kernel("refine_scatter", refine_scatter_kernel, ceil_div(S * k, 256), 256, 0,
                          stream, subset, S, N, k, ti, td, tp, tb, idx, d2, P, beta, rho);
+}
+
+size_t delete_workspace(Carver &c, int64_t N, int D, int k, DeleteWs *ws) {
+    DeleteWs w;
+    w.dead = c.take<int32_t>((size_t)N);
+    w.before = c.take<int64_t>((size_t)N + 1);
+    w.total = c.take<int64_t>(1);
+    w.scan = c.take<int64_t>(scan_partials_count(N));
+    w.X = c.take<float>((size_t)N * D);
+    w.idx = c.take<int32_t>((size_t)N * k);
+    w.d2 = c.take<float>((size_t)N * k);
+    w.beta = c.take<float>((size_t)N);
+    w.rho = c.take<float>((size_t)N);
+    if (ws) *ws = w;
+    return c.bytes();
+}
+
+atsne_status delete_launch(const int32_t *rows, int64_t R, float *X, int64_t N, int D, int k, float perplexity,
+                           int32_t *idx, float *d2, float *P, float *beta, float *rho, const DeleteWs &w,
+                           cudaStream_t stream) {
+    int *status = device_status_word();
+    cudaError_t e = cudaMemsetAsync(w.dead, 0, sizeof(int32_t) * (size_t)N, stream);
+    if (e != cudaSuccess) return cuda_error(e, "delete memset");
+    if (R > 0)
+        ATSNE_TRY(launch_kernel("delete_mark", delete_mark_kernel, ceil_div(R, 256), 256, 0, stream, rows, R, N,
+                                w.dead, status));
+    ATSNE_TRY(scan_rowlen(w.dead, N, 0, w.before, w.total, w.scan, stream));
+    ATSNE_TRY(launch_kernel("delete_compact", delete_compact_kernel, ceil_div(N * 32, 256), 256, 0, stream,
+                            (const float *)X, N, D, k, (const int32_t *)w.dead, (const int64_t *)w.before,
+                            (const int32_t *)idx, (const float *)d2, (const float *)beta, (const float *)rho,
+                            w.X, w.idx, w.d2, w.beta, w.rho));
+    const int64_t n = N - R;
+    if (n <= 0) return ATSNE_OK;
+    e = cudaMemcpyAsync(X, w.X, sizeof(float) * (size_t)n * D, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(idx, w.idx, sizeof(int32_t) * (size_t)n * k, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d2, w.d2, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess && rho)
+        e = cudaMemcpyAsync(rho, w.rho, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return cuda_error(e, "delete copy");
+    return calibrate_launch(d2, n, k, perplexity, 1e-5f, 200, P, beta, stream);
 }
 
 atsne_status u8_copy_launch(const char *name, const float *X, int64_t N, int D, int Dp16, uint8_t *xu8,

@@ -20,6 +20,11 @@ Refine of S listed rows:
   compute  their k nearest among the current rows (the filter seeded with each
            row's current k-th distance) and their Gaussians.
   commit   write the rows (rho = 1).
+Delete of R listed rows (Sec. 5.3.2): the points leave every neighbourhood
+  (rho -= 1/k per point removed), the remaining rows move up in order with
+  every index renumbered, and their Gaussians are calibrated again. Row
+  numbers change, so a deletion is admitted only when no other request is in
+  flight, and the requests after it are numbered against the state it leaves.
 """
 import collections
 import time
@@ -27,13 +32,15 @@ import time
 import numpy as np
 import torch
 
-from . import (OP_KNN, OP_KNN_CROSS_RADIUS, atsne_calibrate_P, atsne_commit_rows, atsne_knn,
-               atsne_knn_cross, atsne_knn_rows, atsne_merge_neighbors, knn_opts, workspace_bytes)
+from . import (OP_DELETE, OP_KNN, OP_KNN_CROSS_RADIUS, atsne_calibrate_P, atsne_commit_rows,
+               atsne_delete_rows, atsne_knn, atsne_knn_cross, atsne_knn_rows, atsne_merge_neighbors,
+               knn_opts, workspace_bytes)
 
 
 class Request:
-    """kind "insert" (points: float32 [B][D] host array) or "refine" (rows:
-    int32 [S] host array of existing rows); arrival in seconds."""
+    """kind "insert" (points: float32 [B][D] host array), "refine" or "delete"
+    (rows: int32 [S] host array of existing rows, numbered as the state is when
+    the request is admitted); arrival in seconds."""
 
     def __init__(self, rid, kind, arrival, points=None, rows=None):
         self.rid, self.kind, self.arrival = rid, kind, float(arrival)
@@ -86,6 +93,8 @@ class Server:
             if N > 0:
                 kc = min(k, n)
                 ws += workspace_bytes(OP_KNN_CROSS_RADIUS, n, D, kc, N, self.opts) + N * (kc * 8 + 5)
+        elif req.kind == "delete":
+            ws = workspace_bytes(OP_DELETE, N, D, k)
         else:
             ws = workspace_bytes(OP_KNN, N, D, k, n, self.opts)
         return ws + n * (k * 12 + 8) + (1 << 20)
@@ -99,7 +108,22 @@ class Server:
             raise ValueError("insert beyond the corpus capacity")
         return self.need_bytes(req) + self.reserve <= self.free_bytes()
 
+    def admit_delete(self, req, now):
+        """A deletion on the state stream, all earlier requests done."""
+        st = self.state
+        with torch.cuda.stream(st):
+            rows = torch.from_numpy(np.ascontiguousarray(req.rows, dtype=np.int32)).to(self.dev)
+            self.N = atsne_delete_rows(self.X, rows, self.perp, self.idx, self.d2, self.P, self.beta,
+                                       self.rho, N=self.N, stream=st)
+            done = torch.cuda.Event()
+            done.record(st)
+        self.x_ready = done  # later requests read the compacted rows
+        req.admitted = now
+        self.inflight.append((req, None, done, [rows]))
+
     def admit(self, req, now):
+        if req.kind == "delete":
+            return self.admit_delete(req, now)
         slot = self.free.pop(0)
         s = self.streams[slot]
         keep = []
@@ -182,10 +206,13 @@ class Server:
                 if done.query():
                     req.done = clock() - t0
                     self.inflight.remove(item)
-                    self.free.append(slot)
+                    if slot is not None:
+                        self.free.append(slot)
                     served.append(req)
                     progress = True
             while pending and pending[0].arrival <= now and self.free:
+                if pending[0].kind == "delete" and self.inflight:
+                    break  # renumbering: wait until nothing else is in flight
                 if not self.fits(pending[0]):
                     if not self.inflight:
                         raise MemoryError("request %d does not fit in free device memory"
@@ -209,7 +236,7 @@ def summarize(served):
            "points_per_s": round(pts / span, 1) if span > 0 else None,
            "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
            "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
-    for kind in ("insert", "refine"):
+    for kind in ("insert", "refine", "delete"):
         lk = np.array([r.done - r.arrival for r in served if r.kind == kind])
         if lk.size:
             out[kind] = {"requests": int(lk.size),
