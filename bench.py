@@ -278,10 +278,15 @@ def bench_serving(at, torch, dev, n_max, seed=5):
     closed loop (every request arriving at once) for the capacity, then open
     loop with Poisson arrivals offering 70% of that capacity in points/s
     (inter-arrival time exponential with mean size / rate). Latency = the
-    completion of a request's state commit minus its arrival."""
+    completion of a request's state commit minus its arrival. Then one step of a
+    sliding window on the full corpus (Sec. 5.3.2, Sec. 5.3.1): the oldest
+    `window` rows deleted, `window` new points of the same distribution inserted."""
     from paper_1512_01655_gb300 import synth
     from paper_1512_01655_gb300.serve import Request, Server
-    X, labels = synth.lognormal_clusters(n_max, 50, seed=seed, return_labels=True)
+    window = 50_000
+    X, labels = synth.lognormal_clusters(n_max + window, 50, seed=seed, return_labels=True)
+    X_next = X[n_max:]
+    X, labels = X[:n_max], labels[:n_max]
     N0 = 100_000
     rng = np.random.default_rng(seed + 1)
     seq, n = [], N0  # (kind, payload), in arrival order
@@ -316,10 +321,19 @@ def bench_serving(at, torch, dev, n_max, seed=5):
     srv = Server(X[:N0], capacity=n_max, k=K_NN, perplexity=PERPLEXITY, precision="bf16", slots=4)
     _, opened = srv.run(requests(arr))
     at.atsne_check()
+    # one sliding-window step: delete the oldest rows, insert as many new points
+    win = [Request(0, "delete", 0.0, rows=np.arange(window, dtype=np.int32)),
+           Request(1, "insert", 0.0, points=X_next)]
+    done, _ = srv.run(win)
+    at.atsne_check()
+    lat = {r.kind: round((r.done - r.arrival) * 1e3, 3) for r in done}
+    slide = {"rows": window, "corpus": srv.N, "delete_ms": lat["delete"],
+             "delete_then_insert_ms": lat["insert"]}
     out = {"workload": "log-normal D=50, 30 clusters; corpus %d -> %d rows; %d requests; BF16+rerank; "
                        "4 slots" % (N0, srv.N, len(seq)),
            "capacity_points_per_s": closed["points_per_s"], "offered_points_per_s": round(rate, 1)}
     out.update(opened)
+    out["sliding_window"] = slide
     del srv
     torch.cuda.empty_cache()
     return out

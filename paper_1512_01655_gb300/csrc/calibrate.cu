@@ -28,6 +28,35 @@ namespace {
 
 constexpr int CAL_THREADS = 128;
 
+// Bisection on beta over the shifted distances s_j of one row (returns the
+// final beta and the normaliser Z); GAPS: the row holds absent entries (+inf).
+template <bool GAPS>
+__device__ __forceinline__ void bisect(const float *row, int k, float target, float tol, int max_iter,
+                                       float &bf, float &Z) {
+    float beta = 1.f, lo = 0.f, hi = INFINITY;
+    for (int it = 1;; ++it) {
+        bf = fminf(beta, FLT_MAX);
+        float z = 0.f, ws = 0.f;
+        for (int j = 0; j < k; ++j) {
+            const float s = row[j];
+            if (GAPS && s == INFINITY) continue;  // absent
+            const float w = expf(-bf * s);
+            z += w;
+            ws = fmaf(w, s, ws);
+        }
+        const float H = logf(z) + bf * ws / z;
+        Z = z;
+        if (fabsf(H - target) < tol || it >= max_iter) break;
+        if (H > target) {
+            lo = beta;
+            beta = isinf(hi) ? 2.f * beta : 0.5f * (beta + hi);
+        } else {
+            hi = beta;
+            beta = 0.5f * (lo + beta);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(CAL_THREADS)
 calibrate_kernel(const float *__restrict__ d2, int64_t rows, int k, float perplexity, float target,
                  float tol, int max_iter, float *__restrict__ P, float *__restrict__ beta_out, int *status) {
@@ -61,28 +90,14 @@ calibrate_kernel(const float *__restrict__ d2, int64_t rows, int k, float perple
         // at beta = 0: when n <= perplexity the bisection's limit is beta = 0,
         // a uniform row, which is taken directly
         const bool flat = present > 0 && (float)present <= perplexity;
-        float beta = 1.f, lo = 0.f, hi = INFINITY, bf = 1.f, Z = 1.f;
+        float bf = 1.f, Z = 1.f;
         if (flat) bf = 0.f, Z = (float)present;
-        for (int it = 1; dmin < INFINITY && !flat; ++it) {
-            bf = fminf(beta, FLT_MAX);
-            float z = 0.f, ws = 0.f;
-            for (int j = 0; j < k; ++j) {
-                const float s = row[j];
-                if (s == INFINITY) continue;  // absent
-                const float w = expf(-bf * s);
-                z += w;
-                ws = fmaf(w, s, ws);
-            }
-            const float H = logf(z) + bf * ws / z;
-            Z = z;
-            if (fabsf(H - target) < tol || it >= max_iter) break;
-            if (H > target) {
-                lo = beta;
-                beta = isinf(hi) ? 2.f * beta : 0.5f * (beta + hi);
-            } else {
-                hi = beta;
-                beta = 0.5f * (lo + beta);
-            }
+        // a full row (the usual case) skips the absent-entry test in the sums
+        if (dmin < INFINITY && !flat) {
+            if (present == k)
+                bisect<false>(row, k, target, tol, max_iter, bf, Z);
+            else
+                bisect<true>(row, k, target, tol, max_iter, bf, Z);
         }
         if (dmin == INFINITY) bf = 0.f;  // no neighbour
         const float inv = dmin < INFINITY ? 1.f / Z : 0.f;
