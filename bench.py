@@ -75,6 +75,8 @@ def parse():
                    help="timed runs of the batched refinement workload (0 = skip)")
     p.add_argument("--exact-reps", type=int, default=5,
                    help="timed runs of the exact path alone per precision (0 = skip)")
+    p.add_argument("--checks-sweep", default="32,64,128,256,512,1024,2048,4096",
+                   help="forest checks values for the precision sweep (empty = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=256)
     return p.parse_args()
@@ -386,8 +388,13 @@ def bench_refine_batch(at, torch, dev, stream, reps, peaks):
     """Batched refinement on its own workload: a 500000 x 256 corpus of 100
     Gaussian clusters (sigma 1, centres N(0, 4^2)) and 512 brushed selections
     of 200..20000 points (log-uniform, 1-3 clusters each), refined in one call
-    (Sec. 4.3, 5.1.1). Median of `reps` CUDA-event timed calls after one warm-up;
-    value = selected points (with repeats) per second and union rows per second."""
+    (Sec. 4.3, 5.1.1). The state starts as the approximate one (forest kNN,
+    T = 4, checks = 1024, and its Gaussians) and is restored before every call,
+    outside the timed region, so each refinement starts from approximate rows
+    (their k-th distances bound the filter). Median of `reps` CUDA-event timed
+    calls after one warm-up, with the rule's column split and then with the
+    split atsne_tune_knn picks for the union's shape; value = selected points
+    (with repeats) per second and union rows per second."""
     from paper_1512_01655_gb300 import synth
     X, labels = synth.gaussian_mixture(500_000, 256, n_centres=100, centre_sigma=4.0, seed=4,
                                        return_labels=True)
@@ -396,33 +403,49 @@ def bench_refine_batch(at, torch, dev, stream, reps, peaks):
     Xd = torch.from_numpy(X).to(dev)
     lists = torch.from_numpy(np.concatenate(subs)).to(dev)
     total = int(lists.numel())
-    idx = torch.zeros((N, k), dtype=torch.int32, device=dev)
-    d2 = torch.zeros((N, k), dtype=torch.float32, device=dev)
-    P = torch.zeros((N, k), dtype=torch.float32, device=dev)
-    beta = torch.zeros(N, dtype=torch.float32, device=dev)
+    idx0, d20 = at.atsne_knn(Xd, k, method="forest", trees=4, checks=1024, seed=7)
+    P0, beta0 = at.atsne_calibrate_P(d20, PERPLEXITY)
+    idx, d2, P, beta = idx0.clone(), d20.clone(), P0.clone(), beta0.clone()
     rho = torch.zeros(N, dtype=torch.float32, device=dev)
-    ws = torch.empty(at.workspace_bytes(at.OP_REFINE_BATCH, N, D, k, total), dtype=torch.uint8,
-                     device=dev)
-    cnt = at.atsne_refine_batch(Xd, lists, PERPLEXITY, idx, d2, P, beta, rho, workspace=ws)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        cnt = at.atsne_refine_batch(Xd, lists, PERPLEXITY, idx, d2, P, beta, rho, workspace=ws)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    at.atsne_check()
-    ms = sorted(ts)[len(ts) // 2]
-    union = int(cnt.item())
+
+    def timed():
+        ws = torch.empty(at.workspace_bytes(at.OP_REFINE_BATCH, N, D, k, total), dtype=torch.uint8,
+                         device=dev)
+        ts, cnt = [], None
+        for it in range(reps + 1):
+            for a, b in ((idx, idx0), (d2, d20), (P, P0), (beta, beta0)):
+                a.copy_(b)
+            rho.fill_(0.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cnt = at.atsne_refine_batch(Xd, lists, PERPLEXITY, idx, d2, P, beta, rho, workspace=ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:
+                ts.append(e0.elapsed_time(e1))
+        at.atsne_check()
+        return sorted(ts)[len(ts) // 2], int(cnt.item())
+
+    at.atsne_tune_clear()
+    ms_rule, union = timed()
+    rows_max = min(N, total)
+    q = torch.arange(rows_max, dtype=torch.int32, device=dev)
+    splits, _ = at.atsne_tune_knn(Xd, k, queries=q, precision="fp32")
+    del q
+    ms_tuned, union = timed()
+    at.atsne_tune_clear()
+    ms = min(ms_rule, ms_tuned)
     flops = 2.0 * union * N * D
     peak = peaks.get("bf16_tflops", 1900.0)
     ach = flops / (ms / 1e3) / 1e12
-    return {"workload": "500000x256 fp32, 100 Gaussian clusters; 512 selections of 200..20000 points",
+    return {"workload": "500000x256 fp32, 100 Gaussian clusters; 512 selections of 200..20000 points; "
+                        "state restored to the forest kNN (T=4, checks=1024) before every call",
             "selections": len(subs), "listed_points": total, "union_rows": union,
-            "ms": round(ms, 2), "listed_points_per_s": round(total / (ms / 1e3), 1),
+            "ms": round(ms, 2), "ms_rule_split": round(ms_rule, 2), "ms_tuned_split": round(ms_tuned, 2),
+            "tuned_splits": splits,
+            "listed_points_per_s": round(total / (ms / 1e3), 1),
             "union_rows_per_s": round(union / (ms / 1e3), 1),
             "tensor": {"achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s (algorithmic 2*U*N*D)",
                        "frac": round(ach / peak, 4), "tensor_passes": 3}}
@@ -654,6 +677,34 @@ def run_ours(args, world, rank, local, pg):
                 entry["recall_vs_fp32"] = round(at.atsne_knn_precision(idx_p, ref_idx)[1], 6)
             exact_p[prec] = entry
 
+    # the approximate path's precision knob: rho (Eq. 9) of the forest search
+    # against the exact FP32 neighbourhoods at each checks value, one forest
+    # (the step's options), median of 3 timed searches after one warm-up
+    sweep = None
+    if args.checks_sweep:
+        sweep = []
+        ref_idx, _ = at.atsne_knn(X, K_NN, opts=pipe.exact_opts)
+        forest = at.atsne_forest_build(X, opts=pipe.forest_opts)
+        for c in [int(v) for v in args.checks_sweep.split(",")]:
+            at.atsne_forest_query(X, forest, K_NN, checks=c)
+            ts = []
+            for _ in range(3):
+                if l2_flush is not None:
+                    l2_flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                idx_c, _, ev_c = at.atsne_forest_query(X, forest, K_NN, checks=c)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            med = sorted(ts)[1]
+            sweep.append({"checks": c, "rho": round(at.atsne_knn_precision(idx_c, ref_idx)[1], 5),
+                          "evaluated_mean": round(float(ev_c.double().mean().item()), 1),
+                          "ms": round(med, 3), "points_per_s": round(N / (med / 1e3), 1)})
+        at.atsne_check()
+        del forest, ref_idx
+
     serving = None
     if args.serve_max > 0 and world == 1:
         serving = bench_serving(at, torch, dev, args.serve_max)
@@ -691,7 +742,7 @@ def run_ours(args, world, rank, local, pg):
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
             "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
-            "refine_batch": refine_batch, "kde": kde, "serving": serving,
+            "forest_checks_sweep": sweep, "refine_batch": refine_batch, "kde": kde, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }

@@ -67,7 +67,8 @@ typedef enum {
     ATSNE_OP_REFINE_BATCH = 6, /* S = total entries of the concatenated selections */
     ATSNE_OP_KNN_CROSS = 7,    /* N = corpus rows, S = query rows */
     ATSNE_OP_KNN_CROSS_RADIUS = 8, /* as KNN_CROSS, with per-row radii */
-    ATSNE_OP_DELETE = 9            /* N = rows before the deletion, D, k */
+    ATSNE_OP_DELETE = 9,           /* N = rows before the deletion, D, k */
+    ATSNE_OP_TUNE_KNN = 10         /* as ATSNE_OP_KNN: the largest candidate's workspace */
 } atsne_op;
 
 /* Options of the kNN step. atsne_knn_opts_default() fills the defaults. */
@@ -218,6 +219,34 @@ atsne_status atsne_knn_rows(const float *X, int64_t N, int32_t D, const int32_t 
                             int32_t k, const atsne_knn_opts *opts, const float *hint_d2,
                             int32_t *idx_out, float *d2_out, void *workspace, size_t ws_bytes,
                             void *stream);
+
+/*
+ * Autotuner of the exact tensor-core kNN. Its tunable is the column split: the
+ * corpus columns are cut into `splits` ranges, each (row tile, range) unit runs
+ * its own streaming top-k, and the partial lists are merged. Fewer splits mean
+ * fewer survivors to merge, more splits more units to fill the SMs with when
+ * the rows are few. This call times the candidates (one split, and the counts
+ * giving about 152 .. 8192 units) on the given problem (the kNN of
+ * atsne_knn with method EXACT on the tensor cores: `queries` [S] or all N rows
+ * when NULL), one warm-up and two timed runs each with CUDA events, and
+ * records the fastest for the shape (N, D, rows, k, precision, rerank_k) in a
+ * process-wide table. Every later call of that shape uses it: atsne_knn,
+ * atsne_knn_rows, atsne_knn_cross (rows = query rows), atsne_refine_subset
+ * (FP32, rows = S) and atsne_refine_batch (FP32, rows = min(N, total)). The
+ * workspace such calls need depends on the recorded split, so size it after
+ * tuning. Results do not depend on the split (every split yields the exact
+ * neighbourhoods), only the time does.
+ *  idx_out/d2_out [rows][k]: scratch, left holding the last run's result.
+ *  splits_out, ms_out (host, may be NULL): the chosen split and its time.
+ * Synchronises the stream (not for use inside a stream capture).
+ * Workspace: atsne_workspace_bytes(ATSNE_OP_TUNE_KNN, N, D, k, S, opts).
+ */
+atsne_status atsne_tune_knn(const float *X, int64_t N, int32_t D, const int32_t *queries, int64_t S,
+                            int32_t k, const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                            void *workspace, size_t ws_bytes, void *stream, int32_t *splits_out,
+                            float *ms_out);
+/* Forgets every split recorded by atsne_tune_knn (the rule applies again). */
+atsne_status atsne_tune_clear(void);
 
 /*
  * k nearest rows of Xc for each row of Xq, Eq. 8 across two point sets; no

@@ -17,7 +17,7 @@ ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPP
 KNN_EXACT, KNN_FOREST = 0, 1
 FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK = 0, 1, 2, 3
 (OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY,
- OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS, OP_DELETE) = range(10)
+ OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS, OP_DELETE, OP_TUNE_KNN) = range(11)
 
 EXPORTED = (
     "atsne_knn_opts_default", "atsne_workspace_bytes", "atsne_knn", "atsne_calibrate_P",
@@ -26,7 +26,8 @@ EXPORTED = (
     "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
     "atsne_refine_subset_noalloc", "atsne_refine_batch", "atsne_kde_map", "atsne_knn_cross",
     "atsne_knn_rows",
-    "atsne_merge_neighbors", "atsne_commit_rows", "atsne_delete_rows",
+    "atsne_merge_neighbors", "atsne_commit_rows", "atsne_delete_rows", "atsne_tune_knn",
+    "atsne_tune_clear",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
@@ -90,6 +91,9 @@ def lib():
                                         _vp, _vp, _vp]
         L.atsne_delete_rows.argtypes = [_vp, _i64, _vp, _i64, _i32, _i32, _f32, _vp, _vp, _vp, _vp,
                                         _vp, _vp, _sz, _vp]
+        L.atsne_tune_knn.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, ctypes.POINTER(KnnOpts), _vp,
+                                     _vp, _vp, _sz, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f32)]
+        L.atsne_tune_clear.argtypes = []
         L.atsne_kde_map.argtypes = [_vp, _i64, _vp, _vp, _f32, _f32, _f32, _i32, _i32, _f32, _f32,
                                     _f32, _vp, _vp, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
@@ -175,6 +179,33 @@ def atsne_knn(X, k, queries=None, opts=None, stream=None, **kw):
     _raise(lib().atsne_knn(_p(X), N, D, _p(queries), S, k, ctypes.byref(o), _p(idx), _p(d2),
                            _p(ws), ws.numel(), _stream(stream)))
     return idx, d2
+
+
+def atsne_tune_knn(X, k, queries=None, opts=None, stream=None, **kw):
+    """Times the exact tensor-core kNN's column-split candidates on this problem
+    and records the fastest for its shape (later calls of the shape use it);
+    returns (splits, ms). Synchronises the stream."""
+    _dev(X, torch.float32, "X")
+    N, D = X.shape
+    o = opts or knn_opts(**kw)
+    S = 0
+    if queries is not None:
+        _dev(queries, torch.int32, "queries")
+        S = queries.shape[0]
+    rows = S if queries is not None else N
+    idx = torch.empty((rows, k), dtype=torch.int32, device=X.device)
+    d2 = torch.empty((rows, k), dtype=torch.float32, device=X.device)
+    ws = _workspace(workspace_bytes(OP_TUNE_KNN, N, D, k, S, o), X.device)
+    splits, ms = _i32(0), _f32(0.0)
+    _raise(lib().atsne_tune_knn(_p(X), N, D, _p(queries), S, k, ctypes.byref(o), _p(idx), _p(d2),
+                                _p(ws), ws.numel(), _stream(stream), ctypes.byref(splits),
+                                ctypes.byref(ms)))
+    return int(splits.value), float(ms.value)
+
+
+def atsne_tune_clear():
+    """Forgets every recorded split (the rule applies again)."""
+    _raise(lib().atsne_tune_clear())
 
 
 def atsne_calibrate_P(d2, perplexity, tol=0.0, max_iter=0, stream=None, P_out=None, beta_out=None):

@@ -1,6 +1,7 @@
 // C ABI entry points (declared in include/atsne.h): argument validation on the
 // host, workspace layouts, the device status word, launch profiling, and the
 // composition of kernels into the four operations.
+#include <float.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -268,6 +269,23 @@ size_t cross_ws(Carver &c, int64_t Nq, int64_t Nc, int32_t D, int32_t k, const a
     return c.bytes();
 }
 
+// Autotuner: room for the largest candidate's tensor-core workspace.
+constexpr int TUNE_MAX_CAND = 8;
+size_t tune_ws(int64_t N, int32_t D, int32_t k, int64_t S, const atsne_knn_opts &o, int *cand, int *n_cand) {
+    const int64_t Q = S > 0 ? S : N;
+    int c_[TUNE_MAX_CAND];
+    int *cs = cand ? cand : c_;
+    const int n = tc_split_candidates(N, D, Q, k, o.precision, o.rerank_k, cs, TUNE_MAX_CAND);
+    if (n_cand) *n_cand = n;
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        Carver c(nullptr);
+        tc_workspace(c, N, D, Q, S > 0, tc_plan(N, D, Q, k, o.precision, o.rerank_k, cs[i]), nullptr);
+        if (c.bytes() > need) need = c.bytes();
+    }
+    return need;
+}
+
 // Batched refinement: the union's rows (padded to min(N, total)), its bitmap,
 // then the refinement of that many rows.
 size_t refine_batch_ws(Carver &c, int64_t N, int32_t D, int64_t total, int32_t k, int32_t **rows,
@@ -326,6 +344,8 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
         return cross_ws(c, S, N, D, k, o, false, nullptr, nullptr);
     case ATSNE_OP_DELETE:
         return delete_workspace(c, N, D, k, nullptr);
+    case ATSNE_OP_TUNE_KNN:
+        return exact_on_tensor_cores(o, k) ? tune_ws(N, D, k, S, o, nullptr, nullptr) : 0;
     case ATSNE_OP_KNN_CROSS_RADIUS:
         return cross_ws(c, S, N, D, k, o, true, nullptr, nullptr);
     case ATSNE_OP_REFINE_BATCH:
@@ -367,6 +387,68 @@ atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *quer
     if ((st = forest_build_launch(X, f, sub, sub_bytes, stream))) return st;
     return forest_query_launch(X, f, queries, nq, k, o.checks, queue_capacity(o), idx_out, d2_out,
                                nullptr, sub, sub_bytes, stream);
+}
+
+atsne_status atsne_tune_knn(const float *X, int64_t N, int32_t D, const int32_t *queries, int64_t S,
+                            int32_t k, const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                            void *workspace, size_t ws_bytes, void *stream_, int32_t *splits_out,
+                            float *ms_out) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_status st = validate_xk(X, N, D, k);
+    if (st) return st;
+    const atsne_knn_opts o = opts_or_default(opts);
+    if ((st = validate_knn_opts(o))) return st;
+    if (!exact_on_tensor_cores(o, k))
+        return set_error(ATSNE_EUNSUPPORTED, "tune: only the exact kNN on the tensor cores has a tunable");
+    if (!idx_out || !d2_out) return set_error(ATSNE_EINVAL, "tune: NULL output");
+    if (queries && S < 1) return set_error(ATSNE_EINVAL, "tune: S=%lld < 1", (long long)S);
+    const int64_t Q = queries ? S : N;
+    int cand[TUNE_MAX_CAND], n_cand = 0;
+    const size_t need = tune_ws(N, D, k, queries ? S : 0, o, cand, &n_cand);
+    if (!workspace || ws_bytes < need)
+        return set_error(ATSNE_ENOMEM, "tune: workspace of %zu bytes, %zu needed", ws_bytes, need);
+    if ((st = check_base(workspace, "tune workspace"))) return st;
+    if (queries && (st = check_indices(queries, S, N, stream))) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = FLT_MAX;
+    for (int i = 0; i < n_cand && e == cudaSuccess && st == ATSNE_OK; ++i) {
+        const TcPlan pl = tc_plan(N, D, Q, k, o.precision, o.rerank_k, cand[i]);
+        Carver c(workspace);
+        TcWs w;
+        tc_workspace(c, N, D, Q, queries != nullptr, pl, &w);
+        float ms = FLT_MAX;
+        for (int rep = 0; rep < 3 && st == ATSNE_OK && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, stream);
+            if (e != cudaSuccess) break;
+            st = knn_exact_tc(X, N, D, queries, Q, k, pl, w, idx_out, d2_out, stream);
+            if (st) break;
+            e = cudaEventRecord(e1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && rep > 0 && t < ms) ms = t;  // the first run warms up
+        }
+        if (st == ATSNE_OK && e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = pl.splits;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_error(e, "tune");
+    set_tuned_splits(N, D, Q, k, o.precision, o.rerank_k, best);
+    if (splits_out) *splits_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return ATSNE_OK;
+}
+
+atsne_status atsne_tune_clear(void) {
+    clear_tuned_splits();
+    return ATSNE_OK;
 }
 
 atsne_status atsne_calibrate_P(const float *d2, int64_t rows, int32_t k, float perplexity,

@@ -36,7 +36,14 @@ struct TcWs {
     float *qnrm = nullptr, *qstats = nullptr;   // queries from another array: norms, error stats
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
 };
-TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k);
+// splits > 0 forces the column split count; else the one atsne_tune_knn
+// recorded for this shape, else the rule.
+TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int splits = 0);
+int tuned_splits(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k);
+void set_tuned_splits(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int splits);
+void clear_tuned_splits();
+// Distinct column split counts worth timing for a shape (at most max_out).
+int tc_split_candidates(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int *out, int max_out);
 size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcPlan &pl, TcWs *ws);
 // Xq != nullptr: the Q queries are the rows of Xq (another array), none excluded.
 // radius != nullptr (with Xq): only neighbours with d^2 < radius[row] are kept,

@@ -47,6 +47,9 @@
 #include <limits.h>
 #include <math.h>
 
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
@@ -1235,7 +1238,55 @@ atsne_status radius_filter_launch(int32_t *idx, float *d2, int64_t rows, int k, 
                          idx, d2, rows, k, radius);
 }
 
-TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) {
+// Column splits chosen by atsne_tune_knn, per problem shape (process-wide).
+namespace {
+struct TunedSplit {
+    int64_t N, Q;
+    int D, k, precision, rerank_k, splits;
+};
+std::mutex g_tuned_mu;
+std::vector<TunedSplit> g_tuned;
+}  // namespace
+
+int tuned_splits(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) {
+    std::lock_guard<std::mutex> g(g_tuned_mu);
+    for (const TunedSplit &t : g_tuned)
+        if (t.N == N && t.Q == Q && t.D == D && t.k == k && t.precision == precision && t.rerank_k == rerank_k)
+            return t.splits;
+    return 0;
+}
+
+void set_tuned_splits(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int splits) {
+    std::lock_guard<std::mutex> g(g_tuned_mu);
+    for (TunedSplit &t : g_tuned)
+        if (t.N == N && t.Q == Q && t.D == D && t.k == k && t.precision == precision && t.rerank_k == rerank_k) {
+            t.splits = splits;
+            return;
+        }
+    g_tuned.push_back({N, Q, D, k, precision, rerank_k, splits});
+}
+
+void clear_tuned_splits() {
+    std::lock_guard<std::mutex> g(g_tuned_mu);
+    g_tuned.clear();
+}
+
+int tc_split_candidates(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int *out, int max_out) {
+    const int64_t row_tiles = (Q + TC_BM - 1) / TC_BM;
+    const int64_t units[] = {0, 152, 304, 608, 1216, 2048, 4096, 8192};
+    int n = 0;
+    for (int64_t u : units) {
+        if (n == max_out) break;
+        const int want = u == 0 ? 1 : (int)((u + row_tiles - 1) / row_tiles);
+        const int s = tc_plan(N, D, Q, k, precision, rerank_k, want).splits;
+        bool dup = false;
+        for (int i = 0; i < n; ++i) dup |= out[i] == s;
+        if (!dup) out[n++] = s;
+    }
+    return n;
+}
+
+TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int splits) {
     TcPlan pl;
     pl.passes = precision == ATSNE_FP32 ? 3 : precision == ATSNE_FP8_RERANK ? 8 : 1;
     const int ke = pl.passes == 8 ? 128 : TC_BK;  // elements per 128-byte row
@@ -1246,7 +1297,8 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k) 
     // alone give every SM at least two units (a split restarts the streaming
     // top-k, whose k' ln(n / k') survivors dominate the epilogue), else about
     // 2048 units, each at least 4 column tiles long
-    int64_t S = pl.row_tiles >= 304 ? 1 : (2048 + pl.row_tiles - 1) / pl.row_tiles;
+    if (splits <= 0) splits = tuned_splits(N, D, Q, k, precision, rerank_k);
+    int64_t S = splits > 0 ? splits : pl.row_tiles >= 304 ? 1 : (2048 + pl.row_tiles - 1) / pl.row_tiles;
     const int64_t max_s = (col_tiles + 3) / 4;
     if (S > max_s) S = max_s;
     if (S < 1) S = 1;
