@@ -632,13 +632,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 const uint32_t taddr = tbase + lane_base + (uint32_t)(acc * TC_BN);
                 // the query's own column, if in this tile (none for another array's queries)
                 const int self_off = cross ? INT_MIN / 2 : qid - (int)ct;
+                // two register sets: the next chunk's load is in flight while
+                // this one's keys are filtered
+                uint32_t ra[32], rb[32];
+                tmem_ld32(taddr, ra);
 #pragma unroll
                 for (int c = 0; c < TC_BN / 32; ++c) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + (uint32_t)(c * 32), r);
+                    uint32_t(&r)[32] = (c & 1) ? rb : ra;
+                    uint32_t(&rn)[32] = (c & 1) ? ra : rb;
                     nyw[lane] = nyc[c];
                     if (PASSES == 8) msw[lane] = msc[c];
-                    tmem_ld_wait();
+                    tmem_ld_wait(r);
+                    if (c + 1 < TC_BN / 32) tmem_ld32(taddr + (uint32_t)((c + 1) * 32), rn);
                     __syncwarp();
                     // branch-free filter: 32 keys, one survivor bit each
                     float kk[32];
