@@ -267,17 +267,46 @@ __device__ __forceinline__ void cq_push_lanes(ColQueue &q, uint64_t e, bool vali
     }
 }
 
+// A lane's fixed place in a five-level descent subtree (lane l < 31 holds
+// subtree node l in level order): its level, its offset below the subtree
+// root's first descendant on that level, the bit of its parent's outcome that
+// leads to it, and the set of its ancestors (itself included).
+struct SubLane {
+    int lvl, off, par;
+    bool left;         // a left child: reached when the parent's query value is below its split
+    unsigned anc;      // lanes of the node and its ancestors
+    unsigned lvl_mask; // lane j < 5: the lanes of subtree level j
+};
+
+__device__ __forceinline__ SubLane sub_lane(int lane) {
+    SubLane L;
+    L.lvl = 31 - __clz(lane + 1);
+    L.off = lane - (1 << L.lvl);
+    L.par = lane > 0 ? (lane - 1) >> 1 : 0;
+    L.left = (lane & 1) != 0;
+    L.anc = 0;
+    for (int a = lane; ; a = (a - 1) >> 1) {
+        L.anc |= 1u << a;
+        if (a == 0) break;
+    }
+    L.lvl_mask = lane < 5 ? ((1u << ((2 << lane) - 1)) - 1u) & ~((1u << ((1 << lane) - 1)) - 1u) : 0u;
+    return L;
+}
+
 // Descend tree `tr` from node v (queue key `key`) to a leaf, pushing the far
 // child of every node passed whose key is at most `cut`; returns the leaf index. Each round covers up to
 // five levels: lane j < 31 loads node j of the five-level subtree below the
 // current node and compares the query with its split, a ballot of the
 // outcomes gives the path, and lane j < (levels) pushes the far child of the
-// path's node on level j. With PT (one point per leaf) the last round also
-// fetches the points of the subtree's leaves and `pt` returns the reached
-// leaf's point (-1 if empty). Node ids fit in 26 bits.
+// path's node on level j. A node is on the path when every node from the
+// subtree root down to it is the child its parent's outcome selects: one
+// ballot of "my parent leads to me" tested against each lane's ancestor set.
+// With PT (one point per leaf) the last round also fetches the points of the
+// subtree's leaves and `pt` returns the reached leaf's point (-1 if empty).
+// Node ids fit in 26 bits.
 template <bool PT, typename QT>
 __device__ __forceinline__ int descend(const FqArgs &A, const QT *qv, ColQueue &q, int tr, int v,
-                                       float key, float cut, int lane, int &pt) {
+                                       float key, float cut, int lane, const SubLane &L, int &pt) {
     const int64_t tb = (int64_t)tr * A.n_int;
     const int32_t *sd = A.split_dim + tb;
     const float *sv = A.split_val + tb;
@@ -292,10 +321,10 @@ __device__ __forceinline__ int descend(const FqArgs &A, const QT *qv, ColQueue &
         int node = 0, lp = -1;
         bool left = false;
         float fk = INFINITY;
-        if (lane < (1 << d) - 1) {
+        const bool in_sub = lane < (1 << d) - 1;
+        if (in_sub) {
             // lane = node (lane + 1 - 2^j) of level j below v, j = floor(log2(lane + 1))
-            const int j = 31 - __clz(lane + 1);
-            node = ((v + 1) << j) + lane - (1 << j);
+            node = ((v + 1) << L.lvl) + L.off;
             const float qd = (float)qv[sd[node]];
             const float val = sv[node];
             left = qd < val;
@@ -304,14 +333,11 @@ __device__ __forceinline__ int descend(const FqArgs &A, const QT *qv, ColQueue &
         }
         if (PT && last && lane < (1 << d)) lp = lpt[((v + 1) << d) - 1 + lane - n_int];
         const unsigned lm = __ballot_sync(FULL, left);
-        int c = 0, my_c = 0;
-#pragma unroll
-        for (int j = 0; j < SUB_DEPTH; ++j) {
-            if (j < d) {
-                if (lane == j) my_c = c;
-                c = 2 * c + 2 - (int)((lm >> c) & 1u);
-            }
-        }
+        const unsigned okm = __ballot_sync(FULL, in_sub && (lane == 0 || (((lm >> L.par) & 1u) != 0) == L.left));
+        const unsigned pm = __ballot_sync(FULL, in_sub && (okm & L.anc) == L.anc);  // one node per level
+        const int my_c = lane < d ? __ffs(pm & L.lvl_mask) - 1 : 0;
+        const int cl = 31 - __clz(pm);  // the path's node on the last level of the round
+        const int c = 2 * cl + 2 - (int)((lm >> cl) & 1u);
         const float pk = __shfl_sync(FULL, fk, my_c);
         const int pn = __shfl_sync(FULL, node, my_c);
         const uint64_t e = qpack(pk, tr, ((lm >> my_c) & 1u) ? 2 * pn + 2 : 2 * pn + 1);
@@ -332,6 +358,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
     if (QB != (A.xu8 != nullptr && *A.u8_bad == 0u)) return;
     extern __shared__ __align__(16) unsigned char fq_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const SubLane SL = sub_lane(lane);
     const size_t heap_b = (size_t)((A.qcap + 31) >> 5) * 32 * 8;
     const size_t q_b = QB ? (size_t)A.Dp16 : ((size_t)A.D * 4 + 15) & ~size_t(15);
     unsigned char *base = fq_smem + w * (heap_b + q_b);
@@ -448,7 +475,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
                     int hp_ = -1;
                     float key = 0.f;
                     if (t < A.T) {
-                        descend<true, QT>(A, qv, q, t, 0, 0.f, cut, lane, hp_);
+                        descend<true, QT>(A, qv, q, t, 0, 0.f, cut, lane, SL, hp_);
                         ++t;
                     } else {
                         if (q.n == 0) break;
@@ -456,7 +483,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
                         key = __uint_as_float((uint32_t)(e >> 32));
                         const int tr = (int)((e >> 26) & 63u);
                         const int v = (int)(e & ((1u << 26) - 1u));
-                        descend<true, QT>(A, qv, q, tr, v, key, cut, lane, hp_);
+                        descend<true, QT>(A, qv, q, tr, v, key, cut, lane, SL, hp_);
                     }
                     // the word is loaded now and only read at the next step
                     uint32_t hw = hp_ >= 0 ? __ldcg(&seen[hp_ >> 5]) : 0u;
@@ -475,7 +502,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
             } else {
                 int unused;
                 for (int t = 0; t < A.T && evaluated < need; ++t) {
-                    scan_leaf(t, descend<false, QT>(A, qv, q, t, 0, 0.f, cut, lane, unused));
+                    scan_leaf(t, descend<false, QT>(A, qv, q, t, 0, 0.f, cut, lane, SL, unused));
                     kfin = 0.f;
                 }
                 while (evaluated < need && q.n > 0) {
@@ -483,7 +510,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
                     const float key = __uint_as_float((uint32_t)(e >> 32));
                     const int tr = (int)((e >> 26) & 63u);
                     const int v = (int)(e & ((1u << 26) - 1u));
-                    scan_leaf(tr, descend<false, QT>(A, qv, q, tr, v, key, cut, lane, unused));
+                    scan_leaf(tr, descend<false, QT>(A, qv, q, tr, v, key, cut, lane, SL, unused));
                     kfin = key;
                 }
             }
