@@ -122,3 +122,28 @@ def test_insertion_fills_the_holes(at):
     clear = (o_d2[:, k] - o_d2[:, k - 1]) / o_d2[:, k] > 1e-4
     for r in np.flatnonzero(clear):
         assert set(g_idx[n0 + r]) == set(o_idx[r, :k])
+
+
+def test_delete_edge_cases(at):
+    mu, k = 4.0, 12
+    X, Xd, idx, d2, P, beta, rho = _state(at, 500, 8, k, mu, seed=9)
+    before = [t.clone() for t in (Xd, idx, d2, P, beta, rho)]
+    # nothing deleted: the state stays, its Gaussians calibrated again (the same)
+    n = at.atsne_delete_rows(Xd, to_dev(np.zeros(0, np.int32)), mu, idx, d2, P, beta, rho)
+    at.atsne_check()
+    assert n == 500
+    for a, b in zip((Xd, idx, d2, P, beta, rho), before):
+        assert torch.equal(a, b)
+    # a row listed twice is refused through the status word
+    n = at.atsne_delete_rows(Xd, to_dev(np.array([3, 3], np.int32)), mu, idx, d2, P, beta, rho)
+    with pytest.raises(at.AtsneError):
+        at.atsne_check()
+    # every row deleted: nothing remains
+    X, Xd, idx, d2, P, beta, rho = _state(at, 300, 8, k, mu, seed=10)
+    n = at.atsne_delete_rows(Xd, to_dev(np.arange(300, dtype=np.int32)), mu, idx, d2, P, beta, rho)
+    at.atsne_check()
+    assert n == 0
+    # more rows than the state holds: refused on the host
+    with pytest.raises(at.AtsneError):
+        at.atsne_delete_rows(Xd, to_dev(np.arange(301, dtype=np.int32) % 300), mu, idx, d2, P, beta,
+                             rho, N=300)
