@@ -281,6 +281,16 @@ atsne_status atsne_knn_cross(const float *Xq, int64_t Nq, const float *Xc, int64
  * receives 1 for a row whose list changed. rho is not touched (insertion does
  * not lower the precision); re-run atsne_calibrate_P on the changed rows.
  */
+/*
+ * d_i^Max of Eq. 11 (Sec. 5.3.1) for each row: the squared distance of its
+ * farthest neighbour in N_i as it stands, i.e. the largest finite entry of
+ * d2[i] (entries of +inf are absent neighbours, left by atsne_delete_rows),
+ * or +inf for a row with no neighbour left. With these radii
+ * atsne_knn_cross finds the new points that enter each row.
+ *  d2 [rows][k] fp32 (device), dmax_out [rows] fp32 (device).
+ */
+atsne_status atsne_row_dmax(const float *d2, int64_t rows, int32_t k, float *dmax_out, void *stream);
+
 atsne_status atsne_merge_neighbors(int32_t *idx, float *d2, int64_t rows, int32_t k,
                                    const int32_t *cand_idx, const float *cand_d2, int32_t kc,
                                    int32_t index_offset, uint8_t *changed, void *stream);
@@ -296,8 +306,9 @@ atsne_status atsne_merge_neighbors(int32_t *idx, float *d2, int64_t rows, int32_
  * compacted in place and every index renumbered. Every remaining row's Gaussian
  * is then calibrated again over its remaining neighbours (Eq. 3, Eq. 4 over
  * N_i; bisection as atsne_calibrate_P with its default tolerance), which the
- * absent entries do not enter. Later insertions fill absent entries first (their
- * d_i^Max is +inf). An index out of range or listed twice raises the device
+ * absent entries do not enter. A later insertion fills an absent entry with a
+ * new point closer than the row's farthest remaining neighbour (d_i^Max over
+ * N_i as it stands, atsne_row_dmax). An index out of range or listed twice raises the device
  * status (ATSNE_EINVAL from atsne_check) and leaves the state unspecified.
  * Workspace: atsne_workspace_bytes(ATSNE_OP_DELETE, N, D, k, 0, NULL).
  */

@@ -26,7 +26,7 @@ EXPORTED = (
     "atsne_profile_enable", "atsne_profile_reset", "atsne_profile_read", "atsne_launch_count",
     "atsne_refine_subset_noalloc", "atsne_refine_batch", "atsne_kde_map", "atsne_knn_cross",
     "atsne_knn_rows",
-    "atsne_merge_neighbors", "atsne_commit_rows", "atsne_delete_rows", "atsne_tune_knn",
+    "atsne_merge_neighbors", "atsne_commit_rows", "atsne_delete_rows", "atsne_tune_knn", "atsne_row_dmax",
     "atsne_tune_clear",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
@@ -94,6 +94,7 @@ def lib():
         L.atsne_tune_knn.argtypes = [_vp, _i64, _i32, _vp, _i64, _i32, ctypes.POINTER(KnnOpts), _vp,
                                      _vp, _vp, _sz, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f32)]
         L.atsne_tune_clear.argtypes = []
+        L.atsne_row_dmax.argtypes = [_vp, _i64, _i32, _vp, _vp]
         L.atsne_kde_map.argtypes = [_vp, _i64, _vp, _vp, _f32, _f32, _f32, _i32, _i32, _f32, _f32,
                                     _f32, _vp, _vp, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
@@ -201,6 +202,16 @@ def atsne_tune_knn(X, k, queries=None, opts=None, stream=None, **kw):
                                 _p(ws), ws.numel(), _stream(stream), ctypes.byref(splits),
                                 ctypes.byref(ms)))
     return int(splits.value), float(ms.value)
+
+
+def atsne_row_dmax(d2, stream=None, out=None):
+    """d_i^Max of Eq. 11 per row: the largest present (finite) entry of d2,
+    +inf for a row with none."""
+    _dev(d2, torch.float32, "d2")
+    rows, k = d2.shape
+    dmax = torch.empty(rows, dtype=torch.float32, device=d2.device) if out is None else out
+    _raise(lib().atsne_row_dmax(_p(d2), rows, k, _p(dmax), _stream(stream)))
+    return dmax
 
 
 def atsne_tune_clear():

@@ -647,6 +647,12 @@ atsne_status atsne_knn_cross(const float *Xq, int64_t Nq, const float *Xc, int64
     return radius_d2 ? radius_filter_launch(idx_out, d2_out, Nq, k, radius_d2, stream) : ATSNE_OK;
 }
 
+atsne_status atsne_row_dmax(const float *d2, int64_t rows, int32_t k, float *dmax_out, void *stream) {
+    if (rows < 0 || k < 1) return set_error(ATSNE_EINVAL, "row dmax: rows=%lld k=%d", (long long)rows, k);
+    if (rows > 0 && (!d2 || !dmax_out)) return set_error(ATSNE_EINVAL, "row dmax: NULL pointer");
+    return row_dmax_launch(d2, rows, k, dmax_out, static_cast<cudaStream_t>(stream));
+}
+
 atsne_status atsne_merge_neighbors(int32_t *idx, float *d2, int64_t rows, int32_t k,
                                    const int32_t *cand_idx, const float *cand_d2, int32_t kc,
                                    int32_t index_offset, uint8_t *changed, void *stream) {

@@ -83,6 +83,7 @@ atsne_status kde_launch(const float *Y, int64_t N, const float *rho, const uint8
                         float y0, float pixel, int W, int H, float h, float cutoff, float lens_k,
                         float *f_out, float *s_out, float *a_out, float *alpha_out,
                         cudaStream_t stream);
+atsne_status row_dmax_launch(const float *d2, int64_t rows, int k, float *dmax, cudaStream_t stream);
 atsne_status gather_hint_launch(const int32_t *rows, int64_t S, int64_t N, int k, const float *d2,
                                 float *hint, cudaStream_t stream);
 atsne_status merge_neighbors_launch(int32_t *idx, float *d2, int64_t rows, int k, const int32_t *cidx,

@@ -187,6 +187,20 @@ merge_neighbors_kernel(int32_t *__restrict__ idx, float *__restrict__ d2, int64_
 
 // hint[s] = d2[rows[s]][k-1]: a listed row's current k-th squared distance,
 // an upper bound of its exact one when the row lists k real points.
+// d_i^Max of Eq. 11 over N_i as it stands: the largest distance among the
+// row's present entries (+inf marks an absent one), +inf when none is left.
+__global__ void row_dmax_kernel(const float *__restrict__ d2, int64_t rows, int k, float *__restrict__ dmax) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    const float *r = d2 + i * k;
+    float m = -1.f;
+    for (int j = 0; j < k; ++j) {
+        const float v = r[j];
+        if (v < INFINITY) m = fmaxf(m, v);
+    }
+    dmax[i] = m < 0.f ? INFINITY : m;
+}
+
 __global__ void gather_hint_kernel(const int32_t *__restrict__ rows, int64_t S, int64_t N, int k,
                                    const float *__restrict__ d2, float *__restrict__ hint) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -283,6 +297,11 @@ delete_compact_kernel(const float *__restrict__ X, int64_t N, int D, int k, cons
 }
 
 }  // namespace
+
+atsne_status row_dmax_launch(const float *d2, int64_t rows, int k, float *dmax, cudaStream_t stream) {
+    if (rows <= 0) return ATSNE_OK;
+    return launch_kernel("row_dmax", row_dmax_kernel, ceil_div(rows, 256), 256, 0, stream, d2, rows, k, dmax);
+}
 
 atsne_status gather_hint_launch(const int32_t *rows, int64_t S, int64_t N, int k, const float *d2,
                                 float *hint, cudaStream_t stream) {

@@ -13,7 +13,8 @@ for that copy. Hence every request's result is the same alone and in the mix.
 Insert of B points as rows [N, N + B):
   compute  the new rows' k nearest among X[:N + B] (exact) and their Gaussians
            (Eq. 3-4); for the existing rows, the new points inside their
-           current radius d_i^Max (atsne_knn_cross with radii, kc = min(k, B)).
+           current radius d_i^Max, the farthest neighbour in N_i as it stands
+           (atsne_row_dmax, then atsne_knn_cross with radii, kc = min(k, B)).
   commit   write the new rows (rho = 1); merge the candidates into the
            existing rows (Eq. 11); re-calibrate the existing rows.
 Refine of S listed rows:
@@ -34,7 +35,7 @@ import torch
 
 from . import (OP_DELETE, OP_KNN, OP_KNN_CROSS_RADIUS, atsne_calibrate_P, atsne_commit_rows,
                atsne_delete_rows, atsne_knn, atsne_knn_cross, atsne_knn_rows, atsne_merge_neighbors,
-               knn_opts, workspace_bytes)
+               atsne_row_dmax, knn_opts, workspace_bytes)
 
 
 class Request:
@@ -142,10 +143,11 @@ class Server:
                 tp, tb = atsne_calibrate_P(td, self.perp, stream=s)
                 cand = None
                 if N0 > 0:
-                    # the existing rows' radii d_i^Max, taken on the state stream
-                    # after the earlier commits (a radius only ever shrinks)
+                    # the existing rows' radii d_i^Max (their farthest neighbour in
+                    # N_i as it stands), taken on the state stream after the
+                    # earlier commits (a radius only ever shrinks)
                     with torch.cuda.stream(self.state):
-                        radius = self.d2[:N0, self.k - 1].contiguous()
+                        radius = atsne_row_dmax(self.d2[:N0], stream=self.state)
                         snap = torch.cuda.Event()
                         snap.record(self.state)
                     radius.record_stream(s)

@@ -82,11 +82,12 @@ def test_symmetrize_after_delete(at):
     assert np.abs(val.cpu().numpy() - o_val).max() * n <= 1e-5
 
 
-def test_insertion_fills_the_holes(at):
+def test_insertion_after_a_deletion(at):
     # serving: a deletion request, then an insertion. An existing row takes the
-    # k smallest of its remaining entries and the new points closer than its
-    # d_i^Max (Eq. 11); a row left with holes has d_i^Max = +inf, so the nearest
-    # new points fill them. The new rows are exact over the corpus now present.
+    # k smallest of its remaining entries and the new points strictly closer
+    # than its d_i^Max, the farthest neighbour left in N_i (Eq. 11); in a row
+    # with holes such points fill them. The new rows are exact over the corpus
+    # now present.
     from paper_1512_01655_gb300.serve import Request, Server
     Xall = synth.gaussian_mixture(3000, 16, seed=31)
     k = 30
@@ -108,15 +109,20 @@ def test_insertion_fills_the_holes(at):
     ok = checked = 0
     for r, i in enumerate(keep):
         rem = [(d, newid[j]) for d, j in zip(e_d2[i], e_idx[i]) if newid[j] >= 0]
-        dmax = rem[-1][0] if len(rem) == k else np.inf
+        dmax = rem[-1][0] if rem else np.inf
         if np.isfinite(dmax) and any(abs(d - dmax) <= 1e-5 * dmax for d in c_d2[r]):
             continue  # a new point at d_i^Max within rounding: either side is right
         merged = sorted(rem + [(d, n0 + j) for d, j in zip(c_d2[r], c_idx[r]) if d < dmax])
         if len(merged) > k and merged[k][0] - merged[k - 1][0] <= 1e-5 * merged[k][0]:
             continue  # a near tie at the k-th place
         checked += 1
-        ok += set(g_idx[r]) == set(j for _, j in merged[:k])
+        row = g_idx[r]
+        ok += (set(row[row >= 0]) == set(j for _, j in merged[:k])
+               and int((row < 0).sum()) == k - min(k, len(merged)))
     assert checked > 0.9 * n0 and ok == checked
+    # rows that lost neighbours and got every hole filled by closer new points
+    lost = np.array([(newid[e_idx[i]] < 0).any() for i in keep])
+    assert (lost & (g_idx[:n0] >= 0).all(1)).sum() > 0
     # the new rows: exact over the present corpus
     o_idx, o_d2 = oracle.knn_exact(Xf, k + 1, queries=np.arange(n0, N))
     clear = (o_d2[:, k] - o_d2[:, k - 1]) / o_d2[:, k] > 1e-4
