@@ -77,6 +77,8 @@ def parse():
                    help="timed runs of the exact path alone per precision (0 = skip)")
     p.add_argument("--checks-sweep", default="32,64,128,256,512,1024,2048,4096",
                    help="forest checks values for the precision sweep (empty = skip)")
+    p.add_argument("--gamma-reps", type=int, default=3,
+                   help="timed runs per precision on the 1M x 128 Gamma workload (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=256)
     return p.parse_args()
@@ -451,6 +453,51 @@ def bench_refine_batch(at, torch, dev, stream, reps, peaks):
                        "frac": round(ach / peak, 4), "tensor_passes": 3}}
 
 
+def bench_gamma(at, torch, dev, stream, reps, peaks):
+    """The precision comparison on its own workload: 1,000,000 x 128
+    non-negative Gamma(2, 1) features scaled per cluster (50 clusters), k = 90,
+    the exact kNN of 100000 sampled rows (every 10th) against all rows, in
+    FP32 (three BF16 passes, certified), BF16+rerank (certified: uncertified
+    rows go to the CUDA cores), BF16+rerank without a certificate (top-4k
+    re-ranked in FP32) and FP8+rerank; median of `reps` CUDA-event timed runs
+    after one warm-up, recall (Eq. 9) against FP32."""
+    from paper_1512_01655_gb300 import synth
+    X = torch.from_numpy(synth.gamma_clusters(N=1_000_000, D=128, seed=3)).to(dev)
+    N, D = X.shape
+    q = torch.arange(0, N, 10, dtype=torch.int32, device=dev)
+    Q = q.numel()
+    out = {"workload": "1000000x128 Gamma(2,1) x per-cluster scales, 50 clusters; 100000 sampled query rows",
+           "k": K_NN}
+    ref = None
+    peak = peaks.get("bf16_tflops", 1900.0)
+    for prec in ("fp32", "bf16", "bf16_approx", "fp8"):
+        o = at.knn_opts(method="exact", precision=prec)
+        at.atsne_knn(X, K_NN, queries=q, opts=o)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            idx, _ = at.atsne_knn(X, K_NN, queries=q, opts=o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        at.atsne_check()
+        ms = sorted(ts)[len(ts) // 2]
+        passes = 3 if prec == "fp32" else 1
+        ent = {"ms": round(ms, 3), "queries_per_s": round(Q / (ms / 1e3), 1),
+               "tensor_frac_algorithmic": round(passes * 2.0 * Q * N * D / (ms / 1e3) / 1e12
+                                                / (peak * (2.0 if prec == "fp8" else 1.0)), 4)}
+        if ref is None:
+            ref = idx
+        else:
+            ent["recall_vs_fp32"] = round(at.atsne_knn_precision(idx, ref)[1], 6)
+        out[prec] = ent
+    del X, ref
+    torch.cuda.empty_cache()
+    return out
+
+
 def algorithmic_flops_knn(N, D):
     return 2.0 * N * N * D
 
@@ -646,7 +693,7 @@ def run_ours(args, world, rank, local, pg):
     if args.exact_reps > 0:
         exact_p = {}
         ref_idx = None
-        for prec in ("fp32", "bf16", "fp8"):
+        for prec in ("fp32", "bf16", "bf16_approx", "fp8"):
             o = at.knn_opts(method="exact", precision=prec)
 
             def run_exact():
@@ -705,6 +752,10 @@ def run_ours(args, world, rank, local, pg):
         at.atsne_check()
         del forest, ref_idx
 
+    gamma = None
+    if args.gamma_reps > 0 and world == 1:
+        gamma = bench_gamma(at, torch, dev, stream, args.gamma_reps, peaks)
+
     serving = None
     if args.serve_max > 0 and world == 1:
         serving = bench_serving(at, torch, dev, args.serve_max)
@@ -742,7 +793,7 @@ def run_ours(args, world, rank, local, pg):
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
             "step_ms": [round(t, 3) for t in step_ms],
             "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
-            "forest_checks_sweep": sweep, "refine_batch": refine_batch, "kde": kde, "serving": serving,
+            "forest_checks_sweep": sweep, "precision_gamma1m": gamma, "refine_batch": refine_batch, "kde": kde, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }

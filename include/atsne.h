@@ -42,18 +42,24 @@ typedef enum {
 
 typedef enum { ATSNE_KNN_EXACT = 0, ATSNE_KNN_FOREST = 1 } atsne_knn_method;
 
-/* Arithmetic of the exact path's distance contraction. Every variant returns the
- * exact kNN under FP32 direct-difference distances: the tensor-core variants
- * re-rank their candidates in FP32 and certify each row (rows that cannot be
- * certified are recomputed on the CUDA cores). */
+/* Arithmetic of the exact path's distance contraction. FP32, BF16_RERANK and
+ * FP32_CUDA_CORES return the exact kNN under FP32 direct-difference distances:
+ * the tensor-core variants re-rank their candidates in FP32 and certify each
+ * row (rows that cannot be certified are recomputed on the CUDA cores). The
+ * two *_RERANK variants without a certificate are approximate. */
 typedef enum {
     ATSNE_FP32 = 0,            /* tensor cores, 3 BF16 passes (hi.hi + hi.lo + lo.hi) */
     ATSNE_BF16_RERANK = 1,     /* tensor cores, 1 BF16 pass, rerank_k candidates per row */
     ATSNE_FP32_CUDA_CORES = 2, /* FP32 direct differences on the CUDA cores */
-    ATSNE_FP8_RERANK = 3       /* tensor cores, 1 FP8 (E4M3, per-row scale) pass; the
+    ATSNE_FP8_RERANK = 3,      /* tensor cores, 1 FP8 (E4M3, per-row scale) pass; the
                                   rerank_k (default 4k, at most 512) best keys per row
                                   re-ranked in FP32, the k best returned: approximate,
                                   no certificate (measure recall against FP32) */
+    ATSNE_BF16_RERANK_APPROX = 4 /* tensor cores, 1 BF16 pass; the rerank_k (default 4k,
+                                  at most 512) best keys per row re-ranked in FP32, the
+                                  k best returned: approximate, no certificate (on data
+                                  whose BF16 error bound exceeds the neighbourhood's
+                                  margin, BF16_RERANK sends most rows to the CUDA cores) */
 } atsne_precision;
 
 /* Operation codes for atsne_workspace_bytes(). */

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libatsne.so")
 
 ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPPORTED = range(6)
 KNN_EXACT, KNN_FOREST = 0, 1
-FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK = 0, 1, 2, 3
+FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK, BF16_RERANK_APPROX = 0, 1, 2, 3, 4
 (OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY,
  OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS, OP_DELETE, OP_TUNE_KNN) = range(11)
 
@@ -149,7 +149,7 @@ def knn_opts(method="exact", precision="fp32", trees=4, top_var_dims=5, checks=1
     lib().atsne_knn_opts_default(ctypes.byref(o))
     o.method = {"exact": KNN_EXACT, "forest": KNN_FOREST}[method] if isinstance(method, str) else method
     o.precision = {"fp32": FP32, "bf16": BF16_RERANK, "fp32_cuda": FP32_CUDA_CORES,
-                   "fp8": FP8_RERANK}[precision] \
+                   "fp8": FP8_RERANK, "bf16_approx": BF16_RERANK_APPROX}[precision] \
         if isinstance(precision, str) else precision
     o.trees, o.top_var_dims, o.checks, o.leaf_size = trees, top_var_dims, checks, leaf_size
     o.queue_cap, o.rerank_k, o.seed = queue_cap, rerank_k, seed

@@ -141,7 +141,8 @@ atsne_status validate_knn_opts(const atsne_knn_opts &o) {
     if (o.method != ATSNE_KNN_EXACT && o.method != ATSNE_KNN_FOREST)
         return set_error(ATSNE_EINVAL, "knn: unknown method %d", o.method);
     if (o.precision != ATSNE_FP32 && o.precision != ATSNE_BF16_RERANK &&
-        o.precision != ATSNE_FP32_CUDA_CORES && o.precision != ATSNE_FP8_RERANK)
+        o.precision != ATSNE_FP32_CUDA_CORES && o.precision != ATSNE_FP8_RERANK &&
+        o.precision != ATSNE_BF16_RERANK_APPROX)
         return set_error(ATSNE_EINVAL, "knn: unknown precision %d", o.precision);
     if (o.rerank_k < 0 || o.rerank_k > 4096)
         return set_error(ATSNE_EINVAL, "knn: rerank_k=%d not in [0, 4096]", o.rerank_k);

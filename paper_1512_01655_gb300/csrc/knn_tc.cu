@@ -1294,6 +1294,7 @@ int tc_split_candidates(int64_t N, int D, int64_t Q, int k, int precision, int r
 TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int splits) {
     TcPlan pl;
     pl.passes = precision == ATSNE_FP32 ? 3 : precision == ATSNE_FP8_RERANK ? 8 : 1;
+    pl.certify = precision != ATSNE_FP8_RERANK && precision != ATSNE_BF16_RERANK_APPROX;
     const int ke = pl.passes == 8 ? 128 : TC_BK;  // elements per 128-byte row
     pl.Dp = ((D + ke - 1) / ke) * ke;
     pl.row_tiles = (int)((Q + TC_BM - 1) / TC_BM);
@@ -1310,8 +1311,8 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, 
     const int64_t tiles_per = (col_tiles + S - 1) / S;
     pl.cols_per_split = (int)(tiles_per * TC_BN);
     pl.splits = (int)((N + pl.cols_per_split - 1) / pl.cols_per_split);
-    int ks = rerank_k > 0 ? rerank_k : (pl.passes == 3 ? k + 38 : pl.passes == 8 ? 4 * k : 2 * k);
-    if (pl.passes == 8 && ks > RCAP_FP8 / 2) ks = RCAP_FP8 / 2;
+    int ks = rerank_k > 0 ? rerank_k : (pl.passes == 3 ? k + 38 : !pl.certify ? 4 * k : 2 * k);
+    if (!pl.certify && ks > RCAP_FP8 / 2) ks = RCAP_FP8 / 2;
     if (ks < k) ks = k;
     pl.ksel = ks;
     // A streaming top-ksel over n columns in random order admits about
@@ -1491,7 +1492,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         return launch_kernel("radius_filter", radius_filter_kernel, ceil_div(Q * k, 256), 256, 0, stream,
                              idx_out, d2_out, Q, k, radius);
     }
-    if (fp8) {
+    if (!pl.certify) {
         const size_t ms = merge_smem_bytes<false, RCAP_FP8, MSTAGE_FP8>();
         e = cudaFuncSetAttribute(knn_merge_kernel<false, RCAP_FP8, MSTAGE_FP8>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);

@@ -606,3 +606,27 @@ def test_knn_fp8_rerank_recall_and_exact_distances(at, kind):
     assert np.all(np.abs(g_d2 - exact) <= 1e-5 * exact + 1e-3)
     assert np.all(np.diff(g_d2, axis=1) >= 0)
     assert np.all(g_idx != rows[:, None])
+
+
+@pytest.mark.parametrize("kind", ["gamma", "gauss"])
+def test_knn_bf16_approx_recall_and_exact_distances(at, kind):
+    # BF16 keys select 4k candidates, re-ranked in FP32, without a certificate:
+    # recall against the oracle, and every returned distance the FP32 direct
+    # difference of its pair. Gamma-distributed features (wide norms) are the
+    # case where the certified BF16 mode sends most rows to the CUDA cores.
+    if kind == "gamma":
+        X = synth.gamma_clusters(N=20000, D=128, seed=3)
+    else:
+        X = synth.gaussian_mixture(4000, 64, seed=1)
+    rows = synth.sample_rows(X.shape[0], 300, seed=52)
+    idx, d2 = at.atsne_knn(to_dev(X), 90, queries=to_dev(rows.astype(np.int32)), precision="bf16_approx")
+    at.atsne_check()
+    o_idx, o_d2 = oracle.knn_exact(X, 90, queries=rows)
+    g_idx, g_d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    recall = np.mean([len(set(g_idx[i]) & set(o_idx[i])) / 90 for i in range(len(rows))])
+    print("bf16 approx recall", kind, recall)
+    assert recall >= 0.999
+    exact = _sq_dists(X, rows, g_idx)
+    assert np.all(np.abs(g_d2 - exact) <= 1e-5 * exact + 1e-3)
+    assert np.all(np.diff(g_d2, axis=1) >= 0)
+    assert np.all(g_idx != rows[:, None])
