@@ -676,9 +676,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     __syncwarp();  // the chunk's norms are read before the next chunk's
                     if (mask) {
                         // spill this row's keys to its own padded shared row and
-                        // walk its survivors, two per step (their shared loads
-                        // issue together): the warp pays the largest count of any
-                        // lane, not the union of survivor positions. Each survivor
+                        // walk its survivors one per step (a chunk rarely holds
+                        // more than one or two of a row's): the warp pays the
+                        // largest count of any lane, not the union of survivor
+                        // positions. Each survivor
                         // is appended (key, column) to the row's buffer and counted
                         // in its bucket by a fire-and-forget shared add.
 #pragma unroll
@@ -710,12 +711,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                         do {
                             const int j0 = __ffs(mask) - 1;
                             mask &= mask - 1;
-                            const int j1 = mask ? __ffs(mask) - 1 : -1;
-                            mask &= mask - 1;
-                            const float k0 = mine[j0];
-                            const float k1 = j1 >= 0 ? mine[j1] : 0.f;
-                            append(k0, colb + j0);
-                            if (j1 >= 0) append(k1, colb + j1);
+                            append(mine[j0], colb + j0);
                         } while (mask);
                     }
                 }
