@@ -189,8 +189,9 @@ class Pipeline:
         # the approximate path runs on its own stream beside the exact one: the
         # two are independent until rho, and their kernels are bound by different
         # units (integer issue and latency for the forest, tensor pipe and
-        # gathers for the exact kNN)
-        self.side = torch.cuda.Stream(device=dev)
+        # gathers for the exact kNN). It is the longer of the two, so its stream
+        # has the higher priority: its blocks are scheduled first when both wait.
+        self.side = torch.cuda.Stream(device=dev, priority=-1)
 
     def step(self):
         import torch
