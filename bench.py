@@ -799,6 +799,9 @@ def run_ours(args, world, rank, local, pg):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "rho": round(rho, 5), "rho_after_refine": round(rho_refined, 5), "nnz_exact_P": nnz,
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
+            "stage_ms_note": "CUDA-event time per step of each kernel label on its own stream; the exact "
+                             "path's kernels overlap the approximate path's (higher-priority stream) and "
+                             "include the time they wait for SMs",
             "step_ms": [round(t, 3) for t in step_ms],
             "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
             "forest_checks_sweep": sweep, "precision_gamma1m": gamma, "refine_batch": refine_batch, "kde": kde, "serving": serving,
