@@ -72,3 +72,24 @@ def test_rejects_bad_arguments(oracle_mod):
         oracle_mod.knn_exact(X, 5)          # k > N - 1
     with pytest.raises(ValueError):
         oracle_mod.knn_exact(X, 2, queries=[7])
+
+
+def test_cross_matches_numpy_brute_force(oracle_mod):
+    # Eq. 8 across two point sets: no point is excluded; ties by index
+    Xq = synth.gaussian_mixture(70, 6, n_centres=3, seed=6)
+    Xc = synth.gaussian_mixture(130, 6, n_centres=3, seed=7)
+    Xc[10] = Xq[3]  # a corpus point equal to a query: distance 0, kept
+    idx, d2 = oracle_mod.knn_cross(Xq, Xc, 12)
+    D2 = ((Xq.astype(np.float64)[:, None, :] - Xc.astype(np.float64)[None, :, :]) ** 2).sum(-1)
+    order = np.lexsort((np.broadcast_to(np.arange(130), D2.shape), D2), axis=1)[:, :12]
+    assert np.array_equal(idx, order)
+    assert np.allclose(d2, np.take_along_axis(D2, order, 1), rtol=1e-12, atol=0)
+    assert idx[3, 0] == 10 and d2[3, 0] == 0.0
+
+
+def test_cross_against_itself_is_the_exact_knn_plus_self(oracle_mod):
+    X = synth.gaussian_mixture(200, 9, n_centres=4, seed=8)
+    c_idx, c_d2 = oracle_mod.knn_cross(X, X, 21)
+    e_idx, e_d2 = oracle_mod.knn_exact(X, 20)
+    assert np.array_equal(c_idx[:, 0], np.arange(200)) and np.all(c_d2[:, 0] == 0.0)
+    assert np.array_equal(c_idx[:, 1:], e_idx) and np.array_equal(c_d2[:, 1:], e_d2)
