@@ -26,6 +26,9 @@ Delete of R listed rows (Sec. 5.3.2): the points leave every neighbourhood
   every index renumbered, and their Gaussians are calibrated again. Row
   numbers change, so a deletion is admitted only when no other request is in
   flight, and the requests after it are numbered against the state it leaves.
+Update of R listed rows with R new vectors (Sec. 5.3.3: a changed point is
+  removed and added again): the deletion of the rows, then the insertion of the
+  new vectors as the last rows, admitted together like a deletion.
 """
 import collections
 import time
@@ -41,7 +44,8 @@ from . import (OP_DELETE, OP_KNN, OP_KNN_CROSS_RADIUS, atsne_calibrate_P, atsne_
 class Request:
     """kind "insert" (points: float32 [B][D] host array), "refine" or "delete"
     (rows: int32 [S] host array of existing rows, numbered as the state is when
-    the request is admitted); arrival in seconds."""
+    the request is admitted), or "update" (both: the rows' new vectors);
+    arrival in seconds."""
 
     def __init__(self, rid, kind, arrival, points=None, rows=None):
         self.rid, self.kind, self.arrival = rid, kind, float(arrival)
@@ -51,7 +55,7 @@ class Request:
 
     @property
     def size(self):
-        return len(self.points) if self.kind == "insert" else len(self.rows)
+        return len(self.points) if self.kind in ("insert", "update") else len(self.rows)
 
 
 class Server:
@@ -96,6 +100,10 @@ class Server:
                 ws += workspace_bytes(OP_KNN_CROSS_RADIUS, n, D, kc, N, self.opts) + N * (kc * 8 + 5)
         elif req.kind == "delete":
             ws = workspace_bytes(OP_DELETE, N, D, k)
+        elif req.kind == "update":
+            ins = Request(req.rid, "insert", req.arrival, points=req.points)
+            return self.need_bytes(Request(req.rid, "delete", req.arrival, rows=req.rows)) + \
+                self.need_bytes(ins)
         else:
             ws = workspace_bytes(OP_KNN, N, D, k, n, self.opts)
         return ws + n * (k * 12 + 8) + (1 << 20)
@@ -105,7 +113,8 @@ class Server:
         return free + torch.cuda.memory_reserved(self.dev) - torch.cuda.memory_allocated(self.dev)
 
     def fits(self, req):
-        if req.kind == "insert" and self.N + req.size > self.cap:
+        grow = req.size if req.kind == "insert" else req.size - len(req.rows) if req.kind == "update" else 0
+        if self.N + grow > self.cap:
             raise ValueError("insert beyond the corpus capacity")
         return self.need_bytes(req) + self.reserve <= self.free_bytes()
 
@@ -122,9 +131,21 @@ class Server:
         req.admitted = now
         self.inflight.append((req, None, done, [rows]))
 
+    def admit_update(self, req, now):
+        """A deletion of the rows, then the insertion of their new vectors."""
+        self.admit_delete(Request(req.rid, "delete", req.arrival, rows=req.rows), now)
+        _, _, _, dkeep = self.inflight.pop()  # the insertion's commit follows it on the state stream
+        ins = Request(req.rid, "insert", req.arrival, points=req.points)
+        self.admit(ins, now)
+        _, slot, done, keep = self.inflight.pop()
+        req.first_row, req.admitted = ins.first_row, now
+        self.inflight.append((req, slot, done, keep + dkeep))
+
     def admit(self, req, now):
         if req.kind == "delete":
             return self.admit_delete(req, now)
+        if req.kind == "update":
+            return self.admit_update(req, now)
         slot = self.free.pop(0)
         s = self.streams[slot]
         keep = []
@@ -213,7 +234,7 @@ class Server:
                     served.append(req)
                     progress = True
             while pending and pending[0].arrival <= now and self.free:
-                if pending[0].kind == "delete" and self.inflight:
+                if pending[0].kind in ("delete", "update") and self.inflight:
                     break  # renumbering: wait until nothing else is in flight
                 if not self.fits(pending[0]):
                     if not self.inflight:
@@ -238,7 +259,7 @@ def summarize(served):
            "points_per_s": round(pts / span, 1) if span > 0 else None,
            "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
            "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
-    for kind in ("insert", "refine", "delete"):
+    for kind in ("insert", "refine", "delete", "update"):
         lk = np.array([r.done - r.arrival for r in served if r.kind == kind])
         if lk.size:
             out[kind] = {"requests": int(lk.size),

@@ -153,3 +153,24 @@ def test_delete_edge_cases(at):
     with pytest.raises(at.AtsneError):
         at.atsne_delete_rows(Xd, to_dev(np.arange(301, dtype=np.int32) % 300), mu, idx, d2, P, beta,
                              rho, N=300)
+
+
+def test_update_is_a_deletion_then_an_insertion(at):
+    # Sec. 5.3.3: a changed point is removed and added again. An "update"
+    # request equals a deletion request followed by an insertion request.
+    from paper_1512_01655_gb300.serve import Request, Server
+    Xall = synth.gaussian_mixture(2500, 12, seed=41)
+    rows = np.array([5, 9, 300, 1999], np.int32)
+    new = Xall[2000:2004]
+    a = Server(Xall[:2000], capacity=2100, k=20, perplexity=6.0, precision="fp32", slots=2)
+    b = Server(Xall[:2000], capacity=2100, k=20, perplexity=6.0, precision="fp32", slots=2)
+    a.run([Request(0, "update", 0.0, rows=rows, points=new),
+           Request(1, "insert", 0.0, points=Xall[2004:2050])])
+    b.run([Request(0, "delete", 0.0, rows=rows), Request(1, "insert", 0.0, points=new),
+           Request(2, "insert", 0.0, points=Xall[2004:2050])])
+    at.atsne_check()
+    assert a.N == b.N == 2046
+    for t in ("X", "idx", "d2", "P", "beta", "rho"):
+        assert torch.equal(getattr(a, t)[:a.N], getattr(b, t)[:b.N]), t
+    keep = np.setdiff1d(np.arange(2000), rows)
+    assert np.array_equal(a.X[:a.N].cpu().numpy(), np.concatenate([Xall[keep], Xall[2000:2050]]))
