@@ -260,7 +260,9 @@ atsne_status atsne_tune_clear(void);
  * the existing points among the inserted ones. Output row r belongs to
  * Xq[r], indices are rows of Xc, sorted by (d^2, index).
  *  Xq [Nq][D], Xc [Nc][D] fp32 (device, finite); 1 <= k <= Nc.
- *  opts: the exact method's precision (FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK).
+ *  opts: the exact method's precision (any atsne_precision). With radii the
+ *        result is exact in every mode: the FP8 mode runs on the CUDA cores (its
+ *        keys carry no error bound) and both BF16 modes certify every row.
  *  radius_d2  NULL, or [Nq] fp32 squared radii: row r then lists only the rows
  *             of Xc with d^2 < radius_d2[r] among its k nearest, the rest of
  *             the row (-1, +inf). With the radius of each existing point's
