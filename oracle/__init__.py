@@ -44,6 +44,12 @@ def lib():
                                           _i32p, _i64p]
         L.oracle_forest_query.argtypes = [_f32p, _i64, _i32, _i32, _i32, _i32p, _f32p, _i32p,
                                           _i64p, _vp, _i64, _i32, _i32, _i32, _i32p, _f64p, _i64p]
+        L.oracle_forest_query_ex.argtypes = [_f32p, _i64, _i32, _i32, _i32, _i32p, _f32p, _i32p,
+                                             _i64p, _i64, _vp, _i64, _i32, _i32, _i32, _i32p, _f64p,
+                                             _i64p]
+        L.oracle_forest_insert.argtypes = [_f32p, _i64, _i64, _i32, _i32, _i32, _i32p, _f32p, _vp,
+                                           _vp, _i32p, _i64p]
+        L.oracle_forest_delete.argtypes = [_i64, _i32, _i32, _i32p, _i64p, _vp, _i64, _i32p, _i64p]
         L.oracle_kde.argtypes = [_f32p, _i64, _vp, _vp, _f64, _f64, _f64, _i32, _i32, _f64, _f64,
                                  _f64, _f64p, _f64p, _f64p, _f64p]
         L.oracle_knn_cross.argtypes = [_f32p, _i64, _f32p, _i64, _i32, _i32, _i32p, _f64p]
@@ -166,7 +172,9 @@ def auto_queue_cap(checks):
 
 def forest_query(X, forest, k, checks, qcap=None, queries=None):
     """Forest search, Sec. 4.2: (idx [Q,k], d2 float64 [Q,k], evaluated [Q]).
-    qcap None selects the default capacity auto_queue_cap(checks)."""
+    qcap None selects the default capacity auto_queue_cap(checks). The forest's
+    leaf offsets are one array for all trees ([2^h + 1], as built) or one per
+    tree ([T][2^h + 1], after points were added or removed)."""
     if qcap is None:
         qcap = auto_queue_cap(checks)
     X = np.ascontiguousarray(X, dtype=np.float32)
@@ -182,10 +190,63 @@ def forest_query(X, forest, k, checks, qcap=None, queries=None):
     idx = np.empty((Q, k), np.int32)
     d2 = np.empty((Q, k), np.float64)
     ev = np.empty(Q, np.int64)
-    _check(lib().oracle_forest_query(X, N, D, T, h, sd, sv, np.ascontiguousarray(forest["perm"]),
-                                     np.ascontiguousarray(forest["leaf_ofs"]), qp, S, k,
-                                     int(checks), int(qcap), idx, d2, ev), "forest_query")
+    ofs = np.ascontiguousarray(forest["leaf_ofs"], dtype=np.int64)
+    stride = ofs.shape[1] if ofs.ndim == 2 else 0
+    if ofs.shape[-1] != (1 << h) + 1 or (stride and ofs.shape[0] != T):
+        raise ValueError("leaf offsets do not match the forest")
+    _check(lib().oracle_forest_query_ex(X, N, D, T, h, sd, sv, np.ascontiguousarray(forest["perm"]),
+                                        ofs, stride, qp, S, k, int(checks), int(qcap), idx, d2, ev),
+           "forest_query")
     return idx, d2, ev
+
+
+def _tree_offsets(forest):
+    ofs = np.asarray(forest["leaf_ofs"], dtype=np.int64)
+    if ofs.ndim == 1:
+        ofs = np.broadcast_to(ofs, (forest["trees"], ofs.shape[0]))
+    return np.ascontiguousarray(ofs)
+
+
+def forest_insert(forest, X, n_old):
+    """Sec. 5.3.1: rows n_old .. N-1 of X join every tree of `forest` (built or
+    updated over the first n_old rows) by a descent to a leaf; returns the new
+    forest (per-tree leaf offsets, perm [T][N])."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    N, D = X.shape
+    T, h = forest["trees"], forest["depth"]
+    n_int = (1 << h) - 1
+    sd = np.ascontiguousarray(np.asarray(forest["split_dim"], np.int32).reshape(T, n_int))
+    sv = np.ascontiguousarray(np.asarray(forest["split_val"], np.float32).reshape(T, n_int))
+    if n_int == 0:
+        sd, sv = np.zeros((T, 1), np.int32), np.zeros((T, 1), np.float32)
+    perm_in = np.ascontiguousarray(forest["perm"], dtype=np.int32)
+    ofs_in = _tree_offsets(forest)
+    perm = np.empty((T, N), np.int32)
+    ofs = np.empty((T, (1 << h) + 1), np.int64)
+    _check(lib().oracle_forest_insert(X, int(n_old), N, D, T, h, sd, sv,
+                                      perm_in.ctypes.data if n_old > 0 else None,
+                                      ofs_in.ctypes.data if n_old > 0 else None, perm, ofs),
+           "forest_insert")
+    out = dict(forest)
+    out.update(N=N, perm=perm, leaf_ofs=ofs)
+    return out
+
+
+def forest_delete(forest, rows):
+    """Sec. 5.3.2: the listed points leave every tree; the remaining ones are
+    renumbered as the corpus rows are. Returns the new forest."""
+    T, h = forest["trees"], forest["depth"]
+    perm_in = np.ascontiguousarray(forest["perm"], dtype=np.int32)
+    N = perm_in.shape[1]
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    perm = np.empty((T, N - rows.shape[0]), np.int32)
+    ofs = np.empty((T, (1 << h) + 1), np.int64)
+    _check(lib().oracle_forest_delete(N, T, h, perm_in, _tree_offsets(forest),
+                                      rows.ctypes.data if rows.shape[0] else None, rows.shape[0],
+                                      perm, ofs), "forest_delete")
+    out = dict(forest)
+    out.update(N=N - rows.shape[0], perm=perm, leaf_ofs=ofs)
+    return out
 
 
 def refine(X, subset, k, perplexity, idx, d2, P, beta, rho, tol=1e-10, max_iter=200):

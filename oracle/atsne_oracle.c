@@ -25,6 +25,9 @@
  *   oracle_knn_cross     Eq. 8 across two point sets (insertion, Sec. 5.3.1)
  *   oracle_delete        Sec. 5.3.2: points leave every neighbourhood, rho_i
  *                        falls by 1/k per point removed, rows renumbered
+ *   oracle_forest_insert Sec. 5.3.1: a new point joins the forest by a descent
+ *                        of every tree to a leaf
+ *   oracle_forest_delete Sec. 5.3.2: a deleted point leaves every tree
  *
  * Readings taken where the paper is silent are stated at each function.
  * Compile with -ffp-contract=off: the forest's float decisions (split value,
@@ -547,6 +550,7 @@ typedef struct {
     int32_t *bj;
     int cnt;
     int64_t evaluated;
+    int64_t ofs_stride;  /* 0: one leaf-offset array for all trees; else per tree */
 } search_t;
 
 /* Descend from (tree, node, key) to a leaf, pushing the far child of every
@@ -570,7 +574,8 @@ static void descend_and_scan(search_t *s, int32_t tr, int64_t v, float key)
     }
     const int64_t m = v - s->n_internal;
     const int32_t *pt = s->perm + (int64_t)tr * s->N;
-    for (int64_t q = s->leaf_ofs[m]; q < s->leaf_ofs[m + 1]; ++q) {
+    const int64_t *lo = s->leaf_ofs + (int64_t)tr * s->ofs_stride;
+    for (int64_t q = lo[m]; q < lo[m + 1]; ++q) {
         const int32_t p = pt[q];
         if (s->seen[p]) continue;
         s->seen[p] = 1;
@@ -601,11 +606,11 @@ static void descend_and_scan(search_t *s, int32_t tr, int64_t v, float key)
  * No pruning by the current k-th distance is applied, so the visiting order
  * does not depend on checks and a larger budget only extends it.
  */
-int oracle_forest_query(const float *X, int64_t N, int32_t D, int32_t T, int32_t h,
-                        const int32_t *split_dim, const float *split_val, const int32_t *perm,
-                        const int64_t *leaf_ofs, const int32_t *queries, int64_t S, int32_t k,
-                        int32_t checks, int32_t qcap, int32_t *idx_out, double *d2_out,
-                        int64_t *evaluated_out)
+int oracle_forest_query_ex(const float *X, int64_t N, int32_t D, int32_t T, int32_t h,
+                           const int32_t *split_dim, const float *split_val, const int32_t *perm,
+                           const int64_t *leaf_ofs, int64_t ofs_stride, const int32_t *queries,
+                           int64_t S, int32_t k, int32_t checks, int32_t qcap, int32_t *idx_out,
+                           double *d2_out, int64_t *evaluated_out)
 {
     if (!X || N < 2 || D < 1 || T < 1 || h < 0 || k < 1 || (int64_t)k > N - 1 || qcap < 1 ||
         !idx_out || !d2_out || !split_dim || !split_val || !perm || !leaf_ofs)
@@ -631,7 +636,7 @@ int oracle_forest_query(const float *X, int64_t N, int32_t D, int32_t T, int32_t
                 const int64_t qi = queries ? (int64_t)queries[s] : s;
                 search_t st = {X, X + qi * D, N, ((int64_t)1 << h) - 1, D, k,
                                split_dim, perm, split_val, leaf_ofs, seen, &pq,
-                               d2_out + s * k, idx_out + s * k, 0, 0};
+                               d2_out + s * k, idx_out + s * k, 0, 0, ofs_stride};
                 memset(seen, 0, (size_t)N);
                 seen[qi] = 1;
                 pq.n = 0;
@@ -654,6 +659,120 @@ int oracle_forest_query(const float *X, int64_t N, int32_t D, int32_t T, int32_t
         free(seen);
         free(pq.e);
     }
+    return rc;
+}
+
+int oracle_forest_query(const float *X, int64_t N, int32_t D, int32_t T, int32_t h,
+                        const int32_t *split_dim, const float *split_val, const int32_t *perm,
+                        const int64_t *leaf_ofs, const int32_t *queries, int64_t S, int32_t k,
+                        int32_t checks, int32_t qcap, int32_t *idx_out, double *d2_out,
+                        int64_t *evaluated_out)
+{
+    return oracle_forest_query_ex(X, N, D, T, h, split_dim, split_val, perm, leaf_ofs, 0, queries, S, k,
+                                  checks, qcap, idx_out, d2_out, evaluated_out);
+}
+
+/*
+ * Insertion into the forest, Sec. 5.3.1: the points N_old .. N_new - 1 of X
+ * (rows appended to the corpus) are added to every tree. A point descends a
+ * tree by the rule of the search (query value below the split value: left
+ * child 2v + 1, else right child 2v + 2) to a leaf and joins that leaf's
+ * bucket after the points already there, the new points in index order. The
+ * split dimensions and values do not change (the paper updates the forest per
+ * point in O(log N), without rebuilding).
+ *  perm_in [T][N_old] and ofs_in [T][2^h + 1] (each tree its own leaf offsets,
+ *  as buckets differ once points are added) -> perm_out [T][N_new], ofs_out.
+ */
+int oracle_forest_insert(const float *X, int64_t N_old, int64_t N_new, int32_t D, int32_t T, int32_t h,
+                         const int32_t *split_dim, const float *split_val, const int32_t *perm_in,
+                         const int64_t *ofs_in, int32_t *perm_out, int64_t *ofs_out)
+{
+    if (!X || N_old < 0 || N_new < N_old || D < 1 || T < 1 || h < 0 || !perm_out || !ofs_out ||
+        (N_old > 0 && (!perm_in || !ofs_in)) || (h > 0 && (!split_dim || !split_val)))
+        return 1;
+    const int64_t L = (int64_t)1 << h, n_int = L - 1, B = N_new - N_old;
+    int64_t *leaf = (int64_t *)malloc(sizeof(int64_t) * (size_t)(B > 0 ? B : 1));
+    int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+    if (!leaf || !cur) {
+        free(leaf);
+        free(cur);
+        return 2;
+    }
+    for (int32_t t = 0; t < T; ++t) {
+        const int64_t *oi = ofs_in ? ofs_in + (int64_t)t * (L + 1) : NULL;
+        int64_t *oo = ofs_out + (int64_t)t * (L + 1);
+        for (int64_t b = 0; b < B; ++b) {
+            const float *x = X + (N_old + b) * D;
+            int64_t v = 0;
+            while (v < n_int) {
+                const int32_t dim = split_dim[(int64_t)t * n_int + v];
+                v = x[dim] < split_val[(int64_t)t * n_int + v] ? 2 * v + 1 : 2 * v + 2;
+            }
+            leaf[b] = v - n_int;
+        }
+        for (int64_t m = 0; m <= L; ++m) oo[m] = 0;
+        for (int64_t m = 0; m < L; ++m) oo[m + 1] = oi ? oi[m + 1] - oi[m] : 0;
+        for (int64_t b = 0; b < B; ++b) oo[leaf[b] + 1]++;
+        for (int64_t m = 0; m < L; ++m) oo[m + 1] += oo[m];
+        int32_t *po = perm_out + (int64_t)t * N_new;
+        for (int64_t m = 0; m < L; ++m) {
+            cur[m] = oo[m];
+            if (oi)
+                for (int64_t q = oi[m]; q < oi[m + 1]; ++q) po[cur[m]++] = perm_in[(int64_t)t * N_old + q];
+        }
+        for (int64_t b = 0; b < B; ++b) po[cur[leaf[b]]++] = (int32_t)(N_old + b);
+    }
+    free(leaf);
+    free(cur);
+    return 0;
+}
+
+/*
+ * Deletion from the forest, Sec. 5.3.2: the listed points (del [R], distinct,
+ * in [0, N)) leave every bucket; the remaining points keep their order and are
+ * renumbered as the corpus rows are (j becomes j minus the number of deleted
+ * points below j). Split dimensions and values do not change.
+ *  perm_in [T][N], ofs_in [T][2^h + 1] -> perm_out [T][N - R], ofs_out.
+ */
+int oracle_forest_delete(int64_t N, int32_t T, int32_t h, const int32_t *perm_in, const int64_t *ofs_in,
+                         const int32_t *del, int64_t R, int32_t *perm_out, int64_t *ofs_out)
+{
+    if (N < 0 || T < 1 || h < 0 || R < 0 || R > N || !perm_in || !ofs_in || !perm_out || !ofs_out ||
+        (R > 0 && !del))
+        return 1;
+    const int64_t L = (int64_t)1 << h, n = N - R;
+    int64_t *before = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    unsigned char *dead = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
+    if (!before || !dead) {
+        free(before);
+        free(dead);
+        return 2;
+    }
+    int rc = 0;
+    for (int64_t r = 0; r < R; ++r) {
+        if (del[r] < 0 || del[r] >= N || dead[del[r]]) rc = 1;
+        else dead[del[r]] = 1;
+    }
+    if (!rc) {
+        for (int64_t j = 0; j < N; ++j) before[j + 1] = before[j] + dead[j];
+        for (int32_t t = 0; t < T; ++t) {
+            const int64_t *oi = ofs_in + (int64_t)t * (L + 1);
+            int64_t *oo = ofs_out + (int64_t)t * (L + 1);
+            const int32_t *pi = perm_in + (int64_t)t * N;
+            int32_t *po = perm_out + (int64_t)t * n;
+            int64_t w = 0;
+            oo[0] = 0;
+            for (int64_t m = 0; m < L; ++m) {
+                for (int64_t q = oi[m]; q < oi[m + 1]; ++q) {
+                    const int32_t p = pi[q];
+                    if (!dead[p]) po[w++] = (int32_t)(p - before[p]);
+                }
+                oo[m + 1] = w;
+            }
+        }
+    }
+    free(before);
+    free(dead);
     return rc;
 }
 
