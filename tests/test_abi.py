@@ -85,3 +85,35 @@ def test_workspace_too_small_is_enomem(L):
     fake = ctypes.c_void_p(256)
     rc = lib.atsne_symmetrize(fake, fake, 100, 5, fake, fake, fake, None, fake, 16, None)
     assert rc == L.ATSNE_ENOMEM
+
+
+def test_tuner_workspace_and_host_checks(L):
+    lib = L.lib()
+    fake = ctypes.c_void_p(256)
+    for prec in ("fp32", "bf16", "bf16_approx", "fp8"):
+        o = L.knn_opts(precision=prec)
+        for N, D, S in [(70000, 784, 0), (500000, 256, 2000), (20000, 50, 300)]:
+            # the tuner's workspace holds the largest candidate, the rule's among them
+            assert L.workspace_bytes(L.OP_TUNE_KNN, N, D, 90, S, o) >= L.workspace_bytes(L.OP_KNN, N, D, 90, S, o)
+    fo = L.knn_opts(method="forest")
+    assert L.workspace_bytes(L.OP_TUNE_KNN, 1000, 16, 10, 0, fo) == 0
+    splits, ms = ctypes.c_int32(0), ctypes.c_float(0)
+    rc = lib.atsne_tune_knn(fake, 1000, 16, None, 0, 10, ctypes.byref(fo), fake, fake, fake, 1 << 20, None,
+                            ctypes.byref(splits), ctypes.byref(ms))
+    assert rc == L.ATSNE_EUNSUPPORTED
+    o = L.knn_opts()
+    rc = lib.atsne_tune_knn(fake, 1000, 16, None, 0, 10, ctypes.byref(o), fake, fake, fake, 16, None,
+                            ctypes.byref(splits), ctypes.byref(ms))
+    assert rc == L.ATSNE_ENOMEM and b"tune" in lib.atsne_last_error()
+
+
+def test_delete_and_row_dmax_host_checks(L):
+    lib = L.lib()
+    fake = ctypes.c_void_p(256)
+    # more rows than the state holds, a perplexity not below k
+    assert lib.atsne_delete_rows(fake, 11, fake, 10, 4, 5, 2.0, fake, fake, fake, None, None, fake, 1 << 20,
+                                 None) == L.ATSNE_EINVAL
+    assert lib.atsne_delete_rows(fake, 1, fake, 10, 4, 5, 5.0, fake, fake, fake, None, None, fake, 1 << 20,
+                                 None) == L.ATSNE_EINVAL
+    assert lib.atsne_row_dmax(fake, -1, 5, fake, None) == L.ATSNE_EINVAL
+    assert lib.atsne_row_dmax(None, 0, 5, None, None) == L.ATSNE_OK  # nothing to do
