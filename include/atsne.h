@@ -74,7 +74,9 @@ typedef enum {
     ATSNE_OP_KNN_CROSS = 7,    /* N = corpus rows, S = query rows */
     ATSNE_OP_KNN_CROSS_RADIUS = 8, /* as KNN_CROSS, with per-row radii */
     ATSNE_OP_DELETE = 9,           /* N = rows before the deletion, D, k */
-    ATSNE_OP_TUNE_KNN = 10         /* as ATSNE_OP_KNN: the largest candidate's workspace */
+    ATSNE_OP_TUNE_KNN = 10,        /* as ATSNE_OP_KNN: the largest candidate's workspace */
+    ATSNE_OP_FOREST_UPDATE = 11    /* N = points the forest was built on, S = rows after an
+                                      insertion / before a deletion */
 } atsne_op;
 
 /* Options of the kNN step. atsne_knn_opts_default() fills the defaults. */
@@ -394,6 +396,53 @@ atsne_status atsne_forest_layout(int64_t N, int32_t D, const atsne_knn_opts *opt
 atsne_status atsne_forest_build(const float *X, int64_t N, int32_t D, const atsne_knn_opts *opts,
                                 void *forest, size_t forest_bytes, void *workspace,
                                 size_t ws_bytes, void *stream);
+/*
+ * Adding and removing points, Sec. 5.3.1 and Sec. 5.3.2: the forest's trees
+ * (split dimensions and values, as built on N_built points with `opts`) stay,
+ * and its leaf buckets change. An updated set of buckets lives in a separate
+ * caller buffer ("buckets") of atsne_forest_buckets_bytes(N, depth, trees)
+ * bytes: perm [T][N] int32 (each tree's points in leaf order), then at a
+ * 256-byte offset the per-tree leaf offsets [T][2^depth + 1] int32 (trees
+ * differ once points are added). depth is atsne_forest_layout's for N_built.
+ *
+ * atsne_forest_insert: rows N_old .. N_new-1 of X join every tree. A new
+ * point descends a tree by the search's rule (value below the split: left
+ * child) to a leaf and joins its bucket after the points already there, the
+ * new points in index order. buckets_in: NULL for the forest's own buckets
+ * (then N_old = N_built), else the buckets of the first N_old rows.
+ * atsne_forest_delete: the listed rows ([R], distinct, in [0, N)) leave every
+ * bucket; the others keep their order and are renumbered as the corpus rows
+ * are (j becomes j minus the deleted rows below j), as atsne_delete_rows
+ * renumbers the state. A row out of range or listed twice raises the device
+ * status; the buckets are then unspecified.
+ * Both write buckets_out (not overlapping buckets_in) and return the largest
+ * bucket in *max_bucket_out (host), which atsne_forest_query_buckets takes:
+ * they synchronise the stream to read it. Workspace:
+ * atsne_workspace_bytes(ATSNE_OP_FOREST_UPDATE, N_built, D, 0, S, opts), S the
+ * rows after an insertion or before a deletion.
+ */
+size_t atsne_forest_buckets_bytes(int64_t N, int32_t depth, int32_t trees);
+atsne_status atsne_forest_insert(const float *X, int64_t N_built, int64_t N_old, int64_t N_new, int32_t D,
+                                 const atsne_knn_opts *opts, const void *forest, const void *buckets_in,
+                                 void *buckets_out, size_t out_bytes, int32_t *max_bucket_out, void *workspace,
+                                 size_t ws_bytes, void *stream);
+atsne_status atsne_forest_delete(const int32_t *rows, int64_t R, int64_t N_built, int64_t N, int32_t D,
+                                 const atsne_knn_opts *opts, const void *forest, const void *buckets_in,
+                                 void *buckets_out, size_t out_bytes, int32_t *max_bucket_out, void *workspace,
+                                 size_t ws_bytes, void *stream);
+/*
+ * atsne_forest_query over updated buckets: the search of Sec. 4.2 with the
+ * trees of `forest` (built on N_built points) and the leaves' points from
+ * `buckets` (N = the rows of X now). Every point of a reached leaf is
+ * evaluated as in a forest built with larger leaves. Workspace:
+ * atsne_workspace_bytes(ATSNE_OP_FOREST_QUERY, N, D, k, S, opts) with
+ * opts->leaf_size = max_bucket.
+ */
+atsne_status atsne_forest_query_buckets(const float *X, int64_t N, int32_t D, int64_t N_built, const void *forest,
+                                        const void *buckets, int32_t max_bucket, const int32_t *queries, int64_t S,
+                                        int32_t k, const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                                        int64_t *evaluated_out, void *workspace, size_t ws_bytes, void *stream);
+
 atsne_status atsne_forest_query(const float *X, int64_t N, int32_t D, const void *forest,
                                 const int32_t *queries, int64_t S, int32_t k,
                                 const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,

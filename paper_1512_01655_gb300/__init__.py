@@ -17,7 +17,7 @@ ATSNE_OK, ATSNE_EINVAL, ATSNE_ENOMEM, ATSNE_ECUDA, ATSNE_ETIMEOUT, ATSNE_EUNSUPP
 KNN_EXACT, KNN_FOREST = 0, 1
 FP32, BF16_RERANK, FP32_CUDA_CORES, FP8_RERANK, BF16_RERANK_APPROX = 0, 1, 2, 3, 4
 (OP_KNN, OP_CALIBRATE, OP_SYMMETRIZE, OP_REFINE, OP_FOREST_BUILD, OP_FOREST_QUERY,
- OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS, OP_DELETE, OP_TUNE_KNN) = range(11)
+ OP_REFINE_BATCH, OP_KNN_CROSS, OP_KNN_CROSS_RADIUS, OP_DELETE, OP_TUNE_KNN, OP_FOREST_UPDATE) = range(12)
 
 EXPORTED = (
     "atsne_knn_opts_default", "atsne_workspace_bytes", "atsne_knn", "atsne_calibrate_P",
@@ -27,7 +27,8 @@ EXPORTED = (
     "atsne_refine_subset_noalloc", "atsne_refine_batch", "atsne_kde_map", "atsne_knn_cross",
     "atsne_knn_rows",
     "atsne_merge_neighbors", "atsne_commit_rows", "atsne_delete_rows", "atsne_tune_knn", "atsne_row_dmax",
-    "atsne_tune_clear",
+    "atsne_tune_clear", "atsne_forest_buckets_bytes", "atsne_forest_insert", "atsne_forest_delete",
+    "atsne_forest_query_buckets",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
@@ -95,6 +96,14 @@ def lib():
                                      _vp, _vp, _sz, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f32)]
         L.atsne_tune_clear.argtypes = []
         L.atsne_row_dmax.argtypes = [_vp, _i64, _i32, _vp, _vp]
+        L.atsne_forest_buckets_bytes.argtypes = [_i64, _i32, _i32]
+        L.atsne_forest_buckets_bytes.restype = _sz
+        L.atsne_forest_insert.argtypes = [_vp, _i64, _i64, _i64, _i32, ctypes.POINTER(KnnOpts), _vp, _vp, _vp,
+                                          _sz, ctypes.POINTER(_i32), _vp, _sz, _vp]
+        L.atsne_forest_delete.argtypes = [_vp, _i64, _i64, _i64, _i32, ctypes.POINTER(KnnOpts), _vp, _vp, _vp,
+                                          _sz, ctypes.POINTER(_i32), _vp, _sz, _vp]
+        L.atsne_forest_query_buckets.argtypes = [_vp, _i64, _i32, _i64, _vp, _vp, _i32, _vp, _i64, _i32,
+                                                 ctypes.POINTER(KnnOpts), _vp, _vp, _vp, _vp, _sz, _vp]
         L.atsne_kde_map.argtypes = [_vp, _i64, _vp, _vp, _f32, _f32, _f32, _i32, _i32, _f32, _f32,
                                     _f32, _vp, _vp, _vp, _vp, _vp]
         L.atsne_forest_layout.argtypes = [_i64, _i32, ctypes.POINTER(KnnOpts),
@@ -115,7 +124,7 @@ def lib():
         for name in EXPORTED:
             f = getattr(L, name)
             if name not in ("atsne_knn_opts_default", "atsne_workspace_bytes",
-                            "atsne_last_error", "atsne_launch_count"):
+                            "atsne_last_error", "atsne_launch_count", "atsne_forest_buckets_bytes"):
                 f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -441,7 +450,63 @@ def atsne_forest_build(X, stream=None, opts=None, **kw):
     return Forest(buf, L, N, D, o)
 
 
-def atsne_forest_query(X, forest, k, checks=None, queries=None, queue_cap=None, stream=None):
+class ForestBuckets:
+    """A forest's leaf buckets after points were added or removed (Sec. 5.3):
+    perm [T][N] and per-tree leaf offsets, in one device buffer; the trees are
+    those of `forest`."""
+
+    def __init__(self, buf, forest, N, max_bucket):
+        self.buf, self.forest, self.N, self.max_bucket = buf, forest, N, max_bucket
+
+    def arrays(self):
+        L, T = self.forest.layout, self.forest.layout.trees
+        n_ofs = (1 << L.depth) + 1
+        size = T * self.N * 4
+        off = (size + 255) & ~255
+        return dict(perm=self.buf[:size].view(torch.int32).view(T, self.N),
+                    leaf_ofs=self.buf[off:off + T * n_ofs * 4].view(torch.int32).view(T, n_ofs))
+
+
+def _buckets_buffer(forest, N, device):
+    n = lib().atsne_forest_buckets_bytes(N, forest.layout.depth, forest.layout.trees)
+    return torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
+
+
+def atsne_forest_insert(X, forest, n_old, buckets=None, stream=None):
+    """Rows n_old .. N-1 of X join every tree of `forest` (Sec. 5.3.1), after
+    the buckets of the first n_old rows (`buckets`, or the forest's own when
+    n_old is the number of points it was built on). Returns ForestBuckets."""
+    _dev(X, torch.float32, "X")
+    N, D = X.shape
+    o = KnnOpts.from_buffer_copy(forest.opts)
+    out = _buckets_buffer(forest, N, X.device)
+    ws = _workspace(workspace_bytes(OP_FOREST_UPDATE, forest.N, D, 0, N, o), X.device)
+    mb = _i32(0)
+    _raise(lib().atsne_forest_insert(_p(X), forest.N, int(n_old), N, D, ctypes.byref(o), _p(forest.buf),
+                                     _p(buckets.buf) if buckets is not None else None, _p(out), out.numel(),
+                                     ctypes.byref(mb), _p(ws), ws.numel(), _stream(stream)))
+    return ForestBuckets(out, forest, N, int(mb.value))
+
+
+def atsne_forest_delete(forest, rows, buckets=None, stream=None):
+    """The listed rows leave every tree (Sec. 5.3.2); the others are renumbered
+    as the corpus rows are. Returns ForestBuckets."""
+    _dev(rows, torch.int32, "rows")
+    N = buckets.N if buckets is not None else forest.N
+    o = KnnOpts.from_buffer_copy(forest.opts)
+    R = rows.shape[0]
+    out = _buckets_buffer(forest, N - R, forest.buf.device)
+    ws = _workspace(workspace_bytes(OP_FOREST_UPDATE, forest.N, forest.D, 0, N, o), forest.buf.device)
+    mb = _i32(0)
+    _raise(lib().atsne_forest_delete(_p(rows), R, forest.N, N, forest.D, ctypes.byref(o), _p(forest.buf),
+                                     _p(buckets.buf) if buckets is not None else None, _p(out), out.numel(),
+                                     ctypes.byref(mb), _p(ws), ws.numel(), _stream(stream)))
+    return ForestBuckets(out, forest, N - R, int(mb.value))
+
+
+def atsne_forest_query(X, forest, k, checks=None, queries=None, queue_cap=None, stream=None, buckets=None):
+    """Forest search (Sec. 4.2); with `buckets` (ForestBuckets), over the
+    leaf buckets after points were added or removed."""
     _dev(X, torch.float32, "X")
     N, D = X.shape
     o = KnnOpts.from_buffer_copy(forest.opts)
@@ -457,6 +522,14 @@ def atsne_forest_query(X, forest, k, checks=None, queries=None, queue_cap=None, 
     idx = torch.empty((rows, k), dtype=torch.int32, device=X.device)
     d2 = torch.empty((rows, k), dtype=torch.float32, device=X.device)
     ev = torch.empty(rows, dtype=torch.int64, device=X.device)
+    if buckets is not None:
+        ob = KnnOpts.from_buffer_copy(o)
+        ob.leaf_size = buckets.max_bucket
+        ws = _workspace(workspace_bytes(OP_FOREST_QUERY, N, D, k, S, ob), X.device)
+        _raise(lib().atsne_forest_query_buckets(_p(X), N, D, forest.N, _p(forest.buf), _p(buckets.buf),
+                                                buckets.max_bucket, _p(queries), S, k, ctypes.byref(o), _p(idx),
+                                                _p(d2), _p(ev), _p(ws), ws.numel(), _stream(stream)))
+        return idx, d2, ev
     ws = _workspace(workspace_bytes(OP_FOREST_QUERY, N, D, k, S, o), X.device)
     _raise(lib().atsne_forest_query(_p(X), N, D, _p(forest.buf), _p(queries), S, k,
                                     ctypes.byref(o), _p(idx), _p(d2), _p(ev), _p(ws), ws.numel(),

@@ -303,6 +303,73 @@ size_t refine_batch_ws(Carver &c, int64_t N, int32_t D, int64_t total, int32_t k
 }  // namespace
 }  // namespace atsne
 
+namespace atsne {
+namespace {
+// The trees of a built forest and, for a buckets buffer, its views.
+struct UpdateArgs {
+    ForestView f;
+    const int32_t *perm_in, *ofs_in;
+    int64_t stride_in;
+    BucketsView out;
+    UpdateWs w;
+};
+
+atsne_status update_args(const float *X, int64_t N_built, int64_t n_in, int64_t n_out, int64_t ws_rows, int32_t D,
+                         const atsne_knn_opts *opts, const void *forest, const void *buckets_in, void *buckets_out,
+                         size_t out_bytes, void *workspace, size_t ws_bytes, const char *what, UpdateArgs *a) {
+    atsne_knn_opts o = opts_or_default(opts);
+    o.method = ATSNE_KNN_FOREST;
+    atsne_status st = validate_knn_opts(o);
+    if (st) return st;
+    if (!forest || !buckets_out || (!buckets_in && n_in != N_built) || (X == nullptr && D < 1))
+        return set_error(ATSNE_EINVAL, "%s: NULL pointer or buckets", what);
+    if (N_built < 2 || N_built > INT32_MAX || n_in < 0 || n_out < 0 || n_in > INT32_MAX || n_out > INT32_MAX ||
+        D < 1)
+        return set_error(ATSNE_EINVAL, "%s: N_built=%lld rows %lld -> %lld D=%d", what, (long long)N_built,
+                         (long long)n_in, (long long)n_out, D);
+    a->f = forest_view(const_cast<void *>(forest), N_built, D, o);
+    const int depth = a->f.depth;
+    if (depth > 25) return set_error(ATSNE_EUNSUPPORTED, "%s: depth %d", what, depth);
+    size_t off = 0;
+    if (buckets_layout(n_out, depth, o.trees, &off) > out_bytes)
+        return set_error(ATSNE_ENOMEM, "%s: buckets buffer of %zu bytes too small", what, out_bytes);
+    if (buckets_in == buckets_out) return set_error(ATSNE_EINVAL, "%s: buckets_in and buckets_out overlap", what);
+    if ((st = check_base(forest, what)) || (st = check_base(buckets_out, what)) ||
+        (buckets_in && (st = check_base(buckets_in, what))) || (st = check_base(workspace, what)))
+        return st;
+    char *bo = static_cast<char *>(buckets_out);
+    a->out.perm = reinterpret_cast<int32_t *>(bo);
+    a->out.ofs = reinterpret_cast<int32_t *>(bo + off);
+    if (buckets_in) {
+        size_t off_in = 0;
+        buckets_layout(n_in, depth, o.trees, &off_in);
+        const char *bi = static_cast<const char *>(buckets_in);
+        a->perm_in = reinterpret_cast<const int32_t *>(bi);
+        a->ofs_in = reinterpret_cast<const int32_t *>(bi + off_in);
+        a->stride_in = ((int64_t)1 << depth) + 1;
+    } else {
+        a->perm_in = a->f.perm;
+        a->ofs_in = a->f.leaf_ofs;
+        a->stride_in = 0;
+    }
+    Carver c(workspace);
+    update_workspace(c, ws_rows, depth, o.trees, &a->w);
+    if (!workspace || ws_bytes < c.bytes())
+        return set_error(ATSNE_ENOMEM, "%s: workspace of %zu bytes, %zu needed", what, ws_bytes, c.bytes());
+    return ATSNE_OK;
+}
+
+atsne_status read_max_bucket(const UpdateWs &w, int32_t *out, cudaStream_t stream) {
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, w.bmax, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_error(e, "forest update: read the largest bucket");
+    if (out) *out = v;
+    return ATSNE_OK;
+}
+}  // namespace
+}  // namespace atsne
+
 using namespace atsne;
 
 extern "C" {
@@ -345,6 +412,8 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
         return cross_ws(c, S, N, D, k, o, false, nullptr, nullptr);
     case ATSNE_OP_DELETE:
         return delete_workspace(c, N, D, k, nullptr);
+    case ATSNE_OP_FOREST_UPDATE:
+        return update_workspace(c, S, forest_depth(N, o.leaf_size), o.trees, nullptr);
     case ATSNE_OP_TUNE_KNN:
         return exact_on_tensor_cores(o, k) ? tune_ws(N, D, k, S, o, nullptr, nullptr) : 0;
     case ATSNE_OP_KNN_CROSS_RADIUS:
@@ -756,6 +825,82 @@ atsne_status atsne_forest_query(const float *X, int64_t N, int32_t D, const void
     return forest_query_launch(X, forest_view(const_cast<void *>(forest), N, D, o), queries, nq, k,
                                o.checks, queue_capacity(o), idx_out, d2_out, evaluated_out, workspace,
                                ws_bytes, stream);
+}
+
+size_t atsne_forest_buckets_bytes(int64_t N, int32_t depth, int32_t trees) {
+    if (N < 0 || depth < 0 || depth > 25 || trees < 1) return 0;
+    return buckets_layout(N, depth, trees, nullptr);
+}
+
+
+atsne_status atsne_forest_insert(const float *X, int64_t N_built, int64_t N_old, int64_t N_new, int32_t D,
+                                 const atsne_knn_opts *opts, const void *forest, const void *buckets_in,
+                                 void *buckets_out, size_t out_bytes, int32_t *max_bucket_out, void *workspace,
+                                 size_t ws_bytes, void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!X) return set_error(ATSNE_EINVAL, "forest insert: NULL X");
+    if (N_new < N_old) return set_error(ATSNE_EINVAL, "forest insert: N_new=%lld < N_old=%lld",
+                                        (long long)N_new, (long long)N_old);
+    UpdateArgs a;
+    atsne_status st = update_args(X, N_built, N_old, N_new, N_new, D, opts, forest, buckets_in, buckets_out,
+                                  out_bytes, workspace, ws_bytes, "forest insert", &a);
+    if (st) return st;
+    if (N_new > N_old && (st = check_finite(X + N_old * (int64_t)D, (N_new - N_old) * (int64_t)D, stream)))
+        return st;
+    if ((st = forest_insert_launch(X, N_old, N_new, D, a.f, a.perm_in, a.ofs_in, a.stride_in, a.out, a.w, stream)))
+        return st;
+    return read_max_bucket(a.w, max_bucket_out, stream);
+}
+
+atsne_status atsne_forest_delete(const int32_t *rows, int64_t R, int64_t N_built, int64_t N, int32_t D,
+                                 const atsne_knn_opts *opts, const void *forest, const void *buckets_in,
+                                 void *buckets_out, size_t out_bytes, int32_t *max_bucket_out, void *workspace,
+                                 size_t ws_bytes, void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (R < 0 || R > N || (R > 0 && !rows))
+        return set_error(ATSNE_EINVAL, "forest delete: R=%lld N=%lld", (long long)R, (long long)N);
+    UpdateArgs a;
+    atsne_status st = update_args(nullptr, N_built, N, N - R, N, D, opts, forest, buckets_in, buckets_out,
+                                  out_bytes, workspace, ws_bytes, "forest delete", &a);
+    if (st) return st;
+    if ((st = forest_delete_launch(rows, R, N, a.f, a.perm_in, a.ofs_in, a.stride_in, a.out, a.w, stream)))
+        return st;
+    return read_max_bucket(a.w, max_bucket_out, stream);
+}
+
+atsne_status atsne_forest_query_buckets(const float *X, int64_t N, int32_t D, int64_t N_built, const void *forest,
+                                        const void *buckets, int32_t max_bucket, const int32_t *queries, int64_t S,
+                                        int32_t k, const atsne_knn_opts *opts, int32_t *idx_out, float *d2_out,
+                                        int64_t *evaluated_out, void *workspace, size_t ws_bytes, void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    atsne_status st = validate_xk(X, N, D, k);
+    if (st) return st;
+    atsne_knn_opts o = opts_or_default(opts);
+    o.method = ATSNE_KNN_FOREST;
+    if ((st = validate_knn_opts(o))) return st;
+    if (!forest || !buckets || !idx_out || !d2_out)
+        return set_error(ATSNE_EINVAL, "forest query buckets: NULL pointer");
+    if (N_built < 2 || N_built > INT32_MAX || max_bucket < 1 || max_bucket > N)
+        return set_error(ATSNE_EINVAL, "forest query buckets: N_built=%lld max_bucket=%d", (long long)N_built,
+                         max_bucket);
+    if (queries && S < 0) return set_error(ATSNE_EINVAL, "forest query buckets: S < 0");
+    if ((st = check_base(forest, "forest query buckets")) || (st = check_base(buckets, "forest query buckets")) ||
+        (st = check_base(workspace, "forest query buckets")))
+        return st;
+    ForestView f = forest_view(const_cast<void *>(forest), N_built, D, o);
+    size_t off = 0;
+    buckets_layout(N, f.depth, o.trees, &off);
+    char *b = static_cast<char *>(const_cast<void *>(buckets));
+    f.N = N;
+    f.perm = reinterpret_cast<int32_t *>(b);
+    f.leaf_ofs = reinterpret_cast<int32_t *>(b + off);
+    f.ofs_stride = ((int64_t)1 << f.depth) + 1;
+    f.leaf_size = max_bucket;
+    const int64_t nq = queries ? S : N;
+    if (nq == 0) return ATSNE_OK;
+    if (queries && (st = check_indices(queries, S, N, stream))) return st;
+    return forest_query_launch(X, f, queries, nq, k, o.checks, queue_capacity(o), idx_out, d2_out, evaluated_out,
+                               workspace, ws_bytes, stream);
 }
 
 atsne_status atsne_check(void *stream) {

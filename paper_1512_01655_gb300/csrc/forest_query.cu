@@ -76,6 +76,7 @@ struct FqArgs {
     const int32_t *leaf_ofs;
     const int32_t *leaf_pt;
     int leaf_size;
+    int64_t ofs_stride;  // 0: leaf offsets shared by the trees; else per tree
     const int32_t *qlist;
     int64_t w0, nw;    // work items of this chunk: leaf positions of tree 0, or list entries
     int64_t *evaluated_out;
@@ -430,8 +431,9 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
             __syncwarp();
 
             auto scan_leaf = [&](int tr, int m) {
-                const int s0 = A.leaf_ofs[m];
-                const int cnt = A.leaf_ofs[m + 1] - s0;
+                const int32_t *lo = A.leaf_ofs + (int64_t)tr * A.ofs_stride;
+                const int s0 = lo[m];
+                const int cnt = lo[m + 1] - s0;
                 const int32_t *pt = A.perm + (int64_t)tr * A.N + s0;
                 for (int b = 0; b < cnt; b += 32) {
                     const int q = b + lane;
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
                     __syncwarp();
                 }
             };
-            if (A.leaf_size == 1) {
+            if (A.leaf_size == 1 && A.ofs_stride == 0) {
                 // one point per leaf: the seen test of step i is resolved after the
                 // descent of step i + 1 (descents never read the bitmap; a step made
                 // past the stopping point only adds queue entries that are not used)
@@ -875,6 +877,7 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     a.leaf_ofs = f.leaf_ofs;
     a.leaf_pt = f.leaf_pt;
     a.leaf_size = f.leaf_size;
+    a.ofs_stride = f.ofs_stride;
     a.qlist = qlist;
     a.evaluated_out = evaluated_out;
     a.xu8 = u8.xu8;

@@ -124,6 +124,10 @@ struct ForestView {
     int32_t *perm;
     int32_t *leaf_ofs;
     int32_t *leaf_pt;
+    // 0: one leaf-offset array for all trees (a forest as built, leaf_pt valid);
+    // else each tree's offsets (buckets after points were added or removed,
+    // leaf_size = the largest bucket)
+    int64_t ofs_stride = 0;
 };
 int forest_depth(int64_t N, int leaf_size);
 size_t forest_layout(int64_t N, int trees, int leaf_size, atsne_forest_layout_t *out);
@@ -132,6 +136,23 @@ atsne_status forest_build_launch(const float *X, const ForestView &f, void *ws_b
                                  cudaStream_t stream);
 size_t forest_query_workspace(Carver &c, int64_t N, int D, int64_t nq, int k, int checks, int leaf_size,
                               void *ws_out);
+// Buckets after points were added or removed (Sec. 5.3.1, 5.3.2): perm
+// [T][N] and per-tree leaf offsets [T][2^h + 1], both int32, in one buffer.
+struct BucketsView {
+    int32_t *perm, *ofs;
+};
+size_t buckets_layout(int64_t N, int depth, int trees, size_t *off_ofs);
+struct UpdateWs {
+    int32_t *leaf = nullptr, *cursor = nullptr, *dead = nullptr, *bmax = nullptr;
+    int64_t *before = nullptr, *total = nullptr, *scan = nullptr;
+};
+size_t update_workspace(Carver &c, int64_t N, int depth, int trees, UpdateWs *ws);
+atsne_status forest_insert_launch(const float *X, int64_t N_old, int64_t N_new, int D, const ForestView &f,
+                                  const int32_t *perm_in, const int32_t *ofs_in, int64_t stride_in,
+                                  const BucketsView &out, const UpdateWs &w, cudaStream_t stream);
+atsne_status forest_delete_launch(const int32_t *rows, int64_t R, int64_t N, const ForestView &f,
+                                  const int32_t *perm_in, const int32_t *ofs_in, int64_t stride_in,
+                                  const BucketsView &out, const UpdateWs &w, cudaStream_t stream);
 atsne_status forest_query_launch(const float *X, const ForestView &f, const int32_t *qlist,
                                  int64_t nq, int k, int checks, int qcap, int32_t *idx_out,
                                  float *d2_out, int64_t *evaluated_out, void *ws_base,

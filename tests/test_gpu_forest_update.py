@@ -1,0 +1,92 @@
+"""Adding points to and removing points from the forest on the GPU (Sec. 5.3.1,
+Sec. 5.3.2) against the oracle: the buckets bit for bit, and the search over
+the updated buckets with the oracle's visiting order."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1512_01655_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def at():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1512_01655_gb300 as pkg
+    return pkg
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def same_buckets(b, o):
+    g = {a: v.cpu().numpy() for a, v in b.arrays().items()}
+    assert np.array_equal(g["perm"], o["perm"])
+    assert np.array_equal(g["leaf_ofs"], o["leaf_ofs"])
+    sizes = np.diff(o["leaf_ofs"], axis=1)
+    assert b.max_bucket == sizes.max()
+
+
+def same_search(at, Xd, X, f, b, o, k, checks):
+    idx, d2, ev = at.atsne_forest_query(Xd, f, k, checks=checks, buckets=b)
+    at.atsne_check()
+    o_idx, o_d2, o_ev = oracle.forest_query(X, o, k, checks)
+    assert np.array_equal(ev.cpu().numpy(), o_ev)  # identical visiting order
+    gi = idx.cpu().numpy()
+    same = np.array([set(gi[r]) == set(o_idx[r]) for r in range(X.shape[0])])
+    assert same.mean() > 0.99
+    assert np.abs(d2.cpu().numpy() - o_d2).max() <= 1e-5 * max(1.0, o_d2.max())
+
+
+@pytest.mark.parametrize("kind", ["gauss", "bytes"])
+def test_insert_delete_and_search_match_oracle(at, kind):
+    if kind == "gauss":
+        X = synth.gaussian_mixture(2200, 16, seed=23)
+    else:
+        X = synth.sparse_prototypes(N=2200, D=784, seed=5)
+    Xd = to_dev(X)
+    f = at.atsne_forest_build(Xd[:1800].contiguous(), trees=3, leaf_size=1, seed=6)
+    o = oracle.forest_build(X[:1800], trees=3, top_var_dims=5, leaf_size=1, seed=6)
+    # two insertions: from the built forest, then from the first one's buckets
+    b1 = at.atsne_forest_insert(Xd[:2000].contiguous(), f, 1800)
+    o1 = oracle.forest_insert(o, X[:2000], 1800)
+    same_buckets(b1, o1)
+    b2 = at.atsne_forest_insert(Xd, f, 2000, buckets=b1)
+    o2 = oracle.forest_insert(o1, X, 2000)
+    same_buckets(b2, o2)
+    same_search(at, Xd, X, f, b2, o2, 20, 300)
+    # a deletion from the updated buckets, then the search over the reduced corpus
+    gone = np.arange(0, 2200, 11).astype(np.int32)
+    b3 = at.atsne_forest_delete(f, to_dev(gone), buckets=b2)
+    at.atsne_check()
+    o3 = oracle.forest_delete(o2, gone)
+    same_buckets(b3, o3)
+    keep = np.setdiff1d(np.arange(2200), gone)
+    Xr = X[keep]
+    same_search(at, to_dev(Xr), Xr, f, b3, o3, 20, 300)
+
+
+def test_delete_from_the_built_forest_and_edge_cases(at):
+    X = synth.gaussian_mixture(1000, 8, seed=24)
+    Xd = to_dev(X)
+    f = at.atsne_forest_build(Xd, trees=2, leaf_size=1, seed=2)
+    o = oracle.forest_build(X, trees=2, top_var_dims=5, leaf_size=1, seed=2)
+    gone = np.array([0, 17, 999], np.int32)
+    b = at.atsne_forest_delete(f, to_dev(gone))
+    at.atsne_check()
+    same_buckets(b, oracle.forest_delete(o, gone))
+    # nothing added, nothing removed: the forest's own buckets
+    b0 = at.atsne_forest_insert(Xd, f, 1000)
+    same_buckets(b0, oracle.forest_insert(o, X, 1000))
+    b00 = at.atsne_forest_delete(f, to_dev(np.zeros(0, np.int32)))
+    at.atsne_check()
+    same_buckets(b00, oracle.forest_delete(o, np.zeros(0, np.int32)))
+    # a row listed twice is reported through the status word
+    at.atsne_forest_delete(f, to_dev(np.array([4, 4], np.int32)))
+    with pytest.raises(at.AtsneError):
+        at.atsne_check()
