@@ -173,15 +173,17 @@ atsne_status atsne_refine_subset(const float *X, int64_t N, int32_t D, const int
 /*
  * Refinement without device allocation. The paper has no counterpart: this is
  * atsne_refine_subset for callers that cannot allocate device memory when they
- * refine (inside an open CUDA stream capture, where cudaMalloc is not allowed;
- * in a render or UI callback that must not wait on an allocator; under a fixed
- * device-memory budget). Instead of a workspace it uses one fixed device array
+ * refine: a render or UI callback of an interactive view that must not stall
+ * on cudaMalloc (which can synchronise the whole device), or a program whose
+ * device-memory budget is fixed up front by another component. Instead of a
+ * workspace it uses one fixed device array
  * inside the library (3 MiB + 8 KiB, held on every GPU that loads the library
  * until the process exits), so it accepts at most
  * ATSNE_REFINE_NOALLOC_MAX_ROWS selected rows and k <= ATSNE_REFINE_NOALLOC_MAX_K;
  * larger requests return ATSNE_ENOMEM with a message. Arguments, outputs and
- * results are those of atsne_refine_subset. The first call on a device looks up
- * the array's address (cudaGetSymbolAddress); make it before any stream
+ * results are those of atsne_refine_subset. The first call on a device (any
+ * size, an empty selection included) looks up the array's address and the
+ * library's status word (cudaGetSymbolAddress); make it before any stream
  * capture. All calls share the array: calls whose work may overlap on the GPU
  * race and must be ordered (one stream, or events).
  */
@@ -415,7 +417,7 @@ atsne_status atsne_forest_build(const float *X, int64_t N, int32_t D, const atsn
  * are (j becomes j minus the deleted rows below j), as atsne_delete_rows
  * renumbers the state. A row out of range or listed twice raises the device
  * status; the buckets are then unspecified.
- * Both write buckets_out (not overlapping buckets_in) and return the largest
+ * Both write buckets_out (no byte of it may overlap buckets_in) and return the largest
  * bucket in *max_bucket_out (host), which atsne_forest_query_buckets takes:
  * they synchronise the stream to read it. Workspace:
  * atsne_workspace_bytes(ATSNE_OP_FOREST_UPDATE, N_built, D, 0, S, opts), S the
@@ -436,7 +438,11 @@ atsne_status atsne_forest_delete(const int32_t *rows, int64_t R, int64_t N_built
  * `buckets` (N = the rows of X now). Every point of a reached leaf is
  * evaluated as in a forest built with larger leaves. Workspace:
  * atsne_workspace_bytes(ATSNE_OP_FOREST_QUERY, N, D, k, S, opts) with
- * opts->leaf_size = max_bucket.
+ * opts->leaf_size = max_bucket. max_bucket must be at least the largest
+ * bucket (the value the update returned): each query's point list is sized
+ * by it. A bucket above max_bucket raises the device status (atsne_check
+ * returns ATSNE_EINVAL); no list is written past its end, and the results
+ * are then unspecified.
  */
 atsne_status atsne_forest_query_buckets(const float *X, int64_t N, int32_t D, int64_t N_built, const void *forest,
                                         const void *buckets, int32_t max_bucket, const int32_t *queries, int64_t S,

@@ -53,6 +53,8 @@ def lib():
         L.oracle_kde.argtypes = [_f32p, _i64, _vp, _vp, _f64, _f64, _f64, _i32, _i32, _f64, _f64,
                                  _f64, _f64p, _f64p, _f64p, _f64p]
         L.oracle_knn_cross.argtypes = [_f32p, _i64, _f32p, _i64, _i32, _i32, _i32p, _f64p]
+        L.oracle_insert.argtypes = [_f32p, _i64, _i64, _i32, _i32, _i32p, _f64p,
+                                    np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")]
         L.oracle_refine.argtypes = [_f32p, _i64, _i32, _i32p, _i64, _i32, _f64, _f64, _i32, _i32p,
                                     _f64p, _f64p, _f64p, _f64p]
         L.oracle_delete.argtypes = [_f32p, _i64, _i32, _i32p, _i64, _i32, _f64, _f64, _i32, _i32p,
@@ -301,3 +303,17 @@ def delete(X, rows, k, perplexity, idx, d2, P, beta, rho, tol=1e-10, max_iter=20
                                int(max_iter), *st, ctypes.byref(n)), "delete")
     n = n.value
     return (X[:n],) + tuple(a[:n] for a in st)
+
+
+def insert(X, n_old, idx, d2):
+    """Eq. 11 (Sec. 5.3.1) on copies of the state: rows n_old.. of X are new
+    points; each of the first n_old rows takes the new points strictly closer
+    than its farthest present neighbour. Returns (idx, d2, changed)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    N, D = X.shape
+    idx = np.array(idx, dtype=np.int32, order="C", copy=True)
+    d2 = np.array(d2, dtype=np.float64, order="C", copy=True)
+    k = idx.shape[1]
+    changed = np.zeros(n_old, np.uint8)
+    _check(lib().oracle_insert(X, int(n_old), N, D, k, idx, d2, changed), "insert")
+    return idx, d2, changed.astype(bool)

@@ -28,6 +28,8 @@
  *   oracle_forest_insert Sec. 5.3.1: a new point joins the forest by a descent
  *                        of every tree to a leaf
  *   oracle_forest_delete Sec. 5.3.2: a deleted point leaves every tree
+ *   oracle_insert        Eq. 11 (Sec. 5.3.1): new points enter the existing
+ *                        neighbourhoods they fall inside
  *
  * Readings taken where the paper is silent are stated at each function.
  * Compile with -ffp-contract=off: the forest's float decisions (split value,
@@ -957,6 +959,54 @@ int oracle_knn_cross(const float *Xq, int64_t Nq, const float *Xc, int64_t Nc, i
         int cnt = 0;
         for (int64_t j = 0; j < Nc; ++j)
             best_insert(bd, bj, k, &cnt, sq_dist(Xq + q * D, Xc + j * D, D), (int32_t)j);
+    }
+    return 0;
+}
+
+/*
+ * Insertion of new points into the existing neighbourhoods, Eq. 11 (Sec. 5.3.1).
+ * X holds N_new rows; rows 0..N_old-1 carry the neighbourhoods idx/d2
+ * ([N_old][k], each sorted by (d2, index); absent entries, index -1 and
+ * distance +inf, come last). For row i, d_i^Max is the largest distance among
+ * its present entries. A new point j (N_old <= j < N_new) enters N_i exactly
+ * when d(i, j) < d_i^Max, strictly, with d in FP64 by direct differences. The
+ * row then holds the k smallest of its present entries and the entering points
+ * in the (d2, index) order: an entering point fills an absent entry while one
+ * is left, and otherwise the farthest neighbour leaves. A tie with a listed
+ * point goes to the listed point, whose index is smaller. A row with no
+ * present entry has no d_i^Max and takes no point. changed[i] = 1 when the
+ * row's list changed. rho_i is not an argument: insertion leaves it as it is.
+ */
+int oracle_insert(const float *X, int64_t N_old, int64_t N_new, int32_t D, int32_t k, int32_t *idx,
+                  double *d2, uint8_t *changed)
+{
+    if (!X || N_old < 0 || N_new < N_old || D < 1 || k < 1 || (N_old > 0 && (!idx || !d2))) return 1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N_old; ++i) {
+        int32_t *ri = idx + i * k;
+        double *rd = d2 + i * k;
+        int cnt = 0;
+        double dmax = -1.0;
+        while (cnt < k && ri[cnt] >= 0) {
+            if (rd[cnt] > dmax) dmax = rd[cnt];
+            ++cnt;
+        }
+        int ch = 0;
+        if (cnt > 0) {
+            const float *xi = X + i * (int64_t)D;
+            for (int64_t j = N_old; j < N_new; ++j) {
+                const double d = sq_dist(xi, X + j * (int64_t)D, D);
+                if (d < dmax) {
+                    best_insert(rd, ri, k, &cnt, d, (int32_t)j);
+                    ch = 1;
+                }
+            }
+            for (int t = cnt; t < k; ++t) {
+                ri[t] = -1;
+                rd[t] = INFINITY;
+            }
+        }
+        if (changed) changed[i] = (uint8_t)ch;
     }
     return 0;
 }

@@ -333,7 +333,14 @@ atsne_status update_args(const float *X, int64_t N_built, int64_t n_in, int64_t 
     size_t off = 0;
     if (buckets_layout(n_out, depth, o.trees, &off) > out_bytes)
         return set_error(ATSNE_ENOMEM, "%s: buckets buffer of %zu bytes too small", what, out_bytes);
-    if (buckets_in == buckets_out) return set_error(ATSNE_EINVAL, "%s: buckets_in and buckets_out overlap", what);
+    if (buckets_in) {  // any overlap of the two byte ranges races the copy with its source
+        const char *i0 = static_cast<const char *>(buckets_in);
+        const char *i1 = i0 + buckets_layout(n_in, depth, o.trees, nullptr);
+        const char *o0 = static_cast<const char *>(buckets_out);
+        const char *o1 = o0 + out_bytes;
+        if (i0 < o1 && o0 < i1)
+            return set_error(ATSNE_EINVAL, "%s: buckets_in and buckets_out overlap", what);
+    }
     if ((st = check_base(forest, what)) || (st = check_base(buckets_out, what)) ||
         (buckets_in && (st = check_base(buckets_in, what))) || (st = check_base(workspace, what)))
         return st;
@@ -899,6 +906,8 @@ atsne_status atsne_forest_query_buckets(const float *X, int64_t N, int32_t D, in
     const int64_t nq = queries ? S : N;
     if (nq == 0) return ATSNE_OK;
     if (queries && (st = check_indices(queries, S, N, stream))) return st;
+    // the lists are sized for buckets of max_bucket points: a larger bucket is flagged
+    if ((st = bucket_bound_check(f.leaf_ofs, o.trees, f.depth, max_bucket, stream))) return st;
     return forest_query_launch(X, f, queries, nq, k, o.checks, queue_capacity(o), idx_out, d2_out, evaluated_out,
                                workspace, ws_bytes, stream);
 }

@@ -91,6 +91,7 @@ struct FqArgs {
     const uint8_t *xu8;      // byte copy of X, when every value is an integer in [0, 255]
     const unsigned *u8_bad;
     int Dp16;
+    int *status;
 };
 
 struct FdArgs {
@@ -433,7 +434,13 @@ __global__ void __launch_bounds__(FQ_WARPS * 32, QB ? 8 : 7) forest_traverse_ker
             auto scan_leaf = [&](int tr, int m) {
                 const int32_t *lo = A.leaf_ofs + (int64_t)tr * A.ofs_stride;
                 const int s0 = lo[m];
-                const int cnt = lo[m + 1] - s0;
+                int cnt = lo[m + 1] - s0;
+                // a bucket larger than the leaf size the list was sized for (a
+                // caller's stale bucket bound) is cut to the list's room and flagged
+                if (cnt > A.mark_cap - n_marked) {
+                    if (lane == 0) raise_status(A.status, DEV_MALFORMED);
+                    cnt = (int)(A.mark_cap - n_marked);
+                }
                 const int32_t *pt = A.perm + (int64_t)tr * A.N + s0;
                 for (int b = 0; b < cnt; b += 32) {
                     const int q = b + lane;
@@ -883,6 +890,7 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
     a.xu8 = u8.xu8;
     a.u8_bad = u8.bad;
     a.Dp16 = u8.Dp16;
+    a.status = device_status_word();
     FdArgs b;
     b.X = X;
     b.D = f.D;

@@ -246,4 +246,21 @@ atsne_status forest_delete_launch(const int32_t *rows, int64_t R, int64_t N, con
                          (const int32_t *)out.ofs, out.perm, N - R, reinterpret_cast<unsigned *>(w.bmax));
 }
 
+// Raises DEV_MALFORMED when a bucket of an updated forest holds more points
+// than `bound`, the leaf size a search over the buckets sizes its lists by.
+__global__ void fu_bucket_bound_kernel(const int32_t *__restrict__ ofs, int T, int64_t L, int bound, int *status) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= L * T) return;
+    const int t = (int)(g / L);
+    const int64_t m = g - (int64_t)t * L;
+    const int32_t *o = ofs + (int64_t)t * (L + 1);
+    if (o[m + 1] - o[m] > bound) raise_status(status, DEV_MALFORMED);
+}
+
+atsne_status bucket_bound_check(const int32_t *ofs, int trees, int depth, int bound, cudaStream_t stream) {
+    const int64_t L = (int64_t)1 << depth;
+    return launch_kernel("forest_update", fu_bucket_bound_kernel, ceil_div(L * trees, 256), 256, 0, stream, ofs,
+                         trees, L, bound, device_status_word());
+}
+
 }  // namespace atsne

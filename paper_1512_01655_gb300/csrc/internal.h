@@ -153,6 +153,9 @@ atsne_status forest_insert_launch(const float *X, int64_t N_old, int64_t N_new, 
 atsne_status forest_delete_launch(const int32_t *rows, int64_t R, int64_t N, const ForestView &f,
                                   const int32_t *perm_in, const int32_t *ofs_in, int64_t stride_in,
                                   const BucketsView &out, const UpdateWs &w, cudaStream_t stream);
+// Flags (DEV_MALFORMED) any bucket of per-tree offsets ofs[trees][2^depth + 1]
+// holding more than `bound` points.
+atsne_status bucket_bound_check(const int32_t *ofs, int trees, int depth, int bound, cudaStream_t stream);
 atsne_status forest_query_launch(const float *X, const ForestView &f, const int32_t *qlist,
                                  int64_t nq, int k, int checks, int qcap, int32_t *idx_out,
                                  float *d2_out, int64_t *evaluated_out, void *ws_base,

@@ -1,18 +1,20 @@
 // Refinement of a selection without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they refine: code
-// that records its work into a CUDA graph while a stream capture is open
-// (cudaMalloc is not allowed there), a render or UI callback that must not
-// block on the allocator, or a host program whose device memory budget is
-// fixed up front. This variant of atsne_refine_subset takes its temporary rows
-// from one file-scope device array instead of a caller workspace. The array is
-// created when the library is loaded on a device and stays allocated on every
-// GPU that loads the library until the process exits.
+// Some callers cannot allocate device memory at the moment they refine: a
+// render or UI callback of an interactive view (the brushing of Sec. 5.1.1
+// runs there) that must not stall on cudaMalloc, which can synchronise the
+// whole device, or a host program whose device memory budget is fixed up
+// front and owned by another component. This variant of atsne_refine_subset
+// takes its temporary rows from one file-scope device array instead of a
+// caller workspace. The array is created when the library is loaded on a
+// device and stays allocated on every GPU that loads the library until the
+// process exits.
 //
 // Set-up: the first call on a device, with that device current, resolves the
-// array's device address with cudaGetSymbolAddress. Make that first call
-// before opening any stream capture. Later calls on the device reuse the
-// address.
+// array's device address and that of the library's device status word with
+// cudaGetSymbolAddress (every first call does, whatever its size, even an
+// empty selection). Make that first call before opening any stream capture.
+// Later calls on the device reuse the addresses.
 //
 // Sharing: every call uses the same array, which keeps the previous call's
 // contents. Each call writes every temporary value before reading it, so
@@ -48,6 +50,9 @@ atsne_status noalloc_scratch(unsigned char **out) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_refine_scratch);
         if (e != cudaSuccess) return cuda_error(e, "refine_noalloc: cudaGetSymbolAddress");
+        // the status word the checks below raise is resolved in the same
+        // set-up, so no later call needs a symbol lookup
+        if (!device_status_word()) return set_error(ATSNE_ECUDA, "refine_noalloc: device status word");
         g_na_ptr[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_na_ptr[dev];

@@ -117,3 +117,23 @@ def test_delete_and_row_dmax_host_checks(L):
                                  None) == L.ATSNE_EINVAL
     assert lib.atsne_row_dmax(fake, -1, 5, fake, None) == L.ATSNE_EINVAL
     assert lib.atsne_row_dmax(None, 0, 5, None, None) == L.ATSNE_OK  # nothing to do
+
+
+def test_forest_update_rejects_overlapping_buckets(L):
+    """buckets_out may not share a byte with buckets_in (the copy would race
+    with its source): equal bases and a partial overlap are both refused on the
+    host, before any device work."""
+    lib = L.lib()
+    N_built, D, trees = 1000, 8, 2
+    o = L.knn_opts(method="forest", trees=trees, leaf_size=1)
+    lay = L.ForestLayout()
+    assert lib.atsne_forest_layout(N_built, D, ctypes.byref(o), ctypes.byref(lay)) == 0
+    n_in = lib.atsne_forest_buckets_bytes(N_built, lay.depth, trees)
+    n_out = lib.atsne_forest_buckets_bytes(N_built + 100, lay.depth, trees)
+    mb = ctypes.c_int32(0)
+    base = 1 << 20  # fake, 256-byte aligned addresses: never dereferenced
+    for out in (base, base + 256 * ((n_in // 2) // 256), base - 256 * ((n_out // 2) // 256)):
+        rc = lib.atsne_forest_insert(ctypes.c_void_p(base), N_built, N_built, N_built + 100, D, ctypes.byref(o),
+                                     ctypes.c_void_p(1 << 30), ctypes.c_void_p(base), ctypes.c_void_p(out), n_out,
+                                     ctypes.byref(mb), ctypes.c_void_p(1 << 31), 1 << 30, None)
+        assert rc == L.ATSNE_EINVAL and b"overlap" in lib.atsne_last_error(), out

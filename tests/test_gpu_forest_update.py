@@ -90,3 +90,24 @@ def test_delete_from_the_built_forest_and_edge_cases(at):
     at.atsne_forest_delete(f, to_dev(np.array([4, 4], np.int32)))
     with pytest.raises(at.AtsneError):
         at.atsne_check()
+
+
+def test_search_flags_a_bucket_bound_below_the_largest_bucket(at):
+    """The search sizes each query's point list by the bucket bound it is
+    given; a bound below the largest bucket (a stale value) is reported through
+    the status word instead of writing past a list."""
+    X = synth.gaussian_mixture(1200, 8, seed=25)
+    Xd = to_dev(X)
+    f = at.atsne_forest_build(Xd[:1000].contiguous(), trees=2, leaf_size=1, seed=3)
+    b = at.atsne_forest_insert(Xd, f, 1000)
+    at.atsne_check()
+    assert b.max_bucket >= 2
+    at.atsne_forest_query(Xd, f, 10, checks=64, buckets=b)
+    at.atsne_check()
+    stale = at.ForestBuckets(b.buf, f, b.N, b.max_bucket - 1)
+    at.atsne_forest_query(Xd, f, 10, checks=64, buckets=stale)
+    with pytest.raises(at.AtsneError):
+        at.atsne_check()
+    # the library stays usable: the right bound searches cleanly again
+    at.atsne_forest_query(Xd, f, 10, checks=64, buckets=b)
+    at.atsne_check()

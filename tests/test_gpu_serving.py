@@ -71,6 +71,55 @@ def test_merge_neighbors_rule(at):
         assert idx.cpu().numpy()[r].tolist() == [p[1] for p in pairs]
 
 
+@pytest.mark.parametrize("kind", ["integer", "gauss"])
+def test_insertion_matches_oracle(at, kind):
+    """Eq. 11 through the library's insertion primitives (d_i^Max of each row,
+    the radius search among the new points, the merge) against oracle.insert,
+    on rows with and without absent entries."""
+    if kind == "integer":  # exact FP32 distances: the lists must be identical
+        X = np.random.default_rng(43).integers(0, 16, size=(2600, 8)).astype(np.float32)
+    else:
+        X = synth.gaussian_mixture(2600, 24, seed=44)
+    n_old, k = 2000, 30
+    i0, d0 = oracle.knn_exact(X[:n_old], k)
+    holes = np.arange(0, n_old, 7)  # absent entries, as a deletion leaves them
+    i0[holes, -3:] = -1
+    d0[holes, -3:] = np.inf
+    d0 = d0.astype(np.float32).astype(np.float64)  # the state the library holds
+    oi, od, och = oracle.insert(X, n_old, i0, d0)
+    Xd, idx, d2 = to_dev(X), to_dev(i0), to_dev(d0.astype(np.float32))
+    radius = at.atsne_row_dmax(d2)
+    cand = at.atsne_knn_cross(Xd[:n_old], Xd[n_old:], min(k, X.shape[0] - n_old), radius_d2=radius)
+    ch = at.atsne_merge_neighbors(idx, d2, cand[0], cand[1], n_old)
+    at.atsne_check()
+    gi, gd, gch = idx.cpu().numpy(), d2.cpu().numpy(), ch.cpu().numpy().astype(bool)
+    if kind == "integer":
+        assert np.array_equal(gi, oi)
+        assert np.array_equal(gd.astype(np.float64), od)
+        assert np.array_equal(gch, och)
+        return
+    # continuous data: where FP32 cannot decide as FP64 does (a new point within
+    # 1e-4 of d_i^Max, or a k-th/(k+1)-th tie in the merged list) rows may differ
+    Xo = X.astype(np.float64)
+    dnew = ((Xo[:n_old, None, :] - Xo[None, n_old:, :]) ** 2).sum(-1)
+    checked = 0
+    for r in range(n_old):
+        present = d0[r][i0[r] >= 0]
+        dmax = present.max()
+        if (np.abs(dnew[r] - dmax) <= 1e-4 * dmax).any():
+            continue
+        u = np.sort(np.concatenate([present, dnew[r][dnew[r] < dmax]]))
+        if len(u) > k and (u[k] - u[k - 1]) <= 1e-4 * u[k]:
+            continue
+        assert set(gi[r]) == set(oi[r]), r
+        assert gch[r] == och[r], r
+        m = oi[r] >= 0
+        assert np.allclose(gd[r][m], od[r][m], rtol=1e-5, atol=1e-5), r
+        checked += 1
+    assert checked > 0.95 * n_old
+    assert och.any() and not och.all()
+
+
 def _requests(at, X0, extra, seed):
     from paper_1512_01655_gb300.serve import Request
     rng = np.random.default_rng(seed)

@@ -1,7 +1,8 @@
 """The no-allocation refinement entry point (atsne_refine_subset_noalloc).
 
 It serves callers that cannot allocate device memory while they refine, such
-as code recording into an open CUDA stream capture. Through the C ABI it must
+as a render callback of an interactive view that must not stall on cudaMalloc,
+or a program with a fixed device-memory budget. Through the C ABI it must
 give the same rows as the workspace-based atsne_refine_subset, on two calls in
 a row that share the library's fixed scratch. Collected last so that a run
 stopping at the first failure has already run every other test.
