@@ -25,6 +25,7 @@ atsne_status knn_bruteforce_rows(const float *X, int64_t N, int D, const int32_t
 // Tensor-core exact kNN: plan (tile split, candidate capacity) and workspace.
 struct TcPlan {
     int passes = 1, Dp = 0, row_tiles = 0, splits = 1, cols_per_split = 0, ksel = 0, cap = 0;
+    int halves = 1;  // candidate buffers per (row, split): one per column half of a tile
     bool certify = true;  // rows certified exact (else the ksel best keys re-ranked, approximate)
 };
 struct TcWs {

@@ -62,15 +62,15 @@ using namespace tc;
 constexpr int TC_BM = 128;       // query rows per tile (TMEM lanes)
 constexpr int TC_BN = 256;       // corpus points per tile (TMEM columns per accumulator)
 constexpr int TC_BK = 64;        // BF16 per k-block (one 128-byte swizzle row)
-constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr int TC_EPI = 128;
 constexpr uint64_t WAIT_NS = 1000000000ull;
 constexpr int MERGE_WARPS = 4;
 constexpr int RCAP = 256;        // candidates re-ranked per row at most (certified modes)
 constexpr int MSTAGE = 1024;     // keys below tau staged per row for the merge's select
-constexpr int RCAP_FP8 = 1024;   // FP8 mode: candidates re-ranked per row at most
-constexpr int MSTAGE_FP8 = 2048;
-constexpr int NBUCKET = 48;      // distance buckets per row: 6 octaves, 8 per octave
+constexpr int RCAP_FP8 = 1024;   // modes without a certificate: the largest re-rank set (ksel <= 512)
+constexpr int NBUCKET = 48;      // a thread's distance buckets: 3 octaves of d^2, 16 per octave
+constexpr int HSHIFT = 19;       // float bits >> HSHIFT: exponent and 4 mantissa bits (16 per octave)
+constexpr int GH_BUCKETS = 48;   // a row's global histogram (column splits): 6 octaves, 8 per octave
+constexpr int GH_SHIFT = 20;
 
 struct Cand {
     float key;
@@ -83,10 +83,18 @@ struct Cand {
 // With PASSES = 3 and every low half zero (data exact in BF16, e.g. 8-bit
 // integers) the two correction passes add exact zeros: the kernel then skips
 // them and runs the same shared memory as MAX_STAGES single-pass stages.
+//
+// One-pass modes run eight epilogue warps (two per TMEM lane quadrant, each
+// filtering half of a tile's columns) so that the filter keeps up with the
+// shorter contraction; the shared memory then holds three stages. The
+// three-pass mode keeps four epilogue warps and two double-width stages.
 template <int PASSES>
 struct TcCfg {
-    static constexpr int STAGES = PASSES == 3 ? 2 : 4;
-    static constexpr int MAX_STAGES = 4;
+    static constexpr int NEPI = PASSES == 3 ? 4 : 8;      // epilogue warps
+    static constexpr int HALVES = NEPI / 4;               // column parts of a tile per lane quadrant
+    static constexpr int THREADS = 64 + 32 * NEPI;        // warp 0 TMA, warp 1 MMA, then the epilogue
+    static constexpr int STAGES = PASSES == 3 ? 2 : 3;
+    static constexpr int MAX_STAGES = PASSES == 3 ? 4 : 3;
     static constexpr int KE = PASSES == 8 ? 128 : TC_BK;  // elements per k-block
     static constexpr int A_BYTES = TC_BM * 128;
     static constexpr int B_BYTES = TC_BN * 128;
@@ -95,15 +103,19 @@ struct TcCfg {
 
 template <int PASSES>
 struct __align__(1024) TcSmem {
+    static constexpr int NEPI = TcCfg<PASSES>::NEPI;
     unsigned char stage[TcCfg<PASSES>::STAGES][TcCfg<PASSES>::STAGE_BYTES];
-    float ny[4][32];            // per epilogue warp: the chunk's corpus norms
-    float ms[4][32];            // FP8: the chunk's -2 * corpus row scales
-    // per epilogue thread: one row of 32 keys (padded to 33) from which its
-    // survivors are read back; between tiles the warp's first 256 words serve
-    // the radix select of an exact compaction
-    float tr[4][32 * 33];
+    float ny[NEPI][32];         // per epilogue warp: the chunk's corpus norms
+    float ms[PASSES == 8 ? NEPI : 1][32];  // FP8: the chunk's -2 * corpus row scales
+    // per epilogue thread: one row of 32 keys (padded to 36, 16-byte rows)
+    // from which its survivors are read back; between tiles the warp's first
+    // 256 words serve the radix select of an exact compaction
+    float tr[NEPI][32 * 36];
     // per epilogue thread: buffered distances by bucket, two 16-bit counts per word
-    uint32_t dhist[4][NBUCKET / 2][32];
+    uint32_t dhist[NEPI][NBUCKET / 2][32];
+    // each half's current tau per query row, tagged with its work unit:
+    // (unit << 32) | tau bits
+    unsigned long long tau_sh[TcCfg<PASSES>::HALVES][TC_BM];
     uint64_t full[TcCfg<PASSES>::MAX_STAGES];
     uint64_t empty[TcCfg<PASSES>::MAX_STAGES];
     uint64_t acc_full[2];
@@ -133,11 +145,23 @@ struct TcParams {
     int KB;                // Dp / 64
     int splits, cols_per_split, row_tiles;
     int ksel, cap;
-    Cand *cand;            // [Q][splits][cap]
-    int4 *meta;            // [Q][splits]: count, tau bits, overflow
-    unsigned *row_hist;    // [Q][NBUCKET]: buffered distances of all splits by bucket (splits > 1)
+    Cand *cand;            // [Q][splits * halves][cap]
+    int4 *meta;            // [Q][splits * halves]: count, tau bits, overflow
+    unsigned *row_hist;    // [Q][GH_BUCKETS]: buffered distances of all splits by bucket (splits > 1)
     int *status;
 };
+
+// Absolute bucket of a squared distance on the thread grid (16 per octave),
+// and the upper edge of bucket b.
+__device__ __forceinline__ int dbucket(float d) { return (int)(__float_as_uint(fmaxf(d, 1e-30f)) >> HSHIFT); }
+__device__ __forceinline__ float bucket_top(int b) { return __uint_as_float((uint32_t)(b + 1) << HSHIFT); }
+
+// (mask << 1) | sign bit of v: one funnel shift per key.
+__device__ __forceinline__ uint32_t sign_into_mask(float v, uint32_t mask) {
+    uint32_t r;
+    asm("shf.l.wrap.b32 %0, %1, %2, 1;" : "=r"(r) : "r"(__float_as_uint(v)), "r"(mask));
+    return r;
+}
 
 __device__ __forceinline__ float key_of_bits(uint32_t u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
@@ -359,7 +383,7 @@ __device__ __forceinline__ float key_error_bound_capped(float4 st, const unsigne
 }
 
 template <int PASSES>
-__global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const __grid_constant__ TcParams p) {
     using C = TcCfg<PASSES>;
     extern __shared__ __align__(16) unsigned char tc_raw[];
     const uint32_t pad = (1024u - (smem_u32(tc_raw) & 1023u)) & 1023u;
@@ -377,13 +401,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&s.acc_full[i], 1);
-            mbar_init(&s.acc_empty[i], TC_EPI);
+            mbar_init(&s.acc_empty[i], 32 * C::NEPI);
         }
         mbar_init(&s.drain, 1);
         s.abort_flag = 0;
         s.zero = 0;
         fence_mbar_init();
     }
+    for (int i = threadIdx.x; i < C::HALVES * TC_BM; i += blockDim.x)
+        (&s.tau_sh[0][0])[i] = ~0ull;  // tagged with no unit
     if (threadIdx.x == 32) {
         tma_prefetch_desc(&p.tm_a_hi);
         tma_prefetch_desc(&p.tm_b_hi);
@@ -516,9 +542,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
         }
     } else {
         // ---------------- epilogue: keys, filter, per-row candidate buffers ----------------
+        // Epilogue warp e reads TMEM lane quadrant (warp % 4); with two warps
+        // per quadrant, warp e filters the columns [half * CW, half * CW + CW)
+        // of every tile. Each thread owns one (query row, column split, half)
+        // stream with its own buffer. The two halves of a row share their
+        // bounds: each half bounds the kh-th smallest key it has seen (kh =
+        // ksel / 2, rounded up), so the larger of the two halves' bounds has
+        // at least ksel keys of the row below it.
+        const int e = warp - 2;
         const int quarter = warp & 3;
+        const int half = e >> 2;
+        constexpr int CW = TC_BN / C::HALVES;  // columns of each tile filtered by this thread
+        constexpr int NCH = CW / 32;           // 32-column TMEM loads per tile
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        uint32_t *hist = reinterpret_cast<uint32_t *>(s.tr[warp - 2]);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(s.tr[e]);
+        const int subs = p.splits * C::HALVES;  // candidate buffers per query row
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
@@ -531,27 +569,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
             const int qraw = row < p.Q ? (cross ? (int)row : (p.qlist ? p.qlist[row] : (int)row)) : -1;
             const bool qv = qraw >= 0 && (cross || qraw < p.N);  // listed rows out of range are flagged by the caller
             const int qid = qv ? qraw : -1;
-            Cand *buf = qv ? p.cand + ((size_t)row * p.splits + sp) * p.cap : nullptr;
+            Cand *buf = qv ? p.cand + ((size_t)row * subs + (size_t)sp * C::HALVES + half) * p.cap : nullptr;
             float tau = qv ? INFINITY : -INFINITY;
+            float th = INFINITY;  // bound of this half's kh-th smallest key
+            const int kh = C::HALVES > 1 ? (p.ksel + 1) / 2 : p.ksel;
             int cnt = 0, since = 0, rovf = 0;
             // radius mode: a fixed threshold, the row's squared radius as a key
             // widened by twice the key error bound, so that no point inside the
             // radius is filtered out; no top-k bookkeeping
             const bool rmode = p.radius != nullptr;
-            // distance buckets (8 per octave) below t0 = (||x|| + max||y||)^2 >= d
+            // the thread's distance grid: NBUCKET buckets, 16 per octave of d^2,
+            // below an anchor; first anchored at t0 = (||x|| + max||y||)^2 >= d
             const float nx = qv ? (cross ? p.qnrm[row] : p.nrm[qid]) : 0.f;
             const float ai = sqrtf(nx), amax = __uint_as_float(p.gmax[0]);
-            int top = (int)(__float_as_uint((ai + amax) * (ai + amax) * 1.0001f + 1e-30f) >> 20);
+            const float t0 = (ai + amax) * (ai + amax) * 1.0001f + 1e-30f;
+            int top = dbucket(t0);
             // With column splits, every split of a row also counts its buffered
-            // distances in one histogram per row in global memory, on the fixed
-            // grid below t0: the splits cover disjoint columns and the counts
-            // only grow, so the bucket where the summed count reaches ksel
-            // bounds the row's ksel-th distance for all of them.
-            unsigned *gh = (p.splits > 1 && qv) ? p.row_hist + (size_t)row * NBUCKET : nullptr;
-            const int gbase = top - (NBUCKET - 1);
+            // distances in one histogram per row in global memory, on a fixed
+            // grid below t0 (8 buckets per octave): the splits cover disjoint
+            // columns and the counts only grow, so the bucket where the summed
+            // count reaches ksel bounds the row's ksel-th distance for all of them.
+            unsigned *gh = (p.splits > 1 && qv) ? p.row_hist + (size_t)row * GH_BUCKETS : nullptr;
+            const int gbase = (int)(__float_as_uint(t0) >> GH_SHIFT) - (GH_BUCKETS - 1);
             auto global_tau = [&]() {
                 int cum = 0, b = 0;
-                for (; b < NBUCKET; b += 4) {
+                for (; b < GH_BUCKETS; b += 4) {
                     const uint4 h4 = __ldcg(reinterpret_cast<const uint4 *>(gh + b));
                     if (cum + (int)(h4.x + h4.y + h4.z + h4.w) >= p.ksel) {
                         if ((cum += h4.x) >= p.ksel) break;
@@ -564,7 +606,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     }
                     cum += h4.x + h4.y + h4.z + h4.w;
                 }
-                if (b < NBUCKET) tau = fminf(tau, __uint_as_float((uint32_t)(gbase + b + 1) << 20) - nx);
+                if (b < GH_BUCKETS)
+                    tau = fminf(tau, __uint_as_float((uint32_t)(gbase + b + 1) << GH_SHIFT) - nx);
             };
             if (gh) global_tau();
             if ((rmode || (p.hint && PASSES != 8)) && qv) {  // FP8 keys carry no error bound
@@ -582,39 +625,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                         1e-6f * (fabsf(rad) + nx);
                     tau = fminf(tau, rad - nx + widen);
                     // the distance grid then only needs to reach the bound
-                    const int ht = (int)(__float_as_uint(fmaxf(rad + widen, 1e-30f) * 1.0001f) >> 20) + 1;
+                    const int ht = dbucket((rad + widen) * 1.0001f) + 1;
                     if (ht < top) top = ht;
                 }
             }
             bool rebased = rmode || (p.hint && PASSES != 8);
             float dmx = 0.f;  // largest buffered distance, for the first re-anchoring of the grid
-            uint32_t *dh = &s.dhist[warp - 2][0][lane];
+            uint32_t *dh = &s.dhist[e][0][lane];
             for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
+            // recount the buffered distances on the grid below `top`
+            auto recount = [&]() {
+                for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
+                for (int i = 0; i < cnt; ++i) {
+                    int bk = dbucket(nx + buf[i].key) - (top - (NBUCKET - 1));
+                    if (bk < NBUCKET) {
+                        bk = max(bk, 0);
+                        dh[(bk >> 1) * 32] += 1u << ((bk & 1) * 16);
+                    }
+                }
+            };
             // corpus norms of the first tile of the unit, then one tile ahead
-            float nyn[TC_BN / 32], msn[TC_BN / 32];
+            // (lane l holds columns l, l + 32, ... of this thread's part)
+            float nyn[NCH], msn[NCH];
 #pragma unroll
-            for (int q = 0; q < TC_BN / 32; ++q) {
-                const int64_t cc = c0 + q * 32 + lane;
+            for (int q = 0; q < NCH; ++q) {
+                const int64_t cc = c0 + half * CW + q * 32 + lane;
                 nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
                 if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
             }
             // FP8: x_i . x_j ~ s_i s_j (q_i . q_j); the row's scale, the
             // columns' -2 s_j beside their norms
             const float si = PASSES == 8 && qv ? (p.qscale ? p.qscale[row] : p.scale[qid]) : 1.f;
-            float *nyw = s.ny[warp - 2];
-            float *msw = s.ms[warp - 2];
-            float *mine = s.tr[warp - 2] + lane * 33;
+            float *nyw = s.ny[e];
+            float *msw = s.ms[PASSES == 8 ? e : 0];
+            float *mine = s.tr[e] + lane * 36;
+            // the partner half may still be on an earlier unit: its bound is
+            // taken only when its tag is this unit
+            volatile unsigned long long *tau_mine = &s.tau_sh[half][quarter * 32 + lane];
+            volatile unsigned long long *tau_peer = &s.tau_sh[half ^ (C::HALVES - 1)][quarter * 32 + lane];
+            auto share_tau = [&]() { *tau_mine = ((unsigned long long)u << 32) | __float_as_uint(th); };
+            share_tau();
             for (int64_t ct = c0; ct < c1; ct += TC_BN) {
-                float nyc[TC_BN / 32], msc[TC_BN / 32];  // lane l: columns l, l + 32, ... of this tile
+                float nyc[NCH], msc[NCH];
 #pragma unroll
-                for (int q = 0; q < TC_BN / 32; ++q) {
+                for (int q = 0; q < NCH; ++q) {
                     nyc[q] = nyn[q];
                     msc[q] = msn[q];
                 }
                 if (ct + TC_BN < c1) {
 #pragma unroll
-                    for (int q = 0; q < TC_BN / 32; ++q) {
-                        const int64_t cc = ct + TC_BN + q * 32 + lane;
+                    for (int q = 0; q < NCH; ++q) {
+                        const int64_t cc = ct + TC_BN + half * CW + q * 32 + lane;
                         nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
                         if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
                     }
@@ -629,48 +690,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     break;
                 }
                 fence_after_sync();
-                const uint32_t taddr = tbase + lane_base + (uint32_t)(acc * TC_BN);
-                // the query's own column, if in this tile (none for another array's queries)
-                const int self_off = cross ? INT_MIN / 2 : qid - (int)ct;
+                const uint32_t taddr = tbase + lane_base + (uint32_t)(acc * TC_BN + half * CW);
+                const int colb0 = (int)ct + half * CW;  // first column of this thread's part
+                // the query's own column, if in this part (none for another array's queries)
+                const int self_off = cross ? INT_MIN / 2 : qid - colb0;
+                // filter threshold: finite, so that a padded column (key +inf)
+                // never passes even while tau is +inf
+                const float tf = fminf(tau, FLT_MAX);
+                const float2 ntau = make_float2(-tf, -tf);
+                const float2 m2 = make_float2(-2.f, -2.f);
+                const float2 si2 = make_float2(si, si);
                 // two register sets: the next chunk's load is in flight while
                 // this one's keys are filtered
                 uint32_t ra[32], rb[32];
                 tmem_ld32(taddr, ra);
 #pragma unroll
-                for (int c = 0; c < TC_BN / 32; ++c) {
+                for (int c = 0; c < NCH; ++c) {
                     uint32_t(&r)[32] = (c & 1) ? rb : ra;
                     uint32_t(&rn)[32] = (c & 1) ? ra : rb;
                     nyw[lane] = nyc[c];
                     if (PASSES == 8) msw[lane] = msc[c];
                     tmem_ld_wait(r);
-                    if (c + 1 < TC_BN / 32) tmem_ld32(taddr + (uint32_t)((c + 1) * 32), rn);
+                    if (c + 1 < NCH) tmem_ld32(taddr + (uint32_t)((c + 1) * 32), rn);
                     __syncwarp();
-                    // branch-free filter: 32 keys, one survivor bit each
+                    // keys two at a time (packed FP32), each key's survivor bit
+                    // the sign of key - tau (exact: a difference of two floats
+                    // is negative exactly when the first is smaller)
                     float kk[32];
                     uint32_t mask = 0;
                     const float4 *ny4 = reinterpret_cast<const float4 *>(nyw);
-                    if (PASSES == 8) {
-                        const float4 *ms4 = reinterpret_cast<const float4 *>(msw);
+                    const float4 *ms4 = reinterpret_cast<const float4 *>(msw);
+                    float dd[32];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 n4 = ny4[q], m4 = ms4[q];
-                            kk[4 * q + 0] = fmaf(__uint_as_float(r[4 * q + 0]) * si, m4.x, n4.x);
-                            kk[4 * q + 1] = fmaf(__uint_as_float(r[4 * q + 1]) * si, m4.y, n4.y);
-                            kk[4 * q + 2] = fmaf(__uint_as_float(r[4 * q + 2]) * si, m4.z, n4.z);
-                            kk[4 * q + 3] = fmaf(__uint_as_float(r[4 * q + 3]) * si, m4.w, n4.w);
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 n4 = ny4[q];
+                        float2 a01 = make_float2(__uint_as_float(r[4 * q + 0]), __uint_as_float(r[4 * q + 1]));
+                        float2 a23 = make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                        float2 k01, k23;
+                        if (PASSES == 8) {
+                            const float4 g4 = ms4[q];
+                            k01 = __ffma2_rn(__fmul2_rn(a01, si2), make_float2(g4.x, g4.y), make_float2(n4.x, n4.y));
+                            k23 = __ffma2_rn(__fmul2_rn(a23, si2), make_float2(g4.z, g4.w), make_float2(n4.z, n4.w));
+                        } else {
+                            k01 = __ffma2_rn(m2, a01, make_float2(n4.x, n4.y));
+                            k23 = __ffma2_rn(m2, a23, make_float2(n4.z, n4.w));
                         }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 n4 = ny4[q];
-                            kk[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), n4.x);
-                            kk[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), n4.y);
-                            kk[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), n4.z);
-                            kk[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), n4.w);
-                        }
+                        const float2 d01 = __fadd2_rn(k01, ntau), d23 = __fadd2_rn(k23, ntau);
+                        kk[4 * q + 0] = k01.x;
+                        kk[4 * q + 1] = k01.y;
+                        kk[4 * q + 2] = k23.x;
+                        kk[4 * q + 3] = k23.y;
+                        dd[4 * q + 0] = d01.x;
+                        dd[4 * q + 1] = d01.y;
+                        dd[4 * q + 2] = d23.x;
+                        dd[4 * q + 3] = d23.y;
                     }
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) mask |= (kk[j] < tau ? 1u : 0u) << j;
+                    for (int j = 31; j >= 0; --j) mask = sign_into_mask(dd[j], mask);  // key j -> bit j
                     const int so = self_off - c * 32;
                     if (so >= 0 && so < 32) mask &= ~(1u << so);
                     __syncwarp();  // the chunk's norms are read before the next chunk's
@@ -679,12 +755,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                         // walk its survivors one per step (a chunk rarely holds
                         // more than one or two of a row's): the warp pays the
                         // largest count of any lane, not the union of survivor
-                        // positions. Each survivor
-                        // is appended (key, column) to the row's buffer and counted
-                        // in its bucket by a fire-and-forget shared add.
+                        // positions. Each survivor is appended (key, column) to
+                        // the thread's buffer and counted in its bucket by a
+                        // fire-and-forget shared add.
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) mine[j] = kk[j];
-                        const int colb = (int)ct + c * 32;
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4 *>(mine + j) = make_float4(kk[j], kk[j + 1], kk[j + 2], kk[j + 3]);
+                        const int colb = colb0 + c * 32;
                         since += __popc(mask);
                         auto append = [&](float key, int col) {
                             if (rmode) {  // no compaction: a full buffer sends the row to the fallback
@@ -695,17 +772,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                                 return;
                             }
                             buf[cnt++] = Cand{key, col};
-                            const float dd = nx + key;
-                            dmx = fmaxf(dmx, dd);
-                            const uint32_t db = __float_as_uint(fmaxf(dd, 1e-30f)) >> 20;
-                            int bk = (int)db - (top - (NBUCKET - 1));
+                            const float dd2 = nx + key;
+                            dmx = fmaxf(dmx, dd2);
+                            const int db = dbucket(dd2);
+                            int bk = db - (top - (NBUCKET - 1));
                             if (bk < NBUCKET) {  // distances above the grid are not counted
                                 bk = max(bk, 0);
                                 red_add_shared(dh + (bk >> 1) * 32, 1u << ((bk & 1) * 16));
                             }
                             if (gh) {
-                                const int gb = (int)db - gbase;
-                                atomicAdd(gh + min(max(gb, 0), NBUCKET - 1), 1u);
+                                const int gb = (int)(__float_as_uint(fmaxf(dd2, 1e-30f)) >> GH_SHIFT) - gbase;
+                                atomicAdd(gh + min(max(gb, 0), GH_BUCKETS - 1), 1u);
                             }
                         };
                         do {
@@ -723,50 +800,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     acc_phase ^= 1u;
                 }
                 if (rmode) continue;  // the threshold is fixed
-                // With column splits (few query rows), once ksel distances are
-                // buffered the grid is re-anchored just above the largest of them
-                // and recounted: the first grid reaches the largest distance any
-                // point could have, which heavy-tailed norms put many octaves
-                // above the neighbourhood, and a split's short stream would not
-                // reach the exact compaction that otherwise re-anchors it.
-                if (!rebased && p.splits > 1 && cnt >= p.ksel) {
+                // Once ksel distances are buffered the grid is re-anchored just
+                // above the largest of them and recounted: the first anchor
+                // bounds the largest distance any point could have, which can
+                // lie octaves above the neighbourhood.
+                if (!rebased && cnt >= kh) {
                     rebased = true;
-                    const int nt = (int)(__float_as_uint(fmaxf(dmx, 1e-30f) * 1.0001f) >> 20) + 1;
+                    const int nt = dbucket(dmx * 1.0001f) + 1;
                     if (nt < top) {
                         top = nt;
-                        for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
-                        for (int i = 0; i < cnt; ++i) {
-                            int bk = (int)(__float_as_uint(fmaxf(nx + buf[i].key, 1e-30f)) >> 20) -
-                                     (top - (NBUCKET - 1));
-                            if (bk < NBUCKET) {
-                                bk = max(bk, 0);
-                                dh[(bk >> 1) * 32] += 1u << ((bk & 1) * 16);
-                            }
-                        }
+                        recount();
                         since = 16;
                     }
                 }
-                // lower tau to the upper edge of the bucket holding the ksel-th distance
-                if (since >= 16 && cnt >= p.ksel) {
+                // lower tau to the upper edge of the bucket holding the ksel-th
+                // distance, th to that of the bucket holding the kh-th
+                if (since >= 16 && cnt >= kh) {
                     uint32_t hw[NBUCKET / 2];
 #pragma unroll
                     for (int bw = 0; bw < NBUCKET / 2; ++bw) hw[bw] = dh[bw * 32];
-                    int cum = 0, bk = NBUCKET;
+                    int cum = 0, bk = NBUCKET, bh = NBUCKET;
 #pragma unroll
                     for (int b2 = 0; b2 < NBUCKET; ++b2) {
                         cum += (int)((hw[b2 >> 1] >> ((b2 & 1) * 16)) & 0xffffu);
+                        if (bh == NBUCKET && cum >= kh) bh = b2;
                         if (bk == NBUCKET && cum >= p.ksel) bk = b2;
                     }
-                    if (bk < NBUCKET) {
-                        const float edge =
-                            __uint_as_float((uint32_t)(top - (NBUCKET - 1) + bk + 1) << 20);
-                        tau = fminf(tau, edge - nx);
-                    }
+                    if (bk < NBUCKET) tau = fminf(tau, bucket_top(top - (NBUCKET - 1) + bk) - nx);
+                    if (bh < NBUCKET) th = fminf(th, bucket_top(top - (NBUCKET - 1) + bh) - nx);
                     since = 0;
                 }
                 if (gh) global_tau();
+                if (C::HALVES > 1) {  // with the other half of the row: ksel keys below the larger bound
+                    share_tau();
+                    const unsigned long long pv = *tau_peer;
+                    if ((int)(pv >> 32) == u) tau = fminf(tau, fmaxf(th, __uint_as_float((uint32_t)pv)));
+                }
                 // a buffer that the next tile could overflow is compacted exactly
-                unsigned m = __ballot_sync(0xffffffffu, cnt > p.cap - TC_BN);
+                unsigned m = __ballot_sync(0xffffffffu, cnt > p.cap - CW);
                 if (m) __syncwarp();
                 const unsigned compacted = m;
                 while (m) {
@@ -782,16 +853,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                     int wpos = 0, eq_seen = 0;
                     for (int base = 0; base < n; base += 32) {
                         const int i = base + lane;
-                        Cand e{INFINITY, -1};
-                        if (i < n) e = b[i];
-                        const uint32_t uk = float_key(e.key);
+                        Cand e2{INFINITY, -1};
+                        if (i < n) e2 = b[i];
+                        const uint32_t uk = float_key(e2.key);
                         const bool lt = i < n && uk < tk;
                         const bool eq = i < n && uk == tk;
                         const unsigned eqm = __ballot_sync(0xffffffffu, eq);
                         const int eq_rank = eq_seen + __popc(eqm & lanemask_lt());
                         const bool keep = lt || (eq && eq_rank < eq_quota);
                         const unsigned km = __ballot_sync(0xffffffffu, keep);
-                        if (keep) b[wpos + __popc(km & lanemask_lt())] = e;
+                        if (keep) b[wpos + __popc(km & lanemask_lt())] = e2;
                         wpos += __popc(km);
                         eq_seen += __popc(eqm);
                     }
@@ -803,26 +874,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_tc_kernel(const __grid_cons
                 }
                 if ((compacted >> lane) & 1u) {
                     // re-base the buckets below the new tau and recount the kept entries
-                    top = (int)(__float_as_uint(fmaxf(nx + tau, 1e-30f) * 1.0001f) >> 20) + 1;
-                    for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
-                    for (int i = 0; i < cnt; ++i) {
-                        int bk = (int)(__float_as_uint(fmaxf(nx + buf[i].key, 1e-30f)) >> 20) -
-                                 (top - (NBUCKET - 1));
-                        if (bk < NBUCKET) {
-                            bk = max(bk, 0);
-                            dh[(bk >> 1) * 32] += 1u << ((bk & 1) * 16);
-                        }
-                    }
+                    top = dbucket((nx + tau) * 1.0001f) + 1;
+                    recount();
                     rebased = true;
                     since = 0;
                 }
             }
             if (!ok) break;
             if (qv)
-                p.meta[(size_t)row * p.splits + sp] = make_int4(cnt, __float_as_int(tau), rovf, 0);
+                p.meta[(size_t)row * subs + (size_t)sp * C::HALVES + half] =
+                    make_int4(cnt, __float_as_int(tau), rovf, 0);
         }
     }
-
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -840,6 +903,7 @@ struct MergeParams {
     const int32_t *qlist;
     const float *X;
     int D, k, ksel;
+    int rc, mst;            // re-rank set and staged keys per row (shared memory)
     const float *nrm;
     const float4 *stats;
     const float *Xq;        // queries from another array (row r = Xq[r]), else nullptr
@@ -861,19 +925,17 @@ __device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st
 }
 
 // CERT (FP32 and BF16 modes): the k nearest, certified exact or sent to the
-// brute-force kernel. Otherwise (FP8 mode): the SEL = ksel best keys re-ranked
-// in FP32 and the k best of them kept, without a certificate. MST keys are
-// staged per row, RC candidates re-ranked at most.
-template <bool CERT, int RC, int MST>
-size_t merge_smem_bytes() {
-    return (size_t)MERGE_WARPS * (256 * 4 + MST * 8 + RC * 8);
-}
+// brute-force kernel. Otherwise (approximate modes): the SEL = ksel best keys
+// re-ranked in FP32 and the k best of them kept, without a certificate.
+// p.mst keys are staged per row, p.rc candidates re-ranked at most.
+size_t merge_smem_bytes(int rc, int mst) { return (size_t)MERGE_WARPS * (256 * 4 + (size_t)mst * 8 + (size_t)rc * 8); }
 
-template <bool CERT, int RC, int MST>
-__global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams p) {
+template <bool CERT>
+__global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergeParams p) {
     extern __shared__ __align__(16) unsigned char mg_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *hist = reinterpret_cast<uint32_t *>(mg_smem) + w * 256;
+    const int MST = p.mst, RC = p.rc;
     float *sk = reinterpret_cast<float *>(mg_smem + MERGE_WARPS * 1024) + w * MST;
     int *sj = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 4)) + w * MST;
     float *rdw = reinterpret_cast<float *>(mg_smem + MERGE_WARPS * (1024 + MST * 8)) + w * RC;
@@ -1000,7 +1062,64 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) knn_merge_kernel(MergeParams
         const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (int64_t)qid * p.D;
         const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
                           (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
+        // rows of at most 256 values (float4-aligned): eight lanes per
+        // candidate, eight candidates in flight per warp, the query's part in
+        // registers; three shuffles reduce a candidate's eight partial sums
+        const bool g8 = vec4 && p.D <= 256;
+        auto rerank_g8 = [&](int from, int to) {
+            const int g = lane >> 3, gl = lane & 7, nv = p.D >> 2;
+            const float4 *q4 = reinterpret_cast<const float4 *>(xq);
+            const float4 *X4 = reinterpret_cast<const float4 *>(p.X);
+            float4 qv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) qv[j] = gl + 8 * j < nv ? q4[gl + 8 * j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int t0 = from; t0 < to; t0 += 8) {
+                const int ta = t0 + g, tb = t0 + 4 + g;
+                const float4 *xa = ta < to ? X4 + (int64_t)rjw[ta] * nv : nullptr;
+                const float4 *xb = tb < to ? X4 + (int64_t)rjw[tb] * nv : nullptr;
+                float4 va[8], vb[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const bool in = gl + 8 * j < nv;
+                    va[j] = in && xa ? xa[gl + 8 * j] : qv[j];
+                    vb[j] = in && xb ? xb[gl + 8 * j] : qv[j];
+                }
+                float sa = 0.f, sb = 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float df = qv[j].x - va[j].x;
+                    sa = fmaf(df, df, sa);
+                    df = qv[j].y - va[j].y;
+                    sa = fmaf(df, df, sa);
+                    df = qv[j].z - va[j].z;
+                    sa = fmaf(df, df, sa);
+                    df = qv[j].w - va[j].w;
+                    sa = fmaf(df, df, sa);
+                    df = qv[j].x - vb[j].x;
+                    sb = fmaf(df, df, sb);
+                    df = qv[j].y - vb[j].y;
+                    sb = fmaf(df, df, sb);
+                    df = qv[j].z - vb[j].z;
+                    sb = fmaf(df, df, sb);
+                    df = qv[j].w - vb[j].w;
+                    sb = fmaf(df, df, sb);
+                }
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+                }
+                if (gl == 0) {
+                    if (ta < to) rdw[ta] = sa;
+                    if (tb < to) rdw[tb] = sb;
+                }
+            }
+        };
         auto rerank = [&](int from, int to) {
+            if (g8) {
+                rerank_g8(from, to);
+                return;
+            }
             for (int t0 = from; t0 < to; t0 += 4) {
                 const float *xc[4];
                 float a[4];
@@ -1226,7 +1345,7 @@ size_t tc_smem_bytes() {
     return sizeof(TcSmem<PASSES>) + 1024;
 }
 static_assert(sizeof(TcSmem<1>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
-static_assert(NBUCKET % 4 == 0, "row histograms are read as uint4");
+static_assert(GH_BUCKETS % 4 == 0, "row histograms are read as uint4");
 static_assert(sizeof(TcSmem<3>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
 static_assert(sizeof(TcSmem<8>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
 
@@ -1312,13 +1431,17 @@ TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, 
     if (ks < k) ks = k;
     pl.ksel = ks;
     // A streaming top-ksel over n columns in random order admits about
-    // ksel (1 + ln(n / ksel)) keys; the bucketed threshold about twice that.
+    // ksel (1 + ln(n / ksel)) keys; the bucketed threshold somewhat more.
     // The buffer holds 2.5x the model so that the exact compaction of a full
-    // buffer (a radix select per row) stays rare.
+    // buffer (a radix select per row) stays rare. With two halves per row
+    // (one-pass modes) each half buffers about half of the row's survivors
+    // after its first ksel, and holds 1.25x the model.
+    pl.halves = pl.passes == 3 ? 1 : 2;
+    const int cw = TC_BN / pl.halves;  // columns of a tile one buffer takes
     const double ncol = (double)hmin(N, (int64_t)pl.cols_per_split);
     const double model = ks * (1.0 + log(fmax(1.0, ncol / ks)));
-    int64_t cap = (int64_t)ceil(2.5 * model) + TC_BN;
-    if (cap < 8 * ks + TC_BN) cap = 8 * ks + TC_BN;
+    int64_t cap = (int64_t)ceil((pl.halves == 1 ? 2.5 : 1.25) * model) + cw;
+    if (cap < (8 / pl.halves) * ks + cw) cap = (8 / pl.halves) * ks + cw;
     // the epilogue's bucket counts are 16 bits and never exceed the buffer's size
     if (cap > 65504) cap = 65504;
     pl.cap = (int)((cap + 31) / 32 * 32);
@@ -1339,9 +1462,9 @@ size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcP
     w.nrm = c.take<float>((size_t)N);
     w.stats = c.take<float>((size_t)N * 4);
     w.gmax = c.take<unsigned>(4);
-    w.cand = c.take<char>((size_t)Q * pl.splits * pl.cap * sizeof(Cand));
-    w.meta = c.take<char>((size_t)Q * pl.splits * sizeof(int4));
-    w.row_hist = pl.splits > 1 ? c.take<unsigned>((size_t)Q * NBUCKET) : nullptr;
+    w.cand = c.take<char>((size_t)Q * pl.splits * pl.halves * pl.cap * sizeof(Cand));
+    w.meta = c.take<char>((size_t)Q * pl.splits * pl.halves * sizeof(int4));
+    w.row_hist = pl.splits > 1 ? c.take<unsigned>((size_t)Q * GH_BUCKETS) : nullptr;
     w.flag_rows = c.take<int32_t>((size_t)Q);
     w.flag_count = c.take<int32_t>(1);
     if (ws) *ws = w;
@@ -1355,7 +1478,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     cudaError_t e = cudaMemsetAsync(w.gmax, 0, 4 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.flag_count, 0, sizeof(int32_t), stream);
     if (e == cudaSuccess && w.row_hist)
-        e = cudaMemsetAsync(w.row_hist, 0, (size_t)Q * NBUCKET * sizeof(unsigned), stream);
+        e = cudaMemsetAsync(w.row_hist, 0, (size_t)Q * GH_BUCKETS * sizeof(unsigned), stream);
     if (e != cudaSuccess) return cuda_error(e, "knn_tc memset");
     const bool fp8 = pl.passes == 8;
     const void *a_hi = w.hi, *a_lo = w.lo;
@@ -1445,22 +1568,22 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         const size_t smem = tc_smem_bytes<3>();
         e = cudaFuncSetAttribute(knn_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "knn_tc attribute");
-        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<3>, grid, TC_THREADS, smem, stream, p));
+        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<3>, grid, TcCfg<3>::THREADS, smem, stream, p));
     } else if (fp8) {
         const size_t smem = tc_smem_bytes<8>();
         e = cudaFuncSetAttribute(knn_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "knn_tc attribute");
-        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<8>, grid, TC_THREADS, smem, stream, p));
+        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<8>, grid, TcCfg<8>::THREADS, smem, stream, p));
     } else {
         const size_t smem = tc_smem_bytes<1>();
         e = cudaFuncSetAttribute(knn_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "knn_tc attribute");
-        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<1>, grid, TC_THREADS, smem, stream, p));
+        ATSNE_TRY(launch_kernel("knn_tc", knn_tc_kernel<1>, grid, TcCfg<1>::THREADS, smem, stream, p));
     }
     MergeParams m;
     m.cand = p.cand;
     m.meta = p.meta;
-    m.splits = pl.splits;
+    m.splits = pl.splits * pl.halves;  // candidate buffers per row
     m.cap = pl.cap;
     m.Q = Q;
     m.N = N;
@@ -1489,16 +1612,23 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
                              idx_out, d2_out, Q, k, radius);
     }
     if (!pl.certify) {
-        const size_t ms = merge_smem_bytes<false, RCAP_FP8, MSTAGE_FP8>();
-        e = cudaFuncSetAttribute(knn_merge_kernel<false, RCAP_FP8, MSTAGE_FP8>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
+        // the re-rank set is the ksel best keys (ties included); the staged
+        // keys are those below the lowest tau, about twice as many
+        int rc = 64;
+        while (rc < pl.ksel + pl.ksel / 4) rc <<= 1;
+        m.rc = rc < RCAP_FP8 ? rc : RCAP_FP8;
+        m.mst = 2 * m.rc;
+        const size_t ms = merge_smem_bytes(m.rc, m.mst);
+        e = cudaFuncSetAttribute(knn_merge_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
         if (e != cudaSuccess) return cuda_error(e, "knn_tc_merge attribute");
-        ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<false, RCAP_FP8, MSTAGE_FP8>,
-                                ceil_div(Q, MERGE_WARPS), MERGE_WARPS * 32, ms, stream, m));
+        ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<false>, ceil_div(Q, MERGE_WARPS),
+                                MERGE_WARPS * 32, ms, stream, m));
     } else {
-        const size_t ms = merge_smem_bytes<true, RCAP, MSTAGE>();
-        ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<true, RCAP, MSTAGE>,
-                                ceil_div(Q, MERGE_WARPS), MERGE_WARPS * 32, ms, stream, m));
+        m.rc = RCAP;
+        m.mst = MSTAGE;
+        const size_t ms = merge_smem_bytes(m.rc, m.mst);
+        ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<true>, ceil_div(Q, MERGE_WARPS),
+                                MERGE_WARPS * 32, ms, stream, m));
     }
     return knn_bruteforce_rows(X, N, D, qlist, w.flag_rows, w.flag_count, Q, k, idx_out, d2_out, stream,
                                Xq);
