@@ -65,9 +65,13 @@ atsne_status calibrate_launch(const float *d2, int64_t rows, int k, float perple
 
 // ---- symmetrize -------------------------------------------------------------
 struct SymWs {
-    int32_t *scol = nullptr;
+    int32_t *scol = nullptr;   // [N][k] conditional rows sorted by column
     float *sval = nullptr;
-    int32_t *rev = nullptr, *cursor = nullptr, *long_rows = nullptr, *n_long = nullptr, *own = nullptr;
+    int32_t *rev_i = nullptr;  // reverse lists: source rows, [N * k]
+    float *rev_p = nullptr;    // and their conditionals
+    int32_t *rcnt = nullptr, *cursor = nullptr, *len = nullptr, *long_rows = nullptr, *n_long = nullptr,
+            *own = nullptr;
+    int64_t *roff = nullptr, *rtot = nullptr;  // reverse list offsets [N + 1], total
     int64_t *scan = nullptr;
 };
 size_t scan_partials_count(int64_t n);
