@@ -1,18 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the A-tSNE similarity path (tSNE's P matrix) on one GB300.
 
-One step = one pass of the whole hot path over the MNIST-shaped synthetic
-workload (N=70000, D=784, integer values in [0, 255], ~80% zeros; perplexity
-30, k = 90):
-  exact P:        exact kNN -> beta bisection -> symmetrised CSR P  (Eq. 8, 3-4, 2)
-  approximate P:  KD-forest build (T=4, V=5) -> forest kNN (checks) -> beta
-                  bisection -> CSR P^A                              (Sec. 4.2)
-  precision:      rho of P^A's neighbourhoods against the exact ones (Eq. 9)
-  refinement:     exact refinement of a brushed selection of P^A's rows, then
-                  the CSR rebuild of Eq. 10                          (Sec. 4.3)
-value = N points / step time (whole job: N points per rank, summed over ranks).
-exact_P reports the exact path alone (kNN + beta + CSR P, N / time) in FP32, in
-BF16+rerank and in FP8+rerank, with their recall against FP32.
+Headline: one step = the exact P matrix of one batch of 1,000,000 x 128
+non-negative Gamma(2, 1) features in 50 clusters (perplexity 30, k = 90):
+    exact kNN (Eq. 8, Sec. 3.1) -> beta bisection (Eq. 3-4) -> symmetrised CSR P (Eq. 2)
+with the distance contraction in BF16 on the tensor cores and the top-4k
+candidates re-ranked in FP32 (recall >= 0.999 against FP32 checked), beside the
+same step in FP32 (three BF16 passes, certified exact), the certified one-pass
+BF16 mode and FP8 with per-row scales. value = N points / step time (whole job:
+N points per rank, summed over ranks).
+
+Beside it: the approximate path and the paper's refinement on the MNIST-shaped
+workload (70000 x 784: forest build, forest kNN at checks 1024, rho of Eq. 9,
+exact refinement of a brushed selection, CSR P^A), the forest's checks sweep,
+serving with p50/p99 latency, the density views and batched refinement.
 
 --impl reference times the FP64 CPU oracle (the plain restatement of the
 method the library is checked against) on the host cores, on a bounded sample
@@ -33,8 +34,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 K_NN, PERPLEXITY = 90, 30.0
+METRIC = "P-matrix points/s at k=90, FP32 vs BF16+rerank at recall≥0.999; p99 latency"
 
 WORKLOADS = {
+    "gamma1m": dict(N=1_000_000, D=128, seed=3, kind="gamma_clusters",
+                    desc="1000000x128 fp32, non-negative Gamma(2,1) features times per-cluster "
+                         "scales U(0.5,2), 50 clusters"),
+    "gamma200k": dict(N=200_000, D=128, seed=3, kind="gamma_clusters",
+                      desc="200000x128 fp32, Gamma-cluster features (profiling case)"),
     "mnist70k": dict(N=70000, D=784, seed=2, kind="sparse_prototypes",
                      desc="70000x784 fp32, integer values in [0,255], ~80% zeros, 10 sparse "
                           "prototypes + noise (MNIST-shaped)"),
@@ -43,12 +50,19 @@ WORKLOADS = {
     "gauss2k": dict(N=2000, D=64, seed=1, kind="gaussian_mixture",
                     desc="2000x64 fp32, 10 isotropic Gaussians (sigma 1, centres N(0,5^2))"),
 }
+PRECISIONS = ("fp32", "bf16", "bf16_approx", "fp8")
+PREC_NAME = {"fp32": "FP32 (three BF16 passes, FP32 re-rank, certified exact)",
+             "bf16": "BF16+rerank, certified (uncertified rows on the CUDA cores)",
+             "bf16_approx": "BF16+rerank (one BF16 pass, top-4k re-ranked in FP32)",
+             "fp8": "FP8 E4M3 with per-row scales + top-4k FP32 re-rank"}
 
 
 def make_data(w):
     from paper_1512_01655_gb300 import synth
     if w["kind"] == "sparse_prototypes":
         X, labels = synth.sparse_prototypes(N=w["N"], D=w["D"], seed=w["seed"], return_labels=True)
+    elif w["kind"] == "gamma_clusters":
+        X, labels = synth.gamma_clusters(N=w["N"], D=w["D"], seed=w["seed"], return_labels=True)
     else:
         X, labels = synth.gaussian_mixture(w["N"], w["D"], seed=w["seed"], return_labels=True)
     return X, labels
@@ -60,25 +74,31 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="mnist70k")
-    p.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="gamma1m",
+                   help="the headline exact-P workload")
+    p.add_argument("--precision", choices=PRECISIONS, default="bf16_approx",
+                   help="precision of the headline step's distance contraction")
+    p.add_argument("--fp32-steps", type=int, default=5, help="timed steps of the FP32 comparison")
+    p.add_argument("--variant-reps", type=int, default=2,
+                   help="timed runs of the certified BF16 and the FP8 variants (0: skip)")
+    p.add_argument("--oracle-rows", type=int, default=48,
+                   help="sampled rows whose kNN the oracle computes for the recall check")
+    p.add_argument("--approx-workload", choices=sorted(WORKLOADS), default="mnist70k")
+    p.add_argument("--approx-steps", type=int, default=5,
+                   help="timed steps of the approximate path with refinement (0: skip)")
     p.add_argument("--trees", type=int, default=4)
     p.add_argument("--checks", type=int, default=1024)
     p.add_argument("--queue-cap", type=int, default=0, help="forest queue capacity (0 = auto)")
     p.add_argument("--refine", type=int, default=2000, help="points in the refined selection")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--serve-max", type=int, default=2_000_000,
-                   help="serving session: corpus size at which it ends (0 = skip)")
+                   help="serving benchmark corpus size (0 to skip)")
     p.add_argument("--kde-reps", type=int, default=5,
-                   help="timed renders of the density / approximation map (0 = skip)")
+                   help="timed density-view renders (0 to skip)")
     p.add_argument("--refine-batch-reps", type=int, default=3,
-                   help="timed runs of the batched refinement workload (0 = skip)")
-    p.add_argument("--exact-reps", type=int, default=5,
-                   help="timed runs of the exact path alone per precision (0 = skip)")
+                   help="timed batched refinements of the 500000 x 256 workload (0 to skip)")
     p.add_argument("--checks-sweep", default="32,64,128,256,512,1024,2048,4096",
-                   help="forest checks values for the precision sweep (empty = skip)")
-    p.add_argument("--gamma-reps", type=int, default=3,
-                   help="timed runs per precision on the 1M x 128 Gamma workload (0 = skip)")
+                   help="forest checks values for the rho sweep (empty to skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=256)
     return p.parse_args()
@@ -183,7 +203,7 @@ class Pipeline:
         from paper_1512_01655_gb300 import synth
         sel = synth.refine_subsets(labels, 1, lo=args.refine, hi=args.refine, seed=4)[0]
         self.subset = torch.from_numpy(sel).to(dev)
-        self.exact_opts = at.knn_opts(method="exact", precision=args.precision)
+        self.exact_opts = at.knn_opts(method="exact", precision="fp32")
         self.forest_opts = at.knn_opts(method="forest", trees=args.trees, checks=args.checks,
                                        leaf_size=1, seed=7, queue_cap=args.queue_cap)
         # the approximate path runs on its own stream beside the exact one: the
@@ -249,9 +269,10 @@ TRAFFIC_SOURCES = {
 }
 
 
-def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    record, or None when there is none or the kernel's sources have changed."""
+def recorded_traffic(kernel, workload, variant=None):
+    """DRAM bytes per launch of `kernel` on `workload` (and precision `variant`)
+    from the committed ncu record, or None when there is none or the kernel's
+    sources have changed."""
     import hashlib
     srcs = TRAFFIC_SOURCES.get(kernel)
     if not srcs:
@@ -265,8 +286,9 @@ def recorded_traffic(kernel, workload):
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as fh:
             for line in fh:
                 parts = line.split()
+                key = workload if variant is None else workload + ":" + variant
                 if len(parts) == 4 and not line.startswith("#") and parts[0] == kernel \
-                        and parts[1] == workload and parts[2] == h.hexdigest():
+                        and parts[1] == key and parts[2] == h.hexdigest():
                     return int(parts[3])
     except OSError:
         return None
@@ -455,76 +477,155 @@ def bench_refine_batch(at, torch, dev, stream, reps, peaks):
                        "frac": round(ach / peak, 4), "tensor_passes": 3}}
 
 
-def bench_gamma(at, torch, dev, stream, reps, peaks):
-    """The precision comparison on its own workload: 1,000,000 x 128
-    non-negative Gamma(2, 1) features scaled per cluster (50 clusters), k = 90,
-    the exact kNN of 100000 sampled rows (every 10th) against all rows, in
-    FP32 (three BF16 passes, certified), BF16+rerank (certified: uncertified
-    rows go to the CUDA cores), BF16+rerank without a certificate (top-4k
-    re-ranked in FP32) and FP8+rerank; median of `reps` CUDA-event timed runs
-    after one warm-up, recall (Eq. 9) against FP32."""
-    from paper_1512_01655_gb300 import synth
-    X = torch.from_numpy(synth.gamma_clusters(N=1_000_000, D=128, seed=3)).to(dev)
-    N, D = X.shape
-    q = torch.arange(0, N, 10, dtype=torch.int32, device=dev)
-    Q = q.numel()
-    out = {"workload": "1000000x128 Gamma(2,1) x per-cluster scales, 50 clusters; 100000 sampled query rows",
-           "k": K_NN}
-    ref = None
-    peak = peaks.get("bf16_tflops", 1900.0)
-    for prec in ("fp32", "bf16", "bf16_approx", "fp8"):
-        o = at.knn_opts(method="exact", precision=prec)
-        at.atsne_knn(X, K_NN, queries=q, opts=o)
-        ts = []
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            idx, _ = at.atsne_knn(X, K_NN, queries=q, opts=o)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        at.atsne_check()
-        ms = sorted(ts)[len(ts) // 2]
-        passes = 3 if prec == "fp32" else 1
-        ent = {"ms": round(ms, 3), "queries_per_s": round(Q / (ms / 1e3), 1),
-               "tensor_frac_algorithmic": round(passes * 2.0 * Q * N * D / (ms / 1e3) / 1e12
-                                                / (peak * (2.0 if prec == "fp8" else 1.0)), 4)}
-        if ref is None:
-            ref = idx
-        else:
-            ent["recall_vs_fp32"] = round(at.atsne_knn_precision(idx, ref)[1], 6)
-        out[prec] = ent
-    del X, ref
-    torch.cuda.empty_cache()
+def algorithmic_flops_knn(Q, N, D):
+    return 2.0 * Q * N * D
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ExactStep:
+    """The exact P matrix of one batch, all through the C ABI binding:
+    exact kNN (prep, tensor-core contraction with fused filter, merge and
+    re-rank) -> beta bisection -> symmetrised CSR P."""
+
+    def __init__(self, at, X, precision):
+        self.at, self.X = at, X
+        self.opts = at.knn_opts(method="exact", precision=precision)
+
+    def step(self):
+        at = self.at
+        idx, d2 = at.atsne_knn(self.X, K_NN, opts=self.opts)
+        P, _ = at.atsne_calibrate_P(d2, PERPLEXITY)
+        csr = at.atsne_symmetrize(idx, P, trim=False)
+        return idx, csr
+
+
+def timed_steps(torch, fn, steps, stream, l2_flush=None):
+    """CUDA events on the launching stream around each step."""
+    evs, out = [], None
+    for _ in range(steps):
+        if l2_flush is not None:
+            l2_flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs], out
+
+
+PROFILED = ["knn_prep", "knn_tc", "knn_tc_merge", "knn_fallback", "knn_bruteforce", "calibrate_beta",
+            "sym_fwd", "sym_rev", "sym_len", "sym_write", "sym_sort_long", "sym_write_long",
+            "scan_reduce", "scan_partials", "scan_down",
+            "forest_traverse", "forest_traverse_u8", "forest_dist", "forest_dist_u8", "forest_u8_prep",
+            "forest_choose", "forest_partial", "forest_sort_smem", "forest_sort_global", "forest_keys",
+            "forest_scatter", "forest_leaf_pt", "refine_scatter", "knn_precision"]
+SYM_PARTS = ("sym_fwd", "sym_rev", "sym_len", "sym_write", "sym_sort_long", "sym_write_long",
+             "scan_reduce", "scan_partials", "scan_down")
+
+
+def read_profile(at):
+    out = {}
+    for name in PROFILED:
+        n, ms = at.profile_read(name)
+        if n:
+            out[name] = {"launches": n, "ms": ms}
     return out
 
 
-def algorithmic_flops_knn(N, D):
-    return 2.0 * N * N * D
+def exact_rooflines(per_kernel, steps, N, D, k, nnz, passes, prec, peaks, workload):
+    """Roofline lines of the exact path's kernels from their CUDA-event times
+    per launch: the tensor-core kNN against the measured BF16 peak (FP8: twice
+    it, the nominal ratio), the bandwidth-bound kernels against the measured HBM
+    copy rate on their algorithmic bytes."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    lines = {}
+    if "knn_tc" in per_kernel:
+        pk = per_kernel["knn_tc"]
+        avg = pk["ms"] / pk["launches"]
+        peak = bf16 * (2.0 if prec == "fp8" else 1.0)
+        ach = algorithmic_flops_knn(N, N, D) / (avg / 1e3) / 1e12
+        lines["knn_tc"] = {
+            "kernel": "knn_tc", "bound": "tensor", "achieved": round(ach, 1), "peak": round(peak, 1),
+            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "launch_ms": round(avg, 3),
+            "traffic": recorded_traffic("knn_tc", workload, prec),
+            "algorithmic_flops_per_launch": algorithmic_flops_knn(N, N, D), "tensor_passes": passes,
+            "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, of measured)" +
+                            (" x 2 (FP8 nominal ratio)" if prec == "fp8" else ""))}
+    Dp = 64 * ((D + 63) // 64)
+    bw = {
+        # X read; BF16 copies (two in FP32 mode), norms and error statistics written
+        "knn_prep": N * D * 4 + N * Dp * 2 * (2 if passes == 3 else 1) + N * 20,
+        # d2 read; P and beta written
+        "calibrate_beta": N * k * 8 + N * 4,
+        # idx and P read; row_ptr, col and val written
+        "symmetrize": N * k * 8 + (N + 1) * 8 + nnz * 8,
+    }
+    for name, bytes_ in bw.items():
+        parts = SYM_PARTS if name == "symmetrize" else (name,)
+        ms = sum(per_kernel[p]["ms"] for p in parts if p in per_kernel) / steps
+        if ms <= 0:
+            continue
+        ach = bytes_ / (ms / 1e3) / 1e9
+        lines[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round(ach / hbm, 4), "ms": round(ms, 3), "algorithmic_bytes": int(bytes_),
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if "calibrate_beta" in lines:
+        lines["calibrate_beta"]["note"] = ("bound by the exponentials of the bisection (about 40-60 "
+                                           "steps of k exp per row), not by its bytes")
+    if "knn_tc_merge" in per_kernel:
+        lines["knn_tc_merge"] = {"bound": "gather", "ms": round(per_kernel["knn_tc_merge"]["ms"] / steps, 3)}
+    return lines
+
+
+def oracle_recall(Xh, idx_by_prec, rows):
+    """Eq. 9 precision of each mode's lists against the oracle's exact kNN on
+    sampled rows, and the rows whose index set equals the oracle's where the
+    k-th/(k+1)-th oracle distance gap exceeds 1e-4 (relative)."""
+    import oracle
+    from paper_1512_01655_gb300 import synth
+    q = synth.sample_rows(Xh.shape[0], rows, seed=19)
+    o_idx, o_d2 = oracle.knn_exact(Xh, K_NN + 1, queries=q)
+    clear = (o_d2[:, K_NN] - o_d2[:, K_NN - 1]) / o_d2[:, K_NN] > 1e-4
+    out = {"rows": int(len(q)), "rows_with_clear_gap": int(clear.sum())}
+    for prec, idx in idx_by_prec.items():
+        g = idx[q.astype(np.int64)]
+        inter = [len(set(g[r]) & set(o_idx[r, :K_NN])) for r in range(len(q))]
+        same = [set(g[r]) == set(o_idx[r, :K_NN]) for r in range(len(q)) if clear[r]]
+        out[prec] = {"recall": round(float(np.mean(inter)) / K_NN, 6),
+                     "clear_rows_identical": int(np.sum(same))}
+    return out
 
 
 def run_ours(args, world, rank, local, pg):
     import torch
     import paper_1512_01655_gb300 as at
     dev = torch.device("cuda", local)
+    peaks = load_peaks()
     w = WORKLOADS[args.workload]
     Xh, labels = make_data(w)
     X = torch.from_numpy(Xh).to(dev)
     N, D = Xh.shape
-    pipe = Pipeline(at, X, labels, args, dev)
     stream = torch.cuda.current_stream()
     l2_flush = None
     if Xh.nbytes < 256 * 2**20:
         l2_flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)
 
+    # ---- headline: the exact P matrix in the headline precision ----
+    head = ExactStep(at, X, args.precision)
     for _ in range(args.warmup):
-        pipe.step()
+        head.step()
     torch.cuda.synchronize()
     at.atsne_check()
-
-    # timed region: K steps, events per step on the launching stream, L2 flushed
-    # between steps when the input alone does not exceed L2
     at.profile_enable(True)
     at.profile_reset()
     launches0 = at.launch_count()
@@ -532,135 +633,32 @@ def run_ours(args, world, rank, local, pg):
     barrier(pg)
     torch.cuda.synchronize()
     clocks.start()
-    times = []
-    for _ in range(args.steps):
-        if l2_flush is not None:
-            l2_flush.fill_(1)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        out = pipe.step()
-        ev1.record(stream)
-        times.append((ev0, ev1))
-    torch.cuda.synchronize()
+    step_ms, out = timed_steps(torch, head.step, args.steps, stream, l2_flush)
     barrier(pg)
     clk = clocks.stop()
     launches = at.launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in times]
-    total_ms = sum(step_ms)
-    per_kernel = {}
-    for name in ["knn_bruteforce", "knn_tc", "knn_tc_merge", "calibrate_beta", "forest_traverse",
-                 "forest_traverse_u8", "forest_dist", "forest_dist_u8", "forest_u8_prep", "forest_choose", "forest_partial", "forest_sort_smem", "forest_sort_global",
-                 "sym_scatter", "sym_count", "sym_sort_rows", "sym_sort_tails", "knn_prep"]:
-        n, ms = at.profile_read(name)
-        if n:
-            per_kernel[name] = {"launches": n, "ms": ms}
+    per_kernel = read_profile(at)
     at.profile_enable(False)
-    csr_e, csr_a, rho_i = out
-    rho_refined = float(rho_i.double().mean().item())
-    rho = float(pipe.rho_sum.item()) / N
-    nnz = int(csr_e[3].item())
     at.atsne_check()
-
-    total_ms = max_over_ranks(pg, total_ms, dev)
+    idx_head = out[0]
+    nnz = int(out[1][3].item())
+    total_ms = max_over_ranks(pg, sum(step_ms), dev)
     value = world * N * args.steps / (total_ms / 1e3)
+    exact_bf16 = bool(torch.equal(X.to(torch.bfloat16).float(), X))  # low halves zero: one pass in FP32 mode
 
-    # FP32 mode runs three BF16 passes unless every value is exact in BF16 (the
-    # low halves are then zero and the kernel skips their passes)
-    passes_run = 1 if args.precision != "fp32" or bool(
-        torch.equal(pipe.X.to(torch.bfloat16).float(), pipe.X)) else 3
-    # roofline of the dominant kernel; the forest search is one step made of two
-    # launches (traversal, then the distances of the points it collected), taken
-    # together against the bytes the search must gather
-    fparts = ("forest_u8_prep", "forest_traverse", "forest_traverse_u8", "forest_dist", "forest_dist_u8")
-    cand = {k_: v["ms"] for k_, v in per_kernel.items() if k_ not in fparts}
-    if "forest_traverse" in per_kernel:
-        cand["forest_query"] = sum(per_kernel[k_]["ms"] for k_ in fparts if k_ in per_kernel)
-    dom = max(cand.items(), key=lambda kv: kv[1])[0] if cand else None
-    roofline = None
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    if dom in ("knn_bruteforce",):
-        # FP32 CUDA-core kernel: 3 flops (sub, fma) per pair and dimension.
-        sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        per_launch_flops = 3.0 * N * N * D
-        avg_ms = per_kernel[dom]["ms"] / per_kernel[dom]["launches"]
-        ach = per_launch_flops / (avg_ms / 1e3) / 1e12
-        roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 2),
-                    "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                    "traffic": None,
-                    "peak_source": "FP32 FMA rate: 152 SMs x 128 lanes x 2 flops x max SM clock"}
-    elif dom == "knn_tc":
-        mult = float(passes_run)
-        peak = peaks.get("bf16_tflops", 1900.0)
-        per_launch_flops = algorithmic_flops_knn(N, D)
-        avg_ms = per_kernel[dom]["ms"] / per_kernel[dom]["launches"]
-        ach = per_launch_flops / (avg_ms / 1e3) / 1e12
-        roofline = {"kernel": dom, "bound": "tensor", "achieved": round(ach, 1),
-                    "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                    "traffic": None, "tensor_passes": mult,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
-    elif dom == "forest_query":
-        # gather-bound: every evaluated point's row (D values) is read once per
-        # query, plus the query row and the k (index, distance) outputs; with one
-        # point per leaf exactly max(checks, k) points are evaluated per query.
-        # Rows are gathered as bytes when every value is an integer in [0, 255]
-        # (the distance kernel then reads the byte copy), else as FP32.
-        need = max(args.checks, K_NN)
-        Xd = pipe.X
-        u8 = D <= 2048 and bool(((Xd >= 0) & (Xd <= 255) & (Xd == torch.round(Xd))).all())
-        vb = 1 if u8 else 4
-        per_launch = N * ((need + 1) * D * vb + K_NN * 8)
-        tr = per_kernel["forest_traverse"]  # one launch per search (the FP32-query instantiation)
-        trn = "forest_traverse_u8" if u8 else "forest_traverse"
-        tw = per_kernel.get(trn, tr)
-        di = per_kernel["forest_dist_u8" if u8 else "forest_dist"]
-        avg_ms = sum(per_kernel[k_]["ms"] for k_ in fparts if k_ in per_kernel) / tr["launches"]
-        ach = per_launch / (avg_ms / 1e3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        dname = "forest_dist_u8" if u8 else "forest_dist"
-        t_tr, t_di = (recorded_traffic(trn, args.workload), recorded_traffic(dname, args.workload))
-        roofline = {"kernel": "forest_query (%s + %s)" % (trn, dname), "bound": "hbm",
-                    "achieved": round(ach, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(ach / peak, 4),
-                    "traffic": t_tr + t_di if t_tr is not None and t_di is not None else None,
-                    "algorithmic_bytes_per_launch": per_launch, "row_bytes_per_value": vb,
-                    "parts": {
-                        trn: {"ms": round(tw["ms"] / tr["launches"], 3),
-                              "traffic": t_tr,
-                              "bound": "instruction issue (queue and tree walk)"},
-                        dname: {"ms": round(di["ms"] / di["launches"], 3),
-                                        "traffic": t_di,
-                                        "achieved": round(per_launch / (di["ms"] / di["launches"] / 1e3)
-                                                          / 1e9, 1),
-                                        "frac": round(per_launch / (di["ms"] / di["launches"] / 1e3)
-                                                      / 1e9 / peak, 4)}},
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    elif dom is not None:
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": None,
-                    "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s", "frac": None,
-                    "traffic": None}
-    # the exact-kNN contraction's own line (the tensor-bound kernel), whichever dominates
-    knn_line = None
-    if "knn_tc" in per_kernel:
-        launches_tc = per_kernel["knn_tc"]["launches"]
-        # one full launch (all N rows) per step plus the refinement's launch
-        full_ms = per_kernel["knn_tc"]["ms"] / args.steps
-        flops = algorithmic_flops_knn(N, D) + 2.0 * pipe.subset.numel() * N * D
-        peak = peaks.get("bf16_tflops", 1900.0)
-        ach = flops / (full_ms / 1e3) / 1e12
-        knn_line = {"kernel": "knn_tc", "bound": "tensor", "launches_per_step": launches_tc // args.steps,
-                    "ms_per_step": round(full_ms, 3), "achieved": round(ach, 1), "peak": peak,
-                    "unit": "TFLOP/s (algorithmic 2*Q*N*D)", "frac": round(ach / peak, 4),
-                    "tensor_passes": passes_run}
+    def passes_of(prec):
+        return 3 if prec == "fp32" and not exact_bf16 else 1
 
-    # end to end through the public API with host buffers: H2D of X from pinned
-    # memory, the step, D2H of both CSR matrices (trimmed to nnz) and rho
+    passes = passes_of(args.precision)
+    rooflines = exact_rooflines(per_kernel, args.steps, N, D, K_NN, nnz, passes, args.precision, peaks,
+                                args.workload)
+    roofline = rooflines.get("knn_tc")
+    idx_by_prec = {args.precision: idx_head.cpu().numpy()}
+    del out, idx_head
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the API with host buffers: X from pinned memory,
+    # the step, the CSR P (trimmed to nnz) back to the host ----
     e2e = None
     if args.e2e_steps > 0:
         Xpin = torch.from_numpy(Xh).pin_memory()
@@ -668,157 +666,204 @@ def run_ours(args, world, rank, local, pg):
         for it in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            pipe.X = Xpin.to(dev, non_blocking=True)
-            csr_e, csr_a, rho_i = pipe.step()
-            host = []
-            for rp, col, val, nz in (csr_e, csr_a):
-                n_ = int(nz.item())
-                host += [rp.cpu(), col[:n_].cpu(), val[:n_].cpu()]
-            host.append(rho_i.cpu())
+            head.X = Xpin.to(dev, non_blocking=True)
+            _, (rp, col, val, nz) = head.step()
+            n_ = int(nz.item())
+            host = [rp.cpu(), col[:n_].cpu(), val[:n_].cpu()]
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             if it > 0:
                 e2e_ms.append((t1 - t0) * 1e3)
                 h2d = Xpin.numel() * 4
                 d2h = sum(t.numel() * t.element_size() for t in host)
-        pipe.X = X
+        head.X = X
+        del Xpin, host
         e2e_total = max_over_ranks(pg, sum(e2e_ms), dev)
         e2e = {"value": round(world * N * len(e2e_ms) / (e2e_total / 1e3), 1),
                "unit": "points/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        torch.cuda.empty_cache()
 
-    # the exact path alone (kNN + beta + CSR P) in each precision: the metric's
-    # FP32 vs BF16+rerank comparison, and the FP8+rerank variant. CUDA events on the launching stream, L2
-    # flushed before each run when the input alone does not exceed it, median of
-    # --exact-reps runs after 3 warm-ups; recall (Eq. 9) of BF16+rerank and
-    # FP8+rerank against FP32.
-    exact_p = None
-    if args.exact_reps > 0:
-        exact_p = {}
-        ref_idx = None
-        for prec in ("fp32", "bf16", "bf16_approx", "fp8"):
-            o = at.knn_opts(method="exact", precision=prec)
-
-            def run_exact():
-                idx_, d2_ = at.atsne_knn(X, K_NN, opts=o)
-                P_, _ = at.atsne_calibrate_P(d2_, PERPLEXITY)
-                at.atsne_symmetrize(idx_, P_, trim=False)
-                return idx_
-
-            for _ in range(3):
-                idx_p = run_exact()
-            ts = []
-            for _ in range(args.exact_reps):
-                if l2_flush is not None:
-                    l2_flush.fill_(1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                idx_p = run_exact()
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            at.atsne_check()
-            med = sorted(ts)[len(ts) // 2]
-            entry = {"ms": round(med, 3), "points_per_s": round(world * N / (med / 1e3), 1)}
-            if ref_idx is None:
-                ref_idx = idx_p
-            else:
-                entry["recall_vs_fp32"] = round(at.atsne_knn_precision(idx_p, ref_idx)[1], 6)
-            exact_p[prec] = entry
-
-    # the approximate path's precision knob: rho (Eq. 9) of the forest search
-    # against the exact FP32 neighbourhoods at each checks value, one forest
-    # (the step's options), median of 3 timed searches after one warm-up
-    sweep = None
-    if args.checks_sweep:
-        sweep = []
-        ref_idx, _ = at.atsne_knn(X, K_NN, opts=pipe.exact_opts)
-        forest = at.atsne_forest_build(X, opts=pipe.forest_opts)
-        for c in [int(v) for v in args.checks_sweep.split(",")]:
-            at.atsne_forest_query(X, forest, K_NN, checks=c)
-            ts = []
-            for _ in range(3):
-                if l2_flush is not None:
-                    l2_flush.fill_(1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                idx_c, _, ev_c = at.atsne_forest_query(X, forest, K_NN, checks=c)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            med = sorted(ts)[1]
-            sweep.append({"checks": c, "rho": round(at.atsne_knn_precision(idx_c, ref_idx)[1], 5),
-                          "evaluated_mean": round(float(ev_c.double().mean().item()), 1),
-                          "ms": round(med, 3), "points_per_s": round(N / (med / 1e3), 1)})
+    # ---- the metric's comparison: the same step in FP32, then the certified
+    # BF16 mode and FP8; recall (Eq. 9) against FP32 over all rows ----
+    modes = {}
+    head_recall = None
+    order = [p for p in ("fp32", "bf16_approx", "bf16", "fp8") if p != args.precision]
+    for prec in order:
+        reps = args.fp32_steps if prec == "fp32" else args.variant_reps
+        if reps <= 0:
+            continue
+        st = ExactStep(at, X, prec)
+        st.step()
+        torch.cuda.synchronize()
+        at.profile_enable(True)
+        at.profile_reset()
+        ms, out = timed_steps(torch, st.step, reps, stream, l2_flush)
+        pk = read_profile(at)
+        at.profile_enable(False)
         at.atsne_check()
-        del forest, ref_idx
+        med = sorted(ms)[len(ms) // 2]
+        rl = exact_rooflines(pk, reps, N, D, K_NN, int(out[1][3].item()), passes_of(prec), prec, peaks,
+                             args.workload)
+        modes[prec] = {"what": PREC_NAME[prec], "steps": reps, "ms": round(med, 3),
+                       "points_per_s": round(world * N / (med / 1e3), 1),
+                       "stage_ms": {k_: round(v["ms"] / reps, 3) for k_, v in pk.items()},
+                       "knn_tc": rl.get("knn_tc")}
+        idx_by_prec[prec] = out[0].cpu().numpy()
+        del out, st
+        torch.cuda.empty_cache()
+    if "fp32" in idx_by_prec:
+        ref = torch.from_numpy(idx_by_prec["fp32"]).to(dev)
+        for prec, idx in idx_by_prec.items():
+            if prec != "fp32":
+                r = round(at.atsne_knn_precision(torch.from_numpy(idx).to(dev), ref)[1], 7)
+                if prec == args.precision:
+                    head_recall = r
+                else:
+                    modes[prec]["recall_vs_fp32"] = r
+        del ref
+    recall_oracle = None
+    if args.oracle_rows > 0 and rank == 0:
+        recall_oracle = oracle_recall(Xh, idx_by_prec, args.oracle_rows)
+    del idx_by_prec
+    torch.cuda.empty_cache()
 
-    gamma = None
-    if args.gamma_reps > 0 and world == 1:
-        gamma = bench_gamma(at, torch, dev, stream, args.gamma_reps, peaks)
-
-    # serving runs in FP32 mode (three BF16 tensor passes, FP32 re-rank,
-    # certified exact): on this data it beats the certified one-pass BF16
-    # mode, whose rows mostly fail the certificate; the latter is run too
+    # ---- the approximate path, its precision and the refinement ----
+    approx = None
+    if args.approx_steps > 0:
+        approx = bench_approx(at, torch, dev, stream, args, peaks)
+        torch.cuda.empty_cache()
     serving = None
     if args.serve_max > 0 and world == 1:
         serving = bench_serving(at, torch, dev, args.serve_max, precision="fp32")
         b = bench_serving(at, torch, dev, args.serve_max, precision="bf16")
         serving["bf16_rerank_certified"] = {kk: b[kk] for kk in ("capacity_points_per_s", "points_per_s",
-                                                                 "p50_ms", "p99_ms", "sliding_window")}
-
-    kde = None
-    if args.kde_reps > 0:
-        kde = bench_kde(at, torch, dev, stream, labels, rho_i, args.kde_reps, clk, peaks)
-
+                                                       "p50_ms", "p99_ms", "sliding_window")}
     refine_batch = None
     if args.refine_batch_reps > 0:
         refine_batch = bench_refine_batch(at, torch, dev, stream, args.refine_batch_reps, peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, Xh, labels)
+        cpu = cpu_baseline(args, Xh)
 
     if rank == 0:
         line = {
-            "metric": "P-matrix points/s at k=90 (exact FP32 kNN + beta bisection + CSR P, "
-                      "KD-forest P^A, rho, refinement)",
+            "metric": METRIC,
             "value": round(value, 1), "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
-            "data": "synthetic (seeded, MNIST-shaped; no dataset)",
-            "config": {"workload": w["desc"], "N": N, "D": D, "k": K_NN,
-                       "perplexity": PERPLEXITY, "exact_precision": args.precision,
-                       "forest": {"trees": args.trees, "top_var_dims": 5, "checks": args.checks,
-                                  "leaf_size": 1,
-                                  "queue_cap": args.queue_cap or default_queue_cap(args.checks)},
-                       "refine_points": int(pipe.subset.numel()),
+            "dtype": "f32" if args.precision == "fp32" else ("e4m3+f32" if args.precision == "fp8" else "bf16+f32"),
+            "data": "synthetic (seeded Gamma-cluster features; no dataset)",
+            "config": {"workload": w["desc"], "N": N, "D": D, "k": K_NN, "perplexity": PERPLEXITY,
+                       "step": "exact kNN (Eq. 8) -> beta bisection (Eq. 3-4) -> symmetrised CSR P (Eq. 2)",
+                       "precision": PREC_NAME[args.precision],
                        "l2": "input larger than L2" if l2_flush is None else "L2 flushed between steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "rho": round(rho, 5), "rho_after_refine": round(rho_refined, 5), "nnz_exact_P": nnz,
+            "recall_vs_fp32": head_recall, "recall_vs_oracle": recall_oracle, "nnz_P": nnz,
             "stage_ms": {k_: round(v["ms"] / args.steps, 3) for k_, v in per_kernel.items()},
-            "stage_ms_note": "CUDA-event time per step of each kernel label on its own stream; the exact "
-                             "path's kernels overlap the approximate path's (higher-priority stream) and "
-                             "include the time they wait for SMs",
             "step_ms": [round(t, 3) for t in step_ms],
-            "roofline": roofline, "knn_tc_roofline": knn_line, "exact_P": exact_p,
-            "forest_checks_sweep": sweep, "precision_gamma1m": gamma, "refine_batch": refine_batch, "kde": kde, "serving": serving,
-            "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clk, "gpu_launches": int(launches),
+            "roofline": roofline, "bandwidth_kernels": {k_: v for k_, v in rooflines.items() if k_ != "knn_tc"},
+            "modes": modes, "approx_path": approx, "refine_batch": refine_batch, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line))
+
+
+def bench_approx(at, torch, dev, stream, args, peaks):
+    """The approximate path on its own workload (MNIST-shaped by default): per
+    step the exact FP32 P (reference for rho), the forest build (T trees, V = 5),
+    the forest kNN at `checks`, its beta bisection, rho (Eq. 9), the exact
+    refinement of a brushed selection and the CSR P^A (Sec. 4.2, 4.3), the two
+    paths on two streams; then the forest's checks sweep and the density views."""
+    w = WORKLOADS[args.approx_workload]
+    Xh, labels = make_data(w)
+    X = torch.from_numpy(Xh).to(dev)
+    N, D = Xh.shape
+    pipe = Pipeline(at, X, labels, args, dev)
+    l2_flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev) if Xh.nbytes < 256 * 2**20 else None
+    for _ in range(3):
+        pipe.step()
+    torch.cuda.synchronize()
+    at.atsne_check()
+    at.profile_enable(True)
+    at.profile_reset()
+    step_ms, out = timed_steps(torch, pipe.step, args.approx_steps, stream, l2_flush)
+    per_kernel = read_profile(at)
+    at.profile_enable(False)
+    at.atsne_check()
+    csr_e, csr_a, rho_i = out
+    rho_refined = float(rho_i.double().mean().item())
+    rho = float(pipe.rho_sum.item()) / N
+    med = sorted(step_ms)[len(step_ms) // 2]
+    # the forest search: gather-bound, every evaluated point's row read once per
+    # query (bytes when every value is an integer in [0, 255], else FP32), the
+    # query row and the k outputs; traversal and distances taken together
+    fparts = ("forest_u8_prep", "forest_traverse", "forest_traverse_u8", "forest_dist", "forest_dist_u8")
+    need = max(args.checks, K_NN)
+    u8 = D <= 2048 and bool(((X >= 0) & (X <= 255) & (X == torch.round(X))).all())
+    vb = 1 if u8 else 4
+    per_launch = N * ((need + 1) * D * vb + K_NN * 8)
+    forest = None
+    if "forest_traverse" in per_kernel:
+        nl = per_kernel["forest_traverse"]["launches"]
+        avg = sum(per_kernel[k_]["ms"] for k_ in fparts if k_ in per_kernel) / nl
+        ach = per_launch / (avg / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        trn = "forest_traverse_u8" if u8 else "forest_traverse"
+        dname = "forest_dist_u8" if u8 else "forest_dist"
+        t_tr, t_di = recorded_traffic(trn, args.approx_workload), recorded_traffic(dname, args.approx_workload)
+        forest = {"kernel": "forest_query (%s + %s)" % (trn, dname), "bound": "hbm", "achieved": round(ach, 1),
+                  "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "launch_ms": round(avg, 3),
+                  "traffic": t_tr + t_di if t_tr is not None and t_di is not None else None,
+                  "algorithmic_bytes_per_launch": per_launch, "row_bytes_per_value": vb,
+                  "traversal_ms": round(per_kernel.get(trn, per_kernel["forest_traverse"])["ms"] / nl, 3),
+                  "traversal_bound": "instruction issue (queue and tree walk)",
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    sweep = None
+    if args.checks_sweep:
+        sweep = []
+        ref_idx, _ = at.atsne_knn(X, K_NN, opts=pipe.exact_opts)
+        fr = at.atsne_forest_build(X, opts=pipe.forest_opts)
+        for c in [int(v) for v in args.checks_sweep.split(",")]:
+            at.atsne_forest_query(X, fr, K_NN, checks=c)
+            ts = []
+            for _ in range(3):
+                if l2_flush is not None:
+                    l2_flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                idx_c, _, ev_c = at.atsne_forest_query(X, fr, K_NN, checks=c)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            sweep.append({"checks": c, "rho": round(at.atsne_knn_precision(idx_c, ref_idx)[1], 5),
+                          "evaluated_mean": round(float(ev_c.double().mean().item()), 1),
+                          "ms": round(sorted(ts)[1], 3), "points_per_s": round(N / (sorted(ts)[1] / 1e3), 1)})
+        at.atsne_check()
+        del fr, ref_idx
+    kde = None
+    if args.kde_reps > 0:
+        kde = bench_kde(at, torch, dev, stream, labels, rho_i, args.kde_reps, None, peaks)
+    return {"workload": w["desc"], "N": N, "D": D,
+            "step": "exact FP32 P and, on a second stream, forest build -> forest kNN -> beta -> rho -> "
+                    "refinement of %d points -> CSR P^A" % int(pipe.subset.numel()),
+            "forest": {"trees": args.trees, "top_var_dims": 5, "checks": args.checks, "leaf_size": 1,
+                       "queue_cap": args.queue_cap or default_queue_cap(args.checks)},
+            "ms_per_step": round(med, 3), "points_per_s": round(N / (med / 1e3), 1),
+            "rho": round(rho, 5), "rho_after_refine": round(rho_refined, 5),
+            "stage_ms": {k_: round(v["ms"] / args.approx_steps, 3) for k_, v in per_kernel.items()},
+            "forest_query_roofline": forest, "checks_sweep": sweep, "kde": kde}
 
 
 # ---------------------------------------------------------------------------
 # oracle timing (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample_timing(Xh, sample_rows, args):
-    """Time the oracle's work for the whole path on a sample of query rows and
-    extrapolate to all N rows: per-row costs (exact kNN, bisection, forest
-    search, refinement) scale with the rows; the forest build and the CSR
-    symmetrisation are timed once at full size on oracle-made inputs."""
+def oracle_sample_timing(Xh, sample_rows):
+    """Time the oracle's exact P path on a sample of query rows and extrapolate
+    to all N rows: the exact kNN and the bisection scale with the rows; the
+    symmetrisation is timed on a 100000-row kNN graph of the same k and scaled
+    by (N log N) / (n log n), the cost of its sort."""
     import oracle
     from paper_1512_01655_gb300 import synth
     N = Xh.shape[0]
@@ -830,36 +875,27 @@ def oracle_sample_timing(Xh, sample_rows, args):
     t0 = time.perf_counter()
     oracle.calibrate(d2_e, PERPLEXITY)
     t["calibrate"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    f = oracle.forest_build(Xh, trees=args.trees, top_var_dims=5, leaf_size=1, seed=7)
-    t["forest_build_full"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.forest_query(Xh, f, K_NN, args.checks, queries=q)
-    t["forest_query"] = time.perf_counter() - t0
-    # symmetrisation at full size on a random valid kNN graph of the same shape
+    n = min(N, 100_000)
     rng = np.random.default_rng(3)
-    g_idx = (np.arange(N)[:, None] + rng.integers(1, N, size=(N, K_NN))) % N
-    g_idx = g_idx.astype(np.int32)
-    g_P = np.full((N, K_NN), 1.0 / K_NN)
+    g_idx = ((np.arange(n)[:, None] + rng.integers(1, n, size=(n, K_NN))) % n).astype(np.int32)
+    g_P = np.full((n, K_NN), 1.0 / K_NN)
     t0 = time.perf_counter()
     oracle.symmetrize(g_idx, g_P)
-    t["symmetrize_full"] = time.perf_counter() - t0
-    per_row = (2 * t["calibrate"] + t["knn_exact"] + t["forest_query"]) / len(q)
-    refine_rows = args.refine
-    est = (per_row * N + t["knn_exact"] / len(q) * refine_rows + t["forest_build_full"]
-           + 2 * t["symmetrize_full"])
+    t["symmetrize_%d_rows" % n] = time.perf_counter() - t0
+    sym_full = t["symmetrize_%d_rows" % n] * (N * np.log(N * K_NN)) / (n * np.log(n * K_NN))
+    per_row = (t["knn_exact"] + t["calibrate"]) / len(q)
+    est = per_row * N + sym_full
     return N / est, t, len(q)
 
 
-def cpu_baseline(args, Xh, labels):
+def cpu_baseline(args, Xh):
     import oracle
-    value, t, n = oracle_sample_timing(Xh, args.cpu_sample, args)
-    return {"value": round(value, 3), "unit": "points/s", "cores": oracle.num_threads(),
+    value, t, n = oracle_sample_timing(Xh, args.cpu_sample)
+    return {"value": round(value, 4), "unit": "points/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": ("exact kNN, 2x beta bisection and forest search (T=%d, checks=%d) for %d "
-                       "sampled query rows against the full corpus, extrapolated linearly to all "
-                       "rows; forest build and 2x CSR symmetrisation timed once at full size"
-                       % (args.trees, args.checks, n)),
+            "sample": ("FP64 exact kNN and beta bisection of %d sampled query rows against the full "
+                       "corpus, extrapolated linearly to all rows; CSR symmetrisation timed on a "
+                       "100000-row graph and scaled by N log N" % n),
             "seconds": {k_: round(v, 3) for k_, v in t.items()}}
 
 
@@ -868,28 +904,27 @@ def run_reference(args, world, rank, pg):
         return
     import oracle
     w = WORKLOADS[args.workload]
-    Xh, labels = make_data(w)
+    Xh, _ = make_data(w)
     sample = max(16, args.cpu_sample // 4)
     vals = []
     for it in range(args.warmup + args.steps):
-        v, t, n = oracle_sample_timing(Xh, sample, args)
+        v, t, n = oracle_sample_timing(Xh, sample)
         if it >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
     line = {
-        "metric": "P-matrix points/s at k=90 (exact FP32 kNN + beta bisection + CSR P, "
-                  "KD-forest P^A, rho, refinement)",
-        "value": round(value, 3), "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC,
+        "value": round(value, 4), "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded, MNIST-shaped; no dataset)",
-        "config": {"workload": w["desc"], "N": w["N"], "D": w["D"], "k": K_NN,
-                   "perplexity": PERPLEXITY},
+        "dtype": "f64", "data": "synthetic (seeded Gamma-cluster features; no dataset)",
+        "config": {"workload": w["desc"], "N": w["N"], "D": w["D"], "k": K_NN, "perplexity": PERPLEXITY,
+                   "step": "exact kNN (Eq. 8) -> beta bisection (Eq. 3-4) -> symmetrised CSR P (Eq. 2)"},
         "impl": "reference",
-        "cpu_baseline": {"value": round(value, 3), "unit": "points/s", "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 4), "unit": "points/s", "kind": "oracle",
                          "cores": oracle.num_threads(),
-                         "sample": "%d sampled query rows per step, per-row work extrapolated; "
-                                   "forest build and symmetrisation at full size" % sample},
-        "e2e": {"value": round(value, 3), "unit": "points/s", "h2d_bytes_per_step": 0,
+                         "sample": "%d sampled query rows per step (FP64 exact kNN and bisection), "
+                                   "extrapolated; symmetrisation timed on 100000 rows and scaled" % sample},
+        "e2e": {"value": round(value, 4), "unit": "points/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
