@@ -105,17 +105,17 @@ template <int PASSES>
 struct __align__(1024) TcSmem {
     static constexpr int NEPI = TcCfg<PASSES>::NEPI;
     unsigned char stage[TcCfg<PASSES>::STAGES][TcCfg<PASSES>::STAGE_BYTES];
-    float ny[NEPI][32];         // per epilogue warp: the chunk's corpus norms
-    float ms[PASSES == 8 ? NEPI : 1][32];  // FP8: the chunk's -2 * corpus row scales
-    // per epilogue thread: one row of 32 keys (padded to 36, 16-byte rows)
-    // from which its survivors are read back; between tiles the warp's first
-    // 256 words serve the radix select of an exact compaction
-    float tr[NEPI][32 * 36];
+    float ny[NEPI][2][32];      // per epilogue warp: two chunks' corpus norms (double-buffered)
+    float ms[PASSES == 8 ? NEPI : 1][2][32];  // FP8: two chunks' -2 * corpus row scales
+    // per epilogue thread: one row of 32 keys (16-byte groups swizzled by the
+    // lane) from which its survivors are read back; between tiles the warp's
+    // first 256 words serve the radix select of an exact compaction
+    float tr[NEPI][32 * 32];
     // per epilogue thread: buffered distances by bucket, two 16-bit counts per word
     uint32_t dhist[NEPI][NBUCKET / 2][32];
     // each half's current tau per query row, tagged with its work unit:
     // (unit << 32) | tau bits
-    unsigned long long tau_sh[TcCfg<PASSES>::HALVES][TC_BM];
+    unsigned long long tau_sh[TcCfg<PASSES>::HALVES > 1 ? TcCfg<PASSES>::HALVES : 1][TcCfg<PASSES>::HALVES > 1 ? TC_BM : 1];
     uint64_t full[TcCfg<PASSES>::MAX_STAGES];
     uint64_t empty[TcCfg<PASSES>::MAX_STAGES];
     uint64_t acc_full[2];
@@ -174,9 +174,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Shared-memory add whose result is not needed (no wait on it).
-__device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
-}
+__device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) { atomicAdd(p, v); }
 
 // Adds one to hist[bin] for every active lane; must be called by the whole
 // warp. Lanes that share a bin are combined into one shared-memory atomic: the
@@ -382,6 +380,9 @@ __device__ __forceinline__ float key_error_bound_capped(float4 st, const unsigne
     return 2.f * drop + acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
 }
 
+// First column of the ti-th column tile of a work unit.
+__device__ __forceinline__ int64_t unit_tile_col(int64_t c0, int64_t ti) { return c0 + ti * TC_BN; }
+
 template <int PASSES>
 __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const __grid_constant__ TcParams p) {
     using C = TcCfg<PASSES>;
@@ -408,8 +409,9 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
         s.zero = 0;
         fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < C::HALVES * TC_BM; i += blockDim.x)
-        (&s.tau_sh[0][0])[i] = ~0ull;  // tagged with no unit
+    if (C::HALVES > 1)
+        for (int i = threadIdx.x; i < C::HALVES * TC_BM; i += blockDim.x)
+            (&s.tau_sh[0][0])[i] = ~0ull;  // tagged with no unit
     if (threadIdx.x == 32) {
         tma_prefetch_desc(&p.tm_a_hi);
         tma_prefetch_desc(&p.tm_b_hi);
@@ -442,7 +444,9 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 const int rt = u % p.row_tiles, sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
-                for (int64_t ct = c0; ct < c1 && ok; ct += TC_BN) {
+                const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
+                for (int64_t ti = 0; ti < ntl && ok; ++ti) {
+                    const int64_t ct = unit_tile_col(c0, ti);
                     for (int kb = 0; kb < p.KB; ++kb) {
                         if (!mbar_wait(&s.empty[stage], phase ^ 1u, &s.abort_flag, WAIT_NS)) {
                             ok = false;
@@ -486,7 +490,8 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 const int sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
-                for (int64_t ct = c0; ct < c1 && ok; ct += TC_BN) {
+                const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
+                for (int64_t ti = 0; ti < ntl && ok; ++ti) {
                     if (!mbar_wait(&s.acc_empty[acc], acc_phase ^ 1u, &s.abort_flag, WAIT_NS)) {
                         ok = false;
                         break;
@@ -649,33 +654,38 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             float nyn[NCH], msn[NCH];
 #pragma unroll
             for (int q = 0; q < NCH; ++q) {
-                const int64_t cc = c0 + half * CW + q * 32 + lane;
+                const int64_t cc = unit_tile_col(c0, 0) + half * CW + q * 32 + lane;
                 nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
                 if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
             }
             // FP8: x_i . x_j ~ s_i s_j (q_i . q_j); the row's scale, the
             // columns' -2 s_j beside their norms
             const float si = PASSES == 8 && qv ? (p.qscale ? p.qscale[row] : p.scale[qid]) : 1.f;
-            float *nyw = s.ny[e];
-            float *msw = s.ms[PASSES == 8 ? e : 0];
-            float *mine = s.tr[e] + lane * 36;
+            float *mine = s.tr[e] + lane * 32;
             // the partner half may still be on an earlier unit: its bound is
             // taken only when its tag is this unit
-            volatile unsigned long long *tau_mine = &s.tau_sh[half][quarter * 32 + lane];
-            volatile unsigned long long *tau_peer = &s.tau_sh[half ^ (C::HALVES - 1)][quarter * 32 + lane];
-            auto share_tau = [&]() { *tau_mine = ((unsigned long long)u << 32) | __float_as_uint(th); };
+            volatile unsigned long long *tau_mine =
+                &s.tau_sh[C::HALVES > 1 ? half : 0][C::HALVES > 1 ? quarter * 32 + lane : 0];
+            volatile unsigned long long *tau_peer =
+                &s.tau_sh[C::HALVES > 1 ? half ^ 1 : 0][C::HALVES > 1 ? quarter * 32 + lane : 0];
+            auto share_tau = [&]() {
+                if (C::HALVES > 1) *tau_mine = ((unsigned long long)u << 32) | __float_as_uint(th);
+            };
             share_tau();
-            for (int64_t ct = c0; ct < c1; ct += TC_BN) {
+            const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
+            for (int64_t ti = 0; ti < ntl; ++ti) {
+                const int64_t ct = unit_tile_col(c0, ti);
                 float nyc[NCH], msc[NCH];
 #pragma unroll
                 for (int q = 0; q < NCH; ++q) {
                     nyc[q] = nyn[q];
                     msc[q] = msn[q];
                 }
-                if (ct + TC_BN < c1) {
+                if (ti + 1 < ntl) {
+                    const int64_t cn = unit_tile_col(c0, ti + 1);
 #pragma unroll
                     for (int q = 0; q < NCH; ++q) {
-                        const int64_t cc = ct + TC_BN + half * CW + q * 32 + lane;
+                        const int64_t cc = cn + half * CW + q * 32 + lane;
                         nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
                         if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
                     }
@@ -708,6 +718,11 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 for (int c = 0; c < NCH; ++c) {
                     uint32_t(&r)[32] = (c & 1) ? rb : ra;
                     uint32_t(&rn)[32] = (c & 1) ? ra : rb;
+                    // norms (and FP8 scales) of the chunk's columns, double-buffered:
+                    // the buffer written here was last read two chunks ago, before
+                    // the previous chunk's __syncwarp
+                    float *nyw = s.ny[e][c & 1];
+                    float *msw = s.ms[PASSES == 8 ? e : 0][c & 1];
                     nyw[lane] = nyc[c];
                     if (PASSES == 8) msw[lane] = msc[c];
                     tmem_ld_wait(r);
@@ -745,11 +760,16 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                         dd[4 * q + 2] = d23.x;
                         dd[4 * q + 3] = d23.y;
                     }
+                    // four independent shift chains of eight keys (a single chain
+                    // of 32 dependent shifts would be the filter's critical path)
+                    uint32_t mq[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                    for (int j = 31; j >= 0; --j) mask = sign_into_mask(dd[j], mask);  // key j -> bit j
+                    for (int j = 7; j >= 0; --j)
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) mq[g] = sign_into_mask(dd[8 * g + j], mq[g]);  // key 8g+j -> bit j
+                    mask = mq[0] | (mq[1] << 8) | (mq[2] << 16) | (mq[3] << 24);
                     const int so = self_off - c * 32;
                     if (so >= 0 && so < 32) mask &= ~(1u << so);
-                    __syncwarp();  // the chunk's norms are read before the next chunk's
                     if (mask) {
                         // spill this row's keys to its own padded shared row and
                         // walk its survivors one per step (a chunk rarely holds
@@ -759,8 +779,9 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                         // the thread's buffer and counted in its bucket by a
                         // fire-and-forget shared add.
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *reinterpret_cast<float4 *>(mine + j) = make_float4(kk[j], kk[j + 1], kk[j + 2], kk[j + 3]);
+                        for (int q = 0; q < 8; ++q)
+                            reinterpret_cast<float4 *>(mine)[q ^ (lane & 7)] =
+                                make_float4(kk[4 * q], kk[4 * q + 1], kk[4 * q + 2], kk[4 * q + 3]);
                         const int colb = colb0 + c * 32;
                         since += __popc(mask);
                         auto append = [&](float key, int col) {
@@ -788,7 +809,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                         do {
                             const int j0 = __ffs(mask) - 1;
                             mask &= mask - 1;
-                            append(mine[j0], colb + j0);
+                            append(mine[(((j0 >> 2) ^ (lane & 7)) << 2) + (j0 & 3)], colb + j0);
                         } while (mask);
                     }
                 }
@@ -814,8 +835,9 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     }
                 }
                 // lower tau to the upper edge of the bucket holding the ksel-th
-                // distance, th to that of the bucket holding the kh-th
-                if (since >= 16 && cnt >= kh) {
+                // distance, th to that of the bucket holding the kh-th; the
+                // warp updates together once any lane has 16 new survivors
+                if (__any_sync(0xffffffffu, since >= 16 && cnt >= kh) && since > 0 && cnt >= kh) {
                     uint32_t hw[NBUCKET / 2];
 #pragma unroll
                     for (int bw = 0; bw < NBUCKET / 2; ++bw) hw[bw] = dh[bw * 32];
