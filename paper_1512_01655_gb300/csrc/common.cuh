@@ -118,6 +118,79 @@ __device__ __forceinline__ void warp_argmax_pair(float &d, int &j, int &pos) {
     }
 }
 
+// Near ties of a sorted neighbour list settled in FP64 (Eq. 8's order on
+// exact distances): d[0, n) ascending with their points j[0, n) (FP32 direct
+// differences, each within (D + 8) 2^-24 of its value; entries of infinite
+// distance are padding and their j is not read). Runs of neighbours
+// whose FP32 gaps are within twice that bound, among the first k + 1, are
+// recomputed as FP64 sums of squared differences of the query row xq and X's
+// rows and put in (FP64 distance, index) order, their distances replaced by
+// the FP64 values rounded to FP32. Outside such runs the FP32 order is the
+// exact one. At most TIE_MAX members are recomputed (the rest keep the FP32
+// order). Warp-cooperative; dm/mp are TIE_MAX doubles and ints of the warp's
+// shared memory.
+constexpr int TIE_MAX = 64;
+__device__ __forceinline__ void fp64_near_ties(float *d, int *j, int n, int k, const float *__restrict__ xq,
+                                               const float *__restrict__ X, int D, double *dm, int *mp,
+                                               int lane) {
+    const int m = n < k + 1 ? n : k + 1;
+    const float band = 2.f * (float)(D + 8) * 0x1p-24f;
+    int nm = 0;
+    for (int t0 = 0; t0 < m; t0 += 32) {
+        const int t = t0 + lane;
+        bool tie_prev = false, tie_next = false;
+        // entries of infinite distance (a list's padding) are never members
+        if (t < m && d[t] < INFINITY) {
+            const float dt = d[t];
+            if (t > 0) tie_prev = dt - d[t - 1] <= band * dt;
+            if (t + 1 < m && d[t + 1] < INFINITY) tie_next = d[t + 1] - dt <= band * d[t + 1];
+        }
+        const bool mem = t < m && (tie_prev || tie_next);
+        const unsigned mm = __ballot_sync(0xffffffffu, mem);
+        const int pos = nm + __popc(mm & ((1u << lane) - 1u));
+        if (mem && pos < TIE_MAX) mp[pos] = t;
+        nm += __popc(mm);
+    }
+    if (nm == 0) return;
+    if (nm > TIE_MAX) nm = TIE_MAX;
+    __syncwarp();
+    for (int i = 0; i < nm; ++i) {
+        const float *xc = X + (int64_t)j[mp[i]] * D;
+        double s = 0.0;
+        for (int c = lane; c < D; c += 32) {
+            const double df = (double)xq[c] - (double)xc[c];
+            s = fma(df, df, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) dm[i] = s;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // each run of consecutive members: insertion sort by (FP64 distance, index)
+        int a = 0;
+        while (a < nm) {
+            int b = a + 1;
+            while (b < nm && mp[b] == mp[b - 1] + 1 && d[mp[b]] - d[mp[b - 1]] <= band * d[mp[b]]) ++b;
+            for (int x = a + 1; x < b; ++x) {
+                const double kd = dm[x];
+                const int kj = j[mp[x]];
+                int y = x - 1;
+                while (y >= a && (dm[y] > kd || (dm[y] == kd && j[mp[y]] > kj))) {
+                    dm[y + 1] = dm[y];
+                    j[mp[y + 1]] = j[mp[y]];
+                    --y;
+                }
+                dm[y + 1] = kd;
+                j[mp[y + 1]] = kj;
+            }
+            for (int x = a; x < b; ++x) d[mp[x]] = (float)dm[x];
+            a = b;
+        }
+    }
+    __syncwarp();
+}
+
 // Order-preserving map of a float to uint32 (-0 folded onto +0, so that the
 // ordering of values equals IEEE comparison order; inputs are finite).
 __device__ __forceinline__ uint32_t float_key(float f) {

@@ -22,6 +22,9 @@ constexpr int BF_QB = 32;       // queries per CTA
 constexpr int BF_CB = 64;       // corpus points per tile
 constexpr int BF_DC = 32;       // dimensions per slice
 constexpr int BF_THREADS = 256;
+// after the tiles, each warp's FP64 near-tie scratch lives in the tile buffers
+static_assert(BF_CB * (BF_DC + 1) * 4 >= (BF_THREADS / 32) * TIE_MAX * 8, "near-tie distances fit the tile buffer");
+static_assert(BF_QB * (BF_CB + 1) * 4 >= (BF_THREADS / 32) * TIE_MAX * 4, "near-tie positions fit the tile buffer");
 
 // Work item s (0 <= s < nq, or < *rows_count when rows_list is given) is output
 // row r = rows_list ? rows_list[s] : s, whose query point is qlist ? qlist[r] : r
@@ -50,6 +53,9 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n_items = rows_count ? (int64_t)*rows_count : nq;
+    // the list keeps the (k+1)-th nearest too where it fits, so that a near tie
+    // across the k-th place is settled in FP64
+    const int kl = k + 1 <= KCAP ? k + 1 : k;
     for (int64_t q0 = (int64_t)blockIdx.x * BF_QB; q0 < n_items; q0 += (int64_t)gridDim.x * BF_QB) {
     if (tid < BF_QB) {
         const int64_t s = q0 + tid;
@@ -130,7 +136,7 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
                     __syncwarp();
                     float bd = -INFINITY;
                     int bj = INT_MIN, bp = 0;
-                    for (int s = lane; s < k; s += 32) {
+                    for (int s = lane; s < kl; s += 32) {
                         float sd = td[r * KCAP + s];
                         int sj = tj[r * KCAP + s];
                         if (pair_less(bd, bj, sd, sj)) {
@@ -154,10 +160,15 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
         __syncthreads();
     }
 
+    // the tile buffers are free now: each warp's FP64 scratch for the near ties
+    double *dm = reinterpret_cast<double *>(Cs) + warp * TIE_MAX;
+    int *mp = reinterpret_cast<int *>(Dt) + warp * TIE_MAX;
     for (int r = warp * 4; r < warp * 4 + 4; ++r) {
         const int64_t o = orow[r];
         if (o < 0) continue;
         warp_bitonic_sort_smem(td + r * KCAP, tj + r * KCAP, KCAP, lane);
+        if (qid[r] >= 0)
+            fp64_near_ties(td + r * KCAP, tj + r * KCAP, kl, k, QX + (int64_t)qid[r] * D, X, D, dm, mp, lane);
         for (int t = lane; t < k; t += 32) {
             idx_out[o * k + t] = tj[r * KCAP + t];
             d2_out[o * k + t] = td[r * KCAP + t];

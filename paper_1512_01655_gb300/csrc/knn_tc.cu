@@ -950,7 +950,9 @@ __device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st
 // brute-force kernel. Otherwise (approximate modes): the SEL = ksel best keys
 // re-ranked in FP32 and the k best of them kept, without a certificate.
 // p.mst keys are staged per row, p.rc candidates re-ranked at most.
-size_t merge_smem_bytes(int rc, int mst) { return (size_t)MERGE_WARPS * (256 * 4 + (size_t)mst * 8 + (size_t)rc * 8); }
+size_t merge_smem_bytes(int rc, int mst) {
+    return (size_t)MERGE_WARPS * (256 * 4 + (size_t)mst * 8 + (size_t)rc * 8 + TIE_MAX * 12);
+}
 
 template <bool CERT>
 __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergeParams p) {
@@ -962,6 +964,9 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
     int *sj = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 4)) + w * MST;
     float *rdw = reinterpret_cast<float *>(mg_smem + MERGE_WARPS * (1024 + MST * 8)) + w * RC;
     int *rjw = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 4)) + w * RC;
+    double *dmw = reinterpret_cast<double *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 8)) + w * TIE_MAX;
+    int *mpw = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 8 + TIE_MAX * 8)) +
+               w * TIE_MAX;
     const int sel = CERT ? p.k : p.ksel;  // rank of the key that bounds the re-rank set
     const int64_t row = (int64_t)blockIdx.x * MERGE_WARPS + w;
     if (row >= p.Q) return;
@@ -1084,105 +1089,37 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
         const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (int64_t)qid * p.D;
         const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
                           (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
-        // rows of at most 256 values (float4-aligned): eight lanes per
-        // candidate, eight candidates in flight per warp, the query's part in
-        // registers; three shuffles reduce a candidate's eight partial sums
-        const bool g8 = vec4 && p.D <= 256;
-        auto rerank_g8 = [&](int from, int to) {
-            const int g = lane >> 3, gl = lane & 7, nv = p.D >> 2;
-            const float4 *q4 = reinterpret_cast<const float4 *>(xq);
-            const float4 *X4 = reinterpret_cast<const float4 *>(p.X);
-            float4 qv[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) qv[j] = gl + 8 * j < nv ? q4[gl + 8 * j] : make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int t0 = from; t0 < to; t0 += 8) {
-                const int ta = t0 + g, tb = t0 + 4 + g;
-                const float4 *xa = ta < to ? X4 + (int64_t)rjw[ta] * nv : nullptr;
-                const float4 *xb = tb < to ? X4 + (int64_t)rjw[tb] * nv : nullptr;
-                float4 va[8], vb[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const bool in = gl + 8 * j < nv;
-                    va[j] = in && xa ? xa[gl + 8 * j] : qv[j];
-                    vb[j] = in && xb ? xb[gl + 8 * j] : qv[j];
-                }
-                float sa = 0.f, sb = 0.f;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float df = qv[j].x - va[j].x;
-                    sa = fmaf(df, df, sa);
-                    df = qv[j].y - va[j].y;
-                    sa = fmaf(df, df, sa);
-                    df = qv[j].z - va[j].z;
-                    sa = fmaf(df, df, sa);
-                    df = qv[j].w - va[j].w;
-                    sa = fmaf(df, df, sa);
-                    df = qv[j].x - vb[j].x;
-                    sb = fmaf(df, df, sb);
-                    df = qv[j].y - vb[j].y;
-                    sb = fmaf(df, df, sb);
-                    df = qv[j].z - vb[j].z;
-                    sb = fmaf(df, df, sb);
-                    df = qv[j].w - vb[j].w;
-                    sb = fmaf(df, df, sb);
-                }
-#pragma unroll
-                for (int o = 1; o < 8; o <<= 1) {
-                    sa += __shfl_xor_sync(0xffffffffu, sa, o);
-                    sb += __shfl_xor_sync(0xffffffffu, sb, o);
-                }
-                if (gl == 0) {
-                    if (ta < to) rdw[ta] = sa;
-                    if (tb < to) rdw[tb] = sb;
-                }
-            }
-        };
+        // exact FP32 distances of rjw[from, to), one candidate per lane, each a
+        // sequential FMA chain over the dimensions in order: the same
+        // operations as the brute-force kernel's, so a row's distances do not
+        // depend on which kernel produced it
         auto rerank = [&](int from, int to) {
-            if (g8) {
-                rerank_g8(from, to);
-                return;
-            }
-            for (int t0 = from; t0 < to; t0 += 4) {
-                const float *xc[4];
-                float a[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    xc[u] = t0 + u < to ? p.X + (int64_t)rjw[t0 + u] * p.D : nullptr;
-                    a[u] = 0.f;
-                }
-                if (vec4) {
-                    const float4 *q4 = reinterpret_cast<const float4 *>(xq);
-                    for (int d = lane; d < (p.D >> 2); d += 32) {
-                        const float4 qv = q4[d];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (!xc[u]) continue;
-                            const float4 cv = reinterpret_cast<const float4 *>(xc[u])[d];
+            for (int t0 = from; t0 < to; t0 += 32) {
+                const int t = t0 + lane;
+                if (t < to) {
+                    const float *xc = p.X + (int64_t)rjw[t] * p.D;
+                    float a = 0.f;
+                    if (vec4) {
+                        const float4 *q4 = reinterpret_cast<const float4 *>(xq);
+                        const float4 *c4 = reinterpret_cast<const float4 *>(xc);
+                        for (int d = 0; d < (p.D >> 2); ++d) {
+                            const float4 qv = q4[d], cv = c4[d];
                             float df = qv.x - cv.x;
-                            a[u] = fmaf(df, df, a[u]);
+                            a = fmaf(df, df, a);
                             df = qv.y - cv.y;
-                            a[u] = fmaf(df, df, a[u]);
+                            a = fmaf(df, df, a);
                             df = qv.z - cv.z;
-                            a[u] = fmaf(df, df, a[u]);
+                            a = fmaf(df, df, a);
                             df = qv.w - cv.w;
-                            a[u] = fmaf(df, df, a[u]);
+                            a = fmaf(df, df, a);
+                        }
+                    } else {
+                        for (int d = 0; d < p.D; ++d) {
+                            const float df = xq[d] - xc[d];
+                            a = fmaf(df, df, a);
                         }
                     }
-                } else {
-                    for (int d = lane; d < p.D; d += 32) {
-                        const float qv = xq[d];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (!xc[u]) continue;
-                            const float df = qv - xc[u][d];
-                            a[u] = fmaf(df, df, a[u]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float r = warp_sum(a[u]);
-                    if (lane == 0 && xc[u]) rdw[t0 + u] = r;
+                    rdw[t] = a;
                 }
             }
         };
@@ -1222,6 +1159,8 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
             }
             __syncwarp();
             warp_bitonic_sort_smem(rdw, rjw, ns2, lane);
+            // near ties among the first k + 1 ordered as the exact distances are
+            fp64_near_ties(rdw, rjw, nr, p.k, xq, p.X, p.D, dmw, mpw, lane);
             if (CERT) {
                 const float dk = rdw[p.k - 1];
                 const float nx = cross ? p.qnrm[row] : p.nrm[qid];
@@ -1281,15 +1220,16 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) radius_merge_kernel(MergePar
     }
     __syncwarp();
     const float *xq = p.Xq + (int64_t)row * p.D;
-    for (int t = 0; t < nr; ++t) {
+    // one candidate per lane, a sequential FMA chain over the dimensions (the
+    // brute-force kernel's operations)
+    for (int t = lane; t < nr; t += 32) {
         const float *xc = p.X + (int64_t)rjw[t] * p.D;
         float a = 0.f;
-        for (int d = lane; d < p.D; d += 32) {
+        for (int d = 0; d < p.D; ++d) {
             const float df = xq[d] - xc[d];
             a = fmaf(df, df, a);
         }
-        a = warp_sum(a);
-        if (lane == 0) rdw[t] = a;
+        rdw[t] = a;
     }
     __syncwarp();
     const float rad = radius[row];
@@ -1649,6 +1589,8 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         m.rc = RCAP;
         m.mst = MSTAGE;
         const size_t ms = merge_smem_bytes(m.rc, m.mst);
+        e = cudaFuncSetAttribute(knn_merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
+        if (e != cudaSuccess) return cuda_error(e, "knn_tc_merge attribute");
         ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<true>, ceil_div(Q, MERGE_WARPS),
                                 MERGE_WARPS * 32, ms, stream, m));
     }

@@ -131,3 +131,39 @@ def test_results_are_true_distances_of_evaluated_points(oracle_mod):
     assert np.array_equal(ref, d2)
     assert np.all(np.diff(d2, axis=1) >= 0)
     assert not np.any(idx == np.arange(300)[:, None])
+
+
+def test_golden_two_identical_trees_bounded_queue(oracle_mod):
+    """Two identical trees and a queue of capacity 4 (hand-derived): pins which
+    entry a full queue drops, the (tree, node) order of equal keys, and that a
+    point found in the second tree is not evaluated again."""
+    g = golden("forest_1d.json")
+    t = g["two_identical_trees"]
+    X = np.array(g["x"], np.float32)[:, None]
+    f = oracle_mod.forest_build(X, trees=t["trees"], top_var_dims=5, leaf_size=1, seed=3)
+    for case in t["cases"]:
+        idx, d2, ev = oracle_mod.forest_query(X, f, case["k"], case["checks"], qcap=case["queue_cap"],
+                                              queries=[g["query"]])
+        assert idx[0].tolist() == case["idx"], case
+        assert d2[0].tolist() == case["d2"], case
+        assert ev[0] == case["evaluated"], case
+
+
+def test_golden_two_distinct_trees(oracle_mod):
+    """Two different trees in 2-D (hand-derived): the split choice among the
+    top-V dimensions, the initial descents of both trees before the first pop,
+    the cross-tree order of equal keys, evictions from a queue of capacity 4 and
+    the completion of a queue that runs dry."""
+    g = golden("forest_2tree.json")
+    X = np.array(g["points"], np.float32)
+    f = oracle_mod.forest_build(X, trees=g["trees"], top_var_dims=g["top_var_dims"], leaf_size=1,
+                                seed=g["seed"])
+    assert f["split_dim"].tolist() == g["split_dim"]
+    assert f["split_val"].tolist() == g["split_val"]
+    assert f["perm"].tolist() == g["perm"]
+    for case in g["cases"]:
+        idx, d2, ev = oracle_mod.forest_query(X, f, case["k"], case["checks"], qcap=case["queue_cap"],
+                                              queries=[g["query"]])
+        assert idx[0].tolist() == case["idx"], case
+        assert d2[0].tolist() == case["d2"], case
+        assert ev[0] == case["evaluated"], case
