@@ -459,6 +459,19 @@ atsne_status atsne_forest_query(const float *X, int64_t N, int32_t D, const void
  * (ATSNE_OK, ATSNE_EINVAL for non-finite or malformed input, ATSNE_ETIMEOUT). */
 atsne_status atsne_check(void *stream);
 
+/*
+ * Failure detection of the tensor-core kNN (the paper has no counterpart):
+ * every wait of its copy -> MMA -> epilogue pipeline is bounded. A wait that
+ * runs out makes the kernel stop issuing work, let its issued copies and MMAs
+ * complete, release its tensor memory and raise the device status, which
+ * atsne_check reports as ATSNE_ETIMEOUT; that call's results are then
+ * unspecified and the library stays usable. This sets the limit of those
+ * waits for later calls (process-wide), in nanoseconds; 0 restores the
+ * default of one second. A very short limit makes a wait run out on purpose
+ * (the timeout path's test). Always ATSNE_OK.
+ */
+atsne_status atsne_set_wait_limit(uint64_t ns);
+
 /* Message of the last error on this thread ("" if none). */
 const char *atsne_last_error(void);
 

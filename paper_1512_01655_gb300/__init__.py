@@ -28,7 +28,7 @@ EXPORTED = (
     "atsne_knn_rows",
     "atsne_merge_neighbors", "atsne_commit_rows", "atsne_delete_rows", "atsne_tune_knn", "atsne_row_dmax",
     "atsne_tune_clear", "atsne_forest_buckets_bytes", "atsne_forest_insert", "atsne_forest_delete",
-    "atsne_forest_query_buckets",
+    "atsne_forest_query_buckets", "atsne_set_wait_limit",
 )
 REFINE_NOALLOC_MAX_ROWS, REFINE_NOALLOC_MAX_K = 2048, 128
 
@@ -113,6 +113,7 @@ def lib():
         L.atsne_forest_query.argtypes = [_vp, _i64, _i32, _vp, _vp, _i64, _i32,
                                          ctypes.POINTER(KnnOpts), _vp, _vp, _vp, _vp, _sz, _vp]
         L.atsne_check.argtypes = [_vp]
+        L.atsne_set_wait_limit.argtypes = [ctypes.c_uint64]
         L.atsne_last_error.restype = ctypes.c_char_p
         L.atsne_last_error.argtypes = []
         L.atsne_launch_count.restype = ctypes.c_int64
@@ -540,6 +541,11 @@ def atsne_forest_query(X, forest, k, checks=None, queries=None, queue_cap=None, 
 def atsne_check(stream=None):
     """Synchronise and raise if a kernel flagged bad input or an expired wait."""
     _raise(lib().atsne_check(_stream(stream)))
+
+
+def set_wait_limit(ns=0):
+    """Limit (ns) of the tensor kNN's pipeline waits; 0 restores the default."""
+    _raise(lib().atsne_set_wait_limit(int(ns)))
 
 
 def launch_count():

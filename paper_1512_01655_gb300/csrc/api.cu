@@ -937,6 +937,11 @@ atsne_status atsne_check(void *stream) {
     }
 }
 
+atsne_status atsne_set_wait_limit(uint64_t ns) {
+    set_pipeline_wait_ns(ns);
+    return ATSNE_OK;
+}
+
 atsne_status atsne_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (on && g_prof_pool.empty()) {

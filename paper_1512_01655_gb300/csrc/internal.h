@@ -38,6 +38,9 @@ struct TcWs {
     float *qnrm = nullptr, *qstats = nullptr;   // queries from another array: norms, error stats
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
 };
+// Limit of the tensor kernel's pipeline waits (process-wide; default 1 s).
+uint64_t pipeline_wait_ns();
+void set_pipeline_wait_ns(uint64_t ns);
 // splits > 0 forces the column split count; else the one atsne_tune_knn
 // recorded for this shape, else the rule.
 TcPlan tc_plan(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int splits = 0);

@@ -47,6 +47,7 @@
 #include <limits.h>
 #include <math.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -149,6 +150,7 @@ struct TcParams {
     int4 *meta;            // [Q][splits * halves]: count, tau bits, overflow
     unsigned *row_hist;    // [Q][GH_BUCKETS]: buffered distances of all splits by bucket (splits > 1)
     int *status;
+    uint64_t wait_ns;      // limit of each pipeline wait (the drains of issued copies and MMAs keep WAIT_NS)
 };
 
 // Absolute bucket of a squared distance on the thread grid (16 per octave),
@@ -448,7 +450,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 for (int64_t ti = 0; ti < ntl && ok; ++ti) {
                     const int64_t ct = unit_tile_col(c0, ti);
                     for (int kb = 0; kb < p.KB; ++kb) {
-                        if (!mbar_wait(&s.empty[stage], phase ^ 1u, &s.abort_flag, WAIT_NS)) {
+                        if (!mbar_wait(&s.empty[stage], phase ^ 1u, &s.abort_flag, p.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -492,14 +494,14 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
                 const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
                 for (int64_t ti = 0; ti < ntl && ok; ++ti) {
-                    if (!mbar_wait(&s.acc_empty[acc], acc_phase ^ 1u, &s.abort_flag, WAIT_NS)) {
+                    if (!mbar_wait(&s.acc_empty[acc], acc_phase ^ 1u, &s.abort_flag, p.wait_ns)) {
                         ok = false;
                         break;
                     }
                     fence_after_sync();
                     const uint32_t d = tbase + (uint32_t)(acc * TC_BN);
                     for (int kb = 0; kb < p.KB; ++kb) {
-                        if (!mbar_wait(&s.full[stage], phase, &s.abort_flag, WAIT_NS)) {
+                        if (!mbar_wait(&s.full[stage], phase, &s.abort_flag, p.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -690,7 +692,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                         if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
                     }
                 }
-                ok = mbar_wait(&s.acc_full[acc], acc_phase, &s.abort_flag, WAIT_NS);
+                ok = mbar_wait(&s.acc_full[acc], acc_phase, &s.abort_flag, p.wait_ns);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) {
                     if (lane == 0) {
@@ -981,7 +983,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
     float tau_min = INFINITY;
     for (int u = lane; u < S; u += 32) {
         const int4 m = mt[u];
-        total += m.x;
+        total += min(max(m.x, 0), p.cap);
         ovf |= m.z;
         tau_min = fminf(tau_min, __int_as_float(m.y));
     }
@@ -1003,7 +1005,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
         const float slim = tau_min;  // the select needs no key above tau_min
         int ns = 0, nlt = 0;
         for (int u0 = 0; u0 < S; u0 += 32) {
-          const int cu = u0 + lane < S ? mt[u0 + lane].x : 0;  // the counts of 32 splits at once
+          const int cu = u0 + lane < S ? min(max(mt[u0 + lane].x, 0), p.cap) : 0;  // the counts of 32 splits at once
           for (int j = 0; j < 32 && u0 + j < S; ++j) {
             const int c = __shfl_sync(0xffffffffu, cu, j);
             const Cand *b = cb + (size_t)(u0 + j) * p.cap;
@@ -1046,7 +1048,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
             prefix = warp_select_visit(
                 [&](auto fn) {
                     for (int u = 0; u < S; ++u) {
-                        const int c = mt[u].x;
+                        const int c = min(max(mt[u].x, 0), p.cap);
                         const Cand *b = cb + (size_t)u * p.cap;
                         for (int base = 0; base < c; base += 32) {
                             const int i = base + lane;
@@ -1074,7 +1076,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
                 }
             } else {
                 for (int u = 0; u < S; ++u) {
-                    const int c = mt[u].x;
+                    const int c = min(max(mt[u].x, 0), p.cap);
                     const Cand *b = cb + (size_t)u * p.cap;
                     for (int base = 0; base < c; base += 32) {
                         const int i = base + lane;
@@ -1202,7 +1204,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) radius_merge_kernel(MergePar
     int total = 0, ovf = 0;
     for (int u = lane; u < S; u += 32) {
         const int4 m = mt[u];
-        total += m.x;
+        total += min(max(m.x, 0), p.cap);
         ovf |= m.z;
     }
     total = (int)__reduce_add_sync(0xffffffffu, (unsigned)total);
@@ -1213,7 +1215,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) radius_merge_kernel(MergePar
     }
     int nr = 0;
     for (int u = 0; u < S; ++u) {
-        const int c = mt[u].x;
+        const int c = min(max(mt[u].x, 0), p.cap);
         const Cand *b = cb + (size_t)u * p.cap;
         for (int i = lane; i < c; i += 32) rjw[nr + i] = b[i].idx;
         nr += c;
@@ -1312,6 +1314,13 @@ static_assert(sizeof(TcSmem<3>) + 1024 <= 232448, "tensor kNN shared memory abov
 static_assert(sizeof(TcSmem<8>) + 1024 <= 232448, "tensor kNN shared memory above 227 KB");
 
 }  // namespace
+
+namespace {
+std::atomic<uint64_t> g_wait_ns{WAIT_NS};
+}  // namespace
+
+uint64_t pipeline_wait_ns() { return g_wait_ns.load(); }
+void set_pipeline_wait_ns(uint64_t ns) { g_wait_ns.store(ns ? ns : WAIT_NS); }
 
 atsne_status radius_filter_launch(int32_t *idx, float *d2, int64_t rows, int k, const float *radius,
                                   cudaStream_t stream) {
@@ -1441,6 +1450,9 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     if (e == cudaSuccess) e = cudaMemsetAsync(w.flag_count, 0, sizeof(int32_t), stream);
     if (e == cudaSuccess && w.row_hist)
         e = cudaMemsetAsync(w.row_hist, 0, (size_t)Q * GH_BUCKETS * sizeof(unsigned), stream);
+    // a unit that a timed-out kernel never finished reads as an empty buffer
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w.meta, 0, (size_t)Q * pl.splits * pl.halves * sizeof(int4), stream);
     if (e != cudaSuccess) return cuda_error(e, "knn_tc memset");
     const bool fp8 = pl.passes == 8;
     const void *a_hi = w.hi, *a_lo = w.lo;
@@ -1524,6 +1536,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     p.meta = reinterpret_cast<int4 *>(w.meta);
     p.row_hist = w.row_hist;
     p.status = status;
+    p.wait_ns = pipeline_wait_ns();
     const int units = pl.row_tiles * pl.splits;
     const int grid = (int)hmin(units, num_sms());
     if (pl.passes == 3) {
