@@ -101,6 +101,12 @@ def parse():
                    help="forest checks values for the rho sweep (empty to skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=256)
+    p.add_argument("--kernel-case", choices=["knn_tc", "bandwidth"], default=None,
+                   help="run one small case of a kernel for a profiler and exit (no timing line): "
+                        "knn_tc = the exact kNN of every --query-every-th row of the workload against "
+                        "all rows; bandwidth = the exact path on the workload's first --case-rows rows")
+    p.add_argument("--query-every", type=int, default=25)
+    p.add_argument("--case-rows", type=int, default=100_000)
     return p.parse_args()
 
 
@@ -295,7 +301,7 @@ def recorded_traffic(kernel, workload, variant=None):
     return None
 
 
-def bench_serving(at, torch, dev, n_max, seed=5, precision="bf16"):
+def bench_serving(at, torch, dev, n_max, seed=5, precision="bf16", forest_trees=0, checks=1024):
     """Serving (Sec. 5.3.1 insertions, Sec. 4.3 refinements) with continuous
     batching: log-normal D = 50 points in 30 clusters, a corpus growing from
     100000 rows to n_max, the exact kNN in `precision`, 4 stream slots, admission by free
@@ -307,7 +313,10 @@ def bench_serving(at, torch, dev, n_max, seed=5, precision="bf16"):
     (inter-arrival time exponential with mean size / rate). Latency = the
     completion of a request's state commit minus its arrival. Then one step of a
     sliding window on the full corpus (Sec. 5.3.2, Sec. 5.3.1): the oldest
-    `window` rows deleted, `window` new points of the same distribution inserted."""
+    `window` rows deleted, `window` new points of the same distribution inserted.
+    With forest_trees > 0 the server keeps a KD-forest resident and inserted
+    points take their neighbourhoods from a forest search (the paper's
+    approximate insertion); the CSR P is resident in both modes."""
     from paper_1512_01655_gb300 import synth
     from paper_1512_01655_gb300.serve import Request, Server
     window = 50_000
@@ -339,13 +348,15 @@ def bench_serving(at, torch, dev, n_max, seed=5, precision="bf16"):
         return out
 
     sizes = np.array([(p[1] - p[0]) if k == "insert" else len(p) for k, p in seq], np.float64)
-    srv = Server(X[:N0], capacity=n_max, k=K_NN, perplexity=PERPLEXITY, precision=precision, slots=4)
+    kw = dict(capacity=n_max, k=K_NN, perplexity=PERPLEXITY, precision=precision, slots=4,
+              forest_trees=forest_trees, checks=checks)
+    srv = Server(X[:N0], **kw)
     _, closed = srv.run(requests(np.zeros(len(seq))))
     del srv
     torch.cuda.empty_cache()
     rate = 0.7 * closed["points_per_s"]
     arr = np.cumsum(rng.exponential(sizes / rate))
-    srv = Server(X[:N0], capacity=n_max, k=K_NN, perplexity=PERPLEXITY, precision=precision, slots=4)
+    srv = Server(X[:N0], **kw)
     _, opened = srv.run(requests(arr))
     at.atsne_check()
     # one sliding-window step: delete the oldest rows, insert as many new points
@@ -359,6 +370,10 @@ def bench_serving(at, torch, dev, n_max, seed=5, precision="bf16"):
     out = {"workload": "log-normal D=50, 30 clusters; corpus %d -> %d rows; %d requests; %s kNN; "
                        "4 slots" % (N0, srv.N, len(seq), precision),
            "precision": precision,
+           "inserts": ("forest search (T=%d, checks=%d, buckets updated; rho of inserted rows %.4f)"
+                       % (forest_trees, checks, srv.rho_forest)) if forest_trees else "exact kNN",
+           "resident": "X, kNN lists, P_{j|i}, beta, rho, CSR P" + (", KD-forest and its buckets"
+                                                                    if forest_trees else ""),
            "capacity_points_per_s": closed["points_per_s"], "offered_points_per_s": round(rate, 1)}
     out.update(opened)
     out["sliding_window"] = slide
@@ -734,10 +749,11 @@ def run_ours(args, world, rank, local, pg):
         torch.cuda.empty_cache()
     serving = None
     if args.serve_max > 0 and world == 1:
-        serving = bench_serving(at, torch, dev, args.serve_max, precision="fp32")
-        b = bench_serving(at, torch, dev, args.serve_max, precision="bf16")
-        serving["bf16_rerank_certified"] = {kk: b[kk] for kk in ("capacity_points_per_s", "points_per_s",
-                                                       "p50_ms", "p99_ms", "sliding_window")}
+        serving = bench_serving(at, torch, dev, args.serve_max, precision="fp32", forest_trees=args.trees,
+                                checks=args.checks)
+        b = bench_serving(at, torch, dev, args.serve_max, precision="fp32")
+        serving["exact_inserts"] = {kk: b[kk] for kk in ("inserts", "capacity_points_per_s", "points_per_s",
+                                                         "p50_ms", "p99_ms", "insert", "refine", "sliding_window")}
     refine_batch = None
     if args.refine_batch_reps > 0:
         refine_batch = bench_refine_batch(at, torch, dev, stream, args.refine_batch_reps, peaks)
@@ -930,8 +946,38 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line))
 
 
+def kernel_case(args):
+    """A small case of one kernel for a profiler capture: a warm-up call and
+    one more, in the headline precision."""
+    import torch
+    import paper_1512_01655_gb300 as at
+    w = WORKLOADS[args.workload]
+    Xh, _ = make_data(w)
+    dev = torch.device("cuda", 0)
+    if args.kernel_case == "knn_tc":
+        X = torch.from_numpy(Xh).to(dev)
+        q = torch.arange(0, X.shape[0], args.query_every, dtype=torch.int32, device=dev)
+        o = at.knn_opts(method="exact", precision=args.precision)
+        for _ in range(2):
+            at.atsne_knn(X, K_NN, queries=q, opts=o)
+        what = "%d query rows" % q.numel()
+    else:
+        X = torch.from_numpy(np.ascontiguousarray(Xh[:args.case_rows])).to(dev)
+        o = at.knn_opts(method="exact", precision=args.precision)
+        for _ in range(2):
+            idx, d2 = at.atsne_knn(X, K_NN, opts=o)
+            P, _ = at.atsne_calibrate_P(d2, PERPLEXITY)
+            at.atsne_symmetrize(idx, P, trim=False)
+        what = "%d rows" % X.shape[0]
+    at.atsne_check()
+    print("kernel case %s: %s, %s, %s" % (args.kernel_case, w["desc"], what, args.precision))
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        kernel_case(args)
+        return
     world, rank, local, pg = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank, pg)

@@ -241,18 +241,25 @@ def atsne_calibrate_P(d2, perplexity, tol=0.0, max_iter=0, stream=None, P_out=No
     return P, beta
 
 
-def atsne_symmetrize(idx, P_cond, stream=None, trim=True):
+def atsne_symmetrize(idx, P_cond, stream=None, trim=True, out=None, workspace=None):
     """Joint P as CSR (row_ptr int64, col int32, val float32) -- Eq. 2 / Eq. 10.
-    With trim=True col/val are cut to nnz (one device-to-host read of nnz)."""
+    With trim=True col/val are cut to nnz (one device-to-host read of nnz).
+    out: (row_ptr [>= N+1], col [>= 2Nk], val [>= 2Nk], nnz [1]) to write into;
+    workspace: a uint8 device buffer of at least the symmetrisation's workspace."""
     _dev(idx, torch.int32, "idx")
     _dev(P_cond, torch.float32, "P_cond")
     N, k = idx.shape
     dev = idx.device
-    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
-    col = torch.empty(2 * N * k, dtype=torch.int32, device=dev)
-    val = torch.empty(2 * N * k, dtype=torch.float32, device=dev)
-    nnz = torch.empty(1, dtype=torch.int64, device=dev)
-    ws = _workspace(workspace_bytes(OP_SYMMETRIZE, N, 0, k), dev)
+    if out is not None:
+        row_ptr, col, val, nnz = out
+        if row_ptr.numel() < N + 1 or col.numel() < 2 * N * k or val.numel() < 2 * N * k:
+            raise ValueError("symmetrize: output buffers too small")
+    else:
+        row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(2 * N * k, dtype=torch.int32, device=dev)
+        val = torch.empty(2 * N * k, dtype=torch.float32, device=dev)
+        nnz = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = workspace if workspace is not None else _workspace(workspace_bytes(OP_SYMMETRIZE, N, 0, k), dev)
     _raise(lib().atsne_symmetrize(_p(idx), _p(P_cond), N, k, _p(row_ptr), _p(col), _p(val),
                                   _p(nnz), _p(ws), ws.numel(), _stream(stream)))
     if trim:

@@ -29,6 +29,20 @@ Delete of R listed rows (Sec. 5.3.2): the points leave every neighbourhood
 Update of R listed rows with R new vectors (Sec. 5.3.3: a changed point is
   removed and added again): the deletion of the rows, then the insertion of the
   new vectors as the last rows, admitted together like a deletion.
+
+With a forest (forest_trees > 0) the state also keeps a randomized KD-forest
+resident, built once on the initial rows, whose leaf buckets follow every
+insertion and deletion (Sec. 5.3.1, Sec. 5.3.2), and an inserted point takes its
+neighbourhood from a forest search (checks) instead of the exact kNN: the
+paper's approximate insertion, whose rho_i is the forest's precision (Eq. 9,
+estimated at start on sampled rows against their exact lists) until a
+refinement makes the row exact. The reverse update of Eq. 11 stays exact.
+The buckets change in arrival order on the state stream.
+
+The symmetrised CSR P (Eq. 2, Eq. 10) of the current rows is kept resident too:
+after commits it is rebuilt on the state stream, at most every csr_interval
+seconds while requests keep arriving and always once the queue drains, so it
+follows the state it was built from (csr_rows).
 """
 import collections
 import time
@@ -36,9 +50,11 @@ import time
 import numpy as np
 import torch
 
-from . import (OP_DELETE, OP_KNN, OP_KNN_CROSS_RADIUS, atsne_calibrate_P, atsne_commit_rows,
-               atsne_delete_rows, atsne_knn, atsne_knn_cross, atsne_knn_rows, atsne_merge_neighbors,
-               atsne_row_dmax, knn_opts, workspace_bytes)
+from . import (OP_DELETE, OP_FOREST_QUERY, OP_FOREST_UPDATE, OP_KNN, OP_KNN_CROSS_RADIUS, OP_SYMMETRIZE,
+               atsne_calibrate_P, atsne_commit_rows, atsne_delete_rows, atsne_forest_build,
+               atsne_forest_delete, atsne_forest_insert, atsne_forest_query, atsne_knn, atsne_knn_cross,
+               atsne_knn_precision, atsne_knn_rows, atsne_merge_neighbors, atsne_row_dmax,
+               atsne_symmetrize, knn_opts, workspace_bytes)
 
 
 class Request:
@@ -60,7 +76,8 @@ class Request:
 
 class Server:
     def __init__(self, X0, capacity, k=90, perplexity=30.0, precision="fp32", slots=4,
-                 reserve_bytes=1 << 30, device="cuda"):
+                 reserve_bytes=1 << 30, device="cuda", forest_trees=0, checks=1024, seed=7,
+                 csr_interval=0.1):
         self.dev = torch.device(device)
         N0, D = X0.shape
         if N0 < k + 1 or capacity < N0:
@@ -81,6 +98,26 @@ class Server:
         atsne_calibrate_P(self.d2[:N0], self.perp, P_out=self.P[:N0], beta_out=self.beta[:N0])
         self.rho[:N0] = 1.0
         self.N = N0
+        # the resident forest: trees of the initial rows, buckets updated in place of a rebuild
+        self.forest = self.buckets = None
+        self.rho_forest = 1.0
+        if forest_trees > 0:
+            self.fopts = knn_opts(method="forest", trees=forest_trees, checks=checks, leaf_size=1, seed=seed)
+            self.checks = checks
+            self.forest = atsne_forest_build(self.X[:N0], opts=self.fopts)
+            sample = torch.arange(0, N0, max(1, N0 // 2048), dtype=torch.int32, device=self.dev)
+            fi, _, _ = atsne_forest_query(self.X[:N0], self.forest, k, queries=sample)
+            self.rho_forest = atsne_knn_precision(fi, self.idx[sample.long()])[1]
+        # the resident CSR P, buffers for the full capacity
+        self.row_ptr = torch.empty(capacity + 1, dtype=torch.int64, device=self.dev)
+        self.col = torch.empty(2 * capacity * k, dtype=torch.int32, device=self.dev)
+        self.val = torch.empty(2 * capacity * k, dtype=torch.float32, device=self.dev)
+        self.nnz = torch.empty(1, dtype=torch.int64, device=self.dev)
+        self.csr_ws = torch.empty(max(1, workspace_bytes(OP_SYMMETRIZE, capacity, 0, k)), dtype=torch.uint8,
+                                  device=self.dev)
+        self.csr_interval = csr_interval
+        self.rebuild_csr(torch.cuda.current_stream(self.dev))
+        self.csr_dirty, self.csr_at = False, 0.0
         torch.cuda.synchronize(self.dev)
         self.state = torch.cuda.Stream(self.dev)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
@@ -89,12 +126,33 @@ class Server:
         self.x_ready = None
         self.inflight = []
 
+    def rebuild_csr(self, stream):
+        """The symmetrised CSR P of rows [0, N) as the state stands, on `stream`."""
+        N = self.N
+        with torch.cuda.stream(stream):
+            atsne_symmetrize(self.idx[:N], self.P[:N], stream=stream, trim=False,
+                             out=(self.row_ptr, self.col, self.val, self.nnz), workspace=self.csr_ws)
+        self.csr_rows = N
+
+    def csr(self):
+        """(row_ptr, col, val) of the resident CSR P (synchronises for nnz)."""
+        torch.cuda.synchronize(self.dev)
+        n = int(self.nnz.item())
+        return self.row_ptr[:self.csr_rows + 1], self.col[:n], self.val[:n]
+
     # ---- admission ----
     def need_bytes(self, req):
         k, D, N = self.k, self.D, self.N
         n = req.size
         if req.kind == "insert":
-            ws = workspace_bytes(OP_KNN, N + n, D, k, n, self.opts)
+            if self.forest is not None:
+                fo = knn_opts(method="forest", trees=self.fopts.trees, checks=self.checks,
+                              leaf_size=max(1, self.buckets.max_bucket if self.buckets else 1) + n)
+                ws = workspace_bytes(OP_FOREST_QUERY, N + n, D, k, n, fo) + \
+                    workspace_bytes(OP_FOREST_UPDATE, self.forest.N, D, 0, N + n, self.fopts) + \
+                    2 * self.fopts.trees * (N + n) * 4
+            else:
+                ws = workspace_bytes(OP_KNN, N + n, D, k, n, self.opts)
             if N > 0:
                 kc = min(k, n)
                 ws += workspace_bytes(OP_KNN_CROSS_RADIUS, n, D, kc, N, self.opts) + N * (kc * 8 + 5)
@@ -123,10 +181,13 @@ class Server:
         st = self.state
         with torch.cuda.stream(st):
             rows = torch.from_numpy(np.ascontiguousarray(req.rows, dtype=np.int32)).to(self.dev)
+            if self.forest is not None:  # the points leave every bucket (Sec. 5.3.2)
+                self.buckets = atsne_forest_delete(self.forest, rows, buckets=self.buckets, stream=st)
             self.N = atsne_delete_rows(self.X, rows, self.perp, self.idx, self.d2, self.P, self.beta,
                                        self.rho, N=self.N, stream=st)
             done = torch.cuda.Event()
             done.record(st)
+        self.csr_dirty = True
         self.x_ready = done  # later requests read the compacted rows
         req.admitted = now
         self.inflight.append((req, None, done, [rows]))
@@ -160,7 +221,21 @@ class Server:
                 self.x_ready = torch.cuda.Event()
                 self.x_ready.record(s)
                 rows = torch.arange(N0, N0 + B, dtype=torch.int32, device=self.dev)
-                ti, td = atsne_knn(self.X[:N0 + B], self.k, queries=rows, opts=self.opts, stream=s)
+                if self.forest is not None:
+                    # the new points join the forest's buckets in arrival order (state
+                    # stream), then their neighbourhoods come from a forest search
+                    with torch.cuda.stream(self.state):
+                        self.state.wait_event(self.x_ready)
+                        self.buckets = atsne_forest_insert(self.X[:N0 + B], self.forest, N0,
+                                                           buckets=self.buckets, stream=self.state)
+                        fdone = torch.cuda.Event()
+                        fdone.record(self.state)
+                    s.wait_event(fdone)
+                    ti, td, _ = atsne_forest_query(self.X[:N0 + B], self.forest, self.k, checks=self.checks,
+                                                   queries=rows, buckets=self.buckets, stream=s)
+                    keep.append(self.buckets.buf)
+                else:
+                    ti, td = atsne_knn(self.X[:N0 + B], self.k, queries=rows, opts=self.opts, stream=s)
                 tp, tb = atsne_calibrate_P(td, self.perp, stream=s)
                 cand = None
                 if N0 > 0:
@@ -202,6 +277,8 @@ class Server:
             st.wait_event(computed)
             atsne_commit_rows(rows, ti, td, tp, tb, self.idx, self.d2, self.P, self.beta, self.rho,
                               stream=st)
+            if req.kind == "insert" and self.forest is not None:
+                self.rho[N0:N0 + req.size].fill_(self.rho_forest)  # approximate rows (Eq. 9)
             if cand is not None:
                 atsne_merge_neighbors(self.idx[:N0], self.d2[:N0], cand[0], cand[1], N0, stream=st)
                 atsne_calibrate_P(self.d2[:N0], self.perp, stream=st, P_out=self.P[:N0],
@@ -213,6 +290,7 @@ class Server:
                 t.record_stream(st)
         req.admitted = now
         self.inflight.append((req, slot, done, keep))
+        self.csr_dirty = True
 
     # ---- the loop ----
     def run(self, requests, clock=time.perf_counter, idle_sleep=2e-4):
@@ -243,8 +321,18 @@ class Server:
                     break
                 self.admit(pending.popleft(), clock() - t0)
                 progress = True
+            # the resident CSR P follows the commits: rebuilt after the last one
+            # enqueued, at most every csr_interval seconds while requests arrive
+            now = clock() - t0
+            if self.csr_dirty and (not self.inflight or now - self.csr_at >= self.csr_interval):
+                self.rebuild_csr(self.state)
+                self.csr_dirty, self.csr_at = False, now
+                progress = True
             if not progress:
                 time.sleep(idle_sleep)
+        if self.csr_dirty:
+            self.rebuild_csr(self.state)
+            self.csr_dirty = False
         torch.cuda.synchronize(self.dev)
         return served, summarize(served)
 

@@ -207,3 +207,78 @@ def test_knn_cross_radius_keeps_exactly_the_points_inside(at, precision):
         assert set(inside) <= set(got) <= set(maybe), r
         assert np.all(np.isinf(g_d2[r][g_idx[r] < 0]))
         assert np.all(g_d2[r][g_idx[r] >= 0] < rad[r])
+
+
+def _oracle_serve(X0, extra, reqs, k, trees, checks, seed):
+    """The oracle's account of a served session with a resident forest: the
+    initial rows exact; an insertion adds the points to the forest's buckets
+    (Sec. 5.3.1), gives them the forest search's neighbourhoods over the
+    updated buckets, and updates the existing rows by Eq. 11; a refinement makes
+    the listed rows exact (Sec. 4.3)."""
+    idx, d2 = oracle.knn_exact(X0, k)
+    f = oracle.forest_build(X0, trees=trees, top_var_dims=5, leaf_size=1, seed=seed)
+    X = X0
+    for r in reqs:
+        n = X.shape[0]
+        if r.kind == "insert":
+            Xg = np.concatenate([X, r.points])
+            f = oracle.forest_insert(f, Xg, n)
+            ni, nd, _ = oracle.forest_query(Xg, f, k, checks, queries=np.arange(n, Xg.shape[0], dtype=np.int32))
+            idx, d2, _ = oracle.insert(Xg, n, idx, d2)
+            idx, d2, X = np.concatenate([idx, ni]), np.concatenate([d2, nd]), Xg
+        else:
+            ri, rd = oracle.knn_exact(X, k, queries=r.rows)
+            idx[r.rows], d2[r.rows] = ri, rd
+    return X, idx, d2
+
+
+def test_forest_serving_state_matches_the_oracle(at):
+    """Serving with the KD-forest resident: integer data (exact distances on
+    both sides), so the served lists equal the oracle's bit for bit."""
+    from paper_1512_01655_gb300.serve import Server
+    rng = np.random.default_rng(41)
+    Xall = rng.integers(0, 24, size=(3500, 12)).astype(np.float32)
+    X0, extra = Xall[:2000], Xall[2000:]
+    srv = Server(X0, capacity=3500, k=20, perplexity=6.0, precision="fp32", slots=3, forest_trees=3,
+                 checks=150, seed=9)
+    reqs, used = _requests(at, X0, extra, seed=42)
+    srv.run(reqs)
+    at.atsne_check()
+    N = srv.N
+    oX, o_idx, o_d2 = _oracle_serve(X0, extra, _requests(at, X0, extra, seed=42)[0], 20, 3, 150, 9)
+    assert N == oX.shape[0]
+    assert np.array_equal(srv.idx[:N].cpu().numpy(), o_idx)
+    assert np.array_equal(srv.d2[:N].cpu().numpy().astype(np.float64), o_d2)
+    # inserted rows carry the forest's estimated precision until refined
+    assert 0.0 < srv.rho_forest <= 1.0
+    # the resident CSR P is the symmetrisation of the served state
+    rp, col, val = srv.csr()
+    e_rp, e_col, e_val = at.atsne_symmetrize(srv.idx[:N], srv.P[:N])
+    assert torch.equal(rp, e_rp) and torch.equal(col, e_col) and torch.equal(val, e_val)
+
+
+def test_forest_serving_same_state_alone_and_in_the_mix(at):
+    from paper_1512_01655_gb300.serve import Server
+    Xall = synth.gaussian_mixture(3500, 16, seed=43)
+    X0, extra = Xall[:2000], Xall[2000:]
+    states = []
+    for slots, spread in ((1, None), (4, 0.0), (3, 0.003)):
+        srv = Server(X0, capacity=3500, k=30, perplexity=10.0, precision="fp32", slots=slots, forest_trees=2,
+                     checks=128)
+        reqs, _ = _requests(at, X0, extra, seed=44)
+        if slots == 1:
+            for r in reqs:
+                srv.run([r])
+        else:
+            for j, r in enumerate(reqs):
+                r.arrival = 0.0 if not spread else j * spread
+            srv.run(reqs)
+        at.atsne_check()
+        N = srv.N
+        b = srv.buckets.arrays()
+        states.append([t[:N].cpu().numpy() for t in (srv.X, srv.idx, srv.d2, srv.P, srv.beta, srv.rho)] +
+                      [b["perm"].cpu().numpy(), b["leaf_ofs"].cpu().numpy()] +
+                      [t.cpu().numpy() for t in srv.csr()])
+    for other in states[1:]:
+        for a, c in zip(states[0], other):
+            assert np.array_equal(a, c)
