@@ -637,7 +637,8 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 }
             }
             bool rebased = rmode || (p.hint && PASSES != 8);
-            float dmx = 0.f;  // largest buffered distance, for the first re-anchoring of the grid
+            // largest and smallest buffered keys, for the first re-anchoring of the grid
+            float kmx = -INFINITY, kmn = INFINITY;
             uint32_t *dh = &s.dhist[e][0][lane];
             for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
             // recount the buffered distances on the grid below `top`
@@ -796,7 +797,8 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                             }
                             buf[cnt++] = Cand{key, col};
                             const float dd2 = nx + key;
-                            dmx = fmaxf(dmx, dd2);
+                            kmx = fmaxf(kmx, key);
+                            kmn = fminf(kmn, key);
                             const int db = dbucket(dd2);
                             int bk = db - (top - (NBUCKET - 1));
                             if (bk < NBUCKET) {  // distances above the grid are not counted
@@ -823,13 +825,27 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     acc_phase ^= 1u;
                 }
                 if (rmode) continue;  // the threshold is fixed
-                // Once ksel distances are buffered the grid is re-anchored just
-                // above the largest of them and recounted: the first anchor
+                // Once kh keys are buffered, the largest of them bounds the
+                // kh-th (and, with ksel buffered, the ksel-th) smallest, and
+                // the grid is re-anchored and recounted: the first anchor
                 // bounds the largest distance any point could have, which can
-                // lie octaves above the neighbourhood.
+                // lie octaves above the neighbourhood. With one buffer per row
+                // (kh = ksel) the new grid ends at twice the smallest buffered
+                // distance, kept within [dmx / 8, dmx] (dmx the largest): on
+                // spread-out data the final ksel-th distance lies far below
+                // the largest of the first distances, near their smallest.
+                // A half's ksel-th lies above its first kh keys, and its grid
+                // ends at the largest. Any anchor gives a valid bound
+                // (distances above the grid are not counted); one too high
+                // leaves the ksel-th in the lowest bucket, which also counts
+                // every distance below the grid, until the buffer fills.
                 if (!rebased && cnt >= kh) {
                     rebased = true;
-                    const int nt = dbucket(dmx * 1.0001f) + 1;
+                    th = fminf(th, kmx);
+                    if (cnt >= p.ksel) tau = fminf(tau, kmx);
+                    const float dmx = nx + kmx, dmn = nx + kmn;
+                    const float anchor = C::HALVES > 1 ? dmx : fminf(dmx, fmaxf(2.f * dmn, 0.125f * dmx));
+                    const int nt = dbucket(anchor * 1.0001f) + 1;
                     if (nt < top) {
                         top = nt;
                         recount();
