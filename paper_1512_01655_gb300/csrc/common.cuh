@@ -118,10 +118,74 @@ __device__ __forceinline__ void warp_argmax_pair(float &d, int &j, int &pos) {
     }
 }
 
+// FP32 squared distances ||q - xa||^2 and ||q - xb||^2 in the one summation
+// order in which every exact kNN kernel returns its distances, so that a row's
+// d2 does not depend on the kernel that computed it. The dimensions are cut
+// into chunks of four; lane g of an 8-lane group sums the chunks g, g + 8,
+// g + 16, ... as one FMA chain in dimension order, and the group's eight
+// partial sums are added by a butterfly (xor 1, 2, 4), which leaves the same
+// value in all eight lanes (floating-point addition commutes). Each group
+// takes its own two points (pass q for an unused one); all 32 lanes of the
+// warp call it together. vec4: D % 4 == 0 and all rows 16-byte aligned (the
+// order is the same either way).
+__device__ __forceinline__ float2 group8_d2_pair(const float *__restrict__ q, const float *__restrict__ xa,
+                                                 const float *__restrict__ xb, int D, bool vec4, int gl) {
+    float sa = 0.f, sb = 0.f;
+    if (vec4) {
+        const int n4 = D >> 2;
+        const float4 *q4 = reinterpret_cast<const float4 *>(q);
+        const float4 *a4 = reinterpret_cast<const float4 *>(xa);
+        const float4 *b4 = reinterpret_cast<const float4 *>(xb);
+#pragma unroll 4
+        for (int j = gl; j < n4; j += 8) {
+            const float4 qv = q4[j], av = a4[j], bv = b4[j];
+            float df = qv.x - av.x;
+            sa = fmaf(df, df, sa);
+            df = qv.y - av.y;
+            sa = fmaf(df, df, sa);
+            df = qv.z - av.z;
+            sa = fmaf(df, df, sa);
+            df = qv.w - av.w;
+            sa = fmaf(df, df, sa);
+            df = qv.x - bv.x;
+            sb = fmaf(df, df, sb);
+            df = qv.y - bv.y;
+            sb = fmaf(df, df, sb);
+            df = qv.z - bv.z;
+            sb = fmaf(df, df, sb);
+            df = qv.w - bv.w;
+            sb = fmaf(df, df, sb);
+        }
+    } else {
+        for (int j = gl; 4 * j < D; j += 8) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int e = 4 * j + c;
+                if (e < D) {
+                    float df = q[e] - xa[e];
+                    sa = fmaf(df, df, sa);
+                    df = q[e] - xb[e];
+                    sb = fmaf(df, df, sb);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    return make_float2(sa, sb);
+}
+
 // Near ties of a sorted neighbour list settled in FP64 (Eq. 8's order on
-// exact distances): d[0, n) ascending with their points j[0, n) (FP32 direct
-// differences, each within (D + 8) 2^-24 of its value; entries of infinite
-// distance are padding and their j is not read). Runs of neighbours
+// exact distances): d[0, n) ascending with their points j[0, n) (FP32
+// distances in the order of group8_d2_pair; entries of infinite distance are
+// padding and their j is not read). Each such distance is within
+// (m + 8) 2^-24 of its value, m = 4 ceil(D / 32) the terms of one lane's FMA
+// chain: a rounded difference squares to within 2u + u^2 (u = 2^-24), the
+// chain of m FMAs (exact products) and the three butterfly additions of
+// positive terms add at most gamma_(m+3). Runs of neighbours
 // whose FP32 gaps are within twice that bound, among the first k + 1, are
 // recomputed as FP64 sums of squared differences of the query row xq and X's
 // rows and put in (FP64 distance, index) order, their distances replaced by
@@ -134,7 +198,7 @@ __device__ __forceinline__ void fp64_near_ties(float *d, int *j, int n, int k, c
                                                const float *__restrict__ X, int D, double *dm, int *mp,
                                                int lane) {
     const int m = n < k + 1 ? n : k + 1;
-    const float band = 2.f * (float)(D + 8) * 0x1p-24f;
+    const float band = 2.f * (float)(4 * ((D + 31) / 32) + 8) * 0x1p-24f;
     int nm = 0;
     for (int t0 = 0; t0 < m; t0 += 32) {
         const int t = t0 + lane;

@@ -5,10 +5,12 @@
 // per thread), then each warp folds a tile's 64 candidates per query into a
 // per-query list of the best k in shared memory. A candidate enters only if it
 // beats the list's current worst entry under the (distance, index) order, so
-// after the first tiles almost every candidate costs one compare. The FP32
-// distances are the exact-path's definition of d2; this kernel is the
-// reference GPU path for small problems and the fallback for rows whose
-// tensor-core candidates cannot be certified.
+// after the first tiles almost every candidate costs one compare. The list's
+// distances are then recomputed in the library's one summation order
+// (group8_d2_pair, as the tensor-core merge computes them) and sorted, so a
+// row's d2 does not depend on which kernel produced it. This kernel is the GPU
+// path for small problems and the fallback for rows whose tensor-core
+// candidates cannot be certified.
 #include <float.h>
 #include <limits.h>
 
@@ -166,6 +168,25 @@ knn_bruteforce_kernel(const float *__restrict__ X, int64_t N, int D,
     for (int r = warp * 4; r < warp * 4 + 4; ++r) {
         const int64_t o = orow[r];
         if (o < 0) continue;
+        if (qid[r] >= 0) {
+            // the list's distances in the library's one summation order
+            const float *qrow = QX + (int64_t)qid[r] * D;
+            const bool vec4 = (D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                              (reinterpret_cast<uintptr_t>(qrow) & 15) == 0;
+            const int g = lane >> 3, gl = lane & 7;
+            for (int t0 = 0; t0 < kl; t0 += 8) {
+                const int ta = t0 + g, tb = t0 + 4 + g;
+                const int ja = ta < kl ? tj[r * KCAP + ta] : INT_MAX;
+                const int jb = tb < kl ? tj[r * KCAP + tb] : INT_MAX;
+                const float2 s2 = group8_d2_pair(qrow, ja != INT_MAX ? X + (int64_t)ja * D : qrow,
+                                                 jb != INT_MAX ? X + (int64_t)jb * D : qrow, D, vec4, gl);
+                if (gl == 0) {
+                    if (ja != INT_MAX) td[r * KCAP + ta] = s2.x;
+                    if (jb != INT_MAX) td[r * KCAP + tb] = s2.y;
+                }
+            }
+            __syncwarp();
+        }
         warp_bitonic_sort_smem(td + r * KCAP, tj + r * KCAP, KCAP, lane);
         if (qid[r] >= 0)
             fp64_near_ties(td + r * KCAP, tj + r * KCAP, kl, k, QX + (int64_t)qid[r] * D, X, D, dm, mp, lane);

@@ -1103,41 +1103,21 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
                 }
             }
         };
-        // exact FP32 direct-difference distances of rjw[from, to), four at a time
         const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (int64_t)qid * p.D;
         const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
                           (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
-        // exact FP32 distances of rjw[from, to), one candidate per lane, each a
-        // sequential FMA chain over the dimensions in order: the same
-        // operations as the brute-force kernel's, so a row's distances do not
-        // depend on which kernel produced it
+        // exact FP32 distances of rjw[from, to) in the library's one summation
+        // order (group8_d2_pair), eight candidates per warp step
         auto rerank = [&](int from, int to) {
-            for (int t0 = from; t0 < to; t0 += 32) {
-                const int t = t0 + lane;
-                if (t < to) {
-                    const float *xc = p.X + (int64_t)rjw[t] * p.D;
-                    float a = 0.f;
-                    if (vec4) {
-                        const float4 *q4 = reinterpret_cast<const float4 *>(xq);
-                        const float4 *c4 = reinterpret_cast<const float4 *>(xc);
-                        for (int d = 0; d < (p.D >> 2); ++d) {
-                            const float4 qv = q4[d], cv = c4[d];
-                            float df = qv.x - cv.x;
-                            a = fmaf(df, df, a);
-                            df = qv.y - cv.y;
-                            a = fmaf(df, df, a);
-                            df = qv.z - cv.z;
-                            a = fmaf(df, df, a);
-                            df = qv.w - cv.w;
-                            a = fmaf(df, df, a);
-                        }
-                    } else {
-                        for (int d = 0; d < p.D; ++d) {
-                            const float df = xq[d] - xc[d];
-                            a = fmaf(df, df, a);
-                        }
-                    }
-                    rdw[t] = a;
+            const int g = lane >> 3, gl = lane & 7;
+            for (int t0 = from; t0 < to; t0 += 8) {
+                const int ta = t0 + g, tb = t0 + 4 + g;
+                const float *xa = ta < to ? p.X + (int64_t)rjw[ta] * p.D : xq;
+                const float *xb = tb < to ? p.X + (int64_t)rjw[tb] * p.D : xq;
+                const float2 s2 = group8_d2_pair(xq, xa, xb, p.D, vec4, gl);
+                if (gl == 0) {
+                    if (ta < to) rdw[ta] = s2.x;
+                    if (tb < to) rdw[tb] = s2.y;
                 }
             }
         };
@@ -1238,16 +1218,21 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) radius_merge_kernel(MergePar
     }
     __syncwarp();
     const float *xq = p.Xq + (int64_t)row * p.D;
-    // one candidate per lane, a sequential FMA chain over the dimensions (the
-    // brute-force kernel's operations)
-    for (int t = lane; t < nr; t += 32) {
-        const float *xc = p.X + (int64_t)rjw[t] * p.D;
-        float a = 0.f;
-        for (int d = 0; d < p.D; ++d) {
-            const float df = xq[d] - xc[d];
-            a = fmaf(df, df, a);
+    const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
+                      (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
+    // the library's one summation order (group8_d2_pair), eight candidates per step
+    {
+        const int g = lane >> 3, gl = lane & 7;
+        for (int t0 = 0; t0 < nr; t0 += 8) {
+            const int ta = t0 + g, tb = t0 + 4 + g;
+            const float *xa = ta < nr ? p.X + (int64_t)rjw[ta] * p.D : xq;
+            const float *xb = tb < nr ? p.X + (int64_t)rjw[tb] * p.D : xq;
+            const float2 s2 = group8_d2_pair(xq, xa, xb, p.D, vec4, gl);
+            if (gl == 0) {
+                if (ta < nr) rdw[ta] = s2.x;
+                if (tb < nr) rdw[tb] = s2.y;
+            }
         }
-        rdw[t] = a;
     }
     __syncwarp();
     const float rad = radius[row];
