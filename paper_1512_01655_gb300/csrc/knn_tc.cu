@@ -68,8 +68,8 @@ constexpr int MERGE_WARPS = 4;
 constexpr int RCAP = 256;        // candidates re-ranked per row at most (certified modes)
 constexpr int MSTAGE = 1024;     // keys below tau staged per row for the merge's select
 constexpr int RCAP_FP8 = 1024;   // modes without a certificate: the largest re-rank set (ksel <= 512)
-constexpr int NBUCKET = 48;      // a thread's distance buckets: 3 octaves of d^2, 16 per octave
-constexpr int HSHIFT = 19;       // float bits >> HSHIFT: exponent and 4 mantissa bits (16 per octave)
+constexpr int NBUCKET = 64;      // a thread's distance buckets: 2 octaves of d^2, 32 per octave
+constexpr int HSHIFT = 18;       // float bits >> HSHIFT: exponent and 5 mantissa bits (32 per octave)
 constexpr int GH_BUCKETS = 48;   // a row's global histogram (column splits): 6 octaves, 8 per octave
 constexpr int GH_SHIFT = 20;
 
@@ -153,7 +153,7 @@ struct TcParams {
     uint64_t wait_ns;      // limit of each pipeline wait (the drains of issued copies and MMAs keep WAIT_NS)
 };
 
-// Absolute bucket of a squared distance on the thread grid (16 per octave),
+// Absolute bucket of a squared distance on the thread grid (32 per octave),
 // and the upper edge of bucket b.
 __device__ __forceinline__ int dbucket(float d) { return (int)(__float_as_uint(fmaxf(d, 1e-30f)) >> HSHIFT); }
 __device__ __forceinline__ float bucket_top(int b) { return __uint_as_float((uint32_t)(b + 1) << HSHIFT); }
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             // widened by twice the key error bound, so that no point inside the
             // radius is filtered out; no top-k bookkeeping
             const bool rmode = p.radius != nullptr;
-            // the thread's distance grid: NBUCKET buckets, 16 per octave of d^2,
+            // the thread's distance grid: NBUCKET buckets, 32 per octave of d^2,
             // below an anchor; first anchored at t0 = (||x|| + max||y||)^2 >= d
             const float nx = qv ? (cross ? p.qnrm[row] : p.nrm[qid]) : 0.f;
             const float ai = sqrtf(nx), amax = __uint_as_float(p.gmax[0]);
@@ -869,6 +869,22 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     if (bk < NBUCKET) tau = fminf(tau, bucket_top(top - (NBUCKET - 1) + bk) - nx);
                     if (bh < NBUCKET) th = fminf(th, bucket_top(top - (NBUCKET - 1) + bh) - nx);
                     since = 0;
+                    // The lowest bucket also counts every distance below the
+                    // grid; when it holds the ksel-th, that distance may lie
+                    // far lower. The grid then slides down by its own span:
+                    // the old lowest bucket becomes the new highest, with its
+                    // whole count (those distances lie at or below its top, so
+                    // the count never exceeds the true one at any edge and the
+                    // bounds stay valid), and later survivors are counted on
+                    // the finer, lower grid. No buffered entry is reread.
+                    // The grid never slides below the bucket of the smallest
+                    // distance the buckets tell apart (dbucket(0)).
+                    if (bk == 0 && top - 2 * (NBUCKET - 1) >= dbucket(0.f)) {
+                        const uint32_t c0 = hw[0] & 0xffffu;
+                        for (int bw = 0; bw < NBUCKET / 2; ++bw) dh[bw * 32] = 0;
+                        dh[(NBUCKET / 2 - 1) * 32] = c0 << 16;
+                        top -= NBUCKET - 1;
+                    }
                 }
                 if (gh) global_tau();
                 if (C::HALVES > 1) {  // with the other half of the row: ksel keys below the larger bound
