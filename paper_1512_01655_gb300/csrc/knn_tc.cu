@@ -108,10 +108,8 @@ struct __align__(1024) TcSmem {
     unsigned char stage[TcCfg<PASSES>::STAGES][TcCfg<PASSES>::STAGE_BYTES];
     float ny[NEPI][2][32];      // per epilogue warp: two chunks' corpus norms (double-buffered)
     float ms[PASSES == 8 ? NEPI : 1][2][32];  // FP8: two chunks' -2 * corpus row scales
-    // per epilogue thread: one row of 32 keys (16-byte groups swizzled by the
-    // lane) from which its survivors are read back; between tiles the warp's
-    // first 256 words serve the radix select of an exact compaction
-    float tr[NEPI][32 * 32];
+    // per epilogue warp: the 256 counters of the radix select of an exact compaction
+    uint32_t sel_hist[NEPI][256];
     // per epilogue thread: buffered distances by bucket, two 16-bit counts per word
     uint32_t dhist[NEPI][NBUCKET / 2][32];
     // each half's current tau per query row, tagged with its work unit:
@@ -562,7 +560,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
         constexpr int CW = TC_BN / C::HALVES;  // columns of each tile filtered by this thread
         constexpr int NCH = CW / 32;           // 32-column TMEM loads per tile
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        uint32_t *hist = reinterpret_cast<uint32_t *>(s.tr[e]);
+        uint32_t *hist = s.sel_hist[e];
         const int subs = p.splits * C::HALVES;  // candidate buffers per query row
         int acc = 0;
         uint32_t acc_phase = 0;
@@ -664,7 +662,6 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             // FP8: x_i . x_j ~ s_i s_j (q_i . q_j); the row's scale, the
             // columns' -2 s_j beside their norms
             const float si = PASSES == 8 && qv ? (p.qscale ? p.qscale[row] : p.scale[qid]) : 1.f;
-            float *mine = s.tr[e] + lane * 32;
             // the partner half may still be on an earlier unit: its bound is
             // taken only when its tag is this unit
             volatile unsigned long long *tau_mine =
@@ -774,17 +771,15 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     const int so = self_off - c * 32;
                     if (so >= 0 && so < 32) mask &= ~(1u << so);
                     if (mask) {
-                        // spill this row's keys to its own padded shared row and
-                        // walk its survivors one per step (a chunk rarely holds
-                        // more than one or two of a row's): the warp pays the
-                        // largest count of any lane, not the union of survivor
-                        // positions. Each survivor is appended (key, column) to
-                        // the thread's buffer and counted in its bucket by a
-                        // fire-and-forget shared add.
-#pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            reinterpret_cast<float4 *>(mine)[q ^ (lane & 7)] =
-                                make_float4(kk[4 * q], kk[4 * q + 1], kk[4 * q + 2], kk[4 * q + 3]);
+                        // walk this row's survivors one per step (a chunk rarely
+                        // holds more than one or two of a row's): the warp pays
+                        // the largest count of any lane, not the union of
+                        // survivor positions. A survivor's key is picked from
+                        // the 32 key registers by a tree of selects on the bits
+                        // of its position (no round trip through shared memory,
+                        // whose pipe the MMA operand reads and the copies keep
+                        // busy), appended (key, column) to the thread's buffer
+                        // and counted in its bucket by a fire-and-forget shared add.
                         const int colb = colb0 + c * 32;
                         since += __popc(mask);
                         auto append = [&](float key, int col) {
@@ -813,7 +808,16 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                         do {
                             const int j0 = __ffs(mask) - 1;
                             mask &= mask - 1;
-                            append(mine[(((j0 >> 2) ^ (lane & 7)) << 2) + (j0 & 3)], colb + j0);
+                            float t16[16], t8[8], t4[4], t2[2];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) t16[i] = (j0 & 1) ? kk[2 * i + 1] : kk[2 * i];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) t8[i] = (j0 & 2) ? t16[2 * i + 1] : t16[2 * i];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) t4[i] = (j0 & 4) ? t8[2 * i + 1] : t8[2 * i];
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) t2[i] = (j0 & 8) ? t4[2 * i + 1] : t4[2 * i];
+                            append((j0 & 16) ? t2[1] : t2[0], colb + j0);
                         } while (mask);
                     }
                 }
