@@ -479,7 +479,7 @@ def bench_refine_batch(at, torch, dev, stream, reps, peaks):
     at.atsne_tune_clear()
     ms = min(ms_rule, ms_tuned)
     flops = 2.0 * union * N * D
-    peak = peaks.get("bf16_tflops", 1900.0)
+    peak, peak_src = peak_of(peaks, "bf16_tflops")
     ach = flops / (ms / 1e3) / 1e12
     return {"workload": "500000x256 fp32, 100 Gaussian clusters; 512 selections of 200..20000 points; "
                         "state restored to the forest kNN (T=4, checks=1024) before every call",
@@ -489,7 +489,7 @@ def bench_refine_batch(at, torch, dev, stream, reps, peaks):
             "listed_points_per_s": round(total / (ms / 1e3), 1),
             "union_rows_per_s": round(union / (ms / 1e3), 1),
             "tensor": {"achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s (algorithmic 2*U*N*D)",
-                       "frac": round(ach / peak, 4), "tensor_passes": 3}}
+                       "frac": round(ach / peak, 4), "tensor_passes": 3, "peak_source": peak_src}}
 
 
 def algorithmic_flops_knn(Q, N, D):
@@ -502,6 +502,18 @@ def load_peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def peak_of(peaks, key):
+    """(value, source label) of a roofline denominator: the pool's measured
+    figure when MEASURED_PEAKS.json holds it, else the recipe's fallback."""
+    if key in peaks:
+        kind = " (burst, of measured)" if key == "bf16_tflops" else " (of measured)"
+        return float(peaks[key]), "MEASURED_PEAKS.json " + key + kind
+    return FALLBACK_PEAKS[key], "fallback %g, no MEASURED_PEAKS.json (of fallback)" % FALLBACK_PEAKS[key]
 
 
 class ExactStep:
@@ -561,8 +573,8 @@ def exact_rooflines(per_kernel, steps, N, D, k, nnz, passes, prec, peaks, worklo
     per launch: the tensor-core kNN against the measured BF16 peak (FP8: twice
     it, the nominal ratio), the bandwidth-bound kernels against the measured HBM
     copy rate on their algorithmic bytes."""
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    bf16 = peaks.get("bf16_tflops", 1900.0)
+    hbm, hbm_src = peak_of(peaks, "hbm_gbs")
+    bf16, bf16_src = peak_of(peaks, "bf16_tflops")
     lines = {}
     if "knn_tc" in per_kernel:
         pk = per_kernel["knn_tc"]
@@ -574,8 +586,7 @@ def exact_rooflines(per_kernel, steps, N, D, k, nnz, passes, prec, peaks, worklo
             "unit": "TFLOP/s", "frac": round(ach / peak, 4), "launch_ms": round(avg, 3),
             "traffic": recorded_traffic("knn_tc", workload, prec),
             "algorithmic_flops_per_launch": algorithmic_flops_knn(N, N, D), "tensor_passes": passes,
-            "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, of measured)" +
-                            (" x 2 (FP8 nominal ratio)" if prec == "fp8" else ""))}
+            "peak_source": bf16_src + (" x 2 (FP8 nominal ratio)" if prec == "fp8" else "")}
     Dp = 64 * ((D + 63) // 64)
     bw = {
         # X read; BF16 copies (two in FP32 mode), norms and error statistics written
@@ -593,7 +604,7 @@ def exact_rooflines(per_kernel, steps, N, D, k, nnz, passes, prec, peaks, worklo
         ach = bytes_ / (ms / 1e3) / 1e9
         lines[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                        "frac": round(ach / hbm, 4), "ms": round(ms, 3), "algorithmic_bytes": int(bytes_),
-                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                       "peak_source": hbm_src}
     if "calibrate_beta" in lines:
         lines["calibrate_beta"]["note"] = ("bound by the exponentials of the bisection (about 40-60 "
                                            "steps of k exp per row), not by its bytes")
@@ -824,7 +835,7 @@ def bench_approx(at, torch, dev, stream, args, peaks):
         nl = per_kernel["forest_traverse"]["launches"]
         avg = sum(per_kernel[k_]["ms"] for k_ in fparts if k_ in per_kernel) / nl
         ach = per_launch / (avg / 1e3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
+        peak, peak_src = peak_of(peaks, "hbm_gbs")
         trn = "forest_traverse_u8" if u8 else "forest_traverse"
         dname = "forest_dist_u8" if u8 else "forest_dist"
         t_tr, t_di = recorded_traffic(trn, args.approx_workload), recorded_traffic(dname, args.approx_workload)
@@ -834,7 +845,7 @@ def bench_approx(at, torch, dev, stream, args, peaks):
                   "algorithmic_bytes_per_launch": per_launch, "row_bytes_per_value": vb,
                   "traversal_ms": round(per_kernel.get(trn, per_kernel["forest_traverse"])["ms"] / nl, 3),
                   "traversal_bound": "instruction issue (queue and tree walk)",
-                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                  "peak_source": peak_src}
     sweep = None
     if args.checks_sweep:
         sweep = []

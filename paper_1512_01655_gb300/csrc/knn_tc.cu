@@ -770,43 +770,25 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     mask = mq[0] | (mq[1] << 8) | (mq[2] << 16) | (mq[3] << 24);
                     const int so = self_off - c * 32;
                     if (so >= 0 && so < 32) mask &= ~(1u << so);
-                    if (mask) {
+                    if (__any_sync(0xffffffffu, mask != 0)) {
                         // walk this row's survivors one per step (a chunk rarely
-                        // holds more than one or two of a row's): the warp pays
-                        // the largest count of any lane, not the union of
-                        // survivor positions. A survivor's key is picked from
-                        // the 32 key registers by a tree of selects on the bits
-                        // of its position (no round trip through shared memory,
+                        // holds more than one or two of a row's): the warp takes
+                        // as many steps as the largest count of any lane, not
+                        // the union of survivor positions, and every step is the
+                        // same straight-line code for all lanes (a lane with no
+                        // survivor left adds nothing), so the walk carries no
+                        // divergent branch. A survivor's key is picked from the
+                        // 32 key registers by a tree of selects on the bits of
+                        // its position (no round trip through shared memory,
                         // whose pipe the MMA operand reads and the copies keep
                         // busy), appended (key, column) to the thread's buffer
                         // and counted in its bucket by a fire-and-forget shared add.
                         const int colb = colb0 + c * 32;
                         since += __popc(mask);
-                        auto append = [&](float key, int col) {
-                            if (rmode) {  // no compaction: a full buffer sends the row to the fallback
-                                if (cnt < p.cap)
-                                    buf[cnt++] = Cand{key, col};
-                                else
-                                    rovf = 1;
-                                return;
-                            }
-                            buf[cnt++] = Cand{key, col};
-                            const float dd2 = nx + key;
-                            kmx = fmaxf(kmx, key);
-                            kmn = fminf(kmn, key);
-                            const int db = dbucket(dd2);
-                            int bk = db - (top - (NBUCKET - 1));
-                            if (bk < NBUCKET) {  // distances above the grid are not counted
-                                bk = max(bk, 0);
-                                red_add_shared(dh + (bk >> 1) * 32, 1u << ((bk & 1) * 16));
-                            }
-                            if (gh) {
-                                const int gb = (int)(__float_as_uint(fmaxf(dd2, 1e-30f)) >> GH_SHIFT) - gbase;
-                                atomicAdd(gh + min(max(gb, 0), GH_BUCKETS - 1), 1u);
-                            }
-                        };
-                        do {
-                            const int j0 = __ffs(mask) - 1;
+                        const int steps = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
+                        for (int st = 0; st < steps; ++st) {
+                            const bool has = mask != 0;
+                            const int j0 = (__ffs(mask) - 1) & 31;
                             mask &= mask - 1;
                             float t16[16], t8[8], t4[4], t2[2];
 #pragma unroll
@@ -817,8 +799,32 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                             for (int i = 0; i < 4; ++i) t4[i] = (j0 & 4) ? t8[2 * i + 1] : t8[2 * i];
 #pragma unroll
                             for (int i = 0; i < 2; ++i) t2[i] = (j0 & 8) ? t4[2 * i + 1] : t4[2 * i];
-                            append((j0 & 16) ? t2[1] : t2[0], colb + j0);
-                        } while (mask);
+                            const float key = (j0 & 16) ? t2[1] : t2[0];
+                            const int col = colb + j0;
+                            if (rmode) {  // no compaction: a full buffer sends the row to the fallback
+                                if (has) {
+                                    if (cnt < p.cap)
+                                        buf[cnt++] = Cand{key, col};
+                                    else
+                                        rovf = 1;
+                                }
+                                continue;
+                            }
+                            if (has) buf[cnt] = Cand{key, col};
+                            cnt += has;
+                            const float dd2 = nx + key;
+                            kmx = has ? fmaxf(kmx, key) : kmx;
+                            kmn = has ? fminf(kmn, key) : kmn;
+                            const int bk = dbucket(dd2) - (top - (NBUCKET - 1));
+                            // distances above the grid are not counted
+                            const int bc = min(max(bk, 0), NBUCKET - 1);
+                            red_add_shared(dh + (bc >> 1) * 32,
+                                           has && bk < NBUCKET ? 1u << ((bc & 1) * 16) : 0u);
+                            if (gh && has) {
+                                const int gb = (int)(__float_as_uint(fmaxf(dd2, 1e-30f)) >> GH_SHIFT) - gbase;
+                                atomicAdd(gh + min(max(gb, 0), GH_BUCKETS - 1), 1u);
+                            }
+                        }
                     }
                 }
                 fence_before_sync();
