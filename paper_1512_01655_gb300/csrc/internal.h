@@ -37,6 +37,7 @@ struct TcWs {
     float *scale = nullptr, *qscale = nullptr;  // FP8 row scales
     float *qnrm = nullptr, *qstats = nullptr;   // queries from another array: norms, error stats
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
+    uint16_t *bext = nullptr, *aext = nullptr;  // one-pass BF16: the norm slices
 };
 // Limit of the tensor kernel's pipeline waits (process-wide; default 1 s).
 uint64_t pipeline_wait_ns();

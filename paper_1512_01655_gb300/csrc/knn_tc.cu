@@ -99,13 +99,21 @@ struct TcCfg {
     static constexpr int KE = PASSES == 8 ? 128 : TC_BK;  // elements per k-block
     static constexpr int A_BYTES = TC_BM * 128;
     static constexpr int B_BYTES = TC_BN * 128;
-    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (PASSES == 3 ? 2 : 1);
+    // One-pass BF16 folds the column norms into the contraction: one more
+    // K = 16 step multiplies a constant query slice (-1/2 three times) with
+    // each corpus row's norm in three BF16 pieces, so the accumulator holds
+    // x.y - ||y||^2 / 2 and the key is -2 times it (exact scaling).
+    static constexpr bool FOLD = PASSES == 1;
+    static constexpr int EXT_A_BYTES = TC_BM * 32;             // the constant slice, resident
+    static constexpr int EXT_B_BYTES = FOLD ? TC_BN * 32 : 0;  // a tile's norm pieces, per stage
+    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (PASSES == 3 ? 2 : 1) + EXT_B_BYTES;
 };
 
 template <int PASSES>
 struct __align__(1024) TcSmem {
     static constexpr int NEPI = TcCfg<PASSES>::NEPI;
     unsigned char stage[TcCfg<PASSES>::STAGES][TcCfg<PASSES>::STAGE_BYTES];
+    unsigned char a_ext[TcCfg<PASSES>::FOLD ? TcCfg<PASSES>::EXT_A_BYTES : 16];  // 1024-aligned
     float ny[NEPI][2][32];      // per epilogue warp: two chunks' corpus norms (double-buffered)
     float ms[PASSES == 8 ? NEPI : 1][2][32];  // FP8: two chunks' -2 * corpus row scales
     // per epilogue warp: the 256 counters of the radix select of an exact compaction
@@ -120,6 +128,7 @@ struct __align__(1024) TcSmem {
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint64_t drain;
+    uint64_t ext_bar;  // the constant query slice has landed
     uint32_t tmem_base;
     int abort_flag;
     int zero;
@@ -127,6 +136,7 @@ struct __align__(1024) TcSmem {
 
 struct TcParams {
     CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;
+    CUtensorMap tm_a_ext, tm_b_ext;  // one-pass BF16: the norm slices
     const float *nrm;      // [N] corpus ||x||^2
     const float *scale;    // FP8: [N] corpus row scales (x ~ scale * q)
     const float *qscale;   // FP8 with a query list: [Q] query row scales
@@ -136,6 +146,7 @@ struct TcParams {
     const float4 *qst;     // queries from another array: their error statistics
     const float4 *st;      // corpus rows' error statistics (for listed queries)
     float acc_coef;        // FP32 accumulation term of the key error bound
+    float sq_coef;         // the same for the folded norms, per max ||y||^2
     const unsigned *gmax;  // max ||x|| over the corpus (float bits)
     const unsigned *lo_max;  // max norm of the corpus' BF16 low halves (float bits), or nullptr
                              // when the queries' low halves are not covered by it
@@ -267,9 +278,13 @@ __global__ void __launch_bounds__(256)
 knn_prep_kernel(const float *__restrict__ X, const int32_t *__restrict__ rows, int64_t nrows, int64_t N,
                 int D, int Dp, int passes, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
                 float *__restrict__ nrm, float4 *__restrict__ stats, unsigned *__restrict__ gmax,
-                int *status) {
+                __nv_bfloat16 *__restrict__ bext, __nv_bfloat16 *__restrict__ aext, int *status) {
     const int lane = threadIdx.x & 31;
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // the constant query slice of the folded norms: -1/2 in its first three columns
+    if (aext && blockIdx.x == 0)
+        for (int t = threadIdx.x; t < TC_BM * 16; t += blockDim.x)
+            aext[t] = __float2bfloat16_rn((t & 15) < 3 ? -0.5f : 0.f);
     if (r >= nrows) return;
     int64_t src = rows ? rows[r] : r;
     if (src < 0 || src >= N) src = 0;  // flagged by the caller's index check
@@ -297,6 +312,15 @@ knn_prep_kernel(const float *__restrict__ X, const int32_t *__restrict__ rows, i
     n = warp_sum(n);
     res = warp_sum(res);
     l2 = warp_sum(l2);
+    if (bext && lane < 16) {
+        // the row's FP32 squared norm as three BF16 pieces h1 + h2 + h3 (each
+        // the rounded remainder of the previous: together within 2^-24 of it)
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(n);
+        const float r1 = n - __bfloat162float(h1);
+        const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 h3 = __float2bfloat16_rn(r1 - __bfloat162float(h2));
+        bext[r * 16 + lane] = lane == 0 ? h1 : lane == 1 ? h2 : lane == 2 ? h3 : __float2bfloat16_rn(0.f);
+    }
     if (!__all_sync(0xffffffffu, finite) && lane == 0) raise_status(status, DEV_NONFINITE);
     if (lane == 0 && nrm) {
         nrm[r] = n;
@@ -356,13 +380,14 @@ knn_prep_fp8_kernel(const float *__restrict__ X, const int32_t *__restrict__ row
 // part) against any corpus point (gmax: the corpus maxima of the same): the
 // terms the BF16 copies drop (Cauchy-Schwarz on the residual norms), the FP32
 // accumulation of the products, and the FP32 norms.
-__device__ __forceinline__ float key_error_bound(float4 st, const unsigned *gmax, float acc_coef) {
+__device__ __forceinline__ float key_error_bound(float4 st, const unsigned *gmax, float acc_coef,
+                                                 float sq_coef) {
     const float amax = __uint_as_float(gmax[0]);
     const float rmax = __uint_as_float(gmax[1]);
     const float lmax = __uint_as_float(gmax[2]);
     const float a = st.x, r = st.y, l = st.z;
     const float drop = l * lmax + r * amax + a * rmax;
-    return 2.f * drop + acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
+    return 2.f * drop + acc_coef * a * amax + (4e-6f + sq_coef) * amax * amax + 4e-6f * a * a;
 }
 
 // The same bound over the corpus points of norm at most amax_cap only (a
@@ -371,13 +396,13 @@ __device__ __forceinline__ float key_error_bound(float4 st, const unsigned *gmax
 // ||x - hi|| <= 2^-9 ||x|| and ||lo|| <= 2^-8 ||x|| (round to nearest, 8
 // significand bits), plus a tiny absolute term for subnormal values.
 __device__ __forceinline__ float key_error_bound_capped(float4 st, const unsigned *gmax, float acc_coef,
-                                                        float amax_cap) {
+                                                        float sq_coef, float amax_cap) {
     const float amax = fminf(__uint_as_float(gmax[0]), amax_cap);
     const float rmax = fminf(__uint_as_float(gmax[1]), 0x1p-9f * amax + 1e-30f);
     const float lmax = fminf(__uint_as_float(gmax[2]), 0x1p-8f * amax + 1e-30f);
     const float a = st.x, r = st.y, l = st.z;
     const float drop = l * lmax + r * amax + a * rmax;
-    return 2.f * drop + acc_coef * a * amax + 4e-6f * (a * a + amax * amax);
+    return 2.f * drop + acc_coef * a * amax + (4e-6f + sq_coef) * amax * amax + 4e-6f * a * a;
 }
 
 // First column of the ti-th column tile of a work unit.
@@ -405,6 +430,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             mbar_init(&s.acc_empty[i], 32 * C::NEPI);
         }
         mbar_init(&s.drain, 1);
+        mbar_init(&s.ext_bar, 1);
         s.abort_flag = 0;
         s.zero = 0;
         fence_mbar_init();
@@ -418,6 +444,10 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
         if (PASSES == 3) {
             tma_prefetch_desc(&p.tm_a_lo);
             tma_prefetch_desc(&p.tm_b_lo);
+        }
+        if (C::FOLD) {
+            tma_prefetch_desc(&p.tm_a_ext);
+            tma_prefetch_desc(&p.tm_b_ext);
         }
     }
     __syncthreads();
@@ -440,6 +470,10 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             uint32_t armed_phase[C::MAX_STAGES];
             bool armed[C::MAX_STAGES];
             for (int i = 0; i < C::MAX_STAGES; ++i) armed[i] = false;
+            if (C::FOLD) {  // the constant query slice, once
+                mbar_arrive_expect_tx(&s.ext_bar, C::EXT_A_BYTES);
+                tma_load_2d(s.a_ext, &p.tm_a_ext, 0, 0, &s.ext_bar);
+            }
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
                 const int rt = u % p.row_tiles, sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
@@ -453,11 +487,14 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                             break;
                         }
                         unsigned char *st = &s.stage[0][0] + stage * sbytes;
-                        mbar_arrive_expect_tx(&s.full[stage], sbytes);
+                        // the tile's norm pieces travel with its last k-block
+                        const bool ext = C::FOLD && kb + 1 == p.KB;
+                        mbar_arrive_expect_tx(&s.full[stage], sbytes - (ext ? 0 : C::EXT_B_BYTES));
                         armed[stage] = true;
                         armed_phase[stage] = phase;
                         tma_load_2d(st, &p.tm_a_hi, kb * C::KE, rt * TC_BM, &s.full[stage]);
                         tma_load_2d(st + C::A_BYTES, &p.tm_b_hi, kb * C::KE, (int)ct, &s.full[stage]);
+                        if (ext) tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.tm_b_ext, 0, (int)ct, &s.full[stage]);
                         if (PASSES == 3 && lo_on) {
                             tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.tm_a_lo, kb * TC_BK,
                                         rt * TC_BM, &s.full[stage]);
@@ -478,6 +515,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 for (int i = 0; i < nst; ++i)
                     if (armed[i]) mbar_wait(&s.full[i], armed_phase[i], &s.zero, WAIT_NS);
             }
+            if (C::FOLD) mbar_wait(&s.ext_bar, 0, &s.zero, WAIT_NS);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -486,6 +524,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             int stage = 0, acc = 0;
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
+            if (C::FOLD && !mbar_wait(&s.ext_bar, 0, &s.abort_flag, p.wait_ns)) ok = false;
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
                 const int sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
@@ -523,6 +562,9 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                                          sw128_kmajor_desc(b_hi + 32 * k), idesc, 1u);
                             }
                         }
+                        if (C::FOLD && kb + 1 == p.KB)  // the norms: -1/2 (h1 + h2 + h3) per column
+                            mma_bf16(d, sw32_kmajor_desc(smem_u32(s.a_ext)), sw32_kmajor_desc(b_hi + C::B_BYTES),
+                                     idesc, 1u);
                         mma_commit(&s.empty[stage]);
                         if (++stage == nst) {
                             stage = 0;
@@ -625,7 +667,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     // query, so their norms are at most ||x|| + sqrt(rad)
                     const float4 qs = cross ? p.qst[row] : p.st[qid];
                     const float widen =
-                        2.f * key_error_bound_capped(qs, p.gmax, p.acc_coef,
+                        2.f * key_error_bound_capped(qs, p.gmax, p.acc_coef, p.sq_coef,
                                                      qs.x + sqrtf(fmaxf(rad, 0.f)) * (1.f + 1e-6f) + 1e-30f) +
                         1e-6f * (fabsf(rad) + nx);
                     tau = fminf(tau, rad - nx + widen);
@@ -656,7 +698,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
 #pragma unroll
             for (int q = 0; q < NCH; ++q) {
                 const int64_t cc = unit_tile_col(c0, 0) + half * CW + q * 32 + lane;
-                nyn[q] = cc < c1 ? p.nrm[cc] : INFINITY;
+                nyn[q] = !C::FOLD && cc < c1 ? p.nrm[cc] : INFINITY;
                 if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
             }
             // FP8: x_i . x_j ~ s_i s_j (q_i . q_j); the row's scale, the
@@ -681,7 +723,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     nyc[q] = nyn[q];
                     msc[q] = msn[q];
                 }
-                if (ti + 1 < ntl) {
+                if (!C::FOLD && ti + 1 < ntl) {
                     const int64_t cn = unit_tile_col(c0, ti + 1);
 #pragma unroll
                     for (int q = 0; q < NCH; ++q) {
@@ -723,14 +765,17 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     // the previous chunk's __syncwarp
                     float *nyw = s.ny[e][c & 1];
                     float *msw = s.ms[PASSES == 8 ? e : 0][c & 1];
-                    nyw[lane] = nyc[c];
+                    if (!C::FOLD) nyw[lane] = nyc[c];
                     if (PASSES == 8) msw[lane] = msc[c];
                     tmem_ld_wait(r);
                     if (c + 1 < NCH) tmem_ld32(taddr + (uint32_t)((c + 1) * 32), rn);
                     __syncwarp();
                     // keys two at a time (packed FP32), each key's survivor bit
                     // the sign of key - tau (exact: a difference of two floats
-                    // is negative exactly when the first is smaller)
+                    // is negative exactly when the first is smaller). With the
+                    // norms folded in, key - tau is one packed FMA of the
+                    // accumulator (-2 acc - tau, -2 acc exact) and a survivor's
+                    // key is -2 times its accumulator value.
                     float kk[32];
                     uint32_t mask = 0;
                     const float4 *ny4 = reinterpret_cast<const float4 *>(nyw);
@@ -738,9 +783,21 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     float dd[32];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const float4 n4 = ny4[q];
                         float2 a01 = make_float2(__uint_as_float(r[4 * q + 0]), __uint_as_float(r[4 * q + 1]));
                         float2 a23 = make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                        if (C::FOLD) {
+                            const float2 d01 = __ffma2_rn(m2, a01, ntau), d23 = __ffma2_rn(m2, a23, ntau);
+                            kk[4 * q + 0] = a01.x;
+                            kk[4 * q + 1] = a01.y;
+                            kk[4 * q + 2] = a23.x;
+                            kk[4 * q + 3] = a23.y;
+                            dd[4 * q + 0] = d01.x;
+                            dd[4 * q + 1] = d01.y;
+                            dd[4 * q + 2] = d23.x;
+                            dd[4 * q + 3] = d23.y;
+                            continue;
+                        }
+                        const float4 n4 = ny4[q];
                         float2 k01, k23;
                         if (PASSES == 8) {
                             const float4 g4 = ms4[q];
@@ -770,6 +827,10 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     mask = mq[0] | (mq[1] << 8) | (mq[2] << 16) | (mq[3] << 24);
                     const int so = self_off - c * 32;
                     if (so >= 0 && so < 32) mask &= ~(1u << so);
+                    if (C::FOLD) {  // columns past the corpus (their accumulators read 0)
+                        const int64_t vc = c1 - (int64_t)(colb0 + c * 32);
+                        if (vc < 32) mask &= vc <= 0 ? 0u : (1u << vc) - 1u;
+                    }
                     if (__any_sync(0xffffffffu, mask != 0)) {
                         // walk this row's survivors one per step (a chunk rarely
                         // holds more than one or two of a row's): the warp takes
@@ -799,7 +860,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                             for (int i = 0; i < 4; ++i) t4[i] = (j0 & 4) ? t8[2 * i + 1] : t8[2 * i];
 #pragma unroll
                             for (int i = 0; i < 2; ++i) t2[i] = (j0 & 8) ? t4[2 * i + 1] : t4[2 * i];
-                            const float key = (j0 & 16) ? t2[1] : t2[0];
+                            const float key = C::FOLD ? -2.f * ((j0 & 16) ? t2[1] : t2[0]) : ((j0 & 16) ? t2[1] : t2[0]);
                             const int col = colb + j0;
                             if (rmode) {  // no compaction: a full buffer sends the row to the fallback
                                 if (has) {
@@ -976,7 +1037,8 @@ struct MergeParams {
     const float *qnrm;
     const float4 *qstats;
     const unsigned *gmax;
-    float acc_coef;        // (passes * Dp / 16 + 8) * 2^-21
+    float acc_coef;        // (K steps of 16 + 8) * 2^-21
+    float sq_coef;         // folded norms: acc_coef / 2, else 0
     int32_t *idx_out;
     float *d2_out;
     int32_t *flag_rows;
@@ -987,7 +1049,7 @@ struct MergeParams {
 // the terms the BF16 copies drop (Cauchy-Schwarz on the residual norms), the
 // FP32 accumulation of the products, and the FP32 norms.
 __device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st) {
-    return key_error_bound(st, p.gmax, p.acc_coef);
+    return key_error_bound(st, p.gmax, p.acc_coef, p.sq_coef);
 }
 
 // CERT (FP32 and BF16 modes): the k nearest, certified exact or sent to the
@@ -1164,7 +1226,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dk0 = fmaxf(dk0, __shfl_xor_sync(0xffffffffu, dk0, o));
             const float4 st = cross ? p.qstats[row] : p.stats[qid];
-            Ec = fminf(E, key_error_bound_capped(st, p.gmax, p.acc_coef,
+            Ec = fminf(E, key_error_bound_capped(st, p.gmax, p.acc_coef, p.sq_coef,
                                                   st.x + sqrtf(dk0) * (1.f + 1e-6f) + 1e-30f));
             collect(theta, theta + 2.f * Ec);
             if (nr > RC) good = false;
@@ -1317,6 +1379,28 @@ atsne_status make_bf16_map(CUtensorMap *m, const void *base, int64_t rows, int D
     return ATSNE_OK;
 }
 
+// Rows of 16 BF16 (32 bytes: the norm slices of the folded one-pass mode),
+// box_rows rows per copy in the 32-byte swizzle layout.
+atsne_status make_ext_map(CUtensorMap *m, const void *base, int64_t rows, int box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return set_error(ATSNE_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {16u, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {32u};
+    cuuint32_t box[2] = {16u, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(ATSNE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ATSNE_OK;
+}
+
+// The FP32 accumulation term of the key error bound: (K steps of 16 + 8) * 2^-21,
+// the folded norms adding one step in the one-pass BF16 mode.
+float acc_coef_of(const TcPlan &pl) {
+    return (float)((pl.passes * pl.Dp / 16 + (pl.passes == 1 ? 1 : 0) + 8) * (1.0 / (1 << 21)));
+}
+
 atsne_status make_u8_map(CUtensorMap *m, const void *base, int64_t rows, int Dp, int box_rows) {
     auto enc = tensor_map_encoder();
     if (!enc) return set_error(ATSNE_ECUDA, "cuTensorMapEncodeTiled unavailable");
@@ -1465,6 +1549,8 @@ size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcP
     w.row_hist = pl.splits > 1 ? c.take<unsigned>((size_t)Q * GH_BUCKETS) : nullptr;
     w.flag_rows = c.take<int32_t>((size_t)Q);
     w.flag_count = c.take<int32_t>(1);
+    w.bext = pl.passes == 1 ? c.take<uint16_t>((size_t)N * 16) : nullptr;
+    w.aext = pl.passes == 1 ? c.take<uint16_t>((size_t)TC_BM * 16) : nullptr;
     if (ws) *ws = w;
     return c.bytes();
 }
@@ -1503,13 +1589,16 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         auto *lo = reinterpret_cast<__nv_bfloat16 *>(w.lo);
         ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
                                 (const int32_t *)nullptr, N, N, D, pl.Dp, pl.passes, hi, lo, w.nrm,
-                                reinterpret_cast<float4 *>(w.stats), w.gmax, status));
+                                reinterpret_cast<float4 *>(w.stats), w.gmax,
+                                reinterpret_cast<__nv_bfloat16 *>(w.bext),
+                                reinterpret_cast<__nv_bfloat16 *>(w.aext), status));
         if (Xq) {
             ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(Q * 32, 256), 256, 0, stream, Xq,
                                     (const int32_t *)nullptr, Q, Q, D, pl.Dp, pl.passes,
                                     reinterpret_cast<__nv_bfloat16 *>(w.qhi),
                                     reinterpret_cast<__nv_bfloat16 *>(w.qlo), w.qnrm,
-                                    reinterpret_cast<float4 *>(w.qstats), (unsigned *)nullptr, status));
+                                    reinterpret_cast<float4 *>(w.qstats), (unsigned *)nullptr,
+                                    (__nv_bfloat16 *)nullptr, (__nv_bfloat16 *)nullptr, status));
             a_hi = w.qhi;
             a_lo = w.qlo;
         } else if (qlist) {
@@ -1517,7 +1606,8 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
                                     qlist, Q, N, D, pl.Dp, pl.passes,
                                     reinterpret_cast<__nv_bfloat16 *>(w.qhi),
                                     reinterpret_cast<__nv_bfloat16 *>(w.qlo), (float *)nullptr,
-                                    (float4 *)nullptr, (unsigned *)nullptr, status));
+                                    (float4 *)nullptr, (unsigned *)nullptr, (__nv_bfloat16 *)nullptr,
+                                    (__nv_bfloat16 *)nullptr, status));
             a_hi = w.qhi;
             a_lo = w.qlo;
         }
@@ -1530,6 +1620,13 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     } else {
         ATSNE_TRY(make_bf16_map(&p.tm_a_hi, a_hi, (qlist || Xq) ? Q : N, pl.Dp, TC_BM));
         ATSNE_TRY(make_bf16_map(&p.tm_b_hi, w.hi, N, pl.Dp, TC_BN));
+    }
+    if (pl.passes == 1) {
+        ATSNE_TRY(make_ext_map(&p.tm_a_ext, w.aext, TC_BM, TC_BM));
+        ATSNE_TRY(make_ext_map(&p.tm_b_ext, w.bext, N, TC_BN));
+    } else {
+        p.tm_a_ext = p.tm_a_hi;
+        p.tm_b_ext = p.tm_b_hi;
     }
     if (pl.passes == 3) {
         ATSNE_TRY(make_bf16_map(&p.tm_a_lo, a_lo, (qlist || Xq) ? Q : N, pl.Dp, TC_BM));
@@ -1545,7 +1642,8 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     p.hint = hint;
     p.qst = reinterpret_cast<const float4 *>(w.qstats);
     p.st = reinterpret_cast<const float4 *>(w.stats);
-    p.acc_coef = (float)((pl.passes * pl.Dp / 16 + 8) * (1.0 / (1 << 21)));
+    p.acc_coef = acc_coef_of(pl);
+    p.sq_coef = pl.passes == 1 ? 0.5f * p.acc_coef : 0.f;
     p.nrm = w.nrm;
     p.gmax = w.gmax;
     // queries that are corpus rows have the corpus' low halves
@@ -1599,7 +1697,8 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     m.qnrm = w.qnrm;
     m.qstats = reinterpret_cast<const float4 *>(w.qstats);
     m.gmax = w.gmax;
-    m.acc_coef = (float)((pl.passes * pl.Dp / 16 + 8) * (1.0 / (1 << 21)));
+    m.acc_coef = acc_coef_of(pl);
+    m.sq_coef = pl.passes == 1 ? 0.5f * m.acc_coef : 0.f;
     m.idx_out = idx_out;
     m.d2_out = d2_out;
     m.flag_rows = w.flag_rows;

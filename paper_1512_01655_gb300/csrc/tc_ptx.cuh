@@ -192,5 +192,14 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t smem_addr) {
            ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// The same for a K-major tile of 32-byte rows (16 BF16) written by TMA with
+// 32-byte swizzle: 8-row groups 256 bytes apart (stride byte offset), layout
+// type 6 (32-byte swizzle) in bits 61-63. One K = 16 BF16 MMA step reads a
+// whole row.
+__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t smem_addr) {
+    return (uint64_t)((smem_addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+}
+
 }  // namespace tc
 }  // namespace atsne
