@@ -405,6 +405,11 @@ __device__ __forceinline__ float key_error_bound_capped(float4 st, const unsigne
     return 2.f * drop + acc_coef * a * amax + (4e-6f + sq_coef) * amax * amax + 4e-6f * a * a;
 }
 
+// Fire-and-forget request of the 128-byte line holding p into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
+
 // First column of the ti-th column tile of a work unit.
 __device__ __forceinline__ int64_t unit_tile_col(int64_t c0, int64_t ti) { return c0 + ti * TC_BN; }
 
@@ -1105,6 +1110,13 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
         // smallest key theta lies among them and is selected there; otherwise
         // the buffers are walked again. Re-rank bands reaching above tau_min
         // are collected from the buffers.
+        // the row's buffers requested into L2 at once (the staging pass below
+        // walks them one 512-byte step at a time)
+        for (int u = 0; u < S; ++u) {
+            const int c = min(max(mt[u].x, 0), p.cap);
+            const char *bb = reinterpret_cast<const char *>(cb + (size_t)u * p.cap);
+            for (int o = lane * 128; o < c * (int)sizeof(Cand); o += 32 * 128) prefetch_l2(bb + o);
+        }
         const float E = CERT ? row_error_bound(p, cross ? p.qstats[row] : p.stats[qid]) : 0.f;
         const float slim = tau_min;  // the select needs no key above tau_min
         int ns = 0, nlt = 0;
@@ -1197,6 +1209,12 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
         // exact FP32 distances of rjw[from, to) in the library's one summation
         // order (group8_d2_pair), eight candidates per warp step
         auto rerank = [&](int from, int to) {
+            // every candidate row requested into L2 first (rows of at most
+            // 1 KB: longer ones gain less than the requests cost)
+            for (int t = from + lane; p.D <= 256 && t < to; t += 32) {
+                const char *xr = reinterpret_cast<const char *>(p.X + (int64_t)rjw[t] * p.D);
+                for (int o = 0; o < p.D * 4; o += 128) prefetch_l2(xr + o);
+            }
             const int g = lane >> 3, gl = lane & 7;
             for (int t0 = from; t0 < to; t0 += 8) {
                 const int ta = t0 + g, tb = t0 + 4 + g;
