@@ -549,7 +549,7 @@ def timed_steps(torch, fn, steps, stream, l2_flush=None):
     return [a.elapsed_time(b) for a, b in evs], out
 
 
-PROFILED = ["knn_prep", "knn_tc", "knn_tc_merge", "knn_fallback", "knn_bruteforce", "calibrate_beta",
+PROFILED = ["knn_order", "knn_prep", "knn_tc", "knn_tc_merge", "knn_fallback", "knn_bruteforce", "calibrate_beta",
             "sym_fwd", "sym_rev", "sym_len", "sym_write", "sym_sort_long", "sym_write_long",
             "scan_reduce", "scan_partials", "scan_down",
             "forest_traverse", "forest_traverse_u8", "forest_dist", "forest_dist_u8", "forest_u8_prep",

@@ -28,6 +28,18 @@ struct TcPlan {
     int halves = 1;  // candidate buffers per (row, split): one per column half of a tile
     bool certify = true;  // rows certified exact (else the ksel best keys re-ranked, approximate)
 };
+// Row and column order of a large self kNN (points grouped by nearest
+// centroid; each row tile streams its own groups' column tiles first).
+constexpr int64_t ORD_MIN_ROWS = 65536;
+constexpr int ORD_MAX_DIM = 256;
+struct OrderWs {
+    float *cent = nullptr, *cn = nullptr, *sum = nullptr;
+    int *cnt = nullptr;
+    int32_t *label = nullptr, *lab_sorted = nullptr;
+    int32_t *perm = nullptr;  // position in the order -> row
+    int32_t *bcnt = nullptr, *coff = nullptr;
+    int32_t *pro = nullptr;   // per row tile: first column tile of its groups, their count
+};
 struct TcWs {
     uint16_t *hi = nullptr, *lo = nullptr, *qhi = nullptr, *qlo = nullptr;
     float *nrm = nullptr, *stats = nullptr;
@@ -38,6 +50,8 @@ struct TcWs {
     float *qnrm = nullptr, *qstats = nullptr;   // queries from another array: norms, error stats
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
     uint16_t *bext = nullptr, *aext = nullptr;  // one-pass BF16: the norm slices
+    bool ordered = false;                       // rows and columns in the order of OrderWs
+    OrderWs ord;
 };
 // Limit of the tensor kernel's pipeline waits (process-wide; default 1 s).
 uint64_t pipeline_wait_ns();
@@ -51,6 +65,10 @@ void clear_tuned_splits();
 // Distinct column split counts worth timing for a shape (at most max_out).
 int tc_split_candidates(int64_t N, int D, int64_t Q, int k, int precision, int rerank_k, int *out, int max_out);
 size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcPlan &pl, TcWs *ws);
+bool knn_ordered(int64_t N, int D, bool list, const TcPlan &pl);
+size_t order_workspace(Carver &c, int64_t N, int D, const TcPlan &pl, OrderWs *ws);
+atsne_status knn_order_launch(const float *X, int64_t N, int D, const TcPlan &pl, int bm, int bn,
+                              const OrderWs &w, cudaStream_t stream);
 // Xq != nullptr: the Q queries are the rows of Xq (another array), none excluded.
 // radius != nullptr (with Xq): only neighbours with d^2 < radius[row] are kept,
 // the row padded with (-1, +inf); the plan's cap is then RADIUS_CAP.

@@ -137,6 +137,8 @@ struct __align__(1024) TcSmem {
 struct TcParams {
     CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;
     CUtensorMap tm_a_ext, tm_b_ext;  // one-pass BF16: the norm slices
+    const int32_t *pro;    // ordered rows and columns: per row tile, the first column tile of its
+                           // groups and their count (streamed first); nullptr: natural order
     const float *nrm;      // [N] corpus ||x||^2
     const float *scale;    // FP8: [N] corpus row scales (x ~ scale * q)
     const float *qscale;   // FP8 with a query list: [Q] query row scales
@@ -413,6 +415,16 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // First column of the ti-th column tile of a work unit.
 __device__ __forceinline__ int64_t unit_tile_col(int64_t c0, int64_t ti) { return c0 + ti * TC_BN; }
 
+// The same with the columns in the order of knn_order.cu (one split, c0 = 0):
+// row tile rt streams its groups' pn column tiles from ps first, then the
+// others in ascending order, so that the CTAs still walk the corpus together.
+__device__ __forceinline__ int64_t tile_col(const int32_t *pro, int rt, int64_t c0, int64_t ti) {
+    if (!pro) return unit_tile_col(c0, ti);
+    const int64_t ps = pro[2 * rt], pn = pro[2 * rt + 1];
+    const int64_t t = ti < pn ? ps + ti : (ti - pn < ps ? ti - pn : ti);
+    return c0 + t * TC_BN;
+}
+
 template <int PASSES>
 __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const __grid_constant__ TcParams p) {
     using C = TcCfg<PASSES>;
@@ -485,7 +497,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
                 const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
                 for (int64_t ti = 0; ti < ntl && ok; ++ti) {
-                    const int64_t ct = unit_tile_col(c0, ti);
+                    const int64_t ct = tile_col(p.pro, rt, c0, ti);
                     for (int kb = 0; kb < p.KB; ++kb) {
                         if (!mbar_wait(&s.empty[stage], phase ^ 1u, &s.abort_flag, p.wait_ns)) {
                             ok = false;
@@ -702,7 +714,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             float nyn[NCH], msn[NCH];
 #pragma unroll
             for (int q = 0; q < NCH; ++q) {
-                const int64_t cc = unit_tile_col(c0, 0) + half * CW + q * 32 + lane;
+                const int64_t cc = tile_col(p.pro, rt, c0, 0) + half * CW + q * 32 + lane;
                 nyn[q] = !C::FOLD && cc < c1 ? p.nrm[cc] : INFINITY;
                 if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
             }
@@ -721,7 +733,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             share_tau();
             const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
             for (int64_t ti = 0; ti < ntl; ++ti) {
-                const int64_t ct = unit_tile_col(c0, ti);
+                const int64_t ct = tile_col(p.pro, rt, c0, ti);
                 float nyc[NCH], msc[NCH];
 #pragma unroll
                 for (int q = 0; q < NCH; ++q) {
@@ -729,7 +741,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     msc[q] = msn[q];
                 }
                 if (!C::FOLD && ti + 1 < ntl) {
-                    const int64_t cn = unit_tile_col(c0, ti + 1);
+                    const int64_t cn = tile_col(p.pro, rt, c0, ti + 1);
 #pragma unroll
                     for (int q = 0; q < NCH; ++q) {
                         const int64_t cc = cn + half * CW + q * 32 + lane;
@@ -1033,6 +1045,9 @@ struct MergeParams {
     int splits, cap;
     int64_t Q, N;
     const int32_t *qlist;
+    // ordered rows and columns (knn_order.cu): position -> row; the kernel's
+    // rows, norms and candidate columns are positions, the outputs rows
+    const int32_t *perm;
     const float *X;
     int D, k, ksel;
     int rc, mst;            // re-rank set and staged keys per row (shared memory)
@@ -1083,6 +1098,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
     if (row >= p.Q) return;
     const bool cross = p.Xq != nullptr;
     const int qid = cross ? (int)row : (p.qlist ? p.qlist[row] : (int)row);
+    const int64_t orow = p.perm ? p.perm[row] : row;  // the output row (and the query's row of X)
     const int S = p.splits;
     const Cand *cb = p.cand + (size_t)row * S * p.cap;
     const int4 *mt = p.meta + (size_t)row * S;
@@ -1180,7 +1196,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
         auto take_batch = [&](bool take, int idx) {
             const unsigned tm = __ballot_sync(0xffffffffu, take);
             const int pos = nr + __popc(tm & lanemask_lt());
-            if (take && pos < RC) rjw[pos] = idx;
+            if (take && pos < RC) rjw[pos] = p.perm ? p.perm[idx] : idx;
             nr += __popc(tm);
         };
         auto collect = [&](float lo, float hi) {  // keys in (lo, hi]
@@ -1203,7 +1219,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
                 }
             }
         };
-        const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (int64_t)qid * p.D;
+        const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (p.perm ? orow : (int64_t)qid) * p.D;
         const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
                           (reinterpret_cast<uintptr_t>(xq) & 15) == 0;
         // exact FP32 distances of rjw[from, to) in the library's one summation
@@ -1278,11 +1294,11 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
     }
     if (good) {
         for (int t = lane; t < p.k; t += 32) {
-            p.idx_out[row * p.k + t] = rjw[t];
-            p.d2_out[row * p.k + t] = rdw[t];
+            p.idx_out[orow * p.k + t] = rjw[t];
+            p.d2_out[orow * p.k + t] = rdw[t];
         }
     } else if (lane == 0) {
-        p.flag_rows[atomicAdd(p.flag_count, 1)] = (int)row;
+        p.flag_rows[atomicAdd(p.flag_count, 1)] = (int)orow;
     }
 }
 
@@ -1569,6 +1585,8 @@ size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcP
     w.flag_count = c.take<int32_t>(1);
     w.bext = pl.passes == 1 ? c.take<uint16_t>((size_t)N * 16) : nullptr;
     w.aext = pl.passes == 1 ? c.take<uint16_t>((size_t)TC_BM * 16) : nullptr;
+    w.ordered = knn_ordered(N, D, list, pl);
+    if (w.ordered) order_workspace(c, N, D, pl, &w.ord);
     if (ws) *ws = w;
     return c.bytes();
 }
@@ -1587,10 +1605,12 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     if (e != cudaSuccess) return cuda_error(e, "knn_tc memset");
     const bool fp8 = pl.passes == 8;
     const void *a_hi = w.hi, *a_lo = w.lo;
+    const bool ordered = w.ordered && !qlist && !Xq;
     if (fp8) {
+        if (ordered) ATSNE_TRY(knn_order_launch(X, N, D, pl, TC_BM, TC_BN, w.ord, stream));
         ATSNE_TRY(launch_kernel("knn_prep", knn_prep_fp8_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
-                                (const int32_t *)nullptr, N, N, D, pl.Dp, w.hi, w.scale, w.nrm, w.gmax,
-                                status));
+                                ordered ? (const int32_t *)w.ord.perm : (const int32_t *)nullptr, N, N, D,
+                                pl.Dp, w.hi, w.scale, w.nrm, w.gmax, status));
         if (Xq) {
             ATSNE_TRY(launch_kernel("knn_prep", knn_prep_fp8_kernel, ceil_div(Q * 32, 256), 256, 0, stream,
                                     Xq, (const int32_t *)nullptr, Q, Q, D, pl.Dp, w.qhi, w.qscale, w.qnrm,
@@ -1605,8 +1625,11 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     } else {
         auto *hi = reinterpret_cast<__nv_bfloat16 *>(w.hi);
         auto *lo = reinterpret_cast<__nv_bfloat16 *>(w.lo);
+        // ordered rows and columns: the copies, norms and statistics in the order
+        if (ordered) ATSNE_TRY(knn_order_launch(X, N, D, pl, TC_BM, TC_BN, w.ord, stream));
         ATSNE_TRY(launch_kernel("knn_prep", knn_prep_kernel, ceil_div(N * 32, 256), 256, 0, stream, X,
-                                (const int32_t *)nullptr, N, N, D, pl.Dp, pl.passes, hi, lo, w.nrm,
+                                ordered ? (const int32_t *)w.ord.perm : (const int32_t *)nullptr, N, N, D,
+                                pl.Dp, pl.passes, hi, lo, w.nrm,
                                 reinterpret_cast<float4 *>(w.stats), w.gmax,
                                 reinterpret_cast<__nv_bfloat16 *>(w.bext),
                                 reinterpret_cast<__nv_bfloat16 *>(w.aext), status));
@@ -1658,6 +1681,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     p.qnrm = Xq ? w.qnrm : nullptr;
     p.radius = radius;
     p.hint = hint;
+    p.pro = ordered ? w.ord.pro : nullptr;
     p.qst = reinterpret_cast<const float4 *>(w.qstats);
     p.st = reinterpret_cast<const float4 *>(w.stats);
     p.acc_coef = acc_coef_of(pl);
@@ -1706,6 +1730,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     m.Q = Q;
     m.N = N;
     m.qlist = qlist;
+    m.perm = ordered ? w.ord.perm : nullptr;
     m.X = X;
     m.D = D;
     m.k = k;
