@@ -19,6 +19,7 @@ namespace atsne {
 namespace {
 
 constexpr int ORD_C = 64;          // centroids
+constexpr int ORD_CC = 64;         // centroids per pass of the assignment
 constexpr int ORD_SAMPLE = 32768;  // rows of the Lloyd iterations
 constexpr int ORD_ITERS = 4;
 constexpr int ORD_BLK = 1024;      // rows per block of the counting sort
@@ -43,47 +44,49 @@ __global__ void ord_norm_kernel(const float *__restrict__ cent, int D, float *__
 
 // label[i] = the centroid nearest to row i * stride (i < n): the smallest
 // ||c||^2 - 2 x.c, ties to the lower centroid. One thread per row; the
-// centroids pass through shared memory ORD_DC dimensions at a time.
+// centroids, ORD_CC at a time, pass through shared memory ORD_DC dimensions
+// at a time.
 __global__ void __launch_bounds__(256) ord_assign_kernel(const float *__restrict__ X, int64_t n, int64_t stride,
                                                          int D, const float *__restrict__ cent,
                                                          const float *__restrict__ cn, int32_t *__restrict__ label) {
-    __shared__ float cs[ORD_C][ORD_DC];
+    __shared__ float cs[ORD_CC][ORD_DC];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < n;
     const float *x = X + (live ? i * stride : 0) * D;
-    float acc[ORD_C];
-#pragma unroll
-    for (int c = 0; c < ORD_C; ++c) acc[c] = 0.f;
-    for (int d0 = 0; d0 < D; d0 += ORD_DC) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < ORD_C * ORD_DC; t += blockDim.x) {
-            const int c = t / ORD_DC, d = d0 + (t - c * ORD_DC);
-            cs[c][t - c * ORD_DC] = d < D ? cent[c * D + d] : 0.f;
-        }
-        __syncthreads();
-        float xv[ORD_DC];
-#pragma unroll
-        for (int j = 0; j < ORD_DC; ++j) xv[j] = d0 + j < D ? x[d0 + j] : 0.f;
-#pragma unroll
-        for (int c = 0; c < ORD_C; ++c) {
-            float a = acc[c];
-#pragma unroll
-            for (int j = 0; j < ORD_DC; ++j) a = fmaf(xv[j], cs[c][j], a);
-            acc[c] = a;
-        }
-    }
-    if (!live) return;
     int best = 0;
-    float bv = cn[0] - 2.f * acc[0];
+    float bv = INFINITY;
+    for (int cb = 0; cb < ORD_C; cb += ORD_CC) {
+        float acc[ORD_CC];
 #pragma unroll
-    for (int c = 1; c < ORD_C; ++c) {
-        const float v = cn[c] - 2.f * acc[c];
-        if (v < bv) {
-            bv = v;
-            best = c;
+        for (int c = 0; c < ORD_CC; ++c) acc[c] = 0.f;
+        for (int d0 = 0; d0 < D; d0 += ORD_DC) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < ORD_CC * ORD_DC; t += blockDim.x) {
+                const int c = t / ORD_DC, d = d0 + (t - c * ORD_DC);
+                cs[c][t - c * ORD_DC] = d < D ? cent[(cb + c) * D + d] : 0.f;
+            }
+            __syncthreads();
+            float xv[ORD_DC];
+#pragma unroll
+            for (int j = 0; j < ORD_DC; ++j) xv[j] = d0 + j < D ? x[d0 + j] : 0.f;
+#pragma unroll
+            for (int c = 0; c < ORD_CC; ++c) {
+                float a = acc[c];
+#pragma unroll
+                for (int j = 0; j < ORD_DC; ++j) a = fmaf(xv[j], cs[c][j], a);
+                acc[c] = a;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < ORD_CC; ++c) {
+            const float v = cn[cb + c] - 2.f * acc[c];
+            if (v < bv) {
+                bv = v;
+                best = cb + c;
+            }
         }
     }
-    label[i] = best;
+    if (live) label[i] = best;
 }
 
 // sums and counts of the sample rows per centroid, one warp per row
