@@ -51,6 +51,7 @@ struct TcWs {
     int32_t *flag_rows = nullptr, *flag_count = nullptr;
     uint16_t *bext = nullptr, *aext = nullptr;  // one-pass BF16: the norm slices
     bool ordered = false;                       // rows and columns in the order of OrderWs
+    unsigned long long *clock = nullptr;        // one split: tiles issued by all CTAs
     OrderWs ord;
 };
 // Limit of the tensor kernel's pipeline waits (process-wide; default 1 s).

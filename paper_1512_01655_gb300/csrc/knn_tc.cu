@@ -129,6 +129,10 @@ struct __align__(1024) TcSmem {
     uint64_t acc_empty[2];
     uint64_t drain;
     uint64_t ext_bar;  // the constant query slice has landed
+    // each unit's first column tile of the main stream, from the producer to
+    // the epilogue (a ring of four units, one barrier each)
+    uint64_t unit_bar[4];
+    uint32_t unit_start[4];
     uint32_t tmem_base;
     int abort_flag;
     int zero;
@@ -139,6 +143,7 @@ struct TcParams {
     CUtensorMap tm_a_ext, tm_b_ext;  // one-pass BF16: the norm slices
     const int32_t *pro;    // ordered rows and columns: per row tile, the first column tile of its
                            // groups and their count (streamed first); nullptr: natural order
+    unsigned long long *clock;  // tiles issued by all CTAs (one split): where a unit's stream starts
     const float *nrm;      // [N] corpus ||x||^2
     const float *scale;    // FP8: [N] corpus row scales (x ~ scale * q)
     const float *qscale;   // FP8 with a query list: [Q] query row scales
@@ -415,13 +420,25 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // First column of the ti-th column tile of a work unit.
 __device__ __forceinline__ int64_t unit_tile_col(int64_t c0, int64_t ti) { return c0 + ti * TC_BN; }
 
-// The same with the columns in the order of knn_order.cu (one split, c0 = 0):
-// row tile rt streams its groups' pn column tiles from ps first, then the
-// others in ascending order, so that the CTAs still walk the corpus together.
-__device__ __forceinline__ int64_t tile_col(const int32_t *pro, int rt, int64_t c0, int64_t ti) {
-    if (!pro) return unit_tile_col(c0, ti);
-    const int64_t ps = pro[2 * rt], pn = pro[2 * rt + 1];
-    const int64_t t = ti < pn ? ps + ti : (ti - pn < ps ? ti - pn : ti);
+// With one split the CTAs walk the corpus together: a unit's stream starts at
+// s0, the tile the CTAs have reached on average (the global count of issued
+// tiles over the grid, modulo the unit's ntl tiles) and wraps around, so that
+// units that start at different times still read the same tiles at the same
+// time, which L2 then holds for all of them. With the columns in the order of
+// knn_order.cu, row tile rt first streams its groups' pn column tiles from ps,
+// then the others from s0 (moved past them if it falls among them). Any order
+// gives the same result; only the filter's work and the DRAM traffic change.
+__device__ __forceinline__ int64_t tile_col(const int32_t *pro, int rt, int64_t s0, int64_t c0, int64_t ntl,
+                                            int64_t ti) {
+    if (!pro && s0 == 0) return unit_tile_col(c0, ti);
+    const int64_t ps = pro ? pro[2 * rt] : 0, pn = pro ? pro[2 * rt + 1] : 0;
+    if (ti < pn) return c0 + (ps + ti) * TC_BN;
+    const int64_t j = ti - pn;
+    int64_t st = s0;
+    if (st >= ps && st < ps + pn) st = ps + pn == ntl ? 0 : ps + pn;
+    const int64_t e0 = ps - st >= 0 ? ps - st : ps - st + ntl;  // the groups' tiles, counted from st
+    int64_t t = st + (j < e0 ? j : j + pn);
+    if (t >= ntl) t -= ntl;
     return c0 + t * TC_BN;
 }
 
@@ -448,6 +465,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
         }
         mbar_init(&s.drain, 1);
         mbar_init(&s.ext_bar, 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&s.unit_bar[i], 1);
         s.abort_flag = 0;
         s.zero = 0;
         fence_mbar_init();
@@ -491,13 +509,20 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 mbar_arrive_expect_tx(&s.ext_bar, C::EXT_A_BYTES);
                 tma_load_2d(s.a_ext, &p.tm_a_ext, 0, 0, &s.ext_bar);
             }
-            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            int un = 0;  // units begun by this CTA
+            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++un) {
                 const int rt = u % p.row_tiles, sp = u / p.row_tiles;
                 const int64_t c0 = (int64_t)sp * p.cols_per_split;
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
                 const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
+                int64_t s0 = 0;
+                if (p.clock) {
+                    s0 = (int64_t)((*(volatile unsigned long long *)p.clock / gridDim.x) % (unsigned long long)ntl);
+                    s.unit_start[un & 3] = (uint32_t)s0;
+                    mbar_arrive(&s.unit_bar[un & 3]);
+                }
                 for (int64_t ti = 0; ti < ntl && ok; ++ti) {
-                    const int64_t ct = tile_col(p.pro, rt, c0, ti);
+                    const int64_t ct = tile_col(p.pro, rt, s0, c0, ntl, ti);
                     for (int kb = 0; kb < p.KB; ++kb) {
                         if (!mbar_wait(&s.empty[stage], phase ^ 1u, &s.abort_flag, p.wait_ns)) {
                             ok = false;
@@ -512,6 +537,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                         tma_load_2d(st, &p.tm_a_hi, kb * C::KE, rt * TC_BM, &s.full[stage]);
                         tma_load_2d(st + C::A_BYTES, &p.tm_b_hi, kb * C::KE, (int)ct, &s.full[stage]);
                         if (ext) tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.tm_b_ext, 0, (int)ct, &s.full[stage]);
+                        if (p.clock && kb == 0) atomicAdd(p.clock, 1ull);
                         if (PASSES == 3 && lo_on) {
                             tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.tm_a_lo, kb * TC_BK,
                                         rt * TC_BM, &s.full[stage]);
@@ -624,10 +650,25 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
-        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        int un = 0;  // units begun by this CTA
+        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++un) {
             const int rt = u % p.row_tiles, sp = u / p.row_tiles;
             const int64_t c0 = (int64_t)sp * p.cols_per_split;
             const int64_t c1 = min(p.N, c0 + p.cols_per_split);
+            const int64_t ntl_u = (c1 - c0 + TC_BN - 1) / TC_BN;
+            int64_t s0 = 0;  // where the producer started this unit's stream
+            if (p.clock) {
+                ok = mbar_wait(&s.unit_bar[un & 3], (uint32_t)((un >> 2) & 1), &s.abort_flag, p.wait_ns);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    if (lane == 0) {
+                        s.abort_flag = 1;
+                        raise_status(p.status, DEV_TIMEOUT);
+                    }
+                    break;
+                }
+                s0 = s.unit_start[un & 3];
+            }
             const int64_t row = (int64_t)rt * TC_BM + quarter * 32 + lane;
             const bool cross = p.qnrm != nullptr;  // queries from another array than the corpus
             const int qraw = row < p.Q ? (cross ? (int)row : (p.qlist ? p.qlist[row] : (int)row)) : -1;
@@ -714,7 +755,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             float nyn[NCH], msn[NCH];
 #pragma unroll
             for (int q = 0; q < NCH; ++q) {
-                const int64_t cc = tile_col(p.pro, rt, c0, 0) + half * CW + q * 32 + lane;
+                const int64_t cc = tile_col(p.pro, rt, s0, c0, ntl_u, 0) + half * CW + q * 32 + lane;
                 nyn[q] = !C::FOLD && cc < c1 ? p.nrm[cc] : INFINITY;
                 if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
             }
@@ -733,7 +774,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             share_tau();
             const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
             for (int64_t ti = 0; ti < ntl; ++ti) {
-                const int64_t ct = tile_col(p.pro, rt, c0, ti);
+                const int64_t ct = tile_col(p.pro, rt, s0, c0, ntl_u, ti);
                 float nyc[NCH], msc[NCH];
 #pragma unroll
                 for (int q = 0; q < NCH; ++q) {
@@ -741,7 +782,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     msc[q] = msn[q];
                 }
                 if (!C::FOLD && ti + 1 < ntl) {
-                    const int64_t cn = tile_col(p.pro, rt, c0, ti + 1);
+                    const int64_t cn = tile_col(p.pro, rt, s0, c0, ntl_u, ti + 1);
 #pragma unroll
                     for (int q = 0; q < NCH; ++q) {
                         const int64_t cc = cn + half * CW + q * 32 + lane;
@@ -1586,6 +1627,10 @@ size_t tc_workspace(Carver &c, int64_t N, int D, int64_t Q, bool list, const TcP
     w.bext = pl.passes == 1 ? c.take<uint16_t>((size_t)N * 16) : nullptr;
     w.aext = pl.passes == 1 ? c.take<uint16_t>((size_t)TC_BM * 16) : nullptr;
     w.ordered = knn_ordered(N, D, list, pl);
+    // the global column clock where many units stream a corpus larger than L2
+    // on short rows (longer rows keep the natural start; the contraction, not
+    // the copies, sets their pace)
+    w.clock = pl.splits == 1 && N >= ORD_MIN_ROWS && D <= ORD_MAX_DIM ? c.take<unsigned long long>(1) : nullptr;
     if (w.ordered) order_workspace(c, N, D, pl, &w.ord);
     if (ws) *ws = w;
     return c.bytes();
@@ -1597,6 +1642,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     int *status = device_status_word();
     cudaError_t e = cudaMemsetAsync(w.gmax, 0, 4 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.flag_count, 0, sizeof(int32_t), stream);
+    if (e == cudaSuccess && w.clock) e = cudaMemsetAsync(w.clock, 0, sizeof(unsigned long long), stream);
     if (e == cudaSuccess && w.row_hist)
         e = cudaMemsetAsync(w.row_hist, 0, (size_t)Q * GH_BUCKETS * sizeof(unsigned), stream);
     // a unit that a timed-out kernel never finished reads as an empty buffer
@@ -1682,6 +1728,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     p.radius = radius;
     p.hint = hint;
     p.pro = ordered ? w.ord.pro : nullptr;
+    p.clock = w.clock;
     p.qst = reinterpret_cast<const float4 *>(w.qstats);
     p.st = reinterpret_cast<const float4 *>(w.stats);
     p.acc_coef = acc_coef_of(pl);
