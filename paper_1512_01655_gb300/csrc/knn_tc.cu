@@ -978,13 +978,13 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     if (nt < top) {
                         top = nt;
                         recount();
-                        since = 16;
+                        since = 32;
                     }
                 }
                 // lower tau to the upper edge of the bucket holding the ksel-th
                 // distance, th to that of the bucket holding the kh-th; the
-                // warp updates together once any lane has 16 new survivors
-                if (__any_sync(0xffffffffu, since >= 16 && cnt >= kh) && since > 0 && cnt >= kh) {
+                // warp updates together once any lane has 32 new survivors
+                if (__any_sync(0xffffffffu, since >= 32 && cnt >= kh) && since > 0 && cnt >= kh) {
                     uint32_t hw[NBUCKET / 2];
 #pragma unroll
                     for (int bw = 0; bw < NBUCKET / 2; ++bw) hw[bw] = dh[bw * 32];
