@@ -428,10 +428,10 @@ __device__ __forceinline__ int64_t unit_tile_col(int64_t c0, int64_t ti) { retur
 // knn_order.cu, row tile rt first streams its groups' pn column tiles from ps,
 // then the others from s0 (moved past them if it falls among them). Any order
 // gives the same result; only the filter's work and the DRAM traffic change.
-__device__ __forceinline__ int64_t tile_col(const int32_t *pro, int rt, int64_t s0, int64_t c0, int64_t ntl,
+// ps, pn: the unit's first group tile and group tile count (0, 0 without the order).
+__device__ __forceinline__ int64_t tile_col(int64_t ps, int64_t pn, int64_t s0, int64_t c0, int64_t ntl,
                                             int64_t ti) {
-    if (!pro && s0 == 0) return unit_tile_col(c0, ti);
-    const int64_t ps = pro ? pro[2 * rt] : 0, pn = pro ? pro[2 * rt + 1] : 0;
+    if (pn == 0 && s0 == 0) return unit_tile_col(c0, ti);
     if (ti < pn) return c0 + (ps + ti) * TC_BN;
     const int64_t j = ti - pn;
     int64_t st = s0;
@@ -516,13 +516,14 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                 const int64_t c1 = min(p.N, c0 + p.cols_per_split);
                 const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
                 int64_t s0 = 0;
+                const int64_t ps = p.pro ? p.pro[2 * rt] : 0, pn = p.pro ? p.pro[2 * rt + 1] : 0;
                 if (p.clock) {
                     s0 = (int64_t)((*(volatile unsigned long long *)p.clock / gridDim.x) % (unsigned long long)ntl);
                     s.unit_start[un & 3] = (uint32_t)s0;
                     mbar_arrive(&s.unit_bar[un & 3]);
                 }
                 for (int64_t ti = 0; ti < ntl && ok; ++ti) {
-                    const int64_t ct = tile_col(p.pro, rt, s0, c0, ntl, ti);
+                    const int64_t ct = tile_col(ps, pn, s0, c0, ntl, ti);
                     for (int kb = 0; kb < p.KB; ++kb) {
                         if (!mbar_wait(&s.empty[stage], phase ^ 1u, &s.abort_flag, p.wait_ns)) {
                             ok = false;
@@ -657,6 +658,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             const int64_t c1 = min(p.N, c0 + p.cols_per_split);
             const int64_t ntl_u = (c1 - c0 + TC_BN - 1) / TC_BN;
             int64_t s0 = 0;  // where the producer started this unit's stream
+            const int64_t ps = p.pro ? p.pro[2 * rt] : 0, pn = p.pro ? p.pro[2 * rt + 1] : 0;
             if (p.clock) {
                 ok = mbar_wait(&s.unit_bar[un & 3], (uint32_t)((un >> 2) & 1), &s.abort_flag, p.wait_ns);
                 ok = __all_sync(0xffffffffu, ok);
@@ -755,7 +757,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             float nyn[NCH], msn[NCH];
 #pragma unroll
             for (int q = 0; q < NCH; ++q) {
-                const int64_t cc = tile_col(p.pro, rt, s0, c0, ntl_u, 0) + half * CW + q * 32 + lane;
+                const int64_t cc = tile_col(ps, pn, s0, c0, ntl_u, 0) + half * CW + q * 32 + lane;
                 nyn[q] = !C::FOLD && cc < c1 ? p.nrm[cc] : INFINITY;
                 if (PASSES == 8) msn[q] = cc < c1 ? -2.f * p.scale[cc] : 0.f;
             }
@@ -774,7 +776,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
             share_tau();
             const int64_t ntl = (c1 - c0 + TC_BN - 1) / TC_BN;
             for (int64_t ti = 0; ti < ntl; ++ti) {
-                const int64_t ct = tile_col(p.pro, rt, s0, c0, ntl_u, ti);
+                const int64_t ct = tile_col(ps, pn, s0, c0, ntl_u, ti);
                 float nyc[NCH], msc[NCH];
 #pragma unroll
                 for (int q = 0; q < NCH; ++q) {
@@ -782,7 +784,7 @@ __global__ void __launch_bounds__(TcCfg<PASSES>::THREADS, 1) knn_tc_kernel(const
                     msc[q] = msn[q];
                 }
                 if (!C::FOLD && ti + 1 < ntl) {
-                    const int64_t cn = tile_col(p.pro, rt, s0, c0, ntl_u, ti + 1);
+                    const int64_t cn = tile_col(ps, pn, s0, c0, ntl_u, ti + 1);
 #pragma unroll
                     for (int q = 0; q < NCH; ++q) {
                         const int64_t cc = cn + half * CW + q * 32 + lane;
