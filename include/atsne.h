@@ -37,7 +37,7 @@ typedef enum {
     ATSNE_ENOMEM = 2,       /* workspace or output buffer too small */
     ATSNE_ECUDA = 3,        /* a CUDA runtime/driver call failed */
     ATSNE_ETIMEOUT = 4,     /* a bounded device-side wait expired */
-    ATSNE_EUNSUPPORTED = 5  /* valid request this build does not handle */
+    ATSNE_EUNSUPPORTED = 5  /* a valid request the library does not handle */
 } atsne_status;
 
 typedef enum { ATSNE_KNN_EXACT = 0, ATSNE_KNN_FOREST = 1 } atsne_knn_method;

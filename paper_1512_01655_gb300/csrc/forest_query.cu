@@ -599,7 +599,7 @@ __device__ __forceinline__ T warp_sum8(T (&v)[8], int lane) {
 // MODE: FD_F32 / FD_F32V (FP32 rows, scalar or float4 loads) or FD_U8 (byte
 // rows, QP 16-byte pieces per lane). The host launches an FP32 and, where byte
 // rows are possible, a byte instantiation; each returns at once unless the
-// prep kernel's verdict (every value an integer in [0, 255] or not) selects it.
+// prep kernel's finding (every value an integer in [0, 255] or not) selects it.
 template <int MODE, int QP>
 __global__ void __launch_bounds__(FD_MAX_WARPS * 32, 8) forest_dist_kernel(FdArgs A) {
     constexpr bool U8 = MODE == FD_U8, VEC = MODE == FD_F32V;
@@ -922,7 +922,7 @@ atsne_status forest_query_launch(const float *X, const ForestView &f, const int3
             st = launch_kernel("forest_traverse_u8", forest_traverse_kernel<true>, grid_b, FQ_WARPS * 32, smem_b,
                                stream, a);
         if (st != ATSNE_OK) return st;
-        // the FP32 and byte instantiations; the prep kernel's verdict picks one
+        // the FP32 and byte instantiations; the prep kernel's finding picks one
         st = vec ? fd_launch_t<FD_F32V, 1>(b, fd_warps, stream) : fd_launch_t<FD_F32, 1>(b, fd_warps, stream);
         if (st != ATSNE_OK) return st;
         if (b.xu8) {
