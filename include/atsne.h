@@ -114,6 +114,9 @@ size_t atsne_workspace_bytes(int32_t op, int64_t N, int32_t D, int32_t k, int64_
  *           queries[s]. A query never lists itself.
  *  k        1 <= k <= N - 1 (the paper uses k = floor(3 * perplexity)).
  *  idx_out  [rows][k] int32, d2_out [rows][k] fp32, sorted as described above.
+ * The exact tensor path of all rows of a large set (N >= 65536, D <= 256) first
+ * groups the points by nearest centroid and streams each row tile's own group
+ * first; the workspace holds that order, and the lists are the same as without it.
  * Errors: EINVAL (sizes, NULLs, index out of range), ENOMEM (workspace), ECUDA.
  */
 atsne_status atsne_knn(const float *X, int64_t N, int32_t D, const int32_t *queries, int64_t S,
