@@ -113,7 +113,33 @@ __global__ void fu_place_new_kernel(const int32_t *__restrict__ leaf, int64_t B,
     perm_out[(int64_t)t * N_new + pos] = (int32_t)(N_old + b);
 }
 
-// The new points of a bucket (placed by atomics) in index order.
+// Ascending order of a[0, n) by heapsort: O(n log n) in one thread, for the
+// buckets that many new points reach at once (duplicate rows all land in one
+// leaf), where an insertion sort would take O(n^2).
+__device__ void heapsort_i32(int32_t *a, int32_t n) {
+    auto sift = [&](int32_t r, int32_t end) {
+        const int32_t x = a[r];
+        for (;;) {
+            int32_t c = 2 * r + 1;
+            if (c >= end) break;
+            if (c + 1 < end && a[c + 1] > a[c]) ++c;
+            if (a[c] <= x) break;
+            a[r] = a[c];
+            r = c;
+        }
+        a[r] = x;
+    };
+    for (int32_t r = n / 2 - 1; r >= 0; --r) sift(r, n);
+    for (int32_t end = n - 1; end > 0; --end) {
+        const int32_t t = a[0];
+        a[0] = a[end];
+        a[end] = t;
+        sift(0, end);
+    }
+}
+
+// The new points of a bucket (placed by atomics) in index order: an insertion
+// sort for the few a bucket usually gets, a heapsort beyond 32.
 __global__ void fu_order_new_kernel(const int32_t *__restrict__ ofs_in, int64_t stride_in, int T, int64_t L,
                                     const int32_t *__restrict__ ofs_out, int32_t *__restrict__ perm_out,
                                     int64_t N_new, unsigned *__restrict__ bmax) {
@@ -125,6 +151,11 @@ __global__ void fu_order_new_kernel(const int32_t *__restrict__ ofs_in, int64_t 
     const int32_t *oo = ofs_out + (int64_t)t * (L + 1);
     int32_t *po = perm_out + (int64_t)t * N_new;
     const int32_t lo = oo[m] + (oi[m + 1] - oi[m]), hi = oo[m + 1];
+    if (hi - lo > 32) {
+        heapsort_i32(po + lo, hi - lo);
+        atomicMax(bmax, (unsigned)(hi - oo[m]));
+        return;
+    }
     for (int32_t i = lo + 1; i < hi; ++i) {
         const int32_t x = po[i];
         int32_t j = i - 1;

@@ -108,3 +108,17 @@ def test_search_flags_a_bucket_bound_below_the_largest_bucket(at):
     # the library stays usable: the right bound searches cleanly again
     at.atsne_forest_query(Xd, f, 10, checks=64, buckets=b)
     at.atsne_check()
+
+
+def test_many_identical_points_share_a_bucket_in_index_order(at):
+    # identical rows all descend to the same leaf of every tree: thousands of
+    # new points in one bucket, placed in index order as the oracle places them
+    base = synth.gaussian_mixture(1800, 16, seed=29)
+    dup = np.repeat(base[:2], [2500, 700], axis=0)
+    X = np.ascontiguousarray(np.concatenate([base, dup]).astype(np.float32))
+    Xd = to_dev(X)
+    f = at.atsne_forest_build(Xd[:1800].contiguous(), trees=2, leaf_size=1, seed=8)
+    o = oracle.forest_build(X[:1800], trees=2, top_var_dims=5, leaf_size=1, seed=8)
+    b = at.atsne_forest_insert(Xd, f, 1800)
+    at.atsne_check()
+    same_buckets(b, oracle.forest_insert(o, X, 1800))
