@@ -271,7 +271,7 @@ TRAFFIC_SOURCES = {
     "forest_traverse_u8": ["forest_query.cu", "common.cuh", "internal.h"],
     "forest_dist": ["forest_query.cu", "common.cuh", "internal.h"],
     "forest_dist_u8": ["forest_query.cu", "common.cuh", "internal.h"],
-    "knn_tc": ["knn_tc.cu", "tc_ptx.cuh", "common.cuh", "internal.h"],
+    "knn_tc": ["knn_tc.cu", "tc_ptx.cuh", "common.cuh", "internal.h", "warp_sort.cuh"],
 }
 
 

@@ -54,6 +54,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
+#include "warp_sort.cuh"
 
 namespace atsne {
 namespace {
@@ -1118,23 +1119,27 @@ __device__ __forceinline__ float row_error_bound(const MergeParams &p, float4 st
 // CERT (FP32 and BF16 modes): the k nearest, certified exact or sent to the
 // brute-force kernel. Otherwise (approximate modes): the SEL = ksel best keys
 // re-ranked in FP32 and the k best of them kept, without a certificate.
-// p.mst keys are staged per row, p.rc candidates re-ranked at most.
-size_t merge_smem_bytes(int rc, int mst) {
-    return (size_t)MERGE_WARPS * (256 * 4 + (size_t)mst * 8 + (size_t)rc * 8 + TIE_MAX * 12);
+// p.mst keys are staged per row, p.rc candidates re-ranked at most. Without a
+// certificate the staged keys are read once, by the collection of the re-rank
+// set, so the re-rank set takes their place (p.rc <= p.mst) and five blocks
+// fit on an SM instead of four.
+size_t merge_smem_bytes(bool cert, int rc, int mst) {
+    return (size_t)MERGE_WARPS * (256 * 4 + (size_t)mst * 8 + (cert ? (size_t)rc * 8 : 0) + TIE_MAX * 12);
 }
 
 template <bool CERT>
-__global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergeParams p) {
+__global__ void __launch_bounds__(MERGE_WARPS * 32, CERT ? 4 : 5) knn_merge_kernel(MergeParams p) {
     extern __shared__ __align__(16) unsigned char mg_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *hist = reinterpret_cast<uint32_t *>(mg_smem) + w * 256;
     const int MST = p.mst, RC = p.rc;
+    const int RCS = CERT ? RC : 0;  // the re-rank set's own region (else it is the staging region)
     float *sk = reinterpret_cast<float *>(mg_smem + MERGE_WARPS * 1024) + w * MST;
     int *sj = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 4)) + w * MST;
-    float *rdw = reinterpret_cast<float *>(mg_smem + MERGE_WARPS * (1024 + MST * 8)) + w * RC;
-    int *rjw = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 4)) + w * RC;
-    double *dmw = reinterpret_cast<double *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 8)) + w * TIE_MAX;
-    int *mpw = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 8 + TIE_MAX * 8)) +
+    float *rdw = CERT ? reinterpret_cast<float *>(mg_smem + MERGE_WARPS * (1024 + MST * 8)) + w * RC : sk;
+    int *rjw = CERT ? reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RC * 4)) + w * RC : sj;
+    double *dmw = reinterpret_cast<double *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RCS * 8)) + w * TIE_MAX;
+    int *mpw = reinterpret_cast<int *>(mg_smem + MERGE_WARPS * (1024 + MST * 8 + RCS * 8 + TIE_MAX * 8)) +
                w * TIE_MAX;
     const int sel = CERT ? p.k : p.ksel;  // rank of the key that bounds the re-rank set
     const int64_t row = (int64_t)blockIdx.x * MERGE_WARPS + w;
@@ -1184,9 +1189,11 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
           for (int j = 0; j < 32 && u0 + j < S; ++j) {
             const int c = __shfl_sync(0xffffffffu, cu, j);
             const Cand *b = cb + (size_t)(u0 + j) * p.cap;
-            for (int base = 0; base < c; base += 64) {
-                const int i = base + 2 * lane;  // two candidates per lane, one 16-byte load
-                Cand e0{INFINITY, -1}, e1{INFINITY, -1};
+            // two candidates per lane in one 16-byte load; two such loads
+            // in flight per step (positions past c are not staged)
+            auto load2 = [&](int i, Cand &e0, Cand &e1) {
+                e0 = Cand{INFINITY, -1};
+                e1 = Cand{INFINITY, -1};
                 if (i + 1 < c) {
                     const float4 v = __ldcs(reinterpret_cast<const float4 *>(b + i));
                     e0 = Cand{v.x, __float_as_int(v.y)};
@@ -1194,8 +1201,10 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
                 } else if (i < c) {
                     e0 = b[i];
                 }
+            };
+            auto stage2 = [&](int i, Cand e0, Cand e1) {
                 nlt += (e0.key < tau_min) + (e1.key < tau_min);
-                const bool t0 = e0.key <= slim, t1 = e1.key <= slim;
+                const bool t0 = i < c && e0.key <= slim, t1 = i + 1 < c && e1.key <= slim;
                 const unsigned m0 = __ballot_sync(0xffffffffu, t0);
                 const unsigned m1 = __ballot_sync(0xffffffffu, t1);
                 const unsigned lt = lanemask_lt();
@@ -1209,6 +1218,14 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
                     sj[pos + t0] = e1.idx;
                 }
                 ns += __popc(m0) + __popc(m1);
+            };
+            for (int base = 0; base < c; base += 128) {
+                const int i = base + 2 * lane;
+                Cand e0, e1, e2, e3;
+                load2(i, e0, e1);
+                load2(i + 64, e2, e3);
+                stage2(i, e0, e1);
+                stage2(i + 64, e2, e3);
             }
           }
         }
@@ -1247,7 +1264,11 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
                 for (int base = 0; base < ns; base += 32) {
                     const int i = base + lane;
                     const bool in = i < ns && sk[i] > lo && sk[i] <= hi;
-                    take_batch(in, i < ns ? sj[i] : -1);
+                    const int idx = i < ns ? sj[i] : -1;
+                    // without a certificate the set is compacted in place
+                    // (position <= i): the batch is read before it is written
+                    if (!CERT) __syncwarp();
+                    take_batch(in, idx);
                 }
             } else {
                 for (int u = 0; u < S; ++u) {
@@ -1321,7 +1342,8 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 4) knn_merge_kernel(MergePar
                 rjw[t] = INT_MAX;
             }
             __syncwarp();
-            warp_bitonic_sort_smem(rdw, rjw, ns2, lane);
+            warp_sort_pow2(rdw, rjw, ns2, lane);
+            __syncwarp();
             // near ties among the first k + 1 ordered as the exact distances are
             fp64_near_ties(rdw, rjw, nr, p.k, xq, p.X, p.D, dmw, mpw, lane);
             if (CERT) {
@@ -1811,7 +1833,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
         while (rc < pl.ksel + pl.ksel / 4) rc <<= 1;
         m.rc = rc < RCAP_FP8 ? rc : RCAP_FP8;
         m.mst = 2 * m.rc;
-        const size_t ms = merge_smem_bytes(m.rc, m.mst);
+        const size_t ms = merge_smem_bytes(false, m.rc, m.mst);
         e = cudaFuncSetAttribute(knn_merge_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
         if (e != cudaSuccess) return cuda_error(e, "knn_tc_merge attribute");
         ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<false>, ceil_div(Q, MERGE_WARPS),
@@ -1819,7 +1841,7 @@ atsne_status knn_exact_tc(const float *X, int64_t N, int D, const int32_t *qlist
     } else {
         m.rc = RCAP;
         m.mst = MSTAGE;
-        const size_t ms = merge_smem_bytes(m.rc, m.mst);
+        const size_t ms = merge_smem_bytes(true, m.rc, m.mst);
         e = cudaFuncSetAttribute(knn_merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
         if (e != cudaSuccess) return cuda_error(e, "knn_tc_merge attribute");
         ATSNE_TRY(launch_kernel("knn_tc_merge", knn_merge_kernel<true>, ceil_div(Q, MERGE_WARPS),

@@ -6,8 +6,8 @@
 // (p_{c|r} + p_{r|c}) / 2N, formed from the same two operands on both sides,
 // so p_rc and p_cr are bit-identical; a column in one of them gets its one
 // conditional / 2N. The transpose is a counting sort by target row:
-//   1. fwd:      each conditional row sorted by column (warp bitonic in shared
-//                memory) and its entries counted into their target rows;
+//   1. fwd:      each conditional row sorted by column (warp bitonic, in
+//                registers) and its entries counted into their target rows;
 //   2. scan:     offsets of the reverse lists;
 //   3. rev:      every entry (i -> j, p_{j|i}) placed in j's reverse list;
 //   4. len:      row length |F_r| + |R_r| - |F_r and R_r| (each reverse entry
@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "warp_sort.cuh"
 
 namespace atsne {
 namespace {
@@ -74,7 +75,8 @@ sym_fwd_kernel(const int32_t *__restrict__ idx, const float *__restrict__ P, int
         vals[w][t] = v;
     }
     __syncwarp();
-    warp_bitonic_sort_smem(keys[w], vals[w], KP, lane);
+    warp_sort_pow2(keys[w], vals[w], KP, lane);
+    __syncwarp();
     int c = 0;  // forward entries (absent ones sorted last)
     for (int t = lane; t < k; t += 32) {
         const int j = keys[w][t];
