@@ -657,3 +657,28 @@ def test_knn_bf16_approx_recall_and_exact_distances(at, kind):
     assert np.all(np.abs(g_d2 - exact) <= 1e-5 * exact + 1e-3)
     assert np.all(np.diff(g_d2, axis=1) >= 0)
     assert np.all(g_idx != rows[:, None])
+
+
+@pytest.mark.parametrize("k", [20, 128])
+def test_knn_bf16_approx_rerank_set_sizes_and_tie_order(at, k):
+    # The re-rank set holds the 4k best keys: at k = 20 the merge sorts sets of
+    # 128 entries in registers, at k = 128 sets of more than 512 entries in
+    # shared memory (k = 90 elsewhere sorts 512 in registers). Half the rows
+    # appear twice, so many distances are exactly equal; both sorts order them
+    # by index, as Eq. 8's (d^2, index) order does.
+    X = synth.sparse_prototypes(N=6000, seed=5)
+    X = np.ascontiguousarray(np.concatenate([X, X[:3000]]))
+    rows = synth.sample_rows(X.shape[0], 200, seed=54)
+    idx, d2 = at.atsne_knn(to_dev(X), k, queries=to_dev(rows.astype(np.int32)), precision="bf16_approx")
+    at.atsne_check()
+    o_idx, _ = oracle.knn_exact(X, k, queries=rows)
+    g_idx, g_d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    recall = np.mean([len(set(g_idx[i]) & set(o_idx[i])) / k for i in range(len(rows))])
+    assert recall >= 0.999
+    exact = _sq_dists(X, rows, g_idx)
+    assert np.all(np.abs(g_d2 - exact) <= 1e-5 * exact + 1e-3)
+    same = g_d2[:, 1:] == g_d2[:, :-1]
+    assert same.any()
+    assert np.all(np.diff(g_d2, axis=1) >= 0)
+    assert np.all((g_idx[:, 1:] > g_idx[:, :-1]) | ~same)
+    assert np.all(g_idx != rows[:, None])
