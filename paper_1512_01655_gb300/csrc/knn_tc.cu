@@ -1256,7 +1256,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, CERT ? 4 : 5) knn_merge_kern
         auto take_batch = [&](bool take, int idx) {
             const unsigned tm = __ballot_sync(0xffffffffu, take);
             const int pos = nr + __popc(tm & lanemask_lt());
-            if (take && pos < RC) rjw[pos] = p.perm ? p.perm[idx] : idx;
+            if (take && pos < RC) rjw[pos] = idx;
             nr += __popc(tm);
         };
         auto collect = [&](float lo, float hi) {  // keys in (lo, hi]
@@ -1282,6 +1282,26 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, CERT ? 4 : 5) knn_merge_kern
                     }
                 }
             }
+        };
+        // ordered columns: the collected positions mapped to rows of X, four
+        // loads in flight per lane (one at a time per batch of the collection
+        // would wait on each)
+        auto map_rows = [&](int from, int to) {
+            if (!p.perm) return;
+            for (int t0 = from; t0 < to; t0 += 128) {
+                int v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + 32 * q + lane;
+                    v[q] = t < to ? p.perm[rjw[t]] : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + 32 * q + lane;
+                    if (t < to) rjw[t] = v[q];
+                }
+            }
+            __syncwarp();
         };
         const float *xq = cross ? p.Xq + (int64_t)row * p.D : p.X + (p.perm ? orow : (int64_t)qid) * p.D;
         const bool vec4 = (p.D & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
@@ -1317,6 +1337,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, CERT ? 4 : 5) knn_merge_kern
             // largest of their exact distances bounds the k-th nearest one, so
             // only points of norm at most ||x|| + sqrt(that) can be nearer, and
             // the bound is taken over those points only
+            map_rows(0, nr1);
             rerank(0, nr1);
             __syncwarp();
             float dk0 = 0.f;
@@ -1329,15 +1350,28 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, CERT ? 4 : 5) knn_merge_kern
             collect(theta, theta + 2.f * Ec);
             if (nr > RC) good = false;
             __syncwarp();
-            if (good) rerank(nr1, nr);
+            if (good) {
+                map_rows(nr1, nr);
+                rerank(nr1, nr);
+            }
         } else if (good) {
+            map_rows(0, nr1);
             rerank(0, nr1);
         }
         __syncwarp();
         if (good && nr >= p.k) {
+            // only the first k + 1 in (distance, index) order are needed: a
+            // set of 129 to 512 is cut to the entries at or below its
+            // (k + 1)-th distance first when at most 128 remain
+            const int m1 = nr < p.k + 1 ? nr : p.k + 1;
+            int nsrt = nr;
+            if (nr > 128 && nr <= 512) {
+                const int c = warp_smallest_to_front(rdw, rjw, nr, m1, 128, lane);
+                if (c >= 0) nsrt = c;
+            }
             int ns2 = 32;
-            while (ns2 < nr) ns2 <<= 1;
-            for (int t = nr + lane; t < ns2; t += 32) {
+            while (ns2 < nsrt) ns2 <<= 1;
+            for (int t = nsrt + lane; t < ns2; t += 32) {
                 rdw[t] = INFINITY;
                 rjw[t] = INT_MAX;
             }

@@ -1,4 +1,5 @@
-// Warp-cooperative sorts of (key, value) pairs held in shared memory.
+// Warp-cooperative sorts and selections of (key, value) pairs held in shared
+// memory.
 #pragma once
 
 #include "common.cuh"
@@ -76,6 +77,69 @@ __device__ __forceinline__ void warp_sort_pow2(K *key, V *val, int n, int lane) 
         case 512: warp_sort_regs<16>(key, val, lane); break;
         default: warp_bitonic_sort_smem(key, val, n, lane);
     }
+}
+
+// Moves the entries of key[0, n) (32 < n <= 512) whose keys are at most the
+// m-th smallest key (1 <= m <= n; every entry equal to it included) to
+// positions [0, c) of key/val, in no particular order, and returns c when
+// c <= cap; otherwise leaves both arrays unchanged and returns -1. The first m
+// entries of the whole set in (key, value) order are then the first m of
+// those c in that order. Keys are non-negative floats, compared through their
+// bit patterns (which order them); the m-th is found by bisection on the bit
+// pattern, counting with the warp's reduction. Entry t sits in lane t % 32.
+// Warp-cooperative; n, m and cap uniform.
+template <typename V>
+__device__ __forceinline__ int warp_smallest_to_front(float *key, V *val, int n, int m, int cap, int lane) {
+    constexpr int R = 16;
+    uint32_t u[R];
+    V v[R];
+    uint32_t lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = r * 32 + lane;
+        u[r] = 0xffffffffu;  // past n: above every key
+        if (t < n) {
+            u[r] = __float_as_uint(key[t]);
+            v[r] = val[t];
+            lo = min(lo, u[r]);
+            hi = max(hi, u[r]);
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    // the smallest T in [lo, hi] with at least m keys at or below it
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        int c0 = 0, c1 = 0;
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+            c0 += u[r] <= mid;
+            c1 += u[r + 1] <= mid;
+        }
+        if ((int)__reduce_add_sync(0xffffffffu, (unsigned)(c0 + c1)) >= m) hi = mid;
+        else lo = mid + 1;
+    }
+    int c0 = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) c0 += u[r] <= lo;
+    const int c = (int)__reduce_add_sync(0xffffffffu, (unsigned)c0);
+    if (c > cap) return -1;
+    __syncwarp();  // every entry is in registers before the front is overwritten
+    const unsigned below = (1u << lane) - 1u;
+    int base = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool in = u[r] <= lo;
+        const unsigned b = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int pos = base + __popc(b & below);
+            key[pos] = __uint_as_float(u[r]);
+            val[pos] = v[r];
+        }
+        base += __popc(b);
+    }
+    __syncwarp();
+    return c;
 }
 
 }  // namespace atsne
